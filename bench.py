@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: Parareal time-to-1e-6 against serial fine stepping on one GB300.
+
+Workload (one "step" = one complete Parareal solve through the C ABI): the
+Galloway-Proctor circularly polarised flow on a 128 x 128 grid, kz = 0.57, Rm = 100,
+fine dt <= 5e-3 over T = 2 pi * 8 split into 64 slices (158 RK443 steps of pi/632
+per slice), complex64 fine propagator, classical coarse propagator on the 64 x 64
+grid, FP64 update and convergence defect, stopping at sigma <= 1e-6.
+
+value  = serial-fine-equivalent throughput of the solve: 3 n^2 x 64 x 158 degrees
+         of freedom x steps per solve / device time of the solve (Mdof.steps/s),
+         summed over ranks (each rank solves its own seeded instance: weak scaling).
+e2e    = the same with the initial field read from pinned host memory and all 65
+         slice states written back to pinned host memory inside the timed region.
+Also reported: serial fine time of the same problem with the same kernels, the
+speedup, k_con, the error against the serial fine solution, the roofline of the
+dominant kernel measured live with CUDA events, clocks during the timed region and
+the oracle timed on a bounded sample (cpu_baseline).
+
+--impl reference times the CPU FP64 oracle (the slow reference program of this
+repository) on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WL = {
+    "workload": "gp_cp_128x128_parareal_64_slices",
+    "flow": "galloway-proctor", "n": 128, "kz": 0.57, "Rm": 100.0, "dt_fine_max": 5e-3,
+    "T": 2 * math.pi * 8, "slices": 64, "n_coarse": 64, "dt_coarse_max": 0.05, "tol": 1e-6,
+    "k_max": 64, "prec_fine": "complex64", "prec_coarse": "complex64", "update": "float64",
+}
+METRIC = "Parareal time-to-1e-6 vs serial fine (1 GB300); fine Mdof·steps/s, HBM % peak"
+UNIT = "Mdof*steps/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def fine_steps_per_slice():
+    dT = WL["T"] / WL["slices"]
+    return math.ceil(dT / WL["dt_fine_max"] - 1e-9)
+
+
+def units_per_solve():
+    """degrees of freedom x steps of the serial fine solution the solve reproduces"""
+    return 3 * WL["n"] ** 2 * WL["slices"] * fine_steps_per_slice()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(nsteps):
+    """Time the oracle's fine propagator for `nsteps` steps of one slice of the workload."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import kd_inputs
+    from oracle import kd_oracle as O
+    n = WL["n"]
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"])
+    b = kd_inputs.initial_field(n, WL["kz"], 0)
+    dT = WL["T"] / WL["slices"]
+    S = fine_steps_per_slice()
+    t = time.perf_counter()
+    O.propagate(b, prob, 0.0, dT / S, nsteps)
+    el = time.perf_counter() - t
+    return 3 * n * n * nsteps / el / 1e6, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = 24   # fine steps of one slice per reference step (~0.5 s of numpy work)
+    for _ in range(args.warmup):
+        oracle_sample(per_step)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, el = oracle_sample(per_step)
+        vals.append(v)
+        secs.append(el)
+    value = args.steps * per_step * 3 * WL["n"] ** 2 / sum(secs) / 1e6
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WL),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d RK443 fine steps of one 128^2 GP slice per step, numpy FP64 oracle" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                smax.append(float(v[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, v[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline
+def col_row_bytes(n, batch_slices):
+    """Algorithmic bytes of one column launch and of one row launch (complex64):
+    the column pass reads and writes the mixed field (3 x P x n); the row pass reads
+    and writes it too and touches 3.5 compact spectral arrays (3 x P x P) on average
+    over the four stages (stage reads + writes: 4, 5, 3, 2)."""
+    K = n // 3
+    P = 2 * K + 1
+    mixed = 3 * P * n * 8
+    spec = 3 * P * P * 8
+    return 2 * mixed * batch_slices, (2 * mixed + 3.5 * spec) * batch_slices
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+
+    n, N, T = WL["n"], WL["slices"], WL["T"]
+    params = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C64,
+                            n_coarse=WL["n_coarse"], dt_coarse=WL["dt_coarse_max"], prec_coarse=kd.KD_C64)
+    ctx = kd.kd_create(params, stream.cuda_stream)
+    b0_host = torch.tensor(kd_inputs.initial_field(n, WL["kz"], 1000 + rank)).pin_memory()
+    b0_dev = b0_host.to("cuda")
+    u_dev = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+    u_host = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve(b0, out):
+        s, st = kd.kd_parareal_run(ctx, b0, T, N, WL["k_max"], WL["tol"], out)
+        if s != kd.KD_OK:
+            raise RuntimeError("Parareal did not converge: " + kd.kd_last_error(ctx))
+        return st
+
+    for _ in range(args.warmup):
+        solve(b0_dev, u_dev)
+
+    def timed(fn, steps, clocks=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        res = []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(steps):
+            flush.fill_(float(i))          # evict L2 between steps (buffer > 129 MB L2)
+            ev[i][0].record(stream)
+            res.append(fn())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        if world > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, res, ck
+
+    # ---- main timed region: device-resident inputs, kernel profile of the fine sweep on
+    launches0 = kd.kd_launch_count(ctx)
+    kd.kd_profile(ctx, 1)
+    ms, stats, clk = timed(lambda: solve(b0_dev, u_dev), args.steps, ClockSampler(local))
+    prof_ms, prof_n = kd.kd_profile_read(ctx)
+    kd.kd_profile(ctx, 0)
+    launches = kd.kd_launch_count(ctx) - launches0
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    units = units_per_solve()
+    value = units * world * args.steps / (total_ms / 1e3) / 1e6
+    st = stats[-1]
+
+    # ---- end to end: host initial field in, all slice states back to host
+    ms_e2e, _, _ = timed(lambda: solve(b0_host, u_host), max(2, args.steps // 2))
+    e2e_total = sum(ms_e2e)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = t.item()
+    e2e_value = units * world * len(ms_e2e) / (e2e_total / 1e3) / 1e6
+    d2h = (N + 1) * 3 * n * n * 16 + 8 * st.k_con + 8 * (N + 1) + 16
+
+    # ---- serial fine stepping of the same problem with the same kernels
+    ser = torch.zeros_like(u_dev)
+    kd.kd_fine_serial(ctx, b0_dev, T, N, ser)
+    ms_ser, _, _ = timed(lambda: kd.kd_fine_serial(ctx, b0_dev, T, N, ser), 2)
+    serial_ms = min(ms_ser)
+    solve(b0_dev, u_dev)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(u_dev[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
+
+    # ---- roofline of the dominant fine kernel, from the live event timing
+    hbm_peak, peak_kind = peaks()
+    dT = T / N
+    S = st.n_fine_steps
+    # fine-sweep batches over one solve: slices k-1..N-1 in iteration k
+    batches = [N - min(k - 1, N - 1) for k in range(1, st.k_con + 1)]
+    col_b = sum(col_row_bytes(n, b)[0] * 4 * S for b in batches) * args.steps
+    row_b = sum(col_row_bytes(n, b)[1] * 4 * S for b in batches) * args.steps
+    kid = 0 if prof_ms[0] >= prof_ms[1] else 1
+    kbytes = (col_b, row_b)[kid]
+    achieved = kbytes / (prof_ms[kid] / 1e3) / 1e9
+    fine_units = 3 * n * n * S * sum(batches) * args.steps
+    fine_rate = fine_units / ((prof_ms[0] + prof_ms[1]) / 1e3) / 1e6
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nsteps = 3 * S
+        v, el = oracle_sample(nsteps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d RK443 fine steps (3 slices) of the 128^2 GP problem, serial, numpy FP64 oracle, %.1f s"
+                         % (nsteps, el)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 fine / f64 update", "data": "synthetic",
+        "config": dict(WL, fine_steps_per_slice=S, coarse_steps_per_slice=st.n_coarse_steps,
+                       l2="flushed between steps (512 MB write)", parallelism="time slices in one launch; "
+                       "ranks solve independent instances"),
+        "time_to_solution_ms": ms_per_step, "serial_fine_ms": serial_ms,
+        "speedup_vs_serial_fine": serial_ms / ms_per_step, "k_con": st.k_con,
+        "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "growth_rate": st.growth_rate,
+        "fine_mdof_steps_per_s": fine_rate,
+        "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
+        "roofline": {"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 16, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    kd.kd_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * kd.h -- C ABI of the GB300 Parareal library for the 2.5D kinematic dynamo.
+ *
+ * The library integrates the monochromatic induction equation (Sec. 2, Eq. 1 with
+ * B = b(x, y, t) exp(i kz z)):
+ *
+ *     d b / dt = nabla_k x (u x b) + Rm^-1 (nabla^2 - kz^2) b,   nabla_k = (d_x, d_y, i kz),
+ *
+ * on the periodic square [0, 2 pi)^2 for the Roberts flow (Sec. 2.1) or the
+ * Galloway-Proctor circularly polarised flow (Sec. 2.2), with a Fourier
+ * pseudo-spectral discretisation (2/3 dealiasing) and the IMEX Runge-Kutta scheme
+ * RK443 (Sec. 4), and runs Parareal (Sec. 3, Eq. 8) on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - A field is complex [3][n][n] = [component x,y,z][ky][kx] of spectral
+ *    coefficients b_hat(k) with b(x) = sum_k b_hat(k) exp(i k.x); indices are in FFT
+ *    order (index i <-> wavenumber i for i < n/2, i - n otherwise).  Complex numbers
+ *    are interleaved (re, im) doubles (complex128) or floats (complex64).
+ *  - Modes outside the dealiased square |kx|, |ky| <= n/3 are ignored on input and
+ *    written as zero on output.
+ *  - The caller owns every buffer it passes; the library never frees them.  The
+ *    context owns its workspace, tables and CUDA graphs.
+ *  - Work is enqueued on the stream given to kd_create (NULL = legacy default
+ *    stream).  Calls documented as synchronous wait for that stream.
+ *  - Errors are return codes; kd_last_error() gives a message.  CUDA failures map
+ *    to KD_ECUDA.  A context is not thread-safe.
+ */
+#ifndef KD_H_
+#define KD_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kd_ctx kd_ctx;
+
+typedef enum {
+  KD_OK = 0,
+  KD_EINVAL = 1,        /* bad argument */
+  KD_ENOMEM = 2,        /* device allocation failed */
+  KD_ECUDA = 3,         /* CUDA runtime error */
+  KD_ENOTCONV = 4,      /* Parareal reached k_max with sigma > tol (results still written) */
+  KD_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
+  KD_ENONFINITE = 6,    /* NaN or Inf met in a norm */
+  KD_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} kd_status;
+
+enum { KD_FLOW_ROBERTS = 0, KD_FLOW_GALLOWAY_PROCTOR = 1, KD_FLOW_NONE = 2 };
+enum { KD_C64 = 0, KD_C128 = 1 };
+enum { KD_COARSE_CLASSICAL = 0, KD_COARSE_LEARNED = 1 };
+
+#define KD_MAX_SLICES 1024
+#define KD_MAX_ITERS 256
+
+/* Problem and discretisation parameters (Sec. 2, Sec. 4, Table 1). */
+typedef struct {
+  int flow;            /* KD_FLOW_*; NONE (u = 0) leaves pure diffusion */
+  int n;               /* fine grid side: 16, 32, 64, 128, 256, 512 or 1024 */
+  double kz;           /* wavenumber along the invariant direction (the paper's kx for GP) */
+  double Rm;           /* magnetic Reynolds number (Eq. 2), > 0 */
+  double dt_fine;      /* fine step delta t (upper bound; see kd_parareal_run) */
+  int prec_fine;       /* KD_C64 or KD_C128 arithmetic of the fine propagator */
+  int n_coarse;        /* coarse grid side N_C (power of two, 16 <= N_C <= n) */
+  double dt_coarse;    /* coarse step Delta t (upper bound) */
+  int prec_coarse;     /* KD_C64 or KD_C128 arithmetic of the classical coarse propagator */
+  int coarse_kind;     /* KD_COARSE_CLASSICAL (only value implemented) */
+  int learned_modes;   /* reserved; 0 */
+} kd_params;
+
+/* Create a context for one problem.  `cuda_stream` is a cudaStream_t (may be NULL).
+ * Allocates the grid tables on the current device.  Returns KD_EINVAL for
+ * unsupported sizes and KD_ECUDA / KD_ENOMEM on device failures. */
+kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out);
+
+/* Release every resource of the context (waits for its stream first).  NULL is a no-op. */
+kd_status kd_destroy(kd_ctx* ctx);
+
+/* Fine propagator F (Sec. 3): advance `batch` independent fields by `nsteps` RK443
+ * steps of params.dt_fine, every field in the same launches.
+ *   b_in, b_out : device, [batch][3][n][n] complex in params.prec_fine; may alias.
+ *   t0          : device double[batch]; absolute start time of each field (step s of
+ *                 field i evaluates the flow at t0[i] + (s + c_j) dt; matters for GP).
+ * Asynchronous on the context stream.  nsteps = 0 copies the masked input. */
+kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const double* t0,
+                          int nsteps, int batch);
+
+/* Classical coarse propagator G (Sec. 3.2, Sec. 5.2): restrict each field to the
+ * N_C grid (Fourier truncation), take `nsteps` RK443 steps of params.dt_coarse in
+ * params.prec_coarse, prolong (zero-pad) back to n.
+ *   b_in, b_out : device, [batch][3][n][n] complex128; may alias.
+ *   t0          : device double[batch] start times.
+ * Asynchronous on the context stream. */
+kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double* t0,
+                    int nsteps, int batch);
+
+typedef struct {
+  int k_con;                           /* iterations done (= first k with sigma <= tol) */
+  int converged;                       /* 1 if sigma <= tol was reached */
+  int n_fine_steps;                    /* fine steps per slice S = ceil(dT / dt_fine) */
+  int n_coarse_steps;                  /* coarse steps per slice */
+  double dt_fine_used;                 /* dT / S */
+  double dt_coarse_used;
+  double sigma[KD_MAX_ITERS];          /* Eq. 9 defect after iteration k (index k-1) */
+  double energy[KD_MAX_SLICES + 1];    /* E(t_n) = sum |b_hat|^2 of the final iterate */
+  double growth_rate;                  /* slope of 0.5 ln E over t >= T/2 */
+  double ms_total;                     /* device time of the whole run */
+  double ms_fine;                      /* parallel fine sweeps */
+  double ms_coarse;                    /* serial coarse sweeps incl. the initial one */
+  int fallback_used;                   /* reserved: 0 */
+  long long n_launches;                /* kernels launched by this call */
+} kd_parareal_stats;
+
+/* Parareal (Sec. 3, Eq. 8; Algorithms of Sec. 4.1) over [0, T] with n_slices slices
+ * of dT = T / n_slices.  Fine: S = ceil(dT / dt_fine) steps of dT / S from
+ * t_n = n dT; coarse: ceil(dT / dt_coarse) steps.  Iterate 0 is the serial coarse
+ * sweep; iteration k+1 sets U_{n+1} = F(U^k_n) + (G(U^{k+1}_n) - G(U^k_n)) with the
+ * fine values of all slices computed in one batched propagation and the update in
+ * FP64.  Stops when sigma (Eq. 9) <= tol or after k_max iterations.
+ *   b0       : complex128 [3][n][n], host or device pointer.
+ *   u_slices : complex128 [n_slices+1][3][n][n] output (host or device), or NULL.
+ *   stats    : host, may be NULL.
+ * Synchronous.  Returns KD_ENOTCONV if tol was not reached (outputs still valid). */
+kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices, int k_max,
+                          double tol, double* u_slices, kd_parareal_stats* stats);
+
+/* Serial fine solution at the slice boundaries, U_{n+1} = F(U_n) with each slice
+ * restarted at t_n = n dT exactly as in kd_parareal_run (the solution Parareal
+ * converges to, Sec. 3.1).  Same arguments and step rule as kd_parareal_run.
+ * Synchronous. */
+kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int n_slices,
+                         double* u_slices);
+
+/* Magnetic energy E_i = sum_{c,k} |b_hat|^2 of `count` complex128 fields
+ * ([count][3][n][n], device) into device double[count].  Deterministic order.
+ * Asynchronous. */
+kd_status kd_energy(kd_ctx* ctx, const double* fields, int count, double* energy_out);
+
+/* Growth rate (Table 1 "Growth Rate"; Sec. 1): least-squares slope of 0.5 ln E(t_i)
+ * over the samples with t_i >= fit_from, where t_i = i T / (n_samples - 1) and
+ * E_i = kd_energy of u_slices[i].
+ *   u_slices : device complex128 [n_samples][3][n][n].
+ *   rate_out : host double.
+ * Synchronous.  KD_ENONFINITE if an energy is 0, NaN or Inf. */
+kd_status kd_growth_rate(kd_ctx* ctx, const double* u_slices, int n_samples, double T,
+                         double fit_from, double* rate_out);
+
+/* Number of kernels this context has launched since kd_create (-1 for NULL). */
+long long kd_launch_count(kd_ctx* ctx);
+
+/* Event timing of the fine propagator's kernels (instrumentation; not needed for
+ * results).  kd_profile(ctx, 1) resets the counters and brackets every launch of the
+ * fine-grid column kernel (index 0) and row kernel (index 1) with CUDA events on the
+ * context stream; kd_profile(ctx, 0) stops.  kd_profile_read waits for the recorded
+ * events and returns the summed device milliseconds ms[2] and launch counts
+ * launches[2] since the last reset.  Synchronous. */
+kd_status kd_profile(kd_ctx* ctx, int enable);
+kd_status kd_profile_read(kd_ctx* ctx, double* ms, long long* launches);
+
+/* Message of the last error on this context ("" if none).  Valid until the next call. */
+const char* kd_last_error(kd_ctx* ctx);
+
+/* Library version string. */
+const char* kd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KD_H_ */

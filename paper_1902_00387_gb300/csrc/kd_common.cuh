@@ -1,0 +1,74 @@
+// Shared device/host definitions of the kd library (CUDA path only).
+//
+// Data layouts used inside the library (the public ABI layout is the full n x n grid,
+// see include/kd.h):
+//   K = n / 3 (2/3 dealiasing: |kx|, |ky| <= K are kept), P = 2K + 1.
+//   compact spectral  S[b][c][iy][ix]  iy = ky + K, ix = kx + K       (P x P per component)
+//   mixed             M[b][c][iy][x]   ky rows, physical x columns    (P x n per component)
+// b = slice / batch index, c = field component (x, y, z).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kd {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// i * a
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mul_i(cx<T> a) { return mk(-a.y, a.x); }
+
+// Flow identifiers (match include/kd.h).
+enum { FLOW_ROBERTS = 0, FLOW_GP = 1, FLOW_NONE = 2 };
+
+// Per-grid device tables, one set per (n, precision): twiddles w_n^e = exp(-2 pi i e / n)
+// and cos / sin of the collocation points 2 pi j / n.  Computed in double on the host.
+struct GridTables {
+  int n;
+  void* tw;    // cx<T>[n]
+  void* cosg;  // T[n]
+  void* sing;  // T[n]
+};
+
+// Everything a fine-step kernel needs about one batched propagation.
+struct FineArgs {
+  int n, K, P;
+  int batch;
+  int flow;
+  double amp;      // flow amplitude: 1 (Roberts), sqrt(3/2) (Galloway-Proctor), 0 (none)
+  double kz, Rm, dt;
+  const double* t0;  // [batch] absolute start time of each slice (device)
+  void* X;           // compact state              [batch][3][P][P]
+  void* R2;          // stage accumulators          [batch][3][P][P]
+  void* R3;
+  void* R4;
+  void* M;           // mixed (inverse-x) field     [batch][3][P][n]
+  void* W;           // mixed (forward-y) product   [batch][3][P][n]
+  const void* tw;
+  const void* cosg;
+  const void* sing;
+  const void* phases;  // Galloway-Proctor flow phases [batch][phase_steps][4 stages][4] (precision T)
+  int phase_steps;     // steps covered by the phase table
+};
+
+}  // namespace kd

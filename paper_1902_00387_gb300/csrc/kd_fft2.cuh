@@ -1,0 +1,148 @@
+// Register-resident complex FFT of length N = R1 * R2 (N <= 256) with one shared-memory
+// transpose (the "four-step" factorisation):
+//   n = a + R2 k (a < R2, k < R1),  m = q + R1 p (q < R1, p < R2)
+//   X[q + R1 p] = sum_a w_R2^{a p} [ w_N^{a q} sum_k x[a + R2 k] w_R1^{k q} ]
+// A transform is owned by R2 threads ("lane" a).  Pass 1: lane a does the R1-point DFT
+// over k of its own R1 values and the twiddle w_N^{a q}; the R1 x R2 matrix goes
+// through shared memory; pass 2: lane a does the R2-point DFTs for q = a + R2 j.
+//
+// Register contract (v[r], r < R1):
+//   input  v[k]           = x[a + R2 k]
+//   output v[j * R2 + p]  = X[(a + R2 j) + R1 p]      (j < R1 / R2, p < R2)
+// Since (a + R2 j) + R1 p = a + R2 (j + (R1 / R2) p), the output of one transform holds
+// exactly the inputs another transform needs in the same lane, after the compile-time
+// register permutation in_from_out().  The three field components are transformed
+// together so that a pass needs one barrier.
+#pragma once
+#include "kd_common.cuh"
+
+namespace kd {
+
+template <int N>
+struct Split;
+template <>
+struct Split<16> { static constexpr int R1 = 4, R2 = 4; };
+template <>
+struct Split<32> { static constexpr int R1 = 8, R2 = 4; };
+template <>
+struct Split<64> { static constexpr int R1 = 8, R2 = 8; };
+template <>
+struct Split<128> { static constexpr int R1 = 16, R2 = 8; };
+template <>
+struct Split<256> { static constexpr int R1 = 16, R2 = 16; };
+
+// cos / sin (e pi / 16), e = 0..8
+__device__ __forceinline__ double cpi16(int e) {
+  switch (e) {
+    case 0: return 1.0;
+    case 1: return 0.98078528040323044913;
+    case 2: return 0.92387953251128675613;
+    case 3: return 0.83146961230254523708;
+    case 4: return 0.70710678118654752440;
+    case 5: return 0.55557023301960222474;
+    case 6: return 0.38268343236508977173;
+    case 7: return 0.19509032201612826785;
+    default: return 0.0;
+  }
+}
+
+// a * w_32^e with w_32 = exp(DIR 2 pi i / 32), 0 <= e < 16 (e is a compile-time
+// constant after unrolling, so the branches fold away).
+template <typename T, int DIR>
+__device__ __forceinline__ cx<T> mul_w32(cx<T> a, int e) {
+  if (e == 0) return a;
+  if (e == 8) return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
+  const T c = (T)(e <= 8 ? cpi16(e) : -cpi16(16 - e));
+  const T s = (T)(DIR * (e <= 8 ? cpi16(8 - e) : cpi16(e - 8)));
+  return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int q) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (q & 1);
+    q >>= 1;
+  }
+  return r;
+}
+
+// In-register R-point DFT (R = 2, 4, 8, 16), radix-2 decimation in frequency.
+// In: v[n] natural order.  Out: X[q] at v[bitrev<R>(q)].
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_dif(cx<T>* v) {
+#pragma unroll
+  for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int start = 0; start < R; start += 2 * span) {
+#pragma unroll
+      for (int i = 0; i < span; ++i) {
+        const cx<T> x0 = v[start + i], x1 = v[start + i + span];
+        v[start + i] = x0 + x1;
+        v[start + i + span] = mul_w32<T, DIR>(x0 - x1, i * (32 / (2 * span)));
+      }
+    }
+  }
+}
+
+template <int N>
+struct FFT2 {
+  static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2, J = R1 / R2;
+  // register holding input element k (= x[a + R2 k]) when taken from an output set
+  __host__ __device__ static constexpr int in_from_out(int k) { return (k % J) * R2 + k / J; }
+  // element index (along the transform) of output register r in lane a
+  __host__ __device__ static constexpr int out_pos_base(int r) { return R2 * (r / R2) + R1 * (r % R2); }
+};
+
+// Three-component transform.  S(c, q, a2) returns the shared-memory slot of matrix
+// element (q, a2) of component c for this thread's transform.  tw[e] = exp(-2 pi i e / N).
+// Ends with the results in registers; the caller must __syncthreads() before the
+// shared exchange buffers are written again.
+template <typename T, int N, int DIR, class Slot>
+__device__ __forceinline__ void fft2_3(cx<T> (&v)[3][Split<N>::R1], int a, const cx<T>* tw, Slot S) {
+  constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2, J = R1 / R2;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    dft_dif<T, R1, DIR>(v[c]);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+      cx<T> y = v[c][bitrev<R1>(q)];
+      if (q != 0) {
+        const cx<T> w = tw[(a * q) & (N - 1)];
+        y = cmul(y, DIR < 0 ? w : mk(w.x, -w.y));
+      }
+      *S(c, q, a) = y;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int q = a + R2 * j;
+      cx<T> u[R2];
+#pragma unroll
+      for (int a2 = 0; a2 < R2; ++a2) u[a2] = *S(c, q, a2);
+      dft_dif<T, R2, DIR>(u);
+#pragma unroll
+      for (int p = 0; p < R2; ++p) v[c][j * R2 + p] = u[bitrev<R2>(p)];
+    }
+  }
+}
+
+// Re-order registers from the output layout of one transform to the input layout of
+// the next (same lane): in[k] = out[in_from_out(k)].
+template <typename T, int N>
+__device__ __forceinline__ void out_to_in(cx<T> (&v)[3][Split<N>::R1]) {
+  constexpr int R1 = Split<N>::R1;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cx<T> t[R1];
+#pragma unroll
+    for (int k = 0; k < R1; ++k) t[k] = v[c][FFT2<N>::in_from_out(k)];
+#pragma unroll
+    for (int k = 0; k < R1; ++k) v[c][k] = t[k];
+  }
+}
+
+}  // namespace kd

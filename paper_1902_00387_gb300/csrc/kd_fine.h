@@ -1,0 +1,60 @@
+// Internal interfaces between the library's translation units.
+#pragma once
+#include "kd_common.cuh"
+
+namespace kd {
+
+// Optional per-launch hook (event timing of the fine kernels); kid 0 = column
+// kernel, 1 = row kernel.  Called on the host around each launch.
+struct LaunchProbe {
+  void (*before)(void* user, int kid);
+  void (*after)(void* user, int kid);
+  void* user;
+};
+
+// ---- kd_fine.cu
+cudaError_t fine_prepare(int prec);
+// bytes of the flow-phase table FineArgs::phases for `batch` fields and `nsteps` steps
+size_t phase_table_bytes(int prec, long batch, int nsteps);
+// fill FineArgs::phases (Galloway-Proctor only); returns kernels launched
+int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
+// ---- kd_fine2.cu (register-FFT kernels, n <= 256)
+cudaError_t fine2_prepare(int prec);
+int fine2_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
+                       const LaunchProbe* probe);
+// Enqueue `nsteps` RK443 steps on the compact state a.X (after filling the phase
+// table a.phases, which must hold phase_table_bytes(prec, a.batch, nsteps)).  prologue: start with the
+// inverse x transform of X (needed unless M already holds it).  store_last: leave M
+// filled for the state after the last step.  Returns the number of kernels launched
+// (negative on an unsupported grid size).
+int fine_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last,
+                      cudaStream_t st, const LaunchProbe* probe = nullptr);
+
+// ---- kd_ops.cu (layout conversions, Parareal update, norms)
+// full [batch][3][n][n] (precision pin) -> compact [batch][3][P][P] (precision pout)
+int full_to_compact(int pin, const void* full, int pout, void* comp, long batch, int n, cudaStream_t st);
+// compact -> full, zeros outside the kept square
+int compact_to_full(int pin, const void* comp, int pout, void* full, long batch, int n, cudaStream_t st);
+// compact (n_src grid, precision pin) -> compact (n_dst grid, precision pout):
+// truncation when n_dst < n_src, zero padding when n_dst > n_src
+int compact_resample(int pin, const void* src, int n_src, int pout, void* dst, int n_dst, long batch,
+                     cudaStream_t st);
+// Parareal update of one slice, FP64:
+//   U_next = F + prolong(g - Gold)   (g given in precision pg on the coarse compact grid)
+//   Gold   = g
+// init != 0: initial coarse sweep, U_next = prolong(g), Gold = g (F unused).
+// If partials != NULL: also per-block sums of |U_next - U_next_old|^2 and |U_next|^2
+// into partials[2 * blockIdx + {0,1}] (deterministic order), returns the block count.
+int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int n_c,
+                    int init, double* partials, cudaStream_t st);
+// sigma = sqrt(sum diff / sum norm) of `nblocks` partial pairs -> out[0]; also the two sums
+int finish_sigma(const double* partials, int nblocks, double* out, cudaStream_t st);
+// E[i] = sum |z|^2 over `len` complex128 entries of field i (stride len), i < count
+int energy_kernel(const double* fields, long len, int count, double* E, cudaStream_t st);
+// least-squares slope of 0.5 ln E_i against t_i = i * dt over t_i >= fit_from -> out[0];
+// out[1] = 1 if every used E_i was finite and > 0
+int growth_fit(const double* E, int count, double dt, double fit_from, double* out, cudaStream_t st);
+// dst[i] = t0 + i * dT
+int fill_times(double* dst, int count, double t0, double dT, cudaStream_t st);
+
+}  // namespace kd

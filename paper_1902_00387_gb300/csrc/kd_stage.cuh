@@ -1,0 +1,99 @@
+// Pointwise pieces of the fine step shared by the kernel families: the flow
+// u(x, y, t) (Sec. 2.1 / 2.2), the cross product u x b, the spectral curl
+// i k3 x w_hat, and the IMEX RK443 stage update with diagonal implicit diffusion.
+#pragma once
+#include "kd_common.cuh"
+
+namespace kd {
+
+// Flow phases of the Galloway-Proctor flow at the stage time t:
+// (cos(cos t), sin(cos t), cos(sin t), sin(sin t)); Roberts: (1, 0, 1, 0).
+template <typename T>
+struct Phase {
+  T cpx, spx, cpy, spy;
+};
+
+template <typename T>
+__device__ __forceinline__ Phase<T> load_phase(const FineArgs& a, long b, int step, int stage) {
+  Phase<T> p;
+  if (a.flow == FLOW_GP) {
+    const T* ph = (const T*)a.phases + (((long)b * a.phase_steps + step) * 4 + stage) * 4;
+    p.cpx = ph[0];
+    p.spx = ph[1];
+    p.cpy = ph[2];
+    p.spy = ph[3];
+  } else {
+    p.cpx = T(1);
+    p.spx = T(0);
+    p.cpy = T(1);
+    p.spy = T(0);
+  }
+  return p;
+}
+
+// w = u x b at the grid point with cos/sin of x and y given;
+// u = A (cos(y + py), sin(x + px), cos(x + px) + sin(y + py)).
+template <typename T>
+__device__ __forceinline__ void cross_u(T A, const Phase<T>& p, T cxg, T sxg, T cyg, T syg, cx<T>& bx, cx<T>& by,
+                                        cx<T>& bz) {
+  const T ux = A * (cyg * p.cpy - syg * p.spy);
+  const T uy = A * (sxg * p.cpx + cxg * p.spx);
+  const T uz = A * ((cxg * p.cpx - sxg * p.spx) + (syg * p.cpy + cyg * p.spy));
+  const cx<T> vx = bx, vy = by, vz = bz;
+  bx = vz * uy - vy * uz;
+  by = vx * uz - vz * ux;
+  bz = vy * ux - vx * uy;
+}
+
+// One IMEX RK443 stage at spectral point s (index into the compact arrays) for the
+// three components: w_hat (already scaled by 1/n^2) -> F = i k3 x w_hat -> new stage
+// value (returned in w).  mode = stage 0..3.
+template <typename T>
+__device__ __forceinline__ void stage_update(const FineArgs& a, int mode, long s0, long cstride, T fkx, T fky,
+                                             cx<T>& w0, cx<T>& w1, cx<T>& w2) {
+  const T dt = (T)a.dt;
+  const T kz = (T)a.kz;
+  cx<T> F[3];
+  F[0] = mul_i(w2 * fky - w1 * kz);
+  F[1] = mul_i(w0 * kz - w2 * fkx);
+  F[2] = mul_i(w1 * fkx - w0 * fky);
+  const T lam = (fkx * fkx + fky * fky + kz * kz) * (T(1) / (T)a.Rm);
+  const T inv_d = T(1) / (T(1) + dt * T(0.5) * lam);
+  const T dl = dt * lam;
+  cx<T>* X = (cx<T>*)a.X;
+  cx<T>* R2 = (cx<T>*)a.R2;
+  cx<T>* R3 = (cx<T>*)a.R3;
+  cx<T>* R4 = (cx<T>*)a.R4;
+  cx<T> out[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long s = s0 + c * cstride;
+    const cx<T> f = F[c];
+    if (mode == 0) {
+      const cx<T> x0 = X[s];
+      const cx<T> x1 = (x0 + f * (dt * T(0.5))) * inv_d;
+      R2[s] = x0 + f * (dt * T(11.0 / 18.0)) - x1 * (dl * T(1.0 / 6.0));
+      R3[s] = x0 + f * (dt * T(5.0 / 6.0)) + x1 * (dl * T(0.5));
+      R4[s] = x0 + f * (dt * T(0.25)) - x1 * (dl * T(1.5));
+      out[c] = x1;
+    } else if (mode == 1) {
+      const cx<T> x2 = (R2[s] + f * (dt * T(1.0 / 18.0))) * inv_d;
+      R3[s] = R3[s] - f * (dt * T(5.0 / 6.0)) - x2 * (dl * T(0.5));
+      R4[s] = R4[s] + f * (dt * T(1.75)) + x2 * (dl * T(1.5));
+      out[c] = x2;
+    } else if (mode == 2) {
+      const cx<T> x3 = (R3[s] + f * (dt * T(0.5))) * inv_d;
+      R4[s] = R4[s] + f * (dt * T(0.75)) - x3 * (dl * T(0.5));
+      out[c] = x3;
+    } else {
+      const cx<T> x4 = (R4[s] - f * (dt * T(1.75))) * inv_d;
+      X[s] = x4;
+      out[c] = x4;
+    }
+  }
+  w0 = out[0];
+  w1 = out[1];
+  w2 = out[2];
+}
+
+}  // namespace kd

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of libkd.so (include/kd.h).
+
+Argument marshalling only: every step of the fine propagator, the coarse
+propagator, the Parareal update and the norms runs in the library's CUDA kernels.
+Functions keep the C names.  Device buffers are torch CUDA tensors; the host
+buffers that kd_parareal_run / kd_fine_serial accept may be numpy arrays or CPU
+tensors.  A missing library raises immediately: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkd.so")
+
+KD_OK, KD_EINVAL, KD_ENOMEM, KD_ECUDA, KD_ENOTCONV, KD_ETIMEOUT, KD_ENONFINITE, KD_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["KD_OK", "KD_EINVAL", "KD_ENOMEM", "KD_ECUDA", "KD_ENOTCONV", "KD_ETIMEOUT",
+                "KD_ENONFINITE", "KD_EUNSUPPORTED"]
+KD_FLOW_ROBERTS, KD_FLOW_GALLOWAY_PROCTOR, KD_FLOW_NONE = 0, 1, 2
+KD_C64, KD_C128 = 0, 1
+KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
+KD_MAX_SLICES = 1024
+KD_MAX_ITERS = 256
+
+
+class KdError(RuntimeError):
+    def __init__(self, status, message):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, message))
+        self.status = status
+
+
+class kd_params(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int), ("n", ctypes.c_int), ("kz", ctypes.c_double),
+                ("Rm", ctypes.c_double), ("dt_fine", ctypes.c_double), ("prec_fine", ctypes.c_int),
+                ("n_coarse", ctypes.c_int), ("dt_coarse", ctypes.c_double), ("prec_coarse", ctypes.c_int),
+                ("coarse_kind", ctypes.c_int), ("learned_modes", ctypes.c_int)]
+
+
+class kd_parareal_stats(ctypes.Structure):
+    _fields_ = [("k_con", ctypes.c_int), ("converged", ctypes.c_int), ("n_fine_steps", ctypes.c_int),
+                ("n_coarse_steps", ctypes.c_int), ("dt_fine_used", ctypes.c_double),
+                ("dt_coarse_used", ctypes.c_double), ("sigma", ctypes.c_double * KD_MAX_ITERS),
+                ("energy", ctypes.c_double * (KD_MAX_SLICES + 1)), ("growth_rate", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_fine", ctypes.c_double), ("ms_coarse", ctypes.c_double),
+                ("fallback_used", ctypes.c_int), ("n_launches", ctypes.c_longlong)]
+
+
+_lib = None
+EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
+           "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
+           "kd_version"]
+
+
+def load():
+    """Load libkd.so once and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libkd.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "kd_create": (I, [ctypes.POINTER(kd_params), P, ctypes.POINTER(P)]),
+        "kd_destroy": (I, [P]),
+        "kd_fine_batched": (I, [P, P, P, P, I, I]),
+        "kd_coarse": (I, [P, P, P, P, I, I]),
+        "kd_parareal_run": (I, [P, P, D, I, I, D, P, ctypes.POINTER(kd_parareal_stats)]),
+        "kd_fine_serial": (I, [P, P, D, I, P]),
+        "kd_energy": (I, [P, P, I, P]),
+        "kd_growth_rate": (I, [P, P, I, D, D, ctypes.POINTER(D)]),
+        "kd_launch_count": (ctypes.c_longlong, [P]),
+        "kd_profile": (I, [P, I]),
+        "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
+        "kd_last_error": (ctypes.c_char_p, [P]),
+        "kd_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_params(flow, n, kz, Rm, dt_fine, prec_fine=KD_C64, n_coarse=None, dt_coarse=None,
+                prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL):
+    return kd_params(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(prec_fine),
+                     int(n_coarse if n_coarse else max(16, n // 2)),
+                     float(dt_coarse if dt_coarse else dt_fine), int(prec_fine if prec_coarse is None else prec_coarse),
+                     int(coarse_kind), 0)
+
+
+def _ptr(x, dtype=None, device=True):
+    """Address of a contiguous buffer (torch tensor or numpy array)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if device:
+            raise TypeError("a device (CUDA) buffer is required here")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        if dtype is not None and x.dtype != np.dtype(dtype):
+            raise TypeError("expected %s, got %s" % (dtype, x.dtype))
+        return x.ctypes.data
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch tensor or numpy array")
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if device and not x.is_cuda:
+        raise TypeError("a CUDA tensor is required here")
+    if dtype is not None:
+        want = {"complex64": torch.complex64, "complex128": torch.complex128, "float64": torch.float64}[dtype]
+        if x.dtype != want:
+            raise TypeError("expected %s, got %s" % (want, x.dtype))
+    return x.data_ptr()
+
+
+def _current_stream():
+    import torch
+    if torch.cuda.is_available() and torch.cuda.is_initialized():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _check(ctx, status, allow=()):
+    if status != KD_OK and status not in allow:
+        msg = load().kd_last_error(ctx) if ctx else b""
+        raise KdError(status, (msg or b"").decode())
+    return status
+
+
+def kd_version():
+    return load().kd_version().decode()
+
+
+def kd_last_error(ctx):
+    return load().kd_last_error(ctx).decode()
+
+
+def kd_create(params, stream=None):
+    """Create a context; `stream` is a cudaStream_t address (default: torch's current stream)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    st = _current_stream() if stream is None else stream
+    s = lib.kd_create(ctypes.byref(params), st, ctypes.byref(out))
+    if s != KD_OK:
+        raise KdError(s, "kd_create failed")
+    return out
+
+
+def kd_destroy(ctx):
+    return _check(None, load().kd_destroy(ctx))
+
+
+def _cdt(params_prec):
+    return "complex128" if params_prec == KD_C128 else "complex64"
+
+
+def kd_fine_batched(ctx, b_in, b_out, t0, nsteps, batch, prec=KD_C64):
+    """F: advance `batch` fields [batch][3][n][n] by `nsteps` fine steps (device tensors)."""
+    dt = _cdt(prec)
+    return _check(ctx, load().kd_fine_batched(ctx, _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
+                                              int(nsteps), int(batch)))
+
+
+def kd_coarse(ctx, b_in, b_out, t0, nsteps, batch):
+    """G: restrict, coarse steps, prolong; complex128 device tensors [batch][3][n][n]."""
+    return _check(ctx, load().kd_coarse(ctx, _ptr(b_in, "complex128"), _ptr(b_out, "complex128"),
+                                        _ptr(t0, "float64"), int(nsteps), int(batch)))
+
+
+def _any_ptr(x, dtype):
+    if isinstance(x, np.ndarray):
+        return _ptr(x, dtype, device=False)
+    return _ptr(x, dtype, device=False) if x is not None else None
+
+
+def kd_parareal_run(ctx, b0, T, n_slices, k_max, tol, u_slices=None):
+    """Parareal over [0, T]; b0 complex128 [3][n][n] and u_slices complex128
+    [n_slices+1][3][n][n] may live on the host or the device.  Returns (status, stats)."""
+    st = kd_parareal_stats()
+    s = load().kd_parareal_run(ctx, _any_ptr(b0, "complex128"), float(T), int(n_slices), int(k_max), float(tol),
+                               _any_ptr(u_slices, "complex128"), ctypes.byref(st))
+    _check(ctx, s, allow=(KD_ENOTCONV,))
+    return s, st
+
+
+def kd_fine_serial(ctx, b0, T, n_slices, u_slices):
+    """Serial fine solution at the slice boundaries (same step rule as kd_parareal_run)."""
+    return _check(ctx, load().kd_fine_serial(ctx, _any_ptr(b0, "complex128"), float(T), int(n_slices),
+                                             _any_ptr(u_slices, "complex128")))
+
+
+def kd_energy(ctx, fields, count, energy_out):
+    return _check(ctx, load().kd_energy(ctx, _ptr(fields, "complex128"), int(count), _ptr(energy_out, "float64")))
+
+
+def kd_growth_rate(ctx, u_slices, n_samples, T, fit_from):
+    rate = ctypes.c_double()
+    _check(ctx, load().kd_growth_rate(ctx, _ptr(u_slices, "complex128"), int(n_samples), float(T),
+                                      float(fit_from), ctypes.byref(rate)))
+    return rate.value
+
+
+def kd_launch_count(ctx):
+    return int(load().kd_launch_count(ctx))
+
+
+def kd_profile(ctx, enable):
+    return _check(ctx, load().kd_profile(ctx, int(bool(enable))))
+
+
+def kd_profile_read(ctx):
+    """(ms[2], launches[2]) of the fine column (0) and row (1) kernels since kd_profile(ctx, 1)."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_longlong * 2)()
+    _check(ctx, load().kd_profile_read(ctx, ms, n))
+    return [ms[0], ms[1]], [n[0], n[1]]
+
+
+def stats_dict(st):
+    k = st.k_con
+    return {"k_con": k, "converged": bool(st.converged), "n_fine_steps": st.n_fine_steps,
+            "n_coarse_steps": st.n_coarse_steps, "dt_fine_used": st.dt_fine_used,
+            "dt_coarse_used": st.dt_coarse_used, "sigma": list(st.sigma[:k]), "growth_rate": st.growth_rate,
+            "ms_total": st.ms_total, "ms_fine": st.ms_fine, "ms_coarse": st.ms_coarse,
+            "n_launches": st.n_launches}

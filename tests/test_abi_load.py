@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every entry point that include/kd.h
+declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "kd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kd_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00387_gb300 as kd
+    return kd.load()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_growth_rate"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_binding_names_match_header(lib):
+    import paper_1902_00387_gb300 as kd
+    for s in declared_symbols():
+        assert callable(getattr(kd, s)), s
+
+
+def test_version_and_argument_validation_without_gpu(lib):
+    import paper_1902_00387_gb300 as kd
+    assert "sm_103a" in kd.kd_version()
+    out = ctypes.c_void_p()
+    bad = kd.make_params(kd.KD_FLOW_ROBERTS, 48, 1.0, 8.0, 1e-2)        # n not a power of two
+    assert lib.kd_create(ctypes.byref(bad), None, ctypes.byref(out)) == kd.KD_EINVAL
+    bad = kd.make_params(kd.KD_FLOW_ROBERTS, 32, 1.0, -8.0, 1e-2)       # Rm <= 0
+    assert lib.kd_create(ctypes.byref(bad), None, ctypes.byref(out)) == kd.KD_EINVAL
+    bad = kd.make_params(kd.KD_FLOW_ROBERTS, 32, 1.0, 8.0, 1e-2, n_coarse=64)
+    assert lib.kd_create(ctypes.byref(bad), None, ctypes.byref(out)) == kd.KD_EINVAL
+    assert lib.kd_destroy(None) == kd.KD_OK
+    assert lib.kd_fine_batched(None, None, None, None, 1, 1) == kd.KD_EINVAL
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    """ctypes mirrors of kd_params / kd_parareal_stats have the C compiler's layout."""
+    import shutil
+    import subprocess
+    import paper_1902_00387_gb300 as kd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    probe = tmp_path / "probe.c"
+    probe.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "kd.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kd_params), offsetof(kd_params, n_coarse),'
+        ' sizeof(kd_parareal_stats), offsetof(kd_parareal_stats, sigma), offsetof(kd_parareal_stats, growth_rate),'
+        ' offsetof(kd_parareal_stats, fallback_used), offsetof(kd_parareal_stats, n_launches)); return 0;}\n')
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(kd.kd_params), kd.kd_params.n_coarse.offset, ctypes.sizeof(kd.kd_parareal_stats),
+            kd.kd_parareal_stats.sigma.offset, kd.kd_parareal_stats.growth_rate.offset,
+            kd.kd_parareal_stats.fallback_used.offset, kd.kd_parareal_stats.n_launches.offset]
+    assert got == want

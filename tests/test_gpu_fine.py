@@ -1,0 +1,182 @@
+"""Parity of the CUDA fine propagator (kd_fine_batched, kd_coarse) with the CPU FP64
+oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import kd_inputs as I
+from oracle import kd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+# FP32 tolerance on relative L2 error per field state (1e-5 per slice state);
+# FP64 tolerance from the round-off of ~10^4 operations per value.
+TOL32 = 1e-5
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    return kd
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def run_fine(kd, flow, n, kz, Rm, dt, prec, b, t0, nsteps):
+    import torch
+    ctx = kd.kd_create(kd.make_params(flow, n, kz, Rm, dt, prec))
+    try:
+        dtype = torch.complex128 if prec == kd.KD_C128 else torch.complex64
+        x = torch.tensor(b, dtype=dtype, device="cuda")
+        y = torch.empty_like(x)
+        tt = torch.tensor(np.asarray(t0, np.float64), device="cuda")
+        kd.kd_fine_batched(ctx, x, y, tt, nsteps, b.shape[0], prec)
+        torch.cuda.synchronize()
+        return y.cpu().numpy().astype(np.complex128)
+    finally:
+        kd.kd_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256])
+@pytest.mark.parametrize("flow", [O.ROBERTS, O.GALLOWAY_PROCTOR])
+def test_few_steps_fp32(kd, n, flow):
+    kz, Rm, dt = 0.57, 100.0, 5e-3
+    b = I.initial_batch(n, kz, [11, 12, 13])          # 3 fields: ragged last block
+    t0 = [0.0, 0.25, 1.7]
+    out = run_fine(kd, flow, n, kz, Rm, dt, kd.KD_C64, b, t0, 3)
+    p = O.Problem(flow, n, kz, Rm)
+    for i in range(3):
+        ref = O.propagate(b[i], p, t0[i], dt, 3)
+        assert rel(out[i], ref) < TOL32
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+@pytest.mark.parametrize("flow", [O.ROBERTS, O.GALLOWAY_PROCTOR])
+def test_few_steps_fp64(kd, n, flow):
+    kz, Rm, dt = 1.0, 8.0, 1e-2
+    b = I.initial_batch(n, kz, [3, 4])
+    t0 = [0.0, 0.9]
+    out = run_fine(kd, flow, n, kz, Rm, dt, kd.KD_C128, b, t0, 5)
+    p = O.Problem(flow, n, kz, Rm)
+    for i in range(2):
+        assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 5)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_large_grids_fp32(kd, n):
+    kz, Rm, dt = 0.57, 1e4, 1e-3
+    b = I.initial_batch(n, kz, [21])
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, [2.0], 2)
+    ref = O.propagate(b[0], O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm), 2.0, dt, 2)
+    assert rel(out[0], ref) < TOL32
+
+
+def test_roberts_slice_fp64_config1(kd):
+    # one Parareal slice of the Roberts 32^2 complex128 problem: 125 steps of 1e-2
+    n, kz, Rm, dt = 32, 1.0, 8.0, 1e-2
+    b = I.initial_batch(n, kz, [0])
+    out = run_fine(kd, O.ROBERTS, n, kz, Rm, dt, kd.KD_C128, b, [0.0], 125)
+    ref = O.propagate(b[0], O.Problem(O.ROBERTS, n, kz, Rm), 0.0, dt, 125)
+    assert rel(out[0], ref) < TOL64
+
+
+def test_gp_slice_fp32_config2(kd):
+    # one Parareal slice of the GP 128^2 problem: dT = pi/4 in 158 steps, from t = 3 dT
+    n, kz, Rm = 128, 0.57, 100.0
+    dT = 2 * np.pi * 8 / 64
+    S = 158
+    dt = dT / S
+    b = I.initial_batch(n, kz, [5])
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, [3 * dT], S)
+    ref = O.propagate(b[0], O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm), 3 * dT, dt, S)
+    assert rel(out[0], ref) < TOL32
+
+
+def test_batch_invariance_bitwise(kd):
+    n, kz, Rm, dt = 64, 0.57, 100.0, 5e-3
+    b = I.initial_batch(n, kz, [1, 2, 3, 4, 5])
+    t0 = [0.1, 0.2, 0.3, 0.4, 0.5]
+    all5 = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, t0, 4)
+    one = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b[3:4], t0[3:4], 4)
+    assert np.array_equal(all5[3], one[0])
+
+
+def test_zero_steps_masks_input(kd):
+    n = 32
+    rng = np.random.default_rng(0)
+    b = (rng.standard_normal((2, 3, n, n)) + 1j * rng.standard_normal((2, 3, n, n)))
+    out = run_fine(kd, O.ROBERTS, n, 1.0, 8.0, 1e-2, kd.KD_C128, b, [0.0, 0.0], 0)
+    assert np.array_equal(out, b * O.kept_mask(n))
+
+
+def test_modes_outside_kept_set_are_ignored(kd):
+    n, kz = 64, 0.8
+    b = I.initial_batch(n, kz, [7])
+    noisy = b.copy()
+    noisy[:, :, ~O.kept_mask(n)] = 1e3
+    a = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, 50.0, 5e-3, kd.KD_C64, b, [0.0], 3)
+    c = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, 50.0, 5e-3, kd.KD_C64, noisy, [0.0], 3)
+    assert np.array_equal(a, c)
+    assert np.abs(a[:, :, ~O.kept_mask(n)]).max() == 0.0
+
+
+@pytest.mark.parametrize("n", [64, 1024])
+def test_pure_diffusion_exact_factor(kd, n):
+    # u = 0: each mode is multiplied by the stability function R(-lambda dt) per step,
+    # a property that holds at any size (checked here at full 1024^2 too).
+    kz, Rm, dt, S = 0.57, 1e4, 1e-3, 20
+    b = I.initial_batch(n, kz, [2])
+    out = run_fine(kd, O.NO_FLOW, n, kz, Rm, dt, kd.KD_C64, b, [0.0], S)
+    lam = O.diffusion_rate(O.Problem(O.NO_FLOW, n, kz, Rm))
+    z = -lam * dt
+    # RK443 implicit stability function: stage recursion with A of the tableau
+    A = O.RK443["A"]
+    R = np.zeros_like(z)
+    X = [np.ones_like(z)]
+    for i in range(1, 5):
+        acc = np.ones_like(z)
+        for j in range(1, i):
+            acc = acc + z * A[i, j] * X[j]
+        X.append(acc / (1 - z * A[i, i]))
+    R = X[4]
+    assert rel(out[0], b[0] * R ** S) < TOL32
+
+
+def test_divergence_free_preserved(kd):
+    n, kz = 128, 0.57
+    b = I.initial_batch(n, kz, [9])
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, 100.0, 5e-3, kd.KD_C64, b, [0.0], 50)
+    kx, ky, kzz = O.wavevector(n, kz)
+    div = kx * out[0, 0] + ky * out[0, 1] + kzz * out[0, 2]
+    k3 = np.sqrt(kx ** 2 + ky ** 2 + kzz ** 2)
+    assert np.linalg.norm(div) / np.linalg.norm(k3 * np.linalg.norm(out[0], axis=0)) < 1e-6
+
+
+def test_coarse_propagator_matches_oracle(kd):
+    import torch
+    n, nc, kz, Rm = 64, 32, 0.57, 100.0
+    dtc = 0.05
+    p = kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, 5e-3, kd.KD_C64, n_coarse=nc, dt_coarse=dtc,
+                       prec_coarse=kd.KD_C128)
+    ctx = kd.kd_create(p)
+    try:
+        b = I.initial_batch(n, kz, [1, 2])
+        x = torch.tensor(b, device="cuda")
+        y = torch.empty_like(x)
+        t0 = torch.tensor([0.0, 0.7], dtype=torch.float64, device="cuda")
+        kd.kd_coarse(ctx, x, y, t0, 6, 2)
+        torch.cuda.synchronize()
+        out = y.cpu().numpy()
+    finally:
+        kd.kd_destroy(ctx)
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i, t in enumerate((0.0, 0.7)):
+        ref = O.coarse_propagate(b[i], prob, nc, t, dtc, 6)
+        assert rel(out[i], ref) < 1e-13

@@ -1,0 +1,162 @@
+"""Parity of the one-GPU Parareal driver (kd_parareal_run, kd_fine_serial) and the
+growth-rate path (kd_energy, kd_growth_rate) with the CPU FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import kd_inputs as I
+from oracle import kd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    return kd
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def oracle_ops(prob, n_c, T, N, dt_f, dt_c):
+    dT = T / N
+    S = math.ceil(dT / dt_f - 1e-9)
+    Sc = math.ceil(dT / dt_c - 1e-9)
+    fine = lambda u, i: O.propagate(u, prob, i * dT, dT / S, S)
+    coarse = lambda u, i: O.coarse_propagate(u, prob, n_c, i * dT, dT / Sc, Sc)
+    return fine, coarse, S, Sc
+
+
+# Roberts 32^2 complex128, kz = 1, Rm = 8, dt = 1e-2, T = 10, 8 slices, Delta t = 0.1, N_C = 16
+C1 = dict(flow=O.ROBERTS, n=32, kz=1.0, Rm=8.0, dt=1e-2, T=10.0, N=8, dtc=0.1, nc=16)
+
+
+def c1_ctx(kd):
+    p = kd.make_params(C1["flow"], C1["n"], C1["kz"], C1["Rm"], C1["dt"], kd.KD_C128, n_coarse=C1["nc"],
+                       dt_coarse=C1["dtc"], prec_coarse=kd.KD_C128)
+    return kd.kd_create(p)
+
+
+def test_parareal_config1_iterates_match_oracle(kd):
+    # Same number of iterations on both sides (tol = 0), FP64 everywhere.
+    b0 = I.initial_field(C1["n"], C1["kz"], 0)
+    kmax = 3
+    ctx = c1_ctx(kd)
+    try:
+        out = np.zeros((C1["N"] + 1, 3, C1["n"], C1["n"]), np.complex128)
+        status, st = kd.kd_parareal_run(ctx, b0, C1["T"], C1["N"], kmax, 0.0, out)
+    finally:
+        kd.kd_destroy(ctx)
+    assert status == kd.KD_ENOTCONV and st.k_con == kmax
+    prob = O.Problem(C1["flow"], C1["n"], C1["kz"], C1["Rm"])
+    fine, coarse, S, Sc = oracle_ops(prob, C1["nc"], C1["T"], C1["N"], C1["dt"], C1["dtc"])
+    assert (st.n_fine_steps, st.n_coarse_steps) == (S, Sc) == (125, 13)
+    ref = O.parareal(b0, fine, coarse, C1["N"], kmax, 0.0)
+    for i in range(C1["N"] + 1):
+        assert rel(out[i], ref["U"][i]) < 1e-11, i
+    for k in range(kmax):
+        assert abs(st.sigma[k] - ref["sigma"][k]) <= 1e-8 * ref["sigma"][k]
+
+
+def test_parareal_k_equals_n_is_serial_fine_bitwise(kd):
+    b0 = I.initial_field(C1["n"], C1["kz"], 1)
+    ctx = c1_ctx(kd)
+    try:
+        par = np.zeros((C1["N"] + 1, 3, C1["n"], C1["n"]), np.complex128)
+        ser = np.zeros_like(par)
+        kd.kd_parareal_run(ctx, b0, C1["T"], C1["N"], C1["N"], 0.0, par)
+        kd.kd_fine_serial(ctx, b0, C1["T"], C1["N"], ser)
+    finally:
+        kd.kd_destroy(ctx)
+    assert np.array_equal(par, ser)
+    prob = O.Problem(C1["flow"], C1["n"], C1["kz"], C1["Rm"])
+    fine, _, _, _ = oracle_ops(prob, C1["nc"], C1["T"], C1["N"], C1["dt"], C1["dtc"])
+    ref = O.serial_fine(b0, fine, C1["N"])
+    assert rel(ser[-1], ref[-1]) < 1e-11
+
+
+def test_parareal_gp_fp32_converges_to_serial_fine(kd):
+    # GP flow, complex64 fine / complex64 coarse on N/2, FP64 update.  The coarse step
+    # 0.05 is inside the explicit stability limit on the 32^2 grid; tol 1e-5 sits above
+    # the FP32 round-off floor of the defect (about sqrt(N) x 2e-7 per slice).
+    n, kz, Rm, T, N = 64, 0.57, 100.0, 2 * np.pi, 16
+    dt, dtc = 5e-3, 0.05
+    p = kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, n_coarse=32, dt_coarse=dtc,
+                       prec_coarse=kd.KD_C64)
+    b0 = I.initial_field(n, kz, 2)
+    ctx = kd.kd_create(p)
+    try:
+        par = np.zeros((N + 1, 3, n, n), np.complex128)
+        ser = np.zeros_like(par)
+        status, st = kd.kd_parareal_run(ctx, b0, T, N, N, 1e-5, par)
+        kd.kd_fine_serial(ctx, b0, T, N, ser)
+    finally:
+        kd.kd_destroy(ctx)
+    assert status == kd.KD_OK and st.converged and st.k_con < N
+    # Parareal reproduces the serial fine solution (same FP32 kernels) to its tolerance
+    assert rel(par[-1], ser[-1]) < 1e-5
+    # and every serial fine slice state matches the FP64 oracle propagated from the same
+    # input state (per-slice tolerance 1e-5; sampled slices)
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    S = st.n_fine_steps
+    dT = T / N
+    for i in (0, 7, N - 1):
+        x = O.propagate(ser[i], prob, i * dT, dT / S, S)
+        assert rel(ser[i + 1], x) < 1e-5, i
+
+
+def test_energy_and_growth_fit_match_oracle(kd):
+    import torch
+    n = 32
+    ctx = c1_ctx(kd)
+    try:
+        fields = np.stack([I.initial_field(n, 1.0, s) * math.exp(0.3 * s) for s in range(9)])
+        x = torch.tensor(fields, device="cuda")
+        E = torch.zeros(9, dtype=torch.float64, device="cuda")
+        kd.kd_energy(ctx, x, 9, E)
+        torch.cuda.synchronize()
+        e = E.cpu().numpy()
+        for i in range(9):
+            assert abs(e[i] - O.energy(fields[i])) <= 1e-14 * O.energy(fields[i])
+        rate = kd.kd_growth_rate(ctx, x, 9, 4.0, 2.0)
+    finally:
+        kd.kd_destroy(ctx)
+    ts = np.linspace(0, 4.0, 9)
+    assert abs(rate - O.growth_rate(ts, [O.energy(f) for f in fields], 2.0)) < 1e-13
+
+
+def test_parareal_stats_growth_rate_matches_oracle(kd):
+    # Roberts Rm = 8, kz = 1: the leading eigenvalue of the spectral operator is ~0.04994
+    b0 = I.initial_field(C1["n"], C1["kz"], 3)
+    ctx = c1_ctx(kd)
+    try:
+        status, st = kd.kd_parareal_run(ctx, b0, 40.0, 32, 32, 1e-10, None)
+    finally:
+        kd.kd_destroy(ctx)
+    prob = O.Problem(C1["flow"], C1["n"], C1["kz"], C1["Rm"])
+    E = list(st.energy[:33])
+    fit = O.growth_rate(np.arange(33) * 40.0 / 32, E, 20.0)
+    assert abs(st.growth_rate - fit) < 1e-12
+    import scipy.sparse.linalg as sla
+    lam = sla.eigs(O.linear_operator(prob).tocsc(), k=3, sigma=0.3, return_eigenvectors=False)
+    assert abs(st.growth_rate - max(lam.real)) < 1e-3
+
+
+def test_invalid_arguments_are_rejected(kd):
+    ctx = c1_ctx(kd)
+    try:
+        with pytest.raises(kd.KdError) as e:
+            kd.kd_parareal_run(ctx, I.initial_field(32, 1.0, 0), 1.0, 0, 3, 1e-6)
+        assert e.value.status == kd.KD_EINVAL
+        with pytest.raises(kd.KdError):
+            kd.kd_parareal_run(ctx, I.initial_field(32, 1.0, 0), -1.0, 4, 3, 1e-6)
+    finally:
+        kd.kd_destroy(ctx)
