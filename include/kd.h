@@ -48,6 +48,15 @@ typedef enum {
 enum { KD_FLOW_ROBERTS = 0, KD_FLOW_GALLOWAY_PROCTOR = 1, KD_FLOW_NONE = 2 };
 enum { KD_C64 = 0, KD_C128 = 1 };
 enum { KD_COARSE_CLASSICAL = 0, KD_COARSE_LEARNED = 1 };
+/* How kd_parareal_run evaluates the fine values F(U^k_n) of its parallel step:
+ * DIRECT propagates U^k_n itself (a complex64 fine propagator then leaves round-off
+ * noise of ~1e-7 per slice in every iterate, which floors the defect sigma near
+ * sqrt(n_slices) x 1e-7); INCREMENT uses the linearity of F in b,
+ * F(U^k) = F(U^{k-1}) + F(U^k - U^{k-1}), propagating only the FP64 increment in the
+ * fine precision and accumulating in FP64, so sigma keeps falling below that floor.
+ * Both are the same iteration in exact arithmetic; DIRECT keeps the bitwise
+ * finite-termination property (after k iterations slices 0..k equal kd_fine_serial). */
+enum { KD_FINE_DIRECT = 0, KD_FINE_INCREMENT = 1 };
 
 #define KD_MAX_SLICES 1024
 #define KD_MAX_ITERS 256
@@ -65,6 +74,7 @@ typedef struct {
   int prec_coarse;     /* KD_C64 or KD_C128 arithmetic of the classical coarse propagator */
   int coarse_kind;     /* KD_COARSE_CLASSICAL (only value implemented) */
   int learned_modes;   /* reserved; 0 */
+  int fine_form;       /* KD_FINE_DIRECT or KD_FINE_INCREMENT (kd_parareal_run) */
 } kd_params;
 
 /* Create a context for one problem.  `cuda_stream` is a cudaStream_t (may be NULL).

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/kd.h"
+#include "kd_coarse.h"
 #include "kd_fine.h"
 
 using namespace kd;
@@ -60,6 +61,9 @@ struct kd_ctx {
   double* U = nullptr;
   double* Fv = nullptr;
   double* Gv = nullptr;
+  double* Uprev = nullptr;    // previous iterate (increment form of the fine sweep)
+  void* ph_c = nullptr;       // coarse flow-phase table of all slices
+  size_t ph_c_bytes = 0;
   double* t0f = nullptr;
   double* t0c = nullptr;
   double* partials = nullptr;
@@ -310,12 +314,16 @@ kd_status ensure_slices(kd_ctx* ctx, long N) {
   dfree(ctx, ctx->Gv);
   dfree(ctx, ctx->t0f);
   dfree(ctx, ctx->t0c);
+  dfree(ctx, ctx->Uprev);
   ctx->cap_slices = 0;
   const int n = ctx->p.n, nc = ctx->p.n_coarse;
   kd_status s;
   if ((s = dalloc(ctx, (void**)&ctx->U, (N + 1) * compact_len(n) * 16, "U")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&ctx->Fv, N * compact_len(n) * 16, "F values")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&ctx->Gv, N * compact_len(nc) * 16, "G values")) != KD_OK) return s;
+  if (ctx->p.fine_form == KD_FINE_INCREMENT &&
+      (s = dalloc(ctx, (void**)&ctx->Uprev, N * compact_len(n) * 16, "previous iterate")) != KD_OK)
+    return s;
   if ((s = dalloc(ctx, (void**)&ctx->t0f, (N + 1) * 8, "t0")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&ctx->t0c, (N + 1) * 8, "t0")) != KD_OK) return s;
   ctx->cap_slices = N;
@@ -339,34 +347,111 @@ kd_status check_params(const kd_params* p, std::string& why) {
   if ((p->prec_fine != KD_C64 && p->prec_fine != KD_C128) || (p->prec_coarse != KD_C64 && p->prec_coarse != KD_C128))
     return why = "precision must be KD_C64 or KD_C128", KD_EINVAL;
   if (p->coarse_kind != KD_COARSE_CLASSICAL) return why = "only the classical coarse propagator is built", KD_EUNSUPPORTED;
+  if (p->fine_form != KD_FINE_DIRECT && p->fine_form != KD_FINE_INCREMENT) return why = "bad fine_form", KD_EINVAL;
   return KD_OK;
 }
 
-// One classical coarse solve of slice `n_slice`: U_n (fine compact FP64) -> coarse
-// state in ws_c.X after `steps` steps.
-kd_status coarse_solve(kd_ctx* ctx, const double* Un, const double* t0, int steps, double dtc) {
+// Coarse flow phases of every slice: [N][Sc][4][4] in the coarse precision.
+kd_status coarse_phases(kd_ctx* ctx, int N, int Sc, double dtc) {
+  if (ctx->p.flow != KD_FLOW_GALLOWAY_PROCTOR) return KD_OK;
+  const size_t need = phase_table_bytes(ctx->p.prec_coarse, N, Sc);
+  if (ctx->ph_c_bytes < need) {
+    dfree(ctx, ctx->ph_c);
+    ctx->ph_c = nullptr;
+    ctx->ph_c_bytes = 0;
+    kd_status s = dalloc(ctx, &ctx->ph_c, need, "coarse phase table");
+    if (s != KD_OK) return s;
+    ctx->ph_c_bytes = need;
+  }
+  FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, ctx->p.n_coarse, N, dtc, ctx->t0c);
+  a.phases = ctx->ph_c;
+  KD_LAUNCH(launch_phases(ctx->p.prec_coarse, a, Sc, ctx->st), "coarse phases");
+  return KD_OK;
+}
+
+CoarseArgs coarse_args(const kd_ctx* ctx, int steps, double dtc) {
+  CoarseArgs c;
+  memset(&c, 0, sizeof(c));
+  c.Kc = ctx->p.n_coarse / 3;
+  c.Kf = ctx->p.n / 3;
+  c.flow = ctx->p.flow;
+  c.amp = ctx->p.flow == KD_FLOW_ROBERTS ? 1.0 : ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? sqrt(1.5) : 0.0;
+  c.kz = ctx->p.kz;
+  c.Rm = ctx->p.Rm;
+  c.dt = dtc;
+  c.nsteps = steps;
+  return c;
+}
+
+// Serial-sweep step of slice i with a coarse solve:
+//   init:      U_{i+1} = G(U_i),                        Gv_i = G(U_i)
+//   direct:    U_{i+1} = Fv_i + (G(U_i) - Gv_i),         Gv_i = G(U_i)
+//   increment: U_{i+1} = Fv_i + G(U_i - Uprev_i)   (G linear; Uprev_i = previous iterate)
+// (+ sigma of U_{i+1} when `last`).
+kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool last) {
   const int n = ctx->p.n, nc = ctx->p.n_coarse, pc = ctx->p.prec_coarse;
-  KD_LAUNCH(compact_resample(KD_C128, Un, n, pc, ctx->ws_c.X, nc, 1, ctx->st), "restrict");
-  FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, 1, dtc, t0);
-  kd_status s = with_phases(ctx, ctx->ws_c, a, steps);
+  const long len = compact_len(n), lenc = compact_len(nc);
+  const bool incr = !init && ctx->p.fine_form == KD_FINE_INCREMENT;
+  if (coarse_conv_supported(nc)) {
+    CoarseArgs c = coarse_args(ctx, Sc, dtc);
+    c.phases = ctx->ph_c ? (const char*)ctx->ph_c + (size_t)i * Sc * 16 * (pc == KD_C64 ? 4 : 8) : nullptr;
+    if (ctx->p.flow != KD_FLOW_GALLOWAY_PROCTOR) c.phases = nullptr;
+    c.Un = ctx->U + 2 * i * len;
+    c.Uprev = incr ? ctx->Uprev + 2 * i * len : nullptr;
+    c.mode = init ? COARSE_INIT : (incr ? COARSE_INCR : COARSE_UPDATE);
+    c.Fv = init ? nullptr : ctx->Fv + 2 * i * len;
+    c.Gold = ctx->Gv + 2 * i * lenc;
+    c.Unext = ctx->U + 2 * (i + 1) * len;
+    c.sigma_out = last ? ctx->scal : nullptr;
+    KD_LAUNCH(coarse_conv_launch(pc, c, 1, nc, ctx->st), "coarse solve");
+    return KD_OK;
+  }
+  // general grids: restrict, multi-kernel RK443 steps, separate update
+  const double* src = ctx->U + 2 * i * len;
+  if (incr) {
+    kd_status s0 = ensure_full_tmp(ctx, (size_t)len * 16);
+    if (s0 != KD_OK) return s0;
+    KD_LAUNCH(diff_kernel(src, ctx->Uprev + 2 * i * len, (double*)ctx->full_tmp, len, ctx->st), "increment");
+    src = (const double*)ctx->full_tmp;
+  }
+  KD_LAUNCH(compact_resample(KD_C128, src, n, pc, ctx->ws_c.X, nc, 1, ctx->st), "restrict");
+  FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, 1, dtc, ctx->t0c + i);
+  kd_status s = with_phases(ctx, ctx->ws_c, a, Sc);
   if (s != KD_OK) return s;
-  KD_LAUNCH(fine_launch_steps(pc, a, steps, true, false, ctx->st), "coarse steps");
+  KD_LAUNCH(fine_launch_steps(pc, a, Sc, true, false, ctx->st), "coarse steps");
+  int nb = parareal_update(init ? nullptr : ctx->Fv + 2 * i * len, ctx->ws_c.X, pc, ctx->Gv + 2 * i * lenc,
+                           ctx->U + 2 * (i + 1) * len, n, nc, init ? 1 : (incr ? 2 : 0),
+                           last ? ctx->partials : nullptr, ctx->st);
+  if (nb < 0) return fail(ctx, KD_ECUDA, "parareal update launch failed");
+  ctx->launches += 1;
+  if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
   return KD_OK;
 }
 
-// Parallel fine step over slices [first, N): Fv[n] = F(U[n]).
-kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt) {
+// Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
+// increment form Fv[n] += F(U[n] - Uprev[n]) (iter > 1).
+kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
   const int n = ctx->p.n, pf = ctx->p.prec_fine;
   const long b = N - first;
   if (b <= 0) return KD_OK;
   const long len = compact_len(n);
-  KD_LAUNCH(compact_resample(KD_C128, ctx->U + 2 * first * len, n, pf, ctx->ws_f.X, n, b, ctx->st), "to fine");
+  const bool incr = ctx->p.fine_form == KD_FINE_INCREMENT;
+  if (incr)
+    KD_LAUNCH(delta_in(pf, ctx->U + 2 * first * len, ctx->Uprev + 2 * first * len, ctx->ws_f.X, b * len,
+                       iter == 1 ? 1 : 0, ctx->st),
+              "increment to fine");
+  else
+    KD_LAUNCH(compact_resample(KD_C128, ctx->U + 2 * first * len, n, pf, ctx->ws_f.X, n, b, ctx->st), "to fine");
   FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, b, dt, ctx->t0f + first);
   kd_status s = with_phases(ctx, ctx->ws_f, a, S);
   if (s != KD_OK) return s;
   LaunchProbe pr = probe_of(ctx);
   KD_LAUNCH(fine_launch_steps(pf, a, S, true, false, ctx->st, ctx->prof ? &pr : nullptr), "fine steps");
-  KD_LAUNCH(compact_resample(pf, ctx->ws_f.X, n, KD_C128, ctx->Fv + 2 * first * len, n, b, ctx->st), "from fine");
+  if (incr)
+    KD_LAUNCH(accum_out(pf, ctx->ws_f.X, ctx->Fv + 2 * first * len, b * len, iter == 1 ? 1 : 0, ctx->st),
+              "accumulate fine");
+  else
+    KD_LAUNCH(compact_resample(pf, ctx->ws_f.X, n, KD_C128, ctx->Fv + 2 * first * len, n, b, ctx->st), "from fine");
   return KD_OK;
 }
 
@@ -414,6 +499,7 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = fine_prepare(params->prec_fine);
   if (e == cudaSuccess) e = fine_prepare(params->prec_coarse);
+  if (e == cudaSuccess) e = coarse_prepare(params->prec_coarse);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e != cudaSuccess) {
     fprintf(stderr, "kd_create: %s\n", cudaGetErrorString(e));
@@ -480,6 +566,30 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
   const size_t fcb = (size_t)batch * compact_len(n) * 16;
   if ((s = ensure_full_tmp(ctx, fcb)) != KD_OK) return s;
   KD_LAUNCH(full_to_compact(KD_C128, b_in, KD_C128, ctx->full_tmp, batch, n, ctx->st), "pack");
+  if (coarse_conv_supported(nc) && nsteps > 0) {
+    // persistent convolution-form solve, one block per field; result in ws_c.X as FP64
+    if ((s = ensure_ws(ctx, ctx->ws_c, nc, KD_C128, batch)) != KD_OK) return s;
+    FineArgs pa = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, batch, ctx->p.dt_coarse, t0);
+    const size_t need = phase_table_bytes(pc, batch, nsteps);
+    if (ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR && ctx->ph_c_bytes < need) {
+      dfree(ctx, ctx->ph_c);
+      ctx->ph_c = nullptr;
+      ctx->ph_c_bytes = 0;
+      if ((s = dalloc(ctx, &ctx->ph_c, need, "coarse phase table")) != KD_OK) return s;
+      ctx->ph_c_bytes = need;
+    }
+    pa.phases = ctx->ph_c;
+    KD_LAUNCH(launch_phases(pc, pa, nsteps, ctx->st), "coarse phases");
+    CoarseArgs c = coarse_args(ctx, nsteps, ctx->p.dt_coarse);
+    c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? ctx->ph_c : nullptr;
+    c.Un = (const double*)ctx->full_tmp;
+    c.mode = COARSE_OUT;
+    c.g64 = (double*)ctx->ws_c.X;
+    KD_LAUNCH(coarse_conv_launch(pc, c, batch, nc, ctx->st), "coarse solve");
+    KD_LAUNCH(compact_resample(KD_C128, ctx->ws_c.X, nc, KD_C128, ctx->full_tmp, n, batch, ctx->st), "prolong");
+    KD_LAUNCH(compact_to_full(KD_C128, ctx->full_tmp, KD_C128, b_out, batch, n, ctx->st), "unpack");
+    return KD_OK;
+  }
   KD_LAUNCH(compact_resample(KD_C128, ctx->full_tmp, n, pc, ctx->ws_c.X, nc, batch, ctx->st), "restrict");
   FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, batch, ctx->p.dt_coarse, t0);
   if ((s = with_phases(ctx, ctx->ws_c, a, nsteps)) != KD_OK) return s;
@@ -511,15 +621,12 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
 
   KD_CUDA(cudaEventRecord(ctx->ev[0], ctx->st), "event");
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
+  if ((s = coarse_phases(ctx, N, Sc, dtc)) != KD_OK) return s;
   float ms_fine = 0.f, ms_coarse = 0.f;
   // iterate 0: serial coarse sweep
   KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
-  for (int i = 0; i < N; ++i) {
-    if ((s = coarse_solve(ctx, ctx->U + 2 * i * len, ctx->t0c + i, Sc, dtc)) != KD_OK) return s;
-    KD_LAUNCH(parareal_update(nullptr, ctx->ws_c.X, ctx->p.prec_coarse, ctx->Gv + 2 * i * lenc,
-                              ctx->U + 2 * (i + 1) * len, n, nc, 1, nullptr, ctx->st),
-              "initial update");
-  }
+  for (int i = 0; i < N; ++i)
+    if ((s = coarse_step(ctx, i, Sc, dtc, true, false)) != KD_OK) return s;
   KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
   KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");
   {
@@ -534,27 +641,21 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     // (the last slice is always swept so that sigma is measured)
     const int first = k - 1 < N - 1 ? k - 1 : N - 1;
     KD_CUDA(cudaEventRecord(ctx->ev[1], ctx->st), "event");
-    if ((s = fine_sweep(ctx, first, N, S, dt)) != KD_OK) return s;
+    if ((s = fine_sweep(ctx, first, N, S, dt, k)) != KD_OK) return s;
     KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
-    // serial step; slice `first` has U_first unchanged, so its coarse terms cancel
-    for (int i = first; i < N; ++i) {
-      const bool last = (i == N - 1);
-      const void* gnew;
-      int pg;
-      if (i == first) {
-        gnew = ctx->Gv + 2 * i * lenc;   // G(U_{k-1}) is the stored value, bit for bit
-        pg = KD_C128;
-      } else {
-        if ((s = coarse_solve(ctx, ctx->U + 2 * i * len, ctx->t0c + i, Sc, dtc)) != KD_OK) return s;
-        gnew = ctx->ws_c.X;
-        pg = ctx->p.prec_coarse;
-      }
-      int nb = parareal_update(ctx->Fv + 2 * i * len, gnew, pg, ctx->Gv + 2 * i * lenc, ctx->U + 2 * (i + 1) * len, n,
-                               nc, 0, last ? ctx->partials : nullptr, ctx->st);
+    // serial step; slice `first` has U_first unchanged, so G(U_first) is the stored
+    // coarse value bit for bit and the coarse terms cancel without a coarse solve
+    {
+      const bool last = (first == N - 1);
+      int nb = parareal_update(ctx->Fv + 2 * first * len, ctx->Gv + 2 * first * lenc, KD_C128,
+                               ctx->Gv + 2 * first * lenc, ctx->U + 2 * (first + 1) * len, n, nc, 0,
+                               last ? ctx->partials : nullptr, ctx->st);
       if (nb < 0) return fail(ctx, KD_ECUDA, "parareal update launch failed");
       ctx->launches += 1;
       if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
     }
+    for (int i = first + 1; i < N; ++i)
+      if ((s = coarse_step(ctx, i, Sc, dtc, false, i == N - 1)) != KD_OK) return s;
     KD_CUDA(cudaMemcpyAsync(ctx->host_scal, ctx->scal, 8, cudaMemcpyDeviceToHost, ctx->st), "sigma copy");
     KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
     KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");

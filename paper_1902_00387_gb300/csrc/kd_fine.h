@@ -39,10 +39,10 @@ int compact_to_full(int pin, const void* comp, int pout, void* full, long batch,
 // truncation when n_dst < n_src, zero padding when n_dst > n_src
 int compact_resample(int pin, const void* src, int n_src, int pout, void* dst, int n_dst, long batch,
                      cudaStream_t st);
-// Parareal update of one slice, FP64:
-//   U_next = F + prolong(g - Gold)   (g given in precision pg on the coarse compact grid)
-//   Gold   = g
-// init != 0: initial coarse sweep, U_next = prolong(g), Gold = g (F unused).
+// Parareal update of one slice, FP64 (g given in precision pg on the coarse compact grid):
+//   init = 0: U_next = F + prolong(g - Gold), Gold = g
+//   init = 1: initial coarse sweep, U_next = prolong(g), Gold = g (F unused)
+//   init = 2: increment form, U_next = F + prolong(g) (g = G of the increment; Gold unused)
 // If partials != NULL: also per-block sums of |U_next - U_next_old|^2 and |U_next|^2
 // into partials[2 * blockIdx + {0,1}] (deterministic order), returns the block count.
 int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int n_c,
@@ -54,6 +54,12 @@ int energy_kernel(const double* fields, long len, int count, double* E, cudaStre
 // least-squares slope of 0.5 ln E_i against t_i = i * dt over t_i >= fit_from -> out[0];
 // out[1] = 1 if every used E_i was finite and > 0
 int growth_fit(const double* E, int count, double dt, double fit_from, double* out, cudaStream_t st);
+// increment form: X = U - Uprev (U if first), Uprev = U (X in precision pout);
+// Fv = X (first) or Fv + X.  `total` counts complex entries.
+int delta_in(int pout, const double* U, double* Uprev, void* X, long total, int first, cudaStream_t st);
+int accum_out(int pin, const void* X, double* Fv, long total, int first, cudaStream_t st);
+// d = U - Uprev over `total` complex entries (FP64)
+int diff_kernel(const double* U, const double* Uprev, double* d, long total, cudaStream_t st);
 // dst[i] = t0 + i * dT
 int fill_times(double* dst, int count, double t0, double dT, cudaStream_t st);
 

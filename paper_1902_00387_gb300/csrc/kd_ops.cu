@@ -104,6 +104,53 @@ int compact_resample(int pin, const void* src, int ns, int pout, void* dst, int 
   return rs<float, float>(src, ns, dst, nd, batch, st);
 }
 
+// ------------------------------------------------- increment form of the fine step
+// F is linear in b, so F(U^k) = F(U^{k-1}) + F(U^k - U^{k-1}).  The fine sweep then
+// rounds only the increment to the fine precision and accumulates in FP64.
+template <typename To>
+__global__ void k_delta_in(const cx<double>* U, cx<double>* Uprev, cx<To>* X, long total, int first) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const cx<double> u = U[i];
+    const cx<double> d = first ? u : u - Uprev[i];
+    X[i] = from_d<To>(d);
+    Uprev[i] = u;
+  }
+}
+
+template <typename Ti>
+__global__ void k_accum_out(const cx<Ti>* X, cx<double>* Fv, long total, int first) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const cx<double> x = to_d(X[i]);
+    Fv[i] = first ? x : Fv[i] + x;
+  }
+}
+
+int delta_in(int pout, const double* U, double* Uprev, void* X, long total, int first, cudaStream_t st) {
+  if (pout == 0)
+    k_delta_in<float><<<grid_for(total), 256, 0, st>>>((const cx<double>*)U, (cx<double>*)Uprev, (cx<float>*)X, total, first);
+  else
+    k_delta_in<double><<<grid_for(total), 256, 0, st>>>((const cx<double>*)U, (cx<double>*)Uprev, (cx<double>*)X, total, first);
+  return (int)cudaGetLastError();
+}
+
+int accum_out(int pin, const void* X, double* Fv, long total, int first, cudaStream_t st) {
+  if (pin == 0)
+    k_accum_out<float><<<grid_for(total), 256, 0, st>>>((const cx<float>*)X, (cx<double>*)Fv, total, first);
+  else
+    k_accum_out<double><<<grid_for(total), 256, 0, st>>>((const cx<double>*)X, (cx<double>*)Fv, total, first);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_diff(const double* U, const double* Uprev, double* d, long total) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * total; i += (long)gridDim.x * blockDim.x)
+    d[i] = U[i] - Uprev[i];
+}
+
+int diff_kernel(const double* U, const double* Uprev, double* d, long total, cudaStream_t st) {
+  k_diff<<<grid_for(2 * total), 256, 0, st>>>(U, Uprev, d, total);
+  return (int)cudaGetLastError();
+}
+
 // ------------------------------------------------------------ parareal update
 constexpr int UPD_THREADS = 256;
 
@@ -125,12 +172,14 @@ k_update(const cx<double>* F, const cx<Tg>* g, cx<double>* Gold, cx<double>* U, 
       go = Gold[ic];
     }
     cx<double> u;
-    if (init) {
-      u = gv;
+    if (init == 1) {
+      u = gv;                       // initial coarse sweep
+    } else if (init == 2) {
+      u = F[i] + gv;                // increment form: F(U^k) + G(U^{k+1} - U^k)
     } else {
-      u = F[i] + (gv - go);
+      u = F[i] + (gv - go);         // F(U^k) + (G(U^{k+1}) - G(U^k))
     }
-    if (ic >= 0) Gold[ic] = gv;
+    if (ic >= 0 && init != 2) Gold[ic] = gv;
     if (partials) {
       const cx<double> old = U[i];
       const cx<double> d = u - old;

@@ -20,6 +20,7 @@ STATUS_NAMES = ["KD_OK", "KD_EINVAL", "KD_ENOMEM", "KD_ECUDA", "KD_ENOTCONV", "K
 KD_FLOW_ROBERTS, KD_FLOW_GALLOWAY_PROCTOR, KD_FLOW_NONE = 0, 1, 2
 KD_C64, KD_C128 = 0, 1
 KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
+KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
 KD_MAX_SLICES = 1024
 KD_MAX_ITERS = 256
 
@@ -35,7 +36,7 @@ class kd_params(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int), ("n", ctypes.c_int), ("kz", ctypes.c_double),
                 ("Rm", ctypes.c_double), ("dt_fine", ctypes.c_double), ("prec_fine", ctypes.c_int),
                 ("n_coarse", ctypes.c_int), ("dt_coarse", ctypes.c_double), ("prec_coarse", ctypes.c_int),
-                ("coarse_kind", ctypes.c_int), ("learned_modes", ctypes.c_int)]
+                ("coarse_kind", ctypes.c_int), ("learned_modes", ctypes.c_int), ("fine_form", ctypes.c_int)]
 
 
 class kd_parareal_stats(ctypes.Structure):
@@ -86,11 +87,11 @@ def load():
 
 
 def make_params(flow, n, kz, Rm, dt_fine, prec_fine=KD_C64, n_coarse=None, dt_coarse=None,
-                prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL):
+                prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL, fine_form=KD_FINE_DIRECT):
     return kd_params(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(prec_fine),
                      int(n_coarse if n_coarse else max(16, n // 2)),
                      float(dt_coarse if dt_coarse else dt_fine), int(prec_fine if prec_coarse is None else prec_coarse),
-                     int(coarse_kind), 0)
+                     int(coarse_kind), 0, int(fine_form))
 
 
 def _ptr(x, dtype=None, device=True):

@@ -1,0 +1,52 @@
+"""Small, repeatable fine-propagator launch for profiling one kernel with ncu.
+
+    python -m paper_1902_00387_gb300.profile_case --n 128 --batch 64 --steps 2
+
+builds the library if needed, propagates `batch` seeded Galloway-Proctor fields by
+`steps` fine steps once to warm up and once more (the launches to capture), and
+prints the device time of the second call.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--kz", type=float, default=0.57)
+    ap.add_argument("--Rm", type=float, default=100.0)
+    ap.add_argument("--dt", type=float, default=5e-3)
+    args = ap.parse_args()
+    import torch
+
+    import kd_inputs
+    from paper_1902_00387_gb300 import build as b
+    b.build()
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64)
+    ctx = kd.kd_create(p)
+    x = torch.tensor(kd_inputs.initial_batch(args.n, args.kz, range(args.batch)), dtype=torch.complex64,
+                     device="cuda")
+    t0 = torch.arange(args.batch, dtype=torch.float64, device="cuda") * 0.785
+    kd.kd_fine_batched(ctx, x, x, t0, args.steps, args.batch)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    kd.kd_fine_batched(ctx, x, x, t0, args.steps, args.batch)
+    e1.record()
+    torch.cuda.synchronize()
+    print("n=%d batch=%d steps=%d: %.3f ms" % (args.n, args.batch, args.steps, e0.elapsed_time(e1)))
+    kd.kd_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

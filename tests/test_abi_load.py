@@ -65,13 +65,14 @@ def test_struct_layout_matches_header(lib, tmp_path):
     probe = tmp_path / "probe.c"
     probe.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "kd.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kd_params), offsetof(kd_params, n_coarse),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kd_params), offsetof(kd_params, n_coarse), offsetof(kd_params, fine_form),'
         ' sizeof(kd_parareal_stats), offsetof(kd_parareal_stats, sigma), offsetof(kd_parareal_stats, growth_rate),'
         ' offsetof(kd_parareal_stats, fallback_used), offsetof(kd_parareal_stats, n_launches)); return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [ctypes.sizeof(kd.kd_params), kd.kd_params.n_coarse.offset, ctypes.sizeof(kd.kd_parareal_stats),
+    want = [ctypes.sizeof(kd.kd_params), kd.kd_params.n_coarse.offset, kd.kd_params.fine_form.offset,
+            ctypes.sizeof(kd.kd_parareal_stats),
             kd.kd_parareal_stats.sigma.offset, kd.kd_parareal_stats.growth_rate.offset,
             kd.kd_parareal_stats.fallback_used.offset, kd.kd_parareal_stats.n_launches.offset]
     assert got == want

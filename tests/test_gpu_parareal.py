@@ -113,6 +113,37 @@ def test_parareal_gp_fp32_converges_to_serial_fine(kd):
         assert rel(ser[i + 1], x) < 1e-5, i
 
 
+def test_parareal_increment_form_passes_fp32_floor(kd):
+    # GP flow, complex64 fine and coarse (coarse: same 64^2 grid, step 0.025).  In the
+    # direct form the FP32 round-off of every F and G evaluation keeps the defect near
+    # 1e-6; in the increment form F(U^k) = F(U^{k-1}) + F(U^k - U^{k-1}) and
+    # G(U^{k+1}) - G(U^k) = G(U^{k+1} - U^k) the defect keeps falling.
+    n, kz, Rm, T, N = 64, 0.57, 100.0, 2 * np.pi, 16
+    res = {}
+    for form in (kd.KD_FINE_DIRECT, kd.KD_FINE_INCREMENT):
+        p = kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, 5e-3, kd.KD_C64, n_coarse=64, dt_coarse=0.025,
+                           prec_coarse=kd.KD_C64, fine_form=form)
+        ctx = kd.kd_create(p)
+        try:
+            par = np.zeros((N + 1, 3, n, n), np.complex128)
+            status, st = kd.kd_parareal_run(ctx, I.initial_field(n, kz, 2), T, N, 8, 0.0, par)
+        finally:
+            kd.kd_destroy(ctx)
+        res[form] = (list(st.sigma[:st.k_con]), par)
+    s_dir, _ = res[kd.KD_FINE_DIRECT]
+    s_inc, par = res[kd.KD_FINE_INCREMENT]
+    assert min(s_dir) > 1e-8                  # round-off floor of the direct form
+    assert s_inc[-1] < 1e-9 and s_inc[-1] < 1e-2 * min(s_dir)
+    # the converged iterate is a fine solution to FP32 accuracy: each slice matches the
+    # FP64 oracle propagated from the iterate's previous slice state
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    S = math.ceil(T / N / 5e-3 - 1e-9)
+    dT = T / N
+    for i in (0, 5, N - 1):
+        x = O.propagate(par[i], prob, i * dT, dT / S, S)
+        assert rel(par[i + 1], x) < 1e-5, i
+
+
 def test_energy_and_growth_fit_match_oracle(kd):
     import torch
     n = 32
