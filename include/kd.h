@@ -154,6 +154,38 @@ kd_status kd_energy(kd_ctx* ctx, const double* fields, int count, double* energy
 kd_status kd_growth_rate(kd_ctx* ctx, const double* u_slices, int n_samples, double T,
                          double fit_from, double* rate_out);
 
+/* Size of the device scratch array used by kd_fine_batched_static (32 MiB). */
+#define KD_STATIC_SCRATCH_BYTES 33554432
+
+/* kd_fine_batched_static: the same fine propagator as kd_fine_batched, for callers that
+ * must not allocate device memory -- for example a library embedded in a host
+ * application whose memory pool already owns the GPU's memory, or a latency-critical
+ * loop that cannot afford cudaMalloc's implicit device synchronisation.  It needs no
+ * context: it takes the parameters directly and makes no cudaMalloc, cudaFree or
+ * other allocating call.  (The paper has no counterpart; this is an integration aid.)
+ *
+ *   params      : as for kd_create; only flow, n, kz, Rm, dt_fine and prec_fine are used.
+ *   b_in, b_out : device, [batch][3][n][n] complex in params->prec_fine; may alias.
+ *   t0          : device double[batch], start time of each field.
+ *   cuda_stream : cudaStream_t the work is enqueued on (NULL = legacy default stream).
+ *
+ * The workspace lives in one file-scope device array of KD_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library keeps until the process exits.  A request needs
+ *   256-byte-aligned sums of: 3 n complex-or-real table entries, 4 x batch x 3 x P^2
+ *   and 2 x batch x 3 x P x n complex values (P = 2 (n/3) + 1), plus for the
+ *   Galloway-Proctor flow batch x nsteps x 16 reals of flow phases,
+ * in the bytes of prec_fine; larger requests return KD_EINVAL with a message on
+ * stderr and enqueue nothing.  The first call on a device also looks up the array's
+ * device address (cudaGetSymbolAddress) and sets the kernels' shared-memory limits,
+ * with that device current; make that first call before any stream capture.  All
+ * calls share the one array: calls that can overlap on the GPU (different streams
+ * without ordering, several host threads) race and corrupt each other's results.
+ * Every part of the array a call reads is written earlier in the same call, so the
+ * previous call's contents never leak into a result.  Asynchronous; returns
+ * KD_EINVAL or KD_ECUDA on failure. */
+kd_status kd_fine_batched_static(const kd_params* params, const void* b_in, void* b_out, const double* t0,
+                                 int nsteps, int batch, void* cuda_stream);
+
 /* Number of kernels this context has launched since kd_create (-1 for NULL). */
 long long kd_launch_count(kd_ctx* ctx);
 

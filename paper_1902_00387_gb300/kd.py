@@ -51,7 +51,8 @@ class kd_parareal_stats(ctypes.Structure):
 _lib = None
 EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
-           "kd_version"]
+           "kd_version", "kd_fine_batched_static"]
+KD_STATIC_SCRATCH_BYTES = 33554432
 
 
 def load():
@@ -72,6 +73,7 @@ def load():
         "kd_fine_serial": (I, [P, P, D, I, P]),
         "kd_energy": (I, [P, P, I, P]),
         "kd_growth_rate": (I, [P, P, I, D, D, ctypes.POINTER(D)]),
+        "kd_fine_batched_static": (I, [ctypes.POINTER(kd_params), P, P, P, I, I, P]),
         "kd_launch_count": (ctypes.c_longlong, [P]),
         "kd_profile": (I, [P, I]),
         "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
@@ -166,6 +168,17 @@ def kd_fine_batched(ctx, b_in, b_out, t0, nsteps, batch, prec=KD_C64):
     dt = _cdt(prec)
     return _check(ctx, load().kd_fine_batched(ctx, _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
                                               int(nsteps), int(batch)))
+
+
+def kd_fine_batched_static(params, b_in, b_out, t0, nsteps, batch, stream=None):
+    """Allocation-free fine propagator (workspace in the library's static device array)."""
+    dt = _cdt(params.prec_fine)
+    st = _current_stream() if stream is None else stream
+    s = load().kd_fine_batched_static(ctypes.byref(params), _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
+                                      int(nsteps), int(batch), st)
+    if s != KD_OK:
+        raise KdError(s, "kd_fine_batched_static failed (see stderr)")
+    return s
 
 
 def kd_coarse(ctx, b_in, b_out, t0, nsteps, batch):
