@@ -13,8 +13,12 @@
 // zeros around the kept square, Xs[c][ky + K + 1][kx + K + 1]; the IMEX RK443 state
 // X0 and accumulators R2..R4 of each mode live in the registers of the thread that
 // owns the mode.  Two barriers per stage.
+#include <cooperative_groups.h>
+
 #include "kd_coarse.h"
 #include "kd_stage.cuh"
+
+namespace cgrp = cooperative_groups;
 
 namespace kd {
 
@@ -247,12 +251,285 @@ __global__ void __launch_bounds__(CB) coarse_conv_kernel(CoarseArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster version: the coarse square is split into row stripes over the CS blocks of
+// a thread-block cluster.  Each block keeps its stripe plus one halo row above and
+// below, double-buffered: a stage reads buffer `cur`, writes its new rows into `nxt`
+// locally and its first / last row into the neighbours' halo rows of `nxt` through
+// distributed shared memory, then one cluster barrier makes `nxt` current.
+constexpr int CCB = 256;   // threads per block of the cluster kernel
+
+template <typename T, int MPT>
+__global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int CS, int H) {
+  cgrp::cluster_group cluster = cgrp::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.Kc, P = 2 * a.Kc + 1, L = P + 2, LH = H + 2;
+  const int Kf = a.Kf, Pf = 2 * a.Kf + 1;
+  const int rank = (int)cluster.block_rank();
+  const int b = blockIdx.x / CS;                  // field of this cluster
+  const int y0 = rank * H;                        // first global row of the stripe
+  const int hr = max(0, min(H, P - y0));          // rows owned
+  cx<T>* buf = (cx<T>*)smem_raw;                  // [2][3][LH][L]
+  T* s_ph = (T*)(buf + 2 * 3 * LH * L);           // [nsteps][4][4] when staged
+  const int bufsz = 3 * LH * L;
+  const double* Un = a.Un + (long)b * 2 * 3 * Pf * Pf;
+  for (int i = threadIdx.x; i < 2 * bufsz; i += CCB) buf[i] = mk(T(0), T(0));
+  const bool stage_ph = a.phases && a.nsteps * 16 <= a.phase_smem;
+  const T* ph_g = a.phases ? (const T*)a.phases + (long)b * a.nsteps * 16 : nullptr;
+  if (stage_ph)
+    for (int i = threadIdx.x; i < a.nsteps * 16; i += CCB) s_ph[i] = ph_g[i];
+  __syncthreads();
+
+  const int M = hr * P;
+  cx<T> x0[MPT][3], r2[MPT][3], r3[MPT][3], r4[MPT][3];
+  T lam_dt[MPT], inv_d[MPT], fkx[MPT], fky[MPT];
+  const T kz = (T)a.kz, dt = (T)a.dt;
+#pragma unroll
+  for (int i = 0; i < MPT; ++i) {
+    const int m = threadIdx.x + CCB * i;
+    const int ly = m < M ? m / P : 0, ix = m < M ? m % P : 0;
+    const int iy = y0 + ly;
+    fkx[i] = (T)(ix - K);
+    fky[i] = (T)(iy - K);
+    const T lam = (fkx[i] * fkx[i] + fky[i] * fky[i] + kz * kz) * (T(1) / (T)a.Rm);
+    lam_dt[i] = dt * lam;
+    inv_d[i] = T(1) / (T(1) + dt * T(0.5) * lam);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      cx<T> v = mk(T(0), T(0));
+      if (m < M) {
+        const long src = ((long)c * Pf + (iy + Kf - K)) * Pf + (ix + Kf - K);
+        if (a.Uprev)
+          v = mk((T)(Un[2 * src] - a.Uprev[2 * src]), (T)(Un[2 * src + 1] - a.Uprev[2 * src + 1]));
+        else
+          v = mk((T)Un[2 * src], (T)Un[2 * src + 1]);
+      }
+      x0[i][c] = v;
+    }
+  }
+  // initial stage value into buffer 0: own rows and the neighbours' halos
+  auto put = [&](int bsel, int ly, int ix, int c, cx<T> v) {
+    buf[bsel * bufsz + (c * LH + ly + 1) * L + ix + 1] = v;
+    if (ly == 0 && rank > 0) {
+      cx<T>* peer = cluster.map_shared_rank(buf, rank - 1);
+      peer[bsel * bufsz + (c * LH + H + 1) * L + ix + 1] = v;
+    }
+    if (ly == hr - 1 && rank < CS - 1 && y0 + hr < P) {
+      cx<T>* peer = cluster.map_shared_rank(buf, rank + 1);
+      peer[bsel * bufsz + (c * LH + 0) * L + ix + 1] = v;
+    }
+  };
+  cluster.sync();   // every block has zeroed its buffers before peers write halos
+#pragma unroll
+  for (int i = 0; i < MPT; ++i) {
+    const int m = threadIdx.x + CCB * i;
+    if (m < M)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) put(0, m / P, m % P, c, x0[i][c]);
+  }
+  cluster.sync();
+
+  const T A = (T)a.amp;
+  int cur = 0;
+  for (int s = 0; s < a.nsteps; ++s) {
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      Phase<T> ph;
+      if (ph_g) {
+        const T* p = stage_ph ? s_ph + (s * 4 + j) * 4 : ph_g + (s * 4 + j) * 4;
+        ph.cpx = p[0];
+        ph.spx = p[1];
+        ph.cpy = p[2];
+        ph.spy = p[3];
+      } else {
+        ph.cpx = T(1);
+        ph.spx = T(0);
+        ph.cpy = T(1);
+        ph.spy = T(0);
+      }
+      const UHat<T> u = uhat<T>(A, ph);
+      const cx<T>* Xs = buf + cur * bufsz;
+#pragma unroll
+      for (int i = 0; i < MPT; ++i) {
+        const int m = threadIdx.x + CCB * i;
+        if (m >= M) continue;
+        const int ly = m / P + 1, ix = m % P + 1;
+        cx<T> w[3] = {mk(T(0), T(0)), mk(T(0), T(0)), mk(T(0), T(0))};
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          const int sx = ix - (sgn == 0 ? 1 : -1);
+          const cx<T> bx = Xs[(0 * LH + ly) * L + sx], by = Xs[(1 * LH + ly) * L + sx], bz = Xs[(2 * LH + ly) * L + sx];
+          const cx<T> uy = u.py[sgn], uz = u.pz[sgn];
+          w[0] = w[0] + cmul(uy, bz) - cmul(uz, by);
+          w[1] = w[1] + cmul(uz, bx);
+          w[2] = w[2] - cmul(uy, bx);
+          const int sy = ly - (sgn == 0 ? 1 : -1);
+          const cx<T> cxv = Xs[(0 * LH + sy) * L + ix], cyv = Xs[(1 * LH + sy) * L + ix], czv = Xs[(2 * LH + sy) * L + ix];
+          const cx<T> ux = u.qx[sgn], uz2 = u.qz[sgn];
+          w[0] = w[0] - cmul(uz2, cyv);
+          w[1] = w[1] + cmul(uz2, cxv) - cmul(ux, czv);
+          w[2] = w[2] + cmul(ux, cyv);
+        }
+        cx<T> F[3];
+        F[0] = mul_i(w[2] * fky[i] - w[1] * kz);
+        F[1] = mul_i(w[0] * kz - w[2] * fkx[i]);
+        F[2] = mul_i(w[1] * fkx[i] - w[0] * fky[i]);
+        const T dl = lam_dt[i], id = inv_d[i];
+        cx<T> xn[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const cx<T> f = F[c];
+          if (j == 0) {
+            const cx<T> x1 = (x0[i][c] + f * (dt * T(0.5))) * id;
+            r2[i][c] = x0[i][c] + f * (dt * T(11.0 / 18.0)) - x1 * (dl * T(1.0 / 6.0));
+            r3[i][c] = x0[i][c] + f * (dt * T(5.0 / 6.0)) + x1 * (dl * T(0.5));
+            r4[i][c] = x0[i][c] + f * (dt * T(0.25)) - x1 * (dl * T(1.5));
+            xn[c] = x1;
+          } else if (j == 1) {
+            const cx<T> x2 = (r2[i][c] + f * (dt * T(1.0 / 18.0))) * id;
+            r3[i][c] = r3[i][c] - f * (dt * T(5.0 / 6.0)) - x2 * (dl * T(0.5));
+            r4[i][c] = r4[i][c] + f * (dt * T(1.75)) + x2 * (dl * T(1.5));
+            xn[c] = x2;
+          } else if (j == 2) {
+            const cx<T> x3 = (r3[i][c] + f * (dt * T(0.5))) * id;
+            r4[i][c] = r4[i][c] + f * (dt * T(0.75)) - x3 * (dl * T(0.5));
+            xn[c] = x3;
+          } else {
+            const cx<T> x4 = (r4[i][c] - f * (dt * T(1.75))) * id;
+            x0[i][c] = x4;
+            xn[c] = x4;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) put(cur ^ 1, ly - 1, ix - 1, c, xn[c]);
+      }
+      cluster.sync();   // new stage values (own rows and halos) are complete everywhere
+      cur ^= 1;
+    }
+  }
+
+  // outputs from the final stage value (buffer `cur`), by stripe
+  const cx<T>* Xf = buf + cur * bufsz;
+  if (a.mode == COARSE_OUT) {
+    double* g = a.g64 + (long)b * 2 * 3 * P * P;
+    for (int i = threadIdx.x; i < 3 * M; i += CCB) {
+      const int c = i / M, r = i - c * M;
+      const int ly = r / P, ix = r % P;
+      const cx<T> v = Xf[(c * LH + ly + 1) * L + ix + 1];
+      const long o = ((long)c * P + y0 + ly) * P + ix;
+      g[2 * o] = (double)v.x;
+      g[2 * o + 1] = (double)v.y;
+    }
+    cluster.sync();
+    return;
+  }
+  // fused Parareal update over the fine rows ky in this block's share of [-Kf, Kf]
+  __shared__ double red_d[CCB / 32], red_n[CCB / 32];
+  __shared__ double cl_d[16], cl_n[16];
+  const int fr0 = (Pf * rank) / CS, fr1 = (Pf * (rank + 1)) / CS;   // fine rows of this block
+  const int Mf = (fr1 - fr0) * Pf;
+  double acc_d = 0.0, acc_n = 0.0;
+  for (int i = threadIdx.x; i < 3 * Mf; i += CCB) {
+    const int c = i / Mf, r = i - c * Mf;
+    const int fy = fr0 + r / Pf, fx = r % Pf;
+    const int ky = fy - Kf, kx = fx - Kf;
+    const long fi = ((long)c * Pf + fy) * Pf + fx;
+    double gx = 0.0, gy = 0.0, ox = 0.0, oy = 0.0;
+    long ic = -1;
+    if (ky >= -K && ky <= K && kx >= -K && kx <= K) {
+      ic = ((long)c * P + ky + K) * P + kx + K;
+      // the coarse value of row ky + K lives in the block owning that row
+      const int iy = ky + K, owner = iy / H;
+      const cx<T>* src = owner == rank ? Xf : cluster.map_shared_rank(Xf, owner);
+      const cx<T> v = src[(c * LH + iy - owner * H + 1) * L + kx + K + 1];
+      gx = (double)v.x;
+      gy = (double)v.y;
+      if (a.mode == COARSE_UPDATE) {
+        ox = a.Gold[2 * ic];
+        oy = a.Gold[2 * ic + 1];
+      }
+    }
+    double ux, uy;
+    if (a.mode == COARSE_INIT) {
+      ux = gx;
+      uy = gy;
+    } else {
+      ux = a.Fv[2 * fi] + (gx - ox);
+      uy = a.Fv[2 * fi + 1] + (gy - oy);
+    }
+    if (ic >= 0 && a.mode != COARSE_INCR) {
+      a.Gold[2 * ic] = gx;
+      a.Gold[2 * ic + 1] = gy;
+    }
+    if (a.sigma_out) {
+      const double dx = ux - a.Unext[2 * fi], dy = uy - a.Unext[2 * fi + 1];
+      acc_d += dx * dx + dy * dy;
+      acc_n += ux * ux + uy * uy;
+    }
+    a.Unext[2 * fi] = ux;
+    a.Unext[2 * fi + 1] = uy;
+  }
+  if (a.sigma_out) {
+    for (int o = 16; o > 0; o >>= 1) {
+      acc_d += __shfl_down_sync(0xffffffffu, acc_d, o);
+      acc_n += __shfl_down_sync(0xffffffffu, acc_n, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red_d[threadIdx.x >> 5] = acc_d;
+      red_n[threadIdx.x >> 5] = acc_n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double d = 0.0, n = 0.0;
+      for (int w = 0; w < CCB / 32; ++w) {
+        d += red_d[w];
+        n += red_n[w];
+      }
+      double* pd = cluster.map_shared_rank(cl_d, 0);
+      double* pn = cluster.map_shared_rank(cl_n, 0);
+      pd[rank] = d;
+      pn[rank] = n;
+    }
+  }
+  cluster.sync();   // partial sums delivered; peers' buffers no longer read
+  if (a.sigma_out && rank == 0 && threadIdx.x == 0) {
+    double d = 0.0, n = 0.0;
+    for (int r = 0; r < CS; ++r) {
+      d += cl_d[r];
+      n += cl_n[r];
+    }
+    a.sigma_out[0] = sqrt(d) / sqrt(n);
+    a.sigma_out[1] = d;
+    a.sigma_out[2] = n;
+  }
+}
+
 size_t coarse_conv_smem(int prec, int n_c) {
   const int K = n_c / 3, L = 2 * K + 3;
   return (size_t)3 * L * L * (prec == 0 ? 8 : 16);
 }
 
 bool coarse_conv_supported(int n_c) { return n_c <= 64; }
+
+// cluster split of a P-row coarse square: CS blocks of H rows
+static void cluster_shape(int P, int* CS, int* H) {
+  int cs = (P + 5) / 6;
+  if (cs > 8) cs = 8;
+  if (cs < 1) cs = 1;
+  *H = (P + cs - 1) / cs;
+  *CS = cs;
+}
+
+static size_t cluster_smem(int prec, int n_c, int nsteps, int* phase_slots) {
+  const int K = n_c / 3, P = 2 * K + 1, L = P + 2;
+  int CS, H;
+  cluster_shape(P, &CS, &H);
+  const size_t es = prec == 0 ? 4 : 8;
+  const size_t base = (size_t)2 * 3 * (H + 2) * L * 2 * es;
+  const int slots = nsteps * 16 <= 8192 ? nsteps * 16 : 0;
+  *phase_slots = slots;
+  return base + (size_t)slots * es;
+}
 
 template <typename T, int MPT>
 static cudaError_t prep1() {
@@ -263,11 +540,43 @@ static cudaError_t prep1() {
 cudaError_t coarse_prepare(int prec) {
   cudaError_t e = prec == 0 ? prep1<float, 1>() : prep1<double, 1>();
   if (e != cudaSuccess) return e;
-  return prec == 0 ? prep1<float, 2>() : prep1<double, 2>();
+  e = prec == 0 ? prep1<float, 2>() : prep1<double, 2>();
+  if (e != cudaSuccess) return e;
+  int slots = 0;
+  const int bytes = (int)cluster_smem(prec, 64, 512, &slots);
+  return prec == 0 ? cudaFuncSetAttribute(coarse_cluster_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                   : cudaFuncSetAttribute(coarse_cluster_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T, int MPT>
+static int launch_cluster(const CoarseArgs& a0, int batch, int n_c, cudaStream_t st) {
+  CoarseArgs a = a0;
+  const int P = 2 * (n_c / 3) + 1;
+  int CS, H, slots;
+  cluster_shape(P, &CS, &H);
+  const size_t sm = cluster_smem(sizeof(T) == 4 ? 0 : 1, n_c, a.nsteps, &slots);
+  a.phase_smem = slots;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(CS * batch), 1, 1);
+  cfg.blockDim = dim3(CCB, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, MPT>, a, CS, H) == cudaSuccess ? 1 : -1;
 }
 
 int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, int n_c, cudaStream_t st) {
   if (!coarse_conv_supported(n_c) || batch <= 0) return -1;
+  if (a.nsteps * 16 <= 8192) {
+    // cluster kernel: rows of each block <= 6, so two modes per thread suffice
+    return prec == 0 ? launch_cluster<float, 2>(a, batch, n_c, st) : launch_cluster<double, 2>(a, batch, n_c, st);
+  }
   const size_t sm = coarse_conv_smem(prec, n_c);
   const int P = 2 * (n_c / 3) + 1;
   const bool one = P * P <= CB;

@@ -24,6 +24,7 @@ struct CoarseArgs {
   double* Gold;         // coarse values of the previous sweep (read, then replaced)
   double* Unext;        // U_{n+1}, fine compact FP64 (written)
   double* sigma_out;    // if not NULL: sigma, |U - U_old|^2, |U|^2 of Unext (3 doubles)
+  int phase_smem;       // (internal) phase values the cluster kernel may stage in shared memory
 };
 
 bool coarse_conv_supported(int n_c);

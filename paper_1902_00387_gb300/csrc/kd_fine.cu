@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(RowGeo<T, N>::BLOCK) row_kernel(FineArgs a, in
       const long b = row / P;
       const int iy = (int)(row - b * P);
       cx<T> w0 = *e0 * inv_n2, w1 = *e1 * inv_n2, w2 = *e2 * inv_n2;
-      stage_update<T>(a, mode, ((b * 3) * P + iy) * (long)P + (kx + K), (long)P * P, (T)kx, (T)(iy - K), w0, w1, w2);
+      stage_update<T>(a, stage_arrays<T>(a), mode, ((b * 3) * P + iy) * (long)P + (kx + K), (long)P * P, (T)kx,
+                      (T)(iy - K), w0, w1, w2);
       *e0 = w0;
       *e1 = w1;
       *e2 = w2;

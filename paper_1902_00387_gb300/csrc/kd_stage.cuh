@@ -45,12 +45,32 @@ __device__ __forceinline__ void cross_u(T A, const Phase<T>& p, T cxg, T sxg, T 
   bz = vy * ux - vx * uy;
 }
 
+// Stage arrays with no aliasing between them, so that loads of several points can be
+// issued before the stores of earlier points.
+template <typename T>
+struct StageArrays {
+  cx<T>* __restrict__ X;
+  cx<T>* __restrict__ R2;
+  cx<T>* __restrict__ R3;
+  cx<T>* __restrict__ R4;
+};
+
+template <typename T>
+__device__ __forceinline__ StageArrays<T> stage_arrays(const FineArgs& a) {
+  StageArrays<T> s;
+  s.X = (cx<T>*)a.X;
+  s.R2 = (cx<T>*)a.R2;
+  s.R3 = (cx<T>*)a.R3;
+  s.R4 = (cx<T>*)a.R4;
+  return s;
+}
+
 // One IMEX RK443 stage at spectral point s (index into the compact arrays) for the
 // three components: w_hat (already scaled by 1/n^2) -> F = i k3 x w_hat -> new stage
 // value (returned in w).  mode = stage 0..3.
 template <typename T>
-__device__ __forceinline__ void stage_update(const FineArgs& a, int mode, long s0, long cstride, T fkx, T fky,
-                                             cx<T>& w0, cx<T>& w1, cx<T>& w2) {
+__device__ __forceinline__ void stage_update(const FineArgs& a, const StageArrays<T>& sa, int mode, long s0,
+                                             long cstride, T fkx, T fky, cx<T>& w0, cx<T>& w1, cx<T>& w2) {
   const T dt = (T)a.dt;
   const T kz = (T)a.kz;
   cx<T> F[3];
@@ -60,10 +80,10 @@ __device__ __forceinline__ void stage_update(const FineArgs& a, int mode, long s
   const T lam = (fkx * fkx + fky * fky + kz * kz) * (T(1) / (T)a.Rm);
   const T inv_d = T(1) / (T(1) + dt * T(0.5) * lam);
   const T dl = dt * lam;
-  cx<T>* X = (cx<T>*)a.X;
-  cx<T>* R2 = (cx<T>*)a.R2;
-  cx<T>* R3 = (cx<T>*)a.R3;
-  cx<T>* R4 = (cx<T>*)a.R4;
+  cx<T>* __restrict__ X = sa.X;
+  cx<T>* __restrict__ R2 = sa.R2;
+  cx<T>* __restrict__ R3 = sa.R3;
+  cx<T>* __restrict__ R4 = sa.R4;
   cx<T> out[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
