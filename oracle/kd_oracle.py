@@ -159,10 +159,13 @@ def diffusion_rate(prob):
     return (kx * kx + ky * ky + kz * kz) / prob.Rm
 
 
-def rhs_fft(bh, prob, t):
+def rhs_fft(bh, prob, t, mask=None):
     """Explicit term nabla_k x (u x b) by the pseudo-spectral route (Sec. 4):
-    inverse FFT, pointwise u x b on the grid, forward FFT, dealias, spectral curl."""
-    mask = kept_mask(prob.n)
+    inverse FFT, pointwise u x b on the grid, forward FFT, dealias, spectral curl.
+    `mask` replaces the 2/3 set by another mode set (alias-free while its largest
+    |k| + 1 < n/2, since u has only |q| = 1 modes)."""
+    if mask is None:
+        mask = kept_mask(prob.n)
     b = to_physical(bh * mask)
     w = cross(velocity(prob.flow, prob.n, t), b)
     return curl_k(to_spectral(w) * mask, prob.kz) * mask
@@ -242,13 +245,15 @@ def imex_step(x0, t, dt, explicit, lam, tab=RK443):
     return X[s]
 
 
-def propagate(bh, prob, t0, dt, nsteps, tab=RK443, explicit=None):
+def propagate(bh, prob, t0, dt, nsteps, tab=RK443, explicit=None, mask=None):
     """nsteps IMEX steps of size dt from absolute time t0 (step s starts at t0 + s dt).
-    This is the fine propagator F of Sec. 3 when run on the fine grid with dt = delta t."""
-    if explicit is None:
-        explicit = rhs_fft
+    This is the fine propagator F of Sec. 3 when run on the fine grid with dt = delta t.
+    `mask` (optional) keeps the state on another mode set than the 2/3 square."""
     lam = diffusion_rate(prob)
-    mask = kept_mask(prob.n)
+    if mask is None:
+        mask = kept_mask(prob.n)
+    if explicit is None:
+        explicit = lambda v, p, tt: rhs_fft(v, p, tt, mask)
     x = bh * mask
     for s in range(nsteps):
         x = imex_step(x, t0 + s * dt, dt, lambda v, tt: explicit(v, prob, tt), lam, tab)
@@ -411,3 +416,61 @@ def to_kept_vector(bh):
     iy = np.array([a for a, _ in idx])
     ix = np.array([b for _, b in idx])
     return np.concatenate([bh[c][iy, ix] for c in range(3)])
+
+
+# ----------------------------------------------------------- learned coarse propagator
+# A complex-linear map W on the mode set kx, ky in [-m/2, m/2) x 3 components (a coarse
+# propagator in the sense of Sec. 3.2), fitted to pairs (x, R F P x) of the fine
+# propagator.  Vectors on the set have the layout [3][m][m] (component, ky, kx).
+def learned_mask(n, m):
+    """Mode set kx, ky in [-m/2, m/2) on the FFT-ordered n x n grid."""
+    k = fft_wavenumbers(n)
+    inset = (k >= -(m // 2)) & (k < m - m // 2)
+    return inset[:, None] & inset[None, :]
+
+
+def learned_restrict(bh, m):
+    """Field [..., 3, n, n] -> learned vector [..., 3 m m] (flattened [3][m][m])."""
+    n = bh.shape[-1]
+    k = np.arange(-(m // 2), m - m // 2) % n
+    v = bh[..., k[:, None], k[None, :]]
+    return v.reshape(v.shape[:-3] + (3 * m * m,))
+
+
+def learned_prolong(x, m, n):
+    """Learned vector [..., 3 m m] -> field [..., 3, n, n] (zero outside the set)."""
+    k = np.arange(-(m // 2), m - m // 2) % n
+    out = np.zeros(x.shape[:-1] + (3, n, n), dtype=complex)
+    out[..., k[:, None], k[None, :]] = x.reshape(x.shape[:-1] + (3, m, m))
+    return out
+
+
+def learned_loss_grad(W, X, Y, W0, wd):
+    """Training objective of the learned operator and its gradient:
+        L = (1/m) sum_i |W x_i - y_i|^2 + wd |W - W0|_F^2,
+        dL/dRe W + i dL/dIm W = (2/m) sum_i r_i x_i^H + 2 wd (W - W0),  r_i = W x_i - y_i.
+    X, Y: [m, nc] (rows are pairs); W, W0: [nc, nc] complex."""
+    m = X.shape[0]
+    R = X @ W.T - Y
+    D = W - W0
+    loss = float(np.sum(np.abs(R) ** 2) / m + wd * np.sum(np.abs(D) ** 2))
+    grad = (2.0 / m) * (R.T @ np.conj(X)) + 2.0 * wd * D
+    return loss, grad
+
+
+def learned_ridge(X, Y, W0, wd):
+    """Minimiser of learned_loss_grad's objective (its gradient vanishes):
+        W (X^T conj(X) / m + wd I) = Y^T conj(X) / m + wd W0."""
+    m, nc = X.shape
+    A = X.T @ np.conj(X) / m + wd * np.eye(nc)
+    B = Y.T @ np.conj(X) / m + wd * W0
+    return np.linalg.solve(A.T, B.T).T
+
+
+def learned_exact_map(prob, m, t0, dt, nsteps):
+    """The fine propagator's map on the learned set, R F P, column by column (one fine
+    propagation of every unit vector; tiny sets only)."""
+    nc = 3 * m * m
+    E = np.eye(nc, dtype=complex)
+    out = propagate(learned_prolong(E, m, prob.n), prob, t0, dt, nsteps)
+    return learned_restrict(out, m).T

@@ -384,3 +384,50 @@ def test_table1_gp_growth_rate_floquet():
         b = nb / O.l2(nb)
     assert abs(g[-1] - g[-2]) < 1e-7
     assert _round2(g[-1]) == row["rate"], g
+
+
+# ------------------------------------------------------ learned coarse propagator
+def test_learned_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    nc, m, wd = 4, 6, 0.3
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    W, W0, X, Y = c(nc, nc), c(nc, nc), c(m, nc), c(m, nc)
+    _, G = O.learned_loss_grad(W, X, Y, W0, wd)
+    h = 1e-6
+    for i in range(nc):
+        for j in range(nc):
+            for part, unit in ((0, 1.0), (1, 1j)):
+                Wp, Wm = W.copy(), W.copy()
+                Wp[i, j] += h * unit
+                Wm[i, j] -= h * unit
+                fd = (O.learned_loss_grad(Wp, X, Y, W0, wd)[0] - O.learned_loss_grad(Wm, X, Y, W0, wd)[0]) / (2 * h)
+                g = G[i, j].real if part == 0 else G[i, j].imag
+                assert abs(fd - g) < 1e-6 * max(1.0, abs(g)), (i, j, part, fd, g)
+
+
+def test_learned_ridge_solution_zeroes_gradient_and_recovers_exact_map():
+    rng = np.random.default_rng(4)
+    nc = 5
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    Wstar, W0 = c(nc, nc), c(nc, nc)
+    X = c(3, nc)                      # underdetermined: 3 pairs, 5 unknowns per row
+    Y = X @ Wstar.T
+    Wr = O.learned_ridge(X, Y, W0, 0.1)
+    assert np.abs(O.learned_loss_grad(Wr, X, Y, W0, 0.1)[1]).max() < 1e-12
+    X = c(12, nc)                     # overdetermined, no regularisation: exact recovery
+    Wr = O.learned_ridge(X, X @ Wstar.T, W0, 0.0)
+    assert np.abs(Wr - Wstar).max() < 1e-10
+
+
+def test_learned_exact_map_reproduces_fine_pairs():
+    # R F P is the fine propagator restricted to the set: zero loss on its own pairs
+    prob = O.Problem(O.GALLOWAY_PROCTOR, 16, 0.57, 30.0)
+    m, dt, S, t0 = 4, 0.01, 6, 0.35
+    Wex = O.learned_exact_map(prob, m, t0, dt, S)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((3, 3 * m * m)) + 1j * rng.standard_normal((3, 3 * m * m))
+    Y = O.learned_restrict(O.propagate(O.learned_prolong(X, m, 16), prob, t0, dt, S), m)
+    loss, _ = O.learned_loss_grad(Wex, X, Y, Wex, 0.0)
+    assert loss < 1e-26 * np.sum(np.abs(Y) ** 2)
+    # restriction and prolongation are inverse on the set
+    assert np.abs(O.learned_restrict(O.learned_prolong(X, m, 16), m) - X).max() == 0.0
