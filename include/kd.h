@@ -72,8 +72,12 @@ typedef struct {
   int n_coarse;        /* coarse grid side N_C (power of two, 16 <= N_C <= n) */
   double dt_coarse;    /* coarse step Delta t (upper bound) */
   int prec_coarse;     /* KD_C64 or KD_C128 arithmetic of the classical coarse propagator */
-  int coarse_kind;     /* KD_COARSE_CLASSICAL (only value implemented) */
-  int learned_modes;   /* reserved; 0 */
+  int coarse_kind;     /* KD_COARSE_CLASSICAL or KD_COARSE_LEARNED (needs kd_learned_init and
+                          fine_form KD_FINE_INCREMENT; falls back to the classical propagator) */
+  int learned_modes;   /* m > 0: coarse mode set kx, ky in [-floor(m/2), m - floor(m/2)) (inside
+                          |k| <= n/3, m <= 64; odd m = 2K+1 gives the square |k| <= K), used by
+                          the learned operator AND by the classical coarse propagator ("same
+                          truncation"); 0: the dealiased set of the n_coarse grid */
   int fine_form;       /* KD_FINE_DIRECT or KD_FINE_INCREMENT (kd_parareal_run) */
 } kd_params;
 
@@ -116,7 +120,7 @@ typedef struct {
   double ms_total;                     /* device time of the whole run */
   double ms_fine;                      /* parallel fine sweeps */
   double ms_coarse;                    /* serial coarse sweeps incl. the initial one */
-  int fallback_used;                   /* reserved: 0 */
+  int fallback_used;                   /* learned coarse propagator replaced by the classical one */
   long long n_launches;                /* kernels launched by this call */
 } kd_parareal_stats;
 
@@ -153,6 +157,57 @@ kd_status kd_energy(kd_ctx* ctx, const double* fields, int count, double* energy
  * Synchronous.  KD_ENONFINITE if an energy is 0, NaN or Inf. */
 kd_status kd_growth_rate(kd_ctx* ctx, const double* u_slices, int n_samples, double T,
                          double fit_from, double* rate_out);
+
+/* ------------------------------------------------------------------------------------
+ * Learned coarse propagator (a coarse-solver strategy in the sense of Sec. 3.2).
+ * A complex-linear map W_p on the mode set kx, ky in [-m/2, m/2) x 3 components
+ * (nc = 3 m^2 complex unknowns, m = params.learned_modes), one per flow phase
+ * p = slice index mod n_phase (the Galloway-Proctor flow has period 2 pi; a slice of
+ * length slice_T starts at phase p when it starts at t = p slice_T).  Operators are
+ * stored in BF16 as [Re W; Im W] ([2 nc][nc]) and applied with FP32 accumulation.
+ * Vectors on the set ("learned vectors") are device complex FP32 [3][m][m] (ky-major),
+ * interleaved (re, im).  The fine solution is the judge: pairs (x, F x) come from the
+ * fine propagator, and kd_learned_eval compares W_p and the classical coarse
+ * propagator against them; phases whose operator loses fall back to the classical one.
+ * ------------------------------------------------------------------------------------ */
+
+/* Operators are stored with rows padded to a multiple of 8 columns internally; every
+ * matrix crossing this interface is [2 nc][nc].
+ * W_p := the classical coarse propagator on the learned set over one slice from
+ * t = p slice_T (built by applying it to every unit vector).  Synchronous. */
+kd_status kd_learned_init(kd_ctx* ctx, int n_phase, double slice_T);
+
+/* y_i = R F(P x_i): the fine propagator over one slice from t = phase[i] slice_T applied
+ * to the learned vector x_i prolonged to the fine grid, restricted back to the set.
+ *   x, y : device learned vectors [n]; phase : host int[n] in [0, n_phase).  Synchronous. */
+kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase, float* y);
+
+/* Train every W_p on its pairs: `epochs` Adam steps (beta 0.9 / 0.999, step size lr
+ * with cosine decay to 0 over the epochs) on
+ *   L = (1/m) sum_i |W x_i - y_i|^2 + weight_decay |W - W_classical|^2,
+ * starting from W_classical; forward product and gradient 2/m (W X - Y) X^H are BF16
+ * tensor-core GEMMs with FP32 accumulation, master weights FP32.
+ *   loss_out : host double[n_phase * epochs] data loss per phase and epoch (may be NULL).
+ * Synchronous. */
+kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,
+                           float weight_decay, double* loss_out);
+
+/* Relative L2 errors per phase of the learned operator and of the classical coarse
+ * propagator against held-out pairs (host double[n_phase] each; -1 for phases without
+ * pairs).  Marks a phase's operator unusable when it is worse than the classical one.
+ * Synchronous. */
+kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, double* err_learned,
+                          double* err_classical);
+
+/* Loss and gradient of the training objective for a given stacked FP32 operator W
+ * ([2 nc][nc], device) and regulariser centre W0 (device or NULL = 0), through the same
+ * kernels as kd_learned_train: *loss_out (host), grad_out (device FP32 [2 nc][nc],
+ * [d/dRe W; d/dIm W]).  Needs params.learned_modes > 0 only.  Synchronous. */
+kd_status kd_learned_loss_grad(kd_ctx* ctx, const float* W, const float* W0, float weight_decay, const float* x,
+                               const float* y, int n, double* loss_out, float* grad_out);
+
+/* y_i = W_phase x_i for n learned vectors (device).  Asynchronous. */
+kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int n);
 
 /* Size of the device scratch array used by kd_fine_batched_static (32 MiB). */
 #define KD_STATIC_SCRATCH_BYTES 33554432

@@ -21,6 +21,7 @@
 #include "../../include/kd.h"
 #include "kd_coarse.h"
 #include "kd_fine.h"
+#include "kd_learned.h"
 
 using namespace kd;
 
@@ -76,6 +77,15 @@ struct kd_ctx {
   std::vector<void*> allocs;
   std::string err;
   long long launches = 0;     // kernels launched by this context
+  int cK = 0, cP = 0;         // coarse mode set k in [-cK, cP - cK)^2
+  // learned coarse propagator (kd_learned_*)
+  int l_nphase = 0;
+  double l_sliceT = 0.0;
+  __nv_bfloat16* l_W = nullptr;   // [nphase][2 nc][nc] BF16 stacked operators
+  float* l_W0 = nullptr;          // [nphase][2 nc][nc] FP32 classical-propagator matrices
+  std::vector<int> l_valid;       // phase operator passed validation against the classical one
+  float* l_x = nullptr;           // sweep vectors [2][nc] complex
+  int fallback = 0;
   // optional event timing of the fine column / row kernels
   int prof = 0;
   std::vector<cudaEvent_t> pev;
@@ -320,7 +330,7 @@ kd_status ensure_slices(kd_ctx* ctx, long N) {
   kd_status s;
   if ((s = dalloc(ctx, (void**)&ctx->U, (N + 1) * compact_len(n) * 16, "U")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&ctx->Fv, N * compact_len(n) * 16, "F values")) != KD_OK) return s;
-  if ((s = dalloc(ctx, (void**)&ctx->Gv, N * compact_len(nc) * 16, "G values")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&ctx->Gv, N * 3L * ctx->cP * ctx->cP * 16, "G values")) != KD_OK) return s;
   if (ctx->p.fine_form == KD_FINE_INCREMENT &&
       (s = dalloc(ctx, (void**)&ctx->Uprev, N * compact_len(n) * 16, "previous iterate")) != KD_OK)
     return s;
@@ -346,7 +356,12 @@ kd_status check_params(const kd_params* p, std::string& why) {
   if (!(p->dt_fine > 0) || !(p->dt_coarse > 0)) return why = "time steps must be > 0", KD_EINVAL;
   if ((p->prec_fine != KD_C64 && p->prec_fine != KD_C128) || (p->prec_coarse != KD_C64 && p->prec_coarse != KD_C128))
     return why = "precision must be KD_C64 or KD_C128", KD_EINVAL;
-  if (p->coarse_kind != KD_COARSE_CLASSICAL) return why = "only the classical coarse propagator is built", KD_EUNSUPPORTED;
+  if (p->coarse_kind != KD_COARSE_CLASSICAL && p->coarse_kind != KD_COARSE_LEARNED) return why = "bad coarse_kind", KD_EINVAL;
+  if (p->learned_modes < 0 || p->learned_modes == 1 || p->learned_modes / 2 > p->n / 3 ||
+      p->learned_modes - p->learned_modes / 2 - 1 > p->n / 3 || p->learned_modes > 64)
+    return why = "learned_modes: the set [-m/2, m - m/2) must lie in |k| <= n/3, m <= 64", KD_EINVAL;
+  if (p->coarse_kind == KD_COARSE_LEARNED && (p->learned_modes == 0 || p->fine_form != KD_FINE_INCREMENT))
+    return why = "the learned coarse propagator needs learned_modes > 0 and fine_form KD_FINE_INCREMENT", KD_EINVAL;
   if (p->fine_form != KD_FINE_DIRECT && p->fine_form != KD_FINE_INCREMENT) return why = "bad fine_form", KD_EINVAL;
   return KD_OK;
 }
@@ -372,8 +387,10 @@ kd_status coarse_phases(kd_ctx* ctx, int N, int Sc, double dtc) {
 CoarseArgs coarse_args(const kd_ctx* ctx, int steps, double dtc) {
   CoarseArgs c;
   memset(&c, 0, sizeof(c));
-  c.Kc = ctx->p.n_coarse / 3;
+  c.Kc = ctx->cK;
+  c.Pc = ctx->cP;
   c.Kf = ctx->p.n / 3;
+  c.Pf = 2 * c.Kf + 1;
   c.flow = ctx->p.flow;
   c.amp = ctx->p.flow == KD_FLOW_ROBERTS ? 1.0 : ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? sqrt(1.5) : 0.0;
   c.kz = ctx->p.kz;
@@ -390,9 +407,9 @@ CoarseArgs coarse_args(const kd_ctx* ctx, int steps, double dtc) {
 // (+ sigma of U_{i+1} when `last`).
 kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool last) {
   const int n = ctx->p.n, nc = ctx->p.n_coarse, pc = ctx->p.prec_coarse;
-  const long len = compact_len(n), lenc = compact_len(nc);
+  const long len = compact_len(n), lenc = 3L * ctx->cP * ctx->cP;
   const bool incr = !init && ctx->p.fine_form == KD_FINE_INCREMENT;
-  if (coarse_conv_supported(nc)) {
+  if (coarse_conv_supported(ctx->cP)) {
     CoarseArgs c = coarse_args(ctx, Sc, dtc);
     c.phases = ctx->ph_c ? (const char*)ctx->ph_c + (size_t)i * Sc * 16 * (pc == KD_C64 ? 4 : 8) : nullptr;
     if (ctx->p.flow != KD_FLOW_GALLOWAY_PROCTOR) c.phases = nullptr;
@@ -403,7 +420,7 @@ kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool la
     c.Gold = ctx->Gv + 2 * i * lenc;
     c.Unext = ctx->U + 2 * (i + 1) * len;
     c.sigma_out = last ? ctx->scal : nullptr;
-    KD_LAUNCH(coarse_conv_launch(pc, c, 1, nc, ctx->st), "coarse solve");
+    KD_LAUNCH(coarse_conv_launch(pc, c, 1, ctx->st), "coarse solve");
     return KD_OK;
   }
   // general grids: restrict, multi-kernel RK443 steps, separate update
@@ -420,12 +437,40 @@ kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool la
   if (s != KD_OK) return s;
   KD_LAUNCH(fine_launch_steps(pc, a, Sc, true, false, ctx->st), "coarse steps");
   int nb = parareal_update(init ? nullptr : ctx->Fv + 2 * i * len, ctx->ws_c.X, pc, ctx->Gv + 2 * i * lenc,
-                           ctx->U + 2 * (i + 1) * len, n, nc, init ? 1 : (incr ? 2 : 0),
+                           ctx->U + 2 * (i + 1) * len, n, nc / 3, 2 * (nc / 3) + 1, init ? 1 : (incr ? 2 : 0),
                            last ? ctx->partials : nullptr, ctx->st);
   if (nb < 0) return fail(ctx, KD_ECUDA, "parareal update launch failed");
   ctx->launches += 1;
   if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
   return KD_OK;
+}
+
+// Serial-sweep step of slice i with the learned coarse operator of phase i mod n_phase:
+//   init:      U_{i+1} = P W R U_i
+//   increment: U_{i+1} = Fv_i + P W R (U_i - Uprev_i)
+kd_status learned_step(kd_ctx* ctx, int i, bool init, bool last) {
+  const int n = ctx->p.n, Kf = n / 3, Pf = 2 * Kf + 1;
+  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P;
+  const long len = compact_len(n);
+  const int ph = i % ctx->l_nphase;
+  float* x = ctx->l_x;
+  float* y = ctx->l_x + 2 * nc;
+  KD_LAUNCH(learned_gather(ctx->U + 2 * i * len, init ? nullptr : ctx->Uprev + 2 * i * len, Kf, Pf, x, K, P, 1,
+                           ctx->st),
+            "learned gather");
+  const int ld = (nc + 7) & ~7;
+  KD_LAUNCH(learned_gemv(ctx->l_W + (size_t)ph * 2 * nc * ld, x, y, nc, ld, 1, ctx->st), "learned gemv");
+  int nb = learned_update(init ? nullptr : ctx->Fv + 2 * i * len, y, K, P, ctx->U + 2 * (i + 1) * len, Kf, Pf,
+                          init ? 1 : 0, last ? ctx->partials : nullptr, ctx->st);
+  if (nb < 0) return fail(ctx, KD_ECUDA, "learned update launch failed");
+  ctx->launches += 1;
+  if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
+  return KD_OK;
+}
+
+bool use_learned(const kd_ctx* ctx, int i) {
+  return ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback && ctx->l_nphase > 0 &&
+         ctx->l_valid[i % ctx->l_nphase];
 }
 
 // Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
@@ -495,6 +540,13 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   }
   kd_ctx* ctx = new kd_ctx();
   ctx->p = *params;
+  if (params->learned_modes > 0) {
+    ctx->cK = params->learned_modes / 2;
+    ctx->cP = params->learned_modes;
+  } else {
+    ctx->cK = params->n_coarse / 3;
+    ctx->cP = 2 * ctx->cK + 1;
+  }
   ctx->st = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = fine_prepare(params->prec_fine);
@@ -566,7 +618,7 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
   const size_t fcb = (size_t)batch * compact_len(n) * 16;
   if ((s = ensure_full_tmp(ctx, fcb)) != KD_OK) return s;
   KD_LAUNCH(full_to_compact(KD_C128, b_in, KD_C128, ctx->full_tmp, batch, n, ctx->st), "pack");
-  if (coarse_conv_supported(nc) && nsteps > 0) {
+  if (coarse_conv_supported(ctx->cP) && nsteps > 0) {
     // persistent convolution-form solve, one block per field; result in ws_c.X as FP64
     if ((s = ensure_ws(ctx, ctx->ws_c, nc, KD_C128, batch)) != KD_OK) return s;
     FineArgs pa = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, batch, ctx->p.dt_coarse, t0);
@@ -585,7 +637,7 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
     c.Un = (const double*)ctx->full_tmp;
     c.mode = COARSE_OUT;
     c.g64 = (double*)ctx->ws_c.X;
-    KD_LAUNCH(coarse_conv_launch(pc, c, batch, nc, ctx->st), "coarse solve");
+    KD_LAUNCH(coarse_conv_launch(pc, c, batch, ctx->st), "coarse solve");
     KD_LAUNCH(compact_resample(KD_C128, ctx->ws_c.X, nc, KD_C128, ctx->full_tmp, n, batch, ctx->st), "prolong");
     KD_LAUNCH(compact_to_full(KD_C128, ctx->full_tmp, KD_C128, b_out, batch, n, ctx->st), "unpack");
     return KD_OK;
@@ -615,7 +667,13 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
   if ((s = ensure_slices(ctx, N)) != KD_OK) return s;
   if ((s = ensure_ws(ctx, ctx->ws_f, n, ctx->p.prec_fine, N)) != KD_OK) return s;
   if ((s = ensure_ws(ctx, ctx->ws_c, nc, ctx->p.prec_coarse, 1)) != KD_OK) return s;
-  const long len = compact_len(n), lenc = compact_len(nc);
+  if (ctx->p.coarse_kind == KD_COARSE_LEARNED) {
+    if (ctx->l_nphase == 0) return fail(ctx, KD_EINVAL, "kd_parareal_run: call kd_learned_init first");
+    if (fabs(dT - ctx->l_sliceT) > 1e-9 * dT)
+      return fail(ctx, KD_EINVAL, "kd_parareal_run: slice length differs from the learned operators' slice");
+  }
+  ctx->fallback = 0;
+  const long len = compact_len(n), lenc = 3L * ctx->cP * ctx->cP;
   KD_LAUNCH(fill_times(ctx->t0f, N + 1, 0.0, dT, ctx->st), "times");
   KD_LAUNCH(fill_times(ctx->t0c, N + 1, 0.0, dT, ctx->st), "times");
 
@@ -626,7 +684,9 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
   // iterate 0: serial coarse sweep
   KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
   for (int i = 0; i < N; ++i)
-    if ((s = coarse_step(ctx, i, Sc, dtc, true, false)) != KD_OK) return s;
+    if ((s = use_learned(ctx, i) ? learned_step(ctx, i, true, false) : coarse_step(ctx, i, Sc, dtc, true, false)) !=
+        KD_OK)
+      return s;
   KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
   KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");
   {
@@ -648,14 +708,16 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     {
       const bool last = (first == N - 1);
       int nb = parareal_update(ctx->Fv + 2 * first * len, ctx->Gv + 2 * first * lenc, KD_C128,
-                               ctx->Gv + 2 * first * lenc, ctx->U + 2 * (first + 1) * len, n, nc, 0,
+                               ctx->Gv + 2 * first * lenc, ctx->U + 2 * (first + 1) * len, n, ctx->cK, ctx->cP, 0,
                                last ? ctx->partials : nullptr, ctx->st);
       if (nb < 0) return fail(ctx, KD_ECUDA, "parareal update launch failed");
       ctx->launches += 1;
       if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
     }
     for (int i = first + 1; i < N; ++i)
-      if ((s = coarse_step(ctx, i, Sc, dtc, false, i == N - 1)) != KD_OK) return s;
+      if ((s = use_learned(ctx, i) ? learned_step(ctx, i, false, i == N - 1)
+                                   : coarse_step(ctx, i, Sc, dtc, false, i == N - 1)) != KD_OK)
+        return s;
     KD_CUDA(cudaMemcpyAsync(ctx->host_scal, ctx->scal, 8, cudaMemcpyDeviceToHost, ctx->st), "sigma copy");
     KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
     KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");
@@ -676,6 +738,12 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
       conv = 1;
       break;
     }
+    // fallback to the classical coarse propagator: the defect grew, or half of the
+    // iteration budget is spent (the increment form needs no stored coarse values, so
+    // the switch keeps the iteration consistent)
+    if (ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback &&
+        ((k >= 2 && sigma > sig[k - 2]) || (k_max > 1 && k >= k_max / 2)))
+      ctx->fallback = 1;
   }
   // energies and growth rate of the final iterate
   KD_LAUNCH(energy_kernel(ctx->U, len, N + 1, ctx->Ebuf, ctx->st), "energy");
@@ -702,6 +770,7 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     stats->ms_fine = ms_fine;
     stats->ms_coarse = ms_coarse;
     stats->n_launches = ctx->launches - launches0;
+    stats->fallback_used = ctx->fallback;
   }
   if (!conv && k_max > 0) return fail(ctx, KD_ENOTCONV, "kd_parareal_run: tol not reached within k_max");
   return KD_OK;
@@ -731,6 +800,353 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
   }
   if ((s = copy_out_slices(ctx, u_slices, N)) != KD_OK) return s;
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  return KD_OK;
+}
+
+
+// ----------------------------------------------------------- learned coarse G
+static size_t roundup4(size_t m) { return (m + 3) & ~(size_t)3; }
+
+kd_status kd_learned_init(kd_ctx* ctx, int n_phase, double slice_T) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->p.learned_modes <= 0) return fail(ctx, KD_EINVAL, "kd_learned_init: params.learned_modes is 0");
+  if (n_phase < 1 || n_phase > 64 || !(slice_T > 0)) return fail(ctx, KD_EINVAL, "kd_learned_init: bad arguments");
+  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P, pc = ctx->p.prec_coarse;
+  const int ld = (nc + 7) & ~7;
+  const size_t wcount = (size_t)2 * nc * ld;
+  kd_status s;
+  dfree(ctx, ctx->l_W);
+  dfree(ctx, ctx->l_W0);
+  ctx->l_W = nullptr;
+  ctx->l_W0 = nullptr;
+  ctx->l_nphase = 0;
+  if ((s = dalloc(ctx, (void**)&ctx->l_W, n_phase * wcount * 2, "learned operators")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&ctx->l_W0, n_phase * wcount * 4, "classical operators")) != KD_OK) return s;
+  if (!ctx->l_x && (s = dalloc(ctx, (void**)&ctx->l_x, 4 * (size_t)nc * 4, "learned vectors")) != KD_OK) return s;
+  KD_CUDA(learned_gemv_prepare(ld), "gemv set-up");
+  KD_CUDA(cudaMemsetAsync(ctx->l_W0, 0, n_phase * wcount * 4, ctx->st), "memset");
+  // the classical coarse propagator on the learned set, applied to every unit vector
+  const int Sc = steps_for(slice_T, ctx->p.dt_coarse);
+  const double dtc = slice_T / Sc;
+  const int chunk = nc < 1152 ? nc : 1152;
+  double *d64 = nullptr, *g64 = nullptr, *t0 = nullptr;
+  void* ph = nullptr;
+  if ((s = dalloc(ctx, (void**)&d64, (size_t)chunk * nc * 16, "unit vectors")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&g64, (size_t)chunk * nc * 16, "classical columns")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&t0, (size_t)chunk * 8, "times")) != KD_OK) return s;
+  if ((s = dalloc(ctx, &ph, phase_table_bytes(pc, chunk, Sc), "phases")) != KD_OK) return s;
+  for (int p = 0; p < n_phase; ++p) {
+    KD_LAUNCH(fill_times(t0, chunk, p * slice_T, 0.0, ctx->st), "times");
+    FineArgs fa = fine_args(ctx, ctx->ws_c, ctx->tab_c, ctx->p.n_coarse, chunk, dtc, t0);
+    fa.phases = ph;
+    KD_LAUNCH(launch_phases(pc, fa, Sc, ctx->st), "phases");
+    float* W0 = ctx->l_W0 + (size_t)p * wcount;
+    for (int j0 = 0; j0 < nc; j0 += chunk) {
+      const int cnt = nc - j0 < chunk ? nc - j0 : chunk;
+      KD_LAUNCH(learned_unit_vectors(d64, nc, j0, cnt, ctx->st), "unit vectors");
+      CoarseArgs c = coarse_args(ctx, Sc, dtc);
+      c.Kf = K;
+      c.Pf = P;
+      c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? ph : nullptr;
+      c.Un = d64;
+      c.mode = COARSE_OUT;
+      c.g64 = g64;
+      KD_LAUNCH(coarse_conv_launch(pc, c, cnt, ctx->st), "classical columns");
+      KD_LAUNCH(learned_columns(g64, nc, ld, j0, cnt, W0, ctx->st), "columns");
+    }
+    KD_LAUNCH(f32_to_bf16(W0, ctx->l_W + (size_t)p * wcount, (long)wcount, ctx->st), "bf16");
+  }
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  dfree(ctx, d64);
+  dfree(ctx, g64);
+  dfree(ctx, t0);
+  dfree(ctx, ph);
+  ctx->l_nphase = n_phase;
+  ctx->l_sliceT = slice_T;
+  ctx->l_valid.assign(n_phase, 1);
+  return KD_OK;
+}
+
+kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase, float* y) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0) return fail(ctx, KD_EINVAL, "kd_learned_pairs: call kd_learned_init first");
+  if (!x || !y || !phase || n < 0) return fail(ctx, KD_EINVAL, "kd_learned_pairs: bad arguments");
+  const int nfine = ctx->p.n, Kf = nfine / 3, Pf = 2 * Kf + 1, pf = ctx->p.prec_fine;
+  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P;
+  const int S = steps_for(ctx->l_sliceT, ctx->p.dt_fine);
+  const double dt = ctx->l_sliceT / S;
+  const int chunk = 512;
+  kd_status s;
+  double* t0 = nullptr;
+  if ((s = dalloc(ctx, (void**)&t0, chunk * 8, "times")) != KD_OK) return s;
+  std::vector<double> th(chunk);
+  for (int off = 0; off < n; off += chunk) {
+    const int cnt = n - off < chunk ? n - off : chunk;
+    for (int i = 0; i < cnt; ++i) {
+      if (phase[off + i] < 0 || phase[off + i] >= ctx->l_nphase) return fail(ctx, KD_EINVAL, "bad phase index");
+      th[i] = phase[off + i] * ctx->l_sliceT;
+    }
+    KD_CUDA(cudaMemcpyAsync(t0, th.data(), cnt * 8, cudaMemcpyHostToDevice, ctx->st), "times");
+    if ((s = ensure_ws(ctx, ctx->ws_f, nfine, pf, cnt)) != KD_OK) return s;
+    KD_LAUNCH(learned_to_fine(x + 2L * off * nc, K, P, ctx->ws_f.X, pf, Kf, Pf, cnt, ctx->st), "to fine");
+    FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, nfine, cnt, dt, t0);
+    if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;
+    KD_LAUNCH(fine_launch_steps(pf, a, S, true, false, ctx->st), "fine steps");
+    KD_LAUNCH(fine_to_learned(ctx->ws_f.X, pf, Kf, Pf, y + 2L * off * nc, K, P, cnt, ctx->st), "to learned");
+    KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  }
+  dfree(ctx, t0);
+  return KD_OK;
+}
+
+namespace {
+
+// Device buffers of one training / gradient evaluation with m pairs (padded to mp).
+struct TrainBufs {
+  float *xp = nullptr, *yp = nullptr, *yT = nullptr, *C1 = nullptr, *C2 = nullptr;
+  __nv_bfloat16 *Xs = nullptr, *XtT = nullptr, *A2 = nullptr, *Wbf = nullptr;
+};
+
+kd_status train_bufs(kd_ctx* ctx, TrainBufs& b, int mp, int nc) {
+  kd_status s;
+  const size_t m2 = 2 * (size_t)mp;
+  const size_t ld = (nc + 7) & ~7;
+  if ((s = dalloc(ctx, (void**)&b.xp, m2 * nc * 4, "pairs x")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.yp, m2 * nc * 4, "pairs y")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.yT, m2 * nc * 4, "y transposed")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.C1, 2 * (size_t)nc * m2 * 4, "forward product")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.C2, 2 * (size_t)nc * ld * 4, "gradient product")) != KD_OK) return s;
+  KD_CUDA(cudaMemsetAsync(b.C2, 0, 2 * (size_t)nc * ld * 4, ctx->st), "memset");   // padding columns stay 0
+  if ((s = dalloc(ctx, (void**)&b.Xs, m2 * ld * 2, "x operand")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.XtT, m2 * nc * 2, "x^T operand")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.A2, 2 * (size_t)nc * m2 * 2, "residual operand")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.Wbf, 2 * (size_t)nc * ld * 2, "bf16 weights")) != KD_OK) return s;
+  return KD_OK;
+}
+
+void free_train_bufs(kd_ctx* ctx, TrainBufs& b) {
+  void* all[] = {b.xp, b.yp, b.yT, b.C1, b.C2, b.Xs, b.XtT, b.A2, b.Wbf};
+  for (void* p : all) dfree(ctx, p);
+  b = TrainBufs();
+}
+
+// gather the pairs `idx` into contiguous zero-padded buffers and build the operands
+kd_status load_pairs(kd_ctx* ctx, TrainBufs& b, const float* x, const float* y, const std::vector<int>& idx, int mp,
+                     int nc) {
+  const size_t vb = 2 * (size_t)nc * 4;
+  KD_CUDA(cudaMemsetAsync(b.xp, 0, mp * vb, ctx->st), "memset");
+  KD_CUDA(cudaMemsetAsync(b.yp, 0, mp * vb, ctx->st), "memset");
+  for (size_t t = 0; t < idx.size(); ++t) {
+    KD_CUDA(cudaMemcpyAsync((char*)b.xp + t * vb, (const char*)x + (size_t)idx[t] * vb, vb, cudaMemcpyDeviceToDevice,
+                            ctx->st),
+            "gather x");
+    KD_CUDA(cudaMemcpyAsync((char*)b.yp + t * vb, (const char*)y + (size_t)idx[t] * vb, vb, cudaMemcpyDeviceToDevice,
+                            ctx->st),
+            "gather y");
+  }
+  KD_LAUNCH(learned_pack_x(b.xp, mp, nc, (nc + 7) & ~7, b.Xs, b.XtT, ctx->st), "pack x");
+  KD_LAUNCH(learned_transpose_y(b.yp, mp, nc, b.yT, ctx->st), "transpose y");
+  return KD_OK;
+}
+
+// forward GEMM, residual (loss sum -> out[0]) and gradient GEMM (-> b.C2) for W in b.Wbf
+kd_status forward_backward(kd_ctx* ctx, TrainBufs& b, int mp, int nc, double* loss_dev) {
+  const int ld = (nc + 7) & ~7;
+  KD_LAUNCH(gemm_bf16_tn(b.Wbf, b.Xs, b.C1, 2 * nc, 2 * mp, ld, 2 * mp, ctx->st), "forward gemm");
+  const int nb = learned_residual(b.C1, b.yT, mp, nc, b.A2, ctx->partials, ctx->st);
+  if (nb < 0) return fail(ctx, KD_ECUDA, "residual launch failed");
+  ctx->launches += 1;
+  KD_LAUNCH(sum_partials(ctx->partials, nb, loss_dev, ctx->st), "loss");
+  KD_LAUNCH(gemm_bf16_tn(b.A2, b.XtT, b.C2, 2 * nc, nc, 2 * mp, ld, ctx->st), "gradient gemm");
+  return KD_OK;
+}
+
+}  // namespace
+
+kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,
+                           float weight_decay, double* loss_out) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0) return fail(ctx, KD_EINVAL, "kd_learned_train: call kd_learned_init first");
+  if (!x || !y || !phase || n <= 0 || epochs < 0 || !(lr >= 0)) return fail(ctx, KD_EINVAL, "kd_learned_train: bad arguments");
+  const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
+  const size_t wcount = (size_t)2 * nc * ld;
+  std::vector<std::vector<int>> byp(ctx->l_nphase);
+  for (int i = 0; i < n; ++i) {
+    if (phase[i] < 0 || phase[i] >= ctx->l_nphase) return fail(ctx, KD_EINVAL, "kd_learned_train: bad phase index");
+    byp[phase[i]].push_back(i);
+  }
+  size_t mmax = 0;
+  for (auto& v : byp) mmax = v.size() > mmax ? v.size() : mmax;
+  const int mp = (int)roundup4(mmax);
+  kd_status s;
+  TrainBufs b;
+  float *Wm = nullptr, *m1 = nullptr, *v = nullptr;
+  double* lossd = nullptr;
+  if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&Wm, wcount * 4, "master weights")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&m1, wcount * 4, "adam m")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&v, wcount * 4, "adam v")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&lossd, (size_t)ctx->l_nphase * (epochs > 0 ? epochs : 1) * 16, "losses")) != KD_OK)
+    return s;
+  for (int p = 0; p < ctx->l_nphase; ++p) {
+    if (byp[p].empty()) continue;
+    if ((s = load_pairs(ctx, b, x, y, byp[p], mp, nc)) != KD_OK) return s;
+    const float* W0 = ctx->l_W0 + (size_t)p * wcount;
+    KD_CUDA(cudaMemcpyAsync(Wm, W0, wcount * 4, cudaMemcpyDeviceToDevice, ctx->st), "init");
+    KD_CUDA(cudaMemsetAsync(m1, 0, wcount * 4, ctx->st), "memset");
+    KD_CUDA(cudaMemsetAsync(v, 0, wcount * 4, ctx->st), "memset");
+    KD_LAUNCH(f32_to_bf16(Wm, b.Wbf, (long)wcount, ctx->st), "bf16");
+    const float scale = 2.f / (float)byp[p].size();
+    for (int e = 0; e < epochs; ++e) {
+      if ((s = forward_backward(ctx, b, mp, nc, lossd + 2 * ((size_t)p * epochs + e))) != KD_OK) return s;
+      // cosine decay of the step size to zero over the epochs
+      const float lr_e = (float)(0.5 * lr * (1.0 + cos(M_PI * e / (double)epochs)));
+      const int nb = learned_adam(Wm, W0, b.C2, m1, v, b.Wbf, (long)wcount, scale, weight_decay, lr_e, 0.9f,
+                                  0.999f, 1e-8f, e + 1, nullptr, ctx->st);
+      if (nb < 0) return fail(ctx, KD_ECUDA, "adam launch failed");
+      ctx->launches += 1;
+    }
+    KD_CUDA(cudaMemcpyAsync(ctx->l_W + (size_t)p * wcount, b.Wbf, wcount * 2, cudaMemcpyDeviceToDevice, ctx->st),
+            "store");
+  }
+  if (loss_out && epochs > 0) {
+    std::vector<double> h((size_t)ctx->l_nphase * epochs * 2);
+    KD_CUDA(cudaMemcpyAsync(h.data(), lossd, h.size() * 8, cudaMemcpyDeviceToHost, ctx->st), "losses");
+    KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+    for (int p = 0; p < ctx->l_nphase; ++p)
+      for (int e = 0; e < epochs; ++e)
+        loss_out[(size_t)p * epochs + e] = byp[p].empty() ? 0.0 : h[2 * ((size_t)p * epochs + e)] / byp[p].size();
+  }
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  free_train_bufs(ctx, b);
+  dfree(ctx, Wm);
+  dfree(ctx, m1);
+  dfree(ctx, v);
+  dfree(ctx, lossd);
+  return KD_OK;
+}
+
+kd_status kd_learned_loss_grad(kd_ctx* ctx, const float* W, const float* W0, float weight_decay, const float* x,
+                               const float* y, int n, double* loss_out, float* grad_out) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->p.learned_modes <= 0 || !W || !x || !y || n <= 0 || !loss_out || !grad_out)
+    return fail(ctx, KD_EINVAL, "kd_learned_loss_grad: bad arguments");
+  const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
+  const size_t wcount = (size_t)2 * nc * ld;
+  const int mp = (int)roundup4(n);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  kd_status s;
+  TrainBufs b;
+  float *Wp = nullptr, *W0p = nullptr, *gp = nullptr;
+  if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
+  // the caller's [2 nc][nc] matrices in the padded [2 nc][ld] layout
+  if ((s = dalloc(ctx, (void**)&Wp, wcount * 4, "weights")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&W0p, wcount * 4, "centre")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&gp, wcount * 4, "gradient")) != KD_OK) return s;
+  KD_CUDA(cudaMemsetAsync(Wp, 0, wcount * 4, ctx->st), "memset");
+  KD_CUDA(cudaMemsetAsync(W0p, 0, wcount * 4, ctx->st), "memset");
+  KD_CUDA(cudaMemcpy2DAsync(Wp, ld * 4, W, nc * 4, nc * 4, 2 * nc, cudaMemcpyDeviceToDevice, ctx->st), "repack");
+  if (W0)
+    KD_CUDA(cudaMemcpy2DAsync(W0p, ld * 4, W0, nc * 4, nc * 4, 2 * nc, cudaMemcpyDeviceToDevice, ctx->st), "repack");
+  if ((s = load_pairs(ctx, b, x, y, idx, mp, nc)) != KD_OK) return s;
+  KD_LAUNCH(f32_to_bf16(Wp, b.Wbf, (long)wcount, ctx->st), "bf16");
+  if ((s = forward_backward(ctx, b, mp, nc, ctx->scal + 8)) != KD_OK) return s;
+  KD_LAUNCH(learned_grad(Wp, W0p, b.C2, gp, (long)wcount, 2.f / n, weight_decay, ctx->st), "gradient");
+  KD_CUDA(cudaMemcpy2DAsync(grad_out, nc * 4, gp, ld * 4, nc * 4, 2 * nc, cudaMemcpyDeviceToDevice, ctx->st), "unpack");
+  const int nb = diff_norms(Wp, W0p, (long)wcount, ctx->partials, ctx->st);
+  if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");
+  KD_LAUNCH(sum_partials(ctx->partials, nb, ctx->scal + 10, ctx->st), "norm");
+  double h[4];
+  KD_CUDA(cudaMemcpyAsync(h, ctx->scal + 8, 32, cudaMemcpyDeviceToHost, ctx->st), "loss");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  *loss_out = h[0] / n + weight_decay * h[2];
+  free_train_bufs(ctx, b);
+  dfree(ctx, Wp);
+  dfree(ctx, W0p);
+  dfree(ctx, gp);
+  return KD_OK;
+}
+
+kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int n) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0 || phase < 0 || phase >= ctx->l_nphase || !x || !y || n < 0)
+    return fail(ctx, KD_EINVAL, "kd_learned_apply: bad arguments");
+  if (n == 0) return KD_OK;
+  const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
+  KD_LAUNCH(learned_gemv(ctx->l_W + (size_t)phase * 2 * nc * ld, x, y, nc, ld, n, ctx->st), "learned gemv");
+  return KD_OK;
+}
+
+kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, double* err_learned,
+                          double* err_classical) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0 || !x || !y || !phase || n <= 0 || !err_learned || !err_classical)
+    return fail(ctx, KD_EINVAL, "kd_learned_eval: bad arguments");
+  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P, pc = ctx->p.prec_coarse;
+  const int Sc = steps_for(ctx->l_sliceT, ctx->p.dt_coarse);
+  const double dtc = ctx->l_sliceT / Sc;
+  std::vector<std::vector<int>> byp(ctx->l_nphase);
+  for (int i = 0; i < n; ++i) {
+    if (phase[i] < 0 || phase[i] >= ctx->l_nphase) return fail(ctx, KD_EINVAL, "kd_learned_eval: bad phase index");
+    byp[phase[i]].push_back(i);
+  }
+  size_t mmax = 0;
+  for (auto& v : byp) mmax = v.size() > mmax ? v.size() : mmax;
+  const int mp = (int)roundup4(mmax);
+  kd_status s;
+  TrainBufs b;
+  double *d64 = nullptr, *g64 = nullptr, *t0 = nullptr;
+  float* pred = nullptr;
+  void* ph = nullptr;
+  if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&d64, (size_t)mp * nc * 16, "inputs")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&g64, (size_t)mp * nc * 16, "outputs")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&pred, (size_t)mp * nc * 8, "prediction")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&t0, (size_t)mp * 8, "times")) != KD_OK) return s;
+  if ((s = dalloc(ctx, &ph, phase_table_bytes(pc, mp, Sc), "phases")) != KD_OK) return s;
+  for (int p = 0; p < ctx->l_nphase; ++p) {
+    err_learned[p] = err_classical[p] = -1.0;
+    const int m = (int)byp[p].size();
+    if (m == 0) continue;
+    if ((s = load_pairs(ctx, b, x, y, byp[p], mp, nc)) != KD_OK) return s;
+    // learned
+    const int ld = (nc + 7) & ~7;
+    KD_LAUNCH(learned_gemv(ctx->l_W + (size_t)p * 2 * nc * ld, b.xp, pred, nc, ld, m, ctx->st), "gemv");
+    int nb = diff_norms(pred, b.yp, 2L * m * nc, ctx->partials, ctx->st);
+    if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");
+    KD_LAUNCH(sum_partials(ctx->partials, nb, ctx->scal + 8, ctx->st), "norm");
+    // classical coarse propagator on the same set
+    KD_LAUNCH(learned_f32_to_f64(b.xp, d64, (long)m * nc, ctx->st), "to f64");
+    KD_LAUNCH(fill_times(t0, m, p * ctx->l_sliceT, 0.0, ctx->st), "times");
+    FineArgs fa = fine_args(ctx, ctx->ws_c, ctx->tab_c, ctx->p.n_coarse, m, dtc, t0);
+    fa.phases = ph;
+    KD_LAUNCH(launch_phases(pc, fa, Sc, ctx->st), "phases");
+    CoarseArgs c = coarse_args(ctx, Sc, dtc);
+    c.Kf = K;
+    c.Pf = P;
+    c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? ph : nullptr;
+    c.Un = d64;
+    c.mode = COARSE_OUT;
+    c.g64 = g64;
+    KD_LAUNCH(coarse_conv_launch(pc, c, m, ctx->st), "classical");
+    KD_LAUNCH(learned_f64_to_f32(g64, pred, (long)m * nc, ctx->st), "to f32");
+    nb = diff_norms(pred, b.yp, 2L * m * nc, ctx->partials, ctx->st);
+    if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");
+    KD_LAUNCH(sum_partials(ctx->partials, nb, ctx->scal + 10, ctx->st), "norm");
+    double h[4];
+    KD_CUDA(cudaMemcpyAsync(h, ctx->scal + 8, 32, cudaMemcpyDeviceToHost, ctx->st), "errors");
+    KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+    err_learned[p] = sqrt(h[0] / h[1]);
+    err_classical[p] = sqrt(h[2] / h[3]);
+    ctx->l_valid[p] = err_learned[p] <= err_classical[p] ? 1 : 0;
+  }
+  free_train_bufs(ctx, b);
+  dfree(ctx, d64);
+  dfree(ctx, g64);
+  dfree(ctx, pred);
+  dfree(ctx, t0);
+  dfree(ctx, ph);
   return KD_OK;
 }
 

@@ -1,5 +1,6 @@
 // Classical coarse propagator G (Sec. 3.2, Sec. 5.2: the same equations on the coarse
-// N_C grid with the coarse step) as one persistent block per field for N_C <= 64,
+// N_C grid with the coarse step) as one persistent thread-block cluster per field for
+// coarse sets of side <= 64,
 // fused with the Fourier restriction of the fine input and, in the Parareal sweep,
 // with the FP64 update U_{n+1} = F + (G_new - G_old) and the defect of Eq. 9.
 //
@@ -9,10 +10,9 @@
 // four Fourier modes and n/3 + 1 < n/2, so the pseudo-spectral product of the fine
 // kernels has no aliasing and this is the same discrete operator (equal to round-off).
 //
-// Layout: the current stage value lives in shared memory with a one-mode ring of
-// zeros around the kept square, Xs[c][ky + K + 1][kx + K + 1]; the IMEX RK443 state
-// X0 and accumulators R2..R4 of each mode live in the registers of the thread that
-// owns the mode.  Two barriers per stage.
+// Layout: the stage values live in shared memory with a one-mode ring of zeros around
+// the kept square; the IMEX RK443 state X0 and accumulators R2..R4 of each mode live in
+// the registers of the thread that owns the mode.
 #include <cooperative_groups.h>
 
 #include "kd_coarse.h"
@@ -21,8 +21,6 @@
 namespace cgrp = cooperative_groups;
 
 namespace kd {
-
-constexpr int CB = 1024;   // threads per block; MPT modes per thread: (2 * 21 + 1)^2 = 1849 <= 2 * 1024
 
 template <typename T>
 struct UHat {
@@ -50,207 +48,6 @@ __device__ __forceinline__ UHat<T> uhat(T A, const Phase<T>& p) {
   return u;
 }
 
-template <typename T, int MPT>
-__global__ void __launch_bounds__(CB) coarse_conv_kernel(CoarseArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = a.Kc, P = 2 * a.Kc + 1, L = P + 2;
-  const int Kf = a.Kf, Pf = 2 * a.Kf + 1;
-  cx<T>* Xs = (cx<T>*)smem_raw;   // [3][L][L]
-  const int b = blockIdx.x;
-  const double* Un = a.Un + (long)b * 2 * 3 * Pf * Pf;
-  for (int i = threadIdx.x; i < 3 * L * L; i += CB) Xs[i] = mk(T(0), T(0));
-  __syncthreads();
-
-  const int M = P * P;
-  cx<T> x0[MPT][3], r2[MPT][3], r3[MPT][3], r4[MPT][3];
-  T lam_dt[MPT], inv_d[MPT], fkx[MPT], fky[MPT];
-  const T kz = (T)a.kz, dt = (T)a.dt;
-#pragma unroll
-  for (int i = 0; i < MPT; ++i) {
-    const int m = threadIdx.x + CB * i;
-    const int iy = m < M ? m / P : 0, ix = m < M ? m % P : 0;
-    fkx[i] = (T)(ix - K);
-    fky[i] = (T)(iy - K);
-    const T lam = (fkx[i] * fkx[i] + fky[i] * fky[i] + kz * kz) * (T(1) / (T)a.Rm);
-    lam_dt[i] = dt * lam;
-    inv_d[i] = T(1) / (T(1) + dt * T(0.5) * lam);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      cx<T> v = mk(T(0), T(0));
-      if (m < M) {
-        const long src = ((long)c * Pf + (iy + Kf - K)) * Pf + (ix + Kf - K);
-        if (a.Uprev)
-          v = mk((T)(Un[2 * src] - a.Uprev[2 * src]), (T)(Un[2 * src + 1] - a.Uprev[2 * src + 1]));
-        else
-          v = mk((T)Un[2 * src], (T)Un[2 * src + 1]);
-        Xs[(c * L + iy + 1) * L + ix + 1] = v;
-      }
-      x0[i][c] = v;
-    }
-  }
-  __syncthreads();
-
-  const T A = (T)a.amp;
-  const T* ph_base = a.phases ? (const T*)a.phases + (long)b * a.nsteps * 16 : nullptr;
-  for (int s = 0; s < a.nsteps; ++s) {
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      Phase<T> ph;
-      if (ph_base) {
-        const T* p = ph_base + (s * 4 + j) * 4;
-        ph.cpx = p[0];
-        ph.spx = p[1];
-        ph.cpy = p[2];
-        ph.spy = p[3];
-      } else {
-        ph.cpx = T(1);
-        ph.spx = T(0);
-        ph.cpy = T(1);
-        ph.spy = T(0);
-      }
-      const UHat<T> u = uhat<T>(A, ph);
-      cx<T> xn[MPT][3];
-#pragma unroll
-      for (int i = 0; i < MPT; ++i) {
-        const int m = threadIdx.x + CB * i;
-        if (m >= M) continue;
-        const int iy = m / P + 1, ix = m % P + 1;
-        // w_hat(k) = sum_q u_hat(q) x b_hat(k - q)
-        cx<T> w[3] = {mk(T(0), T(0)), mk(T(0), T(0)), mk(T(0), T(0))};
-#pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-          // q = (+-1, 0): b_hat(kx -+ 1, ky); u_hat = (0, py, pz)
-          const int sx = ix - (sgn == 0 ? 1 : -1);
-          const cx<T> bx = Xs[(0 * L + iy) * L + sx], by = Xs[(1 * L + iy) * L + sx], bz = Xs[(2 * L + iy) * L + sx];
-          const cx<T> uy = u.py[sgn], uz = u.pz[sgn];
-          w[0] = w[0] + cmul(uy, bz) - cmul(uz, by);
-          w[1] = w[1] + cmul(uz, bx);
-          w[2] = w[2] - cmul(uy, bx);
-          // q = (0, +-1): b_hat(kx, ky -+ 1); u_hat = (qx, 0, qz)
-          const int sy = iy - (sgn == 0 ? 1 : -1);
-          const cx<T> cxv = Xs[(0 * L + sy) * L + ix], cyv = Xs[(1 * L + sy) * L + ix], czv = Xs[(2 * L + sy) * L + ix];
-          const cx<T> ux = u.qx[sgn], uz2 = u.qz[sgn];
-          w[0] = w[0] - cmul(uz2, cyv);
-          w[1] = w[1] + cmul(uz2, cxv) - cmul(ux, czv);
-          w[2] = w[2] + cmul(ux, cyv);
-        }
-        // F = i k3 x w_hat
-        cx<T> F[3];
-        F[0] = mul_i(w[2] * fky[i] - w[1] * kz);
-        F[1] = mul_i(w[0] * kz - w[2] * fkx[i]);
-        F[2] = mul_i(w[1] * fkx[i] - w[0] * fky[i]);
-        const T dl = lam_dt[i], id = inv_d[i];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const cx<T> f = F[c];
-          if (j == 0) {
-            const cx<T> x1 = (x0[i][c] + f * (dt * T(0.5))) * id;
-            r2[i][c] = x0[i][c] + f * (dt * T(11.0 / 18.0)) - x1 * (dl * T(1.0 / 6.0));
-            r3[i][c] = x0[i][c] + f * (dt * T(5.0 / 6.0)) + x1 * (dl * T(0.5));
-            r4[i][c] = x0[i][c] + f * (dt * T(0.25)) - x1 * (dl * T(1.5));
-            xn[i][c] = x1;
-          } else if (j == 1) {
-            const cx<T> x2 = (r2[i][c] + f * (dt * T(1.0 / 18.0))) * id;
-            r3[i][c] = r3[i][c] - f * (dt * T(5.0 / 6.0)) - x2 * (dl * T(0.5));
-            r4[i][c] = r4[i][c] + f * (dt * T(1.75)) + x2 * (dl * T(1.5));
-            xn[i][c] = x2;
-          } else if (j == 2) {
-            const cx<T> x3 = (r3[i][c] + f * (dt * T(0.5))) * id;
-            r4[i][c] = r4[i][c] + f * (dt * T(0.75)) - x3 * (dl * T(0.5));
-            xn[i][c] = x3;
-          } else {
-            const cx<T> x4 = (r4[i][c] - f * (dt * T(1.75))) * id;
-            x0[i][c] = x4;
-            xn[i][c] = x4;
-          }
-        }
-      }
-      __syncthreads();   // every read of the old stage value is done
-#pragma unroll
-      for (int i = 0; i < MPT; ++i) {
-        const int m = threadIdx.x + CB * i;
-        if (m >= M) continue;
-        const int iy = m / P + 1, ix = m % P + 1;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Xs[(c * L + iy) * L + ix] = xn[i][c];
-      }
-      __syncthreads();
-    }
-  }
-
-  // result g = X (coarse compact, FP64) and the fused Parareal update
-  if (a.mode == COARSE_OUT) {
-    double* g = a.g64 + (long)b * 2 * 3 * M;
-    for (int i = threadIdx.x; i < 3 * M; i += CB) {
-      const int c = i / M, r = i - c * M;
-      const cx<T> v = Xs[(c * L + r / P + 1) * L + r % P + 1];
-      g[2 * i] = (double)v.x;
-      g[2 * i + 1] = (double)v.y;
-    }
-    return;
-  }
-  __shared__ double red_d[CB / 32], red_n[CB / 32];
-  double acc_d = 0.0, acc_n = 0.0;
-  const int Mf = Pf * Pf;
-  for (int i = threadIdx.x; i < 3 * Mf; i += CB) {
-    const int c = i / Mf, r = i - c * Mf;
-    const int ky = r / Pf - Kf, kx = r % Pf - Kf;
-    double gx = 0.0, gy = 0.0, ox = 0.0, oy = 0.0;
-    long ic = -1;
-    if (ky >= -K && ky <= K && kx >= -K && kx <= K) {
-      ic = ((long)c * P + ky + K) * P + kx + K;
-      const cx<T> v = Xs[(c * L + ky + K + 1) * L + kx + K + 1];
-      gx = (double)v.x;
-      gy = (double)v.y;
-      if (a.mode == COARSE_UPDATE) {
-        ox = a.Gold[2 * ic];
-        oy = a.Gold[2 * ic + 1];
-      }
-    }
-    double ux, uy;
-    if (a.mode == COARSE_INIT) {
-      ux = gx;
-      uy = gy;
-    } else {
-      ux = a.Fv[2 * i] + (gx - ox);
-      uy = a.Fv[2 * i + 1] + (gy - oy);
-    }
-    if (ic >= 0 && a.mode != COARSE_INCR) {
-      a.Gold[2 * ic] = gx;
-      a.Gold[2 * ic + 1] = gy;
-    }
-    if (a.sigma_out) {
-      const double dx = ux - a.Unext[2 * i], dy = uy - a.Unext[2 * i + 1];
-      acc_d += dx * dx + dy * dy;
-      acc_n += ux * ux + uy * uy;
-    }
-    a.Unext[2 * i] = ux;
-    a.Unext[2 * i + 1] = uy;
-  }
-  if (a.sigma_out) {
-    // fixed-order reduction: warp shuffles, then the warp sums in order
-    for (int o = 16; o > 0; o >>= 1) {
-      acc_d += __shfl_down_sync(0xffffffffu, acc_d, o);
-      acc_n += __shfl_down_sync(0xffffffffu, acc_n, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red_d[threadIdx.x >> 5] = acc_d;
-      red_n[threadIdx.x >> 5] = acc_n;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double d = 0.0, n = 0.0;
-      for (int w = 0; w < CB / 32; ++w) {
-        d += red_d[w];
-        n += red_n[w];
-      }
-      a.sigma_out[0] = sqrt(d) / sqrt(n);
-      a.sigma_out[1] = d;
-      a.sigma_out[2] = n;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Cluster version: the coarse square is split into row stripes over the CS blocks of
 // a thread-block cluster.  Each block keeps its stripe plus one halo row above and
@@ -263,8 +60,8 @@ template <typename T, int MPT>
 __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int CS, int H) {
   cgrp::cluster_group cluster = cgrp::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = a.Kc, P = 2 * a.Kc + 1, L = P + 2, LH = H + 2;
-  const int Kf = a.Kf, Pf = 2 * a.Kf + 1;
+  const int K = a.Kc, P = a.Pc, L = P + 2, LH = H + 2;
+  const int Kf = a.Kf, Pf = a.Pf;
   const int rank = (int)cluster.block_rank();
   const int b = blockIdx.x / CS;                  // field of this cluster
   const int y0 = rank * H;                        // first global row of the stripe
@@ -436,7 +233,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
     const long fi = ((long)c * Pf + fy) * Pf + fx;
     double gx = 0.0, gy = 0.0, ox = 0.0, oy = 0.0;
     long ic = -1;
-    if (ky >= -K && ky <= K && kx >= -K && kx <= K) {
+    if (ky >= -K && ky < P - K && kx >= -K && kx < P - K) {
       ic = ((long)c * P + ky + K) * P + kx + K;
       // the coarse value of row ky + K lives in the block owning that row
       const int iy = ky + K, owner = iy / H;
@@ -504,14 +301,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   }
 }
 
-size_t coarse_conv_smem(int prec, int n_c) {
-  const int K = n_c / 3, L = 2 * K + 3;
-  return (size_t)3 * L * L * (prec == 0 ? 8 : 16);
-}
-
-bool coarse_conv_supported(int n_c) { return n_c <= 64; }
-
-// cluster split of a P-row coarse square: CS blocks of H rows
+// cluster split of a P-row coarse square: CS blocks of H rows (H <= 8 for P <= 64)
 static void cluster_shape(int P, int* CS, int* H) {
   int cs = (P + 5) / 6;
   if (cs > 8) cs = 8;
@@ -520,41 +310,34 @@ static void cluster_shape(int P, int* CS, int* H) {
   *CS = cs;
 }
 
-static size_t cluster_smem(int prec, int n_c, int nsteps, int* phase_slots) {
-  const int K = n_c / 3, P = 2 * K + 1, L = P + 2;
+constexpr int kMaxPhaseSlots = 8192;   // staged flow phases (512 steps x 4 stages x 4)
+
+static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots) {
+  const int L = P + 2;
   int CS, H;
   cluster_shape(P, &CS, &H);
   const size_t es = prec == 0 ? 4 : 8;
   const size_t base = (size_t)2 * 3 * (H + 2) * L * 2 * es;
-  const int slots = nsteps * 16 <= 8192 ? nsteps * 16 : 0;
+  const int slots = nsteps * 16 <= kMaxPhaseSlots ? nsteps * 16 : 0;
   *phase_slots = slots;
   return base + (size_t)slots * es;
 }
 
-template <typename T, int MPT>
-static cudaError_t prep1() {
-  return cudaFuncSetAttribute(coarse_conv_kernel<T, MPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)coarse_conv_smem(sizeof(T) == 4 ? 0 : 1, 64));
-}
+bool coarse_conv_supported(int P) { return P >= 1 && P <= 64; }
 
 cudaError_t coarse_prepare(int prec) {
-  cudaError_t e = prec == 0 ? prep1<float, 1>() : prep1<double, 1>();
-  if (e != cudaSuccess) return e;
-  e = prec == 0 ? prep1<float, 2>() : prep1<double, 2>();
-  if (e != cudaSuccess) return e;
   int slots = 0;
   const int bytes = (int)cluster_smem(prec, 64, 512, &slots);
   return prec == 0 ? cudaFuncSetAttribute(coarse_cluster_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
                    : cudaFuncSetAttribute(coarse_cluster_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <typename T, int MPT>
-static int launch_cluster(const CoarseArgs& a0, int batch, int n_c, cudaStream_t st) {
+template <typename T>
+static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   CoarseArgs a = a0;
-  const int P = 2 * (n_c / 3) + 1;
   int CS, H, slots;
-  cluster_shape(P, &CS, &H);
-  const size_t sm = cluster_smem(sizeof(T) == 4 ? 0 : 1, n_c, a.nsteps, &slots);
+  cluster_shape(a.Pc, &CS, &H);
+  const size_t sm = cluster_smem(sizeof(T) == 4 ? 0 : 1, a.Pc, a.nsteps, &slots);
   a.phase_smem = slots;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CS * batch), 1, 1);
@@ -568,30 +351,12 @@ static int launch_cluster(const CoarseArgs& a0, int batch, int n_c, cudaStream_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, MPT>, a, CS, H) == cudaSuccess ? 1 : -1;
+  return cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H) == cudaSuccess ? 1 : -1;
 }
 
-int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, int n_c, cudaStream_t st) {
-  if (!coarse_conv_supported(n_c) || batch <= 0) return -1;
-  if (a.nsteps * 16 <= 8192) {
-    // cluster kernel: rows of each block <= 6, so two modes per thread suffice
-    return prec == 0 ? launch_cluster<float, 2>(a, batch, n_c, st) : launch_cluster<double, 2>(a, batch, n_c, st);
-  }
-  const size_t sm = coarse_conv_smem(prec, n_c);
-  const int P = 2 * (n_c / 3) + 1;
-  const bool one = P * P <= CB;
-  if (prec == 0) {
-    if (one)
-      coarse_conv_kernel<float, 1><<<batch, CB, sm, st>>>(a);
-    else
-      coarse_conv_kernel<float, 2><<<batch, CB, sm, st>>>(a);
-  } else {
-    if (one)
-      coarse_conv_kernel<double, 1><<<batch, CB, sm, st>>>(a);
-    else
-      coarse_conv_kernel<double, 2><<<batch, CB, sm, st>>>(a);
-  }
-  return 1;
+int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st) {
+  if (!coarse_conv_supported(a.Pc) || batch <= 0) return -1;
+  return prec == 0 ? launch_cluster<float>(a, batch, st) : launch_cluster<double>(a, batch, st);
 }
 
 }  // namespace kd

@@ -9,17 +9,19 @@ namespace kd {
 // COARSE_INCR: U_{n+1} = F + G(U_n - Uprev_n)  (increment form; Gold unused).
 enum { COARSE_OUT = 0, COARSE_INIT = 1, COARSE_UPDATE = 2, COARSE_INCR = 3 };
 
+// Mode sets are squares k in [-K, P - K)^2 per axis (the dealiased sets are K = n/3,
+// P = 2K + 1; the learned operator's set is K = m/2, P = m).
 struct CoarseArgs {
-  int Kc;             // coarse cutoff n_c / 3
-  int Kf;             // fine cutoff n / 3 (input / update layout)
+  int Kc, Pc;         // coarse set
+  int Kf, Pf;         // input / update set (fine compact layout)
   int flow;
   double amp, kz, Rm, dt;
   int nsteps;
   const void* phases;   // [batch][nsteps][4][4] flow phases (precision T) or NULL (steady flow)
   const double* Un;     // fine compact FP64 inputs [batch][3][Pf][Pf] (complex interleaved)
   const double* Uprev;  // COARSE_INCR: previous iterate of the same slice (input is Un - Uprev)
-  int mode;             // COARSE_OUT: write g64; COARSE_INIT / COARSE_UPDATE: Parareal update (batch 1)
-  double* g64;          // COARSE_OUT: coarse compact FP64 outputs [batch][3][Pc][Pc]
+  int mode;             // COARSE_OUT: write g64; otherwise the Parareal update (batch 1)
+  double* g64;          // COARSE_OUT: coarse-set FP64 outputs [batch][3][Pc][Pc]
   const double* Fv;     // COARSE_UPDATE: fine values F(U_n), fine compact FP64
   double* Gold;         // coarse values of the previous sweep (read, then replaced)
   double* Unext;        // U_{n+1}, fine compact FP64 (written)
@@ -27,10 +29,9 @@ struct CoarseArgs {
   int phase_smem;       // (internal) phase values the cluster kernel may stage in shared memory
 };
 
-bool coarse_conv_supported(int n_c);
-size_t coarse_conv_smem(int prec, int n_c);
+bool coarse_conv_supported(int P);   // coarse set side P <= 64
 cudaError_t coarse_prepare(int prec);
-// One block per field; returns 1 (kernels launched) or -1 if n_c is not supported.
-int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, int n_c, cudaStream_t st);
+// One thread-block cluster per field; returns 1 (kernels launched) or -1 if unsupported.
+int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st);
 
 }  // namespace kd

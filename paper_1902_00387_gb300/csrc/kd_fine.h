@@ -45,7 +45,8 @@ int compact_resample(int pin, const void* src, int n_src, int pout, void* dst, i
 //   init = 2: increment form, U_next = F + prolong(g) (g = G of the increment; Gold unused)
 // If partials != NULL: also per-block sums of |U_next - U_next_old|^2 and |U_next|^2
 // into partials[2 * blockIdx + {0,1}] (deterministic order), returns the block count.
-int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int n_c,
+// (coarse set k in [-Kc, Pc - Kc)^2)
+int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int Kc, int Pc,
                     int init, double* partials, cudaStream_t st);
 // sigma = sqrt(sum diff / sum norm) of `nblocks` partial pairs -> out[0]; also the two sums
 int finish_sigma(const double* partials, int nblocks, double* out, cudaStream_t st);

@@ -166,7 +166,7 @@ k_update(const cx<double>* F, const cx<Tg>* g, cx<double>* Gold, cx<double>* U, 
     const int ky = r / Pf - Kf, kx = r % Pf - Kf;
     cx<double> gv = mk(0.0, 0.0), go = mk(0.0, 0.0);
     long ic = -1;
-    if (ky >= -Kc && ky <= Kc && kx >= -Kc && kx <= Kc) {
+    if (ky >= -Kc && ky < Pc - Kc && kx >= -Kc && kx < Pc - Kc) {
       ic = ((long)c * Pc + ky + Kc) * Pc + kx + Kc;
       gv = to_d(g[ic]);
       go = Gold[ic];
@@ -206,9 +206,9 @@ k_update(const cx<double>* F, const cx<Tg>* g, cx<double>* Gold, cx<double>* U, 
   }
 }
 
-int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int n_c, int init,
-                    double* partials, cudaStream_t st) {
-  const int Kf = n / 3, Pf = 2 * Kf + 1, Kc = n_c / 3, Pc = 2 * Kc + 1;
+int parareal_update(const double* F, const void* g, int pg, double* Gold, double* U_next, int n, int Kc, int Pc,
+                    int init, double* partials, cudaStream_t st) {
+  const int Kf = n / 3, Pf = 2 * Kf + 1;
   const long total = 3L * Pf * Pf;
   unsigned grid = nblk(total, UPD_THREADS);
   if (grid > 1024) grid = 1024;

@@ -51,7 +51,8 @@ class kd_parareal_stats(ctypes.Structure):
 _lib = None
 EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
-           "kd_version", "kd_fine_batched_static"]
+           "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
+           "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -74,6 +75,12 @@ def load():
         "kd_energy": (I, [P, P, I, P]),
         "kd_growth_rate": (I, [P, P, I, D, D, ctypes.POINTER(D)]),
         "kd_fine_batched_static": (I, [ctypes.POINTER(kd_params), P, P, P, I, I, P]),
+        "kd_learned_init": (I, [P, I, D]),
+        "kd_learned_pairs": (I, [P, P, I, P, P]),
+        "kd_learned_train": (I, [P, P, P, P, I, I, ctypes.c_float, ctypes.c_float, P]),
+        "kd_learned_eval": (I, [P, P, P, P, I, P, P]),
+        "kd_learned_loss_grad": (I, [P, P, P, ctypes.c_float, P, P, I, ctypes.POINTER(D), P]),
+        "kd_learned_apply": (I, [P, P, P, I, I]),
         "kd_launch_count": (ctypes.c_longlong, [P]),
         "kd_profile": (I, [P, I]),
         "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
@@ -89,11 +96,11 @@ def load():
 
 
 def make_params(flow, n, kz, Rm, dt_fine, prec_fine=KD_C64, n_coarse=None, dt_coarse=None,
-                prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL, fine_form=KD_FINE_DIRECT):
+                prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL, fine_form=KD_FINE_DIRECT, learned_modes=0):
     return kd_params(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(prec_fine),
                      int(n_coarse if n_coarse else max(16, n // 2)),
                      float(dt_coarse if dt_coarse else dt_fine), int(prec_fine if prec_coarse is None else prec_coarse),
-                     int(coarse_kind), 0, int(fine_form))
+                     int(coarse_kind), int(learned_modes), int(fine_form))
 
 
 def _ptr(x, dtype=None, device=True):
@@ -220,6 +227,52 @@ def kd_growth_rate(ctx, u_slices, n_samples, T, fit_from):
     return rate.value
 
 
+def _phase_arr(phase):
+    a = np.ascontiguousarray(np.asarray(phase, dtype=np.int32))
+    return a, a.ctypes.data
+
+
+def kd_learned_init(ctx, n_phase, slice_T):
+    return _check(ctx, load().kd_learned_init(ctx, int(n_phase), float(slice_T)))
+
+
+def kd_learned_pairs(ctx, x, n, phase, y):
+    """y_i = R F(P x_i); x, y: complex64 CUDA tensors [n][3][m][m]; phase: ints."""
+    ph, pp = _phase_arr(phase)
+    return _check(ctx, load().kd_learned_pairs(ctx, _ptr(x, "complex64"), int(n), pp, _ptr(y, "complex64")))
+
+
+def kd_learned_train(ctx, x, y, phase, n, epochs, lr, weight_decay, n_phase):
+    """Adam training of every phase operator; returns the data loss [n_phase][epochs]."""
+    ph, pp = _phase_arr(phase)
+    loss = np.zeros((n_phase, max(1, epochs)), np.float64)
+    _check(ctx, load().kd_learned_train(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), pp, int(n), int(epochs),
+                                        float(lr), float(weight_decay), loss.ctypes.data))
+    return loss[:, :epochs]
+
+
+def kd_learned_eval(ctx, x, y, phase, n, n_phase):
+    """Per-phase relative errors (learned, classical) against the pairs."""
+    ph, pp = _phase_arr(phase)
+    el = np.zeros(n_phase, np.float64)
+    ec = np.zeros(n_phase, np.float64)
+    _check(ctx, load().kd_learned_eval(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), pp, int(n), el.ctypes.data,
+                                       ec.ctypes.data))
+    return el, ec
+
+
+def kd_learned_loss_grad(ctx, W, W0, weight_decay, x, y, n, grad):
+    loss = ctypes.c_double()
+    _check(ctx, load().kd_learned_loss_grad(ctx, _ptr(W, None), _ptr(W0, None) if W0 is not None else None,
+                                            float(weight_decay), _ptr(x, "complex64"), _ptr(y, "complex64"), int(n),
+                                            ctypes.byref(loss), _ptr(grad, None)))
+    return loss.value
+
+
+def kd_learned_apply(ctx, x, y, phase, n):
+    return _check(ctx, load().kd_learned_apply(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), int(phase), int(n)))
+
+
 def kd_launch_count(ctx):
     return int(load().kd_launch_count(ctx))
 
@@ -242,4 +295,4 @@ def stats_dict(st):
             "n_coarse_steps": st.n_coarse_steps, "dt_fine_used": st.dt_fine_used,
             "dt_coarse_used": st.dt_coarse_used, "sigma": list(st.sigma[:k]), "growth_rate": st.growth_rate,
             "ms_total": st.ms_total, "ms_fine": st.ms_fine, "ms_coarse": st.ms_coarse,
-            "n_launches": st.n_launches}
+            "n_launches": st.n_launches, "fallback_used": bool(st.fallback_used)}
