@@ -168,6 +168,109 @@ def col_row_bytes(n, batch_slices):
     return 2 * mixed * batch_slices, (2 * mixed + 3.5 * spec) * batch_slices
 
 
+# --------------------------------------------------- learned coarse propagator run
+LEARNED_WL = {
+    "workload": "gp_cp_256x256_parareal_128_slices_learned_coarse",
+    "flow": "galloway-proctor", "n": 256, "kz": 0.57, "Rm": 1000.0, "slices": 128, "slice": 2 * math.pi / 16,
+    "fine_steps_per_slice": 800, "coarse_dt_over_fine_dt": 20, "learned_modes": 49, "phases": 16,
+    "pairs_per_phase": 256, "epochs": 300, "lr": 0.5, "optimizer": "momentum", "tol": 1e-6, "k_max": 32,
+}
+
+
+def run_learned(args):
+    """Time-to-solution of Parareal with the learned coarse propagator against the
+    classical coarse propagator (20x the fine step, same mode set) and serial fine
+    stepping, GP 256^2, Rm = 1000, 128 slices of 2 pi / 16."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    from oracle import kd_oracle as O
+    kd.load()
+    torch.cuda.init()
+    W = LEARNED_WL
+    n, N, m = W["n"], W["slices"], W["learned_modes"]
+    T = N * W["slice"]
+    dt = W["slice"] / W["fine_steps_per_slice"]
+    dtc = dt * W["coarse_dt_over_fine_dt"]
+    b0 = torch.tensor(kd_inputs.initial_field(n, W["kz"], 1000)).cuda()
+    out = {"impl": "ours", "config": dict(W), "metric": "Parareal time-to-1e-6, learned vs classical coarse",
+           "unit": "ms", "higher_is_better": False}
+
+    def ctx_for(kind):
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], dt, kd.KD_C64, n_coarse=64,
+                           dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT, learned_modes=m,
+                           coarse_kind=kind)
+        return kd.kd_create(p)
+
+    def solve(ctx):
+        u = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s, st = kd.kd_parareal_run(ctx, b0, T, N, W["k_max"], W["tol"], u)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st, u
+
+    # classical coarse propagator on the same mode set
+    ctx = ctx_for(kd.KD_COARSE_CLASSICAL)
+    solve(ctx)
+    ms_c, st_c, u_c = solve(ctx)
+    ser = torch.zeros_like(u_c)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    kd.kd_fine_serial(ctx, b0, T, N, ser)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    kd.kd_destroy(ctx)
+
+    # learned: build from the classical propagator, pairs from the fine propagator, train
+    ctx = ctx_for(kd.KD_COARSE_LEARNED)
+    t = time.perf_counter()
+    kd.kd_learned_init(ctx, W["phases"], W["slice"])
+    npair = W["pairs_per_phase"] * W["phases"]
+    # training inputs: seeded |k|^-2 fields drawn on an 80^2 grid (|k| <= 26 covers the set)
+    x = np.stack([O.learned_restrict(kd_inputs.initial_field(80, W["kz"], 10_000 + i), m) for i in range(npair)])
+    xt = torch.tensor(x.astype(np.complex64), device="cuda")
+    yt = torch.zeros_like(xt)
+    ph = np.arange(npair) % W["phases"]
+    kd.kd_learned_pairs(ctx, xt, npair, ph, yt)
+    t_pairs = time.perf_counter() - t
+    t = time.perf_counter()
+    loss = kd.kd_learned_train(ctx, xt, yt, ph, npair, W["epochs"], W["lr"], 0.0, W["phases"], kd.KD_TRAIN_MOMENTUM)
+    t_train = time.perf_counter() - t
+    nv = 16 * W["phases"]
+    xv = np.stack([O.learned_restrict(kd_inputs.initial_field(80, W["kz"], 90_000 + i), m) for i in range(nv)])
+    xvt = torch.tensor(xv.astype(np.complex64), device="cuda")
+    yvt = torch.zeros_like(xvt)
+    phv = np.arange(nv) % W["phases"]
+    kd.kd_learned_pairs(ctx, xvt, nv, phv, yvt)
+    el, ec = kd.kd_learned_eval(ctx, xvt, yvt, phv, nv, W["phases"])
+    solve(ctx)
+    ms_l, st_l, u_l = solve(ctx)
+    kd.kd_destroy(ctx)
+    err = lambda u: (torch.linalg.norm(u[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
+    out.update({
+        "serial_fine_ms": ms_s,
+        "classical": {"ms": ms_c, "k_con": st_c.k_con, "sigma": list(st_c.sigma[:st_c.k_con]),
+                      "err_vs_serial_fine": err(u_c), "speedup_vs_serial_fine": ms_s / ms_c,
+                      "growth_rate": st_c.growth_rate},
+        "learned": {"ms": ms_l, "k_con": st_l.k_con, "sigma": list(st_l.sigma[:st_l.k_con]),
+                    "fallback_used": bool(st_l.fallback_used), "err_vs_serial_fine": err(u_l),
+                    "speedup_vs_serial_fine": ms_s / ms_l, "phases_kept": int(np.sum(el <= ec)),
+                    "heldout_err_learned_median": float(np.median(el)),
+                    "heldout_err_classical_median": float(np.median(ec)),
+                    "train_loss_first_last": [float(loss[:, 0].mean()), float(loss[:, -1].mean())],
+                    "pairs_s": t_pairs, "train_s": t_train},
+    })
+    out["value"] = ms_l
+    print(json.dumps(out), flush=True)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -185,10 +288,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="parareal", choices=["parareal", "learned"],
+                    help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "learned":
+        run_learned(args)
         return
 
     import numpy as np

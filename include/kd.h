@@ -182,15 +182,21 @@ kd_status kd_learned_init(kd_ctx* ctx, int n_phase, double slice_T);
  *   x, y : device learned vectors [n]; phase : host int[n] in [0, n_phase).  Synchronous. */
 kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase, float* y);
 
-/* Train every W_p on its pairs: `epochs` Adam steps (beta 0.9 / 0.999, step size lr
- * with cosine decay to 0 over the epochs) on
- *   L = (1/m) sum_i |W x_i - y_i|^2 + weight_decay |W - W_classical|^2,
- * starting from W_classical; forward product and gradient 2/m (W X - Y) X^H are BF16
- * tensor-core GEMMs with FP32 accumulation, master weights FP32.
+enum { KD_TRAIN_ADAM = 0, KD_TRAIN_MOMENTUM = 1 };
+
+/* Train every W_p on its pairs, starting from W_classical, on
+ *   L = (1/m) sum_i |W x_i - y_i|^2 + weight_decay |W - W_classical|^2;
+ * forward product and gradient 2/m (W X - Y) X^H are BF16 tensor-core GEMMs with FP32
+ * accumulation, master weights FP32.  method:
+ *   KD_TRAIN_ADAM      Adam (beta 0.9 / 0.999), step lr with cosine decay to 0;
+ *   KD_TRAIN_MOMENTUM  heavy-ball gradient descent (momentum 0.9), step lr / lambda with
+ *                      lambda = (2/m) sum |x_i|^2 (lr <= 1); its updates stay in the span
+ *                      of the training inputs, which matters when pairs are fewer than
+ *                      the 3 m^2 unknowns of a row (Adam's per-weight scaling does not).
  *   loss_out : host double[n_phase * epochs] data loss per phase and epoch (may be NULL).
  * Synchronous. */
 kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,
-                           float weight_decay, double* loss_out);
+                           float weight_decay, int method, double* loss_out);
 
 /* Relative L2 errors per phase of the learned operator and of the classical coarse
  * propagator against held-out pairs (host double[n_phase] each; -1 for phases without

@@ -964,10 +964,12 @@ kd_status forward_backward(kd_ctx* ctx, TrainBufs& b, int mp, int nc, double* lo
 }  // namespace
 
 kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,
-                           float weight_decay, double* loss_out) {
+                           float weight_decay, int method, double* loss_out) {
   if (!ctx) return KD_EINVAL;
   if (ctx->l_nphase == 0) return fail(ctx, KD_EINVAL, "kd_learned_train: call kd_learned_init first");
-  if (!x || !y || !phase || n <= 0 || epochs < 0 || !(lr >= 0)) return fail(ctx, KD_EINVAL, "kd_learned_train: bad arguments");
+  if (!x || !y || !phase || n <= 0 || epochs < 0 || !(lr >= 0) ||
+      (method != KD_TRAIN_ADAM && method != KD_TRAIN_MOMENTUM))
+    return fail(ctx, KD_EINVAL, "kd_learned_train: bad arguments");
   const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
   const size_t wcount = (size_t)2 * nc * ld;
   std::vector<std::vector<int>> byp(ctx->l_nphase);
@@ -997,14 +999,30 @@ kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const in
     KD_CUDA(cudaMemsetAsync(v, 0, wcount * 4, ctx->st), "memset");
     KD_LAUNCH(f32_to_bf16(Wm, b.Wbf, (long)wcount, ctx->st), "bf16");
     const float scale = 2.f / (float)byp[p].size();
+    float eta = 0.f;
+    if (method == KD_TRAIN_MOMENTUM) {
+      // step size lr / lambda, lambda = (2/m) sum |x_i|^2 bounds the Hessian (2/m) X^H X
+      const int nb = diff_norms(b.xp, b.xp, 2L * mp * nc, ctx->partials, ctx->st);
+      if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");
+      KD_LAUNCH(sum_partials(ctx->partials, nb, ctx->scal + 12, ctx->st), "norm");
+      double h[2];
+      KD_CUDA(cudaMemcpyAsync(h, ctx->scal + 12, 16, cudaMemcpyDeviceToHost, ctx->st), "norm");
+      KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+      eta = (float)(lr / (scale * h[1] + 2.0 * weight_decay));
+    }
     for (int e = 0; e < epochs; ++e) {
       if ((s = forward_backward(ctx, b, mp, nc, lossd + 2 * ((size_t)p * epochs + e))) != KD_OK) return s;
-      // cosine decay of the step size to zero over the epochs
-      const float lr_e = (float)(0.5 * lr * (1.0 + cos(M_PI * e / (double)epochs)));
-      const int nb = learned_adam(Wm, W0, b.C2, m1, v, b.Wbf, (long)wcount, scale, weight_decay, lr_e, 0.9f,
-                                  0.999f, 1e-8f, e + 1, nullptr, ctx->st);
-      if (nb < 0) return fail(ctx, KD_ECUDA, "adam launch failed");
-      ctx->launches += 1;
+      if (method == KD_TRAIN_ADAM) {
+        // cosine decay of the step size to zero over the epochs
+        const float lr_e = (float)(0.5 * lr * (1.0 + cos(M_PI * e / (double)epochs)));
+        const int nb = learned_adam(Wm, W0, b.C2, m1, v, b.Wbf, (long)wcount, scale, weight_decay, lr_e, 0.9f,
+                                    0.999f, 1e-8f, e + 1, nullptr, ctx->st);
+        if (nb < 0) return fail(ctx, KD_ECUDA, "adam launch failed");
+        ctx->launches += 1;
+      } else {
+        KD_LAUNCH(learned_momentum(Wm, W0, b.C2, v, b.Wbf, (long)wcount, scale, weight_decay, eta, 0.9f, ctx->st),
+                  "momentum");
+      }
     }
     KD_CUDA(cudaMemcpyAsync(ctx->l_W + (size_t)p * wcount, b.Wbf, wcount * 2, cudaMemcpyDeviceToDevice, ctx->st),
             "store");

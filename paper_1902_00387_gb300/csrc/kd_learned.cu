@@ -480,6 +480,27 @@ int learned_adam(float* W, const float* W0, const float* C2, float* m1, float* v
   return e != cudaSuccess ? -(int)e : (int)g;
 }
 
+// heavy-ball gradient descent: v = mu v + g, W -= eta v (updates stay in the span of
+// the gradients, i.e. of the training inputs, when started from W0 with wd = 0)
+__global__ void k_momentum(float* W, const float* W0, const float* C2, float* v, __nv_bfloat16* Wbf, long count,
+                           float scale, float wd, float eta, float mu) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const float w = W[i];
+    const float g = scale * C2[i] + 2.f * wd * (W0 ? w - W0[i] : w);
+    const float vv = mu * v[i] + g;
+    v[i] = vv;
+    const float wn = w - eta * vv;
+    W[i] = wn;
+    Wbf[i] = __float2bfloat16(wn);
+  }
+}
+
+int learned_momentum(float* W, const float* W0, const float* C2, float* v, __nv_bfloat16* Wbf, long count,
+                     float scale, float wd, float eta, float mu, cudaStream_t st) {
+  k_momentum<<<grid1(count), TB, 0, st>>>(W, W0, C2, v, Wbf, count, scale, wd, eta, mu);
+  return (int)cudaGetLastError();
+}
+
 __global__ void k_grad(const float* W, const float* W0, const float* C2, float* grad, long count, float scale,
                        float wd) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {

@@ -59,6 +59,9 @@ int learned_residual(const float* C1, const float* yT, int m, int nc, __nv_bfloa
 int learned_adam(float* W, const float* W0, const float* C2, float* m1, float* v, __nv_bfloat16* Wbf, long count,
                  float scale, float wd, float lr, float beta1, float beta2, float eps, int step, double* partials2,
                  cudaStream_t st);
+// heavy-ball step: g as above, v = mu v + g, W -= eta v, Wbf = bf16(W)
+int learned_momentum(float* W, const float* W0, const float* C2, float* v, __nv_bfloat16* Wbf, long count,
+                     float scale, float wd, float eta, float mu, cudaStream_t st);
 // plain gradient (no update): grad = scale * C2 + 2 wd (W - W0)   (W0 may be NULL)
 int learned_grad(const float* W, const float* W0, const float* C2, float* grad, long count, float scale, float wd,
                  cudaStream_t st);

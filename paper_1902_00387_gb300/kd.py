@@ -21,6 +21,7 @@ KD_FLOW_ROBERTS, KD_FLOW_GALLOWAY_PROCTOR, KD_FLOW_NONE = 0, 1, 2
 KD_C64, KD_C128 = 0, 1
 KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
 KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
+KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
 KD_MAX_SLICES = 1024
 KD_MAX_ITERS = 256
 
@@ -77,7 +78,7 @@ def load():
         "kd_fine_batched_static": (I, [ctypes.POINTER(kd_params), P, P, P, I, I, P]),
         "kd_learned_init": (I, [P, I, D]),
         "kd_learned_pairs": (I, [P, P, I, P, P]),
-        "kd_learned_train": (I, [P, P, P, P, I, I, ctypes.c_float, ctypes.c_float, P]),
+        "kd_learned_train": (I, [P, P, P, P, I, I, ctypes.c_float, ctypes.c_float, I, P]),
         "kd_learned_eval": (I, [P, P, P, P, I, P, P]),
         "kd_learned_loss_grad": (I, [P, P, P, ctypes.c_float, P, P, I, ctypes.POINTER(D), P]),
         "kd_learned_apply": (I, [P, P, P, I, I]),
@@ -242,12 +243,12 @@ def kd_learned_pairs(ctx, x, n, phase, y):
     return _check(ctx, load().kd_learned_pairs(ctx, _ptr(x, "complex64"), int(n), pp, _ptr(y, "complex64")))
 
 
-def kd_learned_train(ctx, x, y, phase, n, epochs, lr, weight_decay, n_phase):
-    """Adam training of every phase operator; returns the data loss [n_phase][epochs]."""
+def kd_learned_train(ctx, x, y, phase, n, epochs, lr, weight_decay, n_phase, method=KD_TRAIN_ADAM):
+    """Train every phase operator; returns the data loss [n_phase][epochs]."""
     ph, pp = _phase_arr(phase)
     loss = np.zeros((n_phase, max(1, epochs)), np.float64)
     _check(ctx, load().kd_learned_train(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), pp, int(n), int(epochs),
-                                        float(lr), float(weight_decay), loss.ctypes.data))
+                                        float(lr), float(weight_decay), int(method), loss.ctypes.data))
     return loss[:, :epochs]
 
 

@@ -141,7 +141,7 @@ def _train(kd, ctx, n_per_phase, seed0, epochs=300, lr=1e-2, wd=0.0, m_set=M_SET
     xt = torch.tensor(x, device="cuda")
     yt = torch.zeros_like(xt)
     kd.kd_learned_pairs(ctx, xt, n, phase, yt)
-    loss = kd.kd_learned_train(ctx, xt, yt, phase, n, epochs, lr, wd, N_PHASE)
+    loss = kd.kd_learned_train(ctx, xt, yt, phase, n, epochs, lr, wd, N_PHASE, kd.KD_TRAIN_ADAM)
     return loss
 
 
