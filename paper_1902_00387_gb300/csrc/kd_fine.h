@@ -18,6 +18,10 @@ cudaError_t fine_prepare(int prec);
 size_t phase_table_bytes(int prec, long batch, int nsteps);
 // fill FineArgs::phases (Galloway-Proctor only); returns kernels launched
 int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
+// ---- kd_fine3.cu (register-FFT kernels, n = 512, 1024)
+cudaError_t fine3_prepare(int prec);
+int fine3_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
+                       const LaunchProbe* probe);
 // ---- kd_fine2.cu (register-FFT kernels, n <= 256)
 cudaError_t fine2_prepare(int prec);
 int fine2_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
