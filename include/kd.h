@@ -247,6 +247,80 @@ kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int
 kd_status kd_fine_batched_static(const kd_params* params, const void* b_in, void* b_out, const double* t0,
                                  int nsteps, int batch, void* cuda_stream);
 
+/* ------------------------------------------------------------------------------------
+ * Launch plans and the autotuner.
+ *
+ * The fine step's column and row kernels exist in several variants per grid and
+ * precision (columns or rows per thread block; the row kernel's stage update run from
+ * shared memory or from registers).  A plan is the pair (col, row) of variant indices;
+ * {0, 0} is the default.  grid: 0 = the fine grid n, 1 = the coarse grid n_coarse. */
+enum { KD_GRID_FINE = 0, KD_GRID_COARSE = 1 };
+
+/* Number of column / row variants of the context's grid.  KD_EINVAL for a bad grid. */
+kd_status kd_plan_variants(kd_ctx* ctx, int grid, int* n_col, int* n_row);
+/* Set / read the plan of a grid.  KD_EINVAL if an index is out of range. */
+kd_status kd_set_plan(kd_ctx* ctx, int grid, int col, int row);
+kd_status kd_get_plan(kd_ctx* ctx, int grid, int* col, int* row);
+
+/* Autotune the plan of a grid for batches of `batch` fields: if `cache_path` (may be
+ * NULL) names a JSON file holding an entry for (device name, n, precision, batch rounded
+ * up to a power of two), that entry's plan is used; otherwise every (col, row) pair is
+ * timed with CUDA events over `nsteps` fine steps (after one untimed step) on seeded
+ * workspace data, the fastest is set and, with cache_path, written to the file (other
+ * entries are kept).  ms_per_step (may be NULL) receives the chosen plan's time, or -1
+ * when it came from the cache.  Synchronous.  KD_EINVAL for bad arguments, KD_ECUDA on
+ * device failures; an unreadable or malformed cache file is ignored and rewritten. */
+kd_status kd_autotune(kd_ctx* ctx, int grid, int batch, int nsteps, const char* cache_path,
+                      double* ms_per_step);
+
+/* ------------------------------------------------------------------------------------
+ * Batched sweep of independent Parareal problems (instances of different grids, flows,
+ * kz and Rm; Sec. 3 applied to each).  Instances are grouped by (n, n_coarse); within a
+ * group every instance's slices advance together in the same batched fine launches (each
+ * field with its own dt, kz, Rm and flow, fields ordered by decreasing step count so that
+ * the fields still stepping are a prefix of the batch), and the serial sweeps of all
+ * instances run together slice by slice.  Fine propagator complex64, classical coarse
+ * propagator complex64 on the n_coarse grid, the increment form of the correction
+ * (U_{n+1} = F(U_n) accumulated + G(U_n - U_n^prev)) and the defect in FP64.  An instance
+ * stops iterating when its defect reaches tol (or at k_max) while the others go on. */
+typedef struct {
+  int flow;            /* KD_FLOW_* */
+  int n;               /* fine grid side, power of two in [16, 1024] */
+  double kz, Rm;
+  double dt_fine;      /* fine step; the slice length is split into ceil(dT / dt_fine) equal steps */
+  int n_coarse;        /* coarse grid side, power of two in [16, n] */
+  double dt_coarse;    /* coarse step (rounded like dt_fine) */
+} kd_instance;
+
+typedef struct {
+  int status;              /* KD_OK, KD_ENOTCONV or KD_ENONFINITE for this instance */
+  int k_con;               /* iterations taken */
+  int n_fine_steps, n_coarse_steps;
+  double dt_fine_used, dt_coarse_used;
+  double sigma[KD_MAX_ITERS];  /* Eq. 9 defect after iteration k (index k-1) */
+  double growth_rate;      /* 0.5 d ln E / dt fitted over t >= T/2 at the slice boundaries */
+} kd_instance_result;
+
+typedef struct {
+  int n_groups;
+  double ms_total, ms_fine, ms_coarse;
+  long long n_launches;
+  double fine_dof_steps;   /* sum over fine launches of 3 n^2 x fields x steps actually advanced */
+} kd_sweep_stats;
+
+/* Run Parareal with n_slices slices of T / n_slices on every instance.  b0[i]: instance
+ * i's initial field, complex128 [3][n_i][n_i] (host or device pointer).  u_final (may be
+ * NULL, entries may be NULL): receives instance i's final-iterate state at t = T in the
+ * same layout.  results[n_inst] (may be NULL), stats (may be NULL).  tune_cache (may be
+ * NULL): JSON cache of kd_autotune; when given, each group's fine plan is autotuned (or
+ * read from the cache) before the run.  Synchronous on cuda_stream.  Returns KD_OK when
+ * every instance converged, KD_ENOTCONV if some did not (outputs still written),
+ * KD_ENONFINITE if an instance's defect was not finite, KD_EINVAL / KD_ENOMEM / KD_ECUDA
+ * otherwise; err (may be NULL, >= 256 bytes) receives a message. */
+kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const double* const* b0, double T, int n_slices,
+                       int k_max, double tol, const char* tune_cache, double* const* u_final,
+                       kd_instance_result* results, kd_sweep_stats* stats, void* cuda_stream, char* err);
+
 /* Number of kernels this context has launched since kd_create (-1 for NULL). */
 long long kd_launch_count(kd_ctx* ctx);
 

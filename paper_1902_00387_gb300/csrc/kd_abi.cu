@@ -20,82 +20,14 @@
 
 #include "../../include/kd.h"
 #include "kd_coarse.h"
+#include "kd_ctx.h"
 #include "kd_fine.h"
 #include "kd_learned.h"
 
 using namespace kd;
+using namespace kdi;
 
-namespace {
-
-struct Tables {
-  int n = 0, prec = -1;
-  void* tw = nullptr;
-  void* cosg = nullptr;
-  void* sing = nullptr;
-};
-
-struct FineWs {
-  long cap = 0;
-  int n = 0, prec = 0;
-  void* X = nullptr;
-  void* R2 = nullptr;
-  void* R3 = nullptr;
-  void* R4 = nullptr;
-  void* M = nullptr;
-  void* W = nullptr;
-  void* ph = nullptr;      // flow-phase table
-  size_t ph_bytes = 0;
-};
-
-size_t csize(int prec) { return prec == KD_C128 ? 16 : 8; }
-
-}  // namespace
-
-struct kd_ctx {
-  kd_params p;
-  cudaStream_t st = nullptr;
-  int device = 0;
-  Tables tab_f, tab_c;
-  FineWs ws_f, ws_c;
-  // Parareal / serial buffers
-  long cap_slices = 0;
-  double* U = nullptr;
-  double* Fv = nullptr;
-  double* Gv = nullptr;
-  double* Uprev = nullptr;    // previous iterate (increment form of the fine sweep)
-  void* ph_c = nullptr;       // coarse flow-phase table of all slices
-  size_t ph_c_bytes = 0;
-  double* t0f = nullptr;
-  double* t0c = nullptr;
-  double* partials = nullptr;
-  double* scal = nullptr;     // device scalars (sigma, fit)
-  double* Ebuf = nullptr;
-  void* full_tmp = nullptr;   // full-grid FP64 staging [max(N+1, batch)][3][n][n]
-  size_t full_tmp_bytes = 0;
-  double* host_scal = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  std::vector<void*> allocs;
-  std::string err;
-  long long launches = 0;     // kernels launched by this context
-  int cK = 0, cP = 0;         // coarse mode set k in [-cK, cP - cK)^2
-  // learned coarse propagator (kd_learned_*)
-  int l_nphase = 0;
-  double l_sliceT = 0.0;
-  __nv_bfloat16* l_W = nullptr;   // [nphase][2 nc][nc] BF16 stacked operators
-  float* l_W0 = nullptr;          // [nphase][2 nc][nc] FP32 classical-propagator matrices
-  std::vector<int> l_valid;       // phase operator passed validation against the classical one
-  float* l_x = nullptr;           // sweep vectors [2][nc] complex
-  int fallback = 0;
-  // optional event timing of the fine column / row kernels
-  int prof = 0;
-  std::vector<cudaEvent_t> pev;
-  std::vector<int> pkid;
-  size_t pev_used = 0;
-  double prof_ms[2] = {0.0, 0.0};
-  long long prof_n[2] = {0, 0};
-};
-
-namespace {
+namespace kdi {
 
 kd_status fail(kd_ctx* c, kd_status s, const std::string& m) {
   if (c) c->err = m;
@@ -107,26 +39,9 @@ kd_status cuda_fail(kd_ctx* c, cudaError_t e, const char* where) {
               std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define KD_CUDA(call, where)                           \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
-  } while (0)
-
-#define KD_LAUNCH(expr, where)                                        \
-  do {                                                                \
-    int r_ = (expr);                                                  \
-    if (r_ < 0) return fail(ctx, KD_ECUDA, std::string(where) + ": launch failed"); \
-    ctx->launches += r_ > 0 ? r_ : 1;                                 \
-    cudaError_t e_ = cudaGetLastError();                              \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);          \
-  } while (0)
-
 bool valid_n(int n) {
   return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
 }
-int kept(int n) { return 2 * (n / 3) + 1; }
-long compact_len(int n) { return 3L * kept(n) * kept(n); }  // complex entries per field
 
 kd_status dalloc(kd_ctx* ctx, void** p, size_t bytes, const char* what) {
   *p = nullptr;
@@ -244,6 +159,7 @@ FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int n, l
   a.sing = t.sing;
   a.phases = nullptr;
   a.phase_steps = 0;
+  a.sp = nullptr;
   return a;
 }
 
@@ -305,6 +221,19 @@ kd_status with_phases(kd_ctx* ctx, FineWs& w, FineArgs& a, int nsteps) {
   }
   a.phases = w.ph;
   return KD_OK;
+}
+
+int run_fine(kd_ctx* ctx, int g, int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last,
+             const LaunchProbe* probe, const int* active) {
+  StepCfg cfg;
+  cfg.nsteps = nsteps;
+  cfg.prologue = prologue;
+  cfg.store_last = store_last;
+  cfg.active = active;
+  cfg.probe = probe;
+  cfg.plan = ctx->plan[g];
+  cfg.st = ctx->st;
+  return fine_run(prec, a, cfg);
 }
 
 kd_status ensure_full_tmp(kd_ctx* ctx, size_t bytes) {
@@ -435,7 +364,7 @@ kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool la
   FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, 1, dtc, ctx->t0c + i);
   kd_status s = with_phases(ctx, ctx->ws_c, a, Sc);
   if (s != KD_OK) return s;
-  KD_LAUNCH(fine_launch_steps(pc, a, Sc, true, false, ctx->st), "coarse steps");
+  KD_LAUNCH(run_fine(ctx, 1, pc, a, Sc, true, false), "coarse steps");
   int nb = parareal_update(init ? nullptr : ctx->Fv + 2 * i * len, ctx->ws_c.X, pc, ctx->Gv + 2 * i * lenc,
                            ctx->U + 2 * (i + 1) * len, n, nc / 3, 2 * (nc / 3) + 1, init ? 1 : (incr ? 2 : 0),
                            last ? ctx->partials : nullptr, ctx->st);
@@ -491,7 +420,7 @@ kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) 
   kd_status s = with_phases(ctx, ctx->ws_f, a, S);
   if (s != KD_OK) return s;
   LaunchProbe pr = probe_of(ctx);
-  KD_LAUNCH(fine_launch_steps(pf, a, S, true, false, ctx->st, ctx->prof ? &pr : nullptr), "fine steps");
+  KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false, ctx->prof ? &pr : nullptr), "fine steps");
   if (incr)
     KD_LAUNCH(accum_out(pf, ctx->ws_f.X, ctx->Fv + 2 * first * len, b * len, iter == 1 ? 1 : 0, ctx->st),
               "accumulate fine");
@@ -521,7 +450,7 @@ kd_status copy_out_slices(kd_ctx* ctx, double* u_slices, int N) {
   return KD_OK;
 }
 
-}  // namespace
+}  // namespace kdi
 
 extern "C" {
 
@@ -601,7 +530,7 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
   if ((s = with_phases(ctx, ctx->ws_f, a, nsteps)) != KD_OK) return s;
   LaunchProbe pr = probe_of(ctx);
   if (nsteps > 0)
-    KD_LAUNCH(fine_launch_steps(pf, a, nsteps, true, false, ctx->st, ctx->prof ? &pr : nullptr), "fine steps");
+    KD_LAUNCH(run_fine(ctx, 0, pf, a, nsteps, true, false, ctx->prof ? &pr : nullptr), "fine steps");
   KD_LAUNCH(compact_to_full(pf, ctx->ws_f.X, pf, b_out, batch, n, ctx->st), "unpack");
   return KD_OK;
 }
@@ -645,7 +574,7 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
   KD_LAUNCH(compact_resample(KD_C128, ctx->full_tmp, n, pc, ctx->ws_c.X, nc, batch, ctx->st), "restrict");
   FineArgs a = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, batch, ctx->p.dt_coarse, t0);
   if ((s = with_phases(ctx, ctx->ws_c, a, nsteps)) != KD_OK) return s;
-  if (nsteps > 0) KD_LAUNCH(fine_launch_steps(pc, a, nsteps, true, false, ctx->st), "coarse steps");
+  if (nsteps > 0) KD_LAUNCH(run_fine(ctx, 1, pc, a, nsteps, true, false), "coarse steps");
   KD_LAUNCH(compact_resample(pc, ctx->ws_c.X, nc, KD_C128, ctx->full_tmp, n, batch, ctx->st), "prolong");
   KD_LAUNCH(compact_to_full(KD_C128, ctx->full_tmp, KD_C128, b_out, batch, n, ctx->st), "unpack");
   return KD_OK;
@@ -795,7 +724,7 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
     KD_LAUNCH(compact_resample(KD_C128, ctx->U + 2 * i * len, n, pf, ctx->ws_f.X, n, 1, ctx->st), "to fine");
     FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, 1, dt, ctx->t0f + i);
     if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;
-    KD_LAUNCH(fine_launch_steps(pf, a, S, true, false, ctx->st), "fine steps");
+    KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false), "fine steps");
     KD_LAUNCH(compact_resample(pf, ctx->ws_f.X, n, KD_C128, ctx->U + 2 * (i + 1) * len, n, 1, ctx->st), "from fine");
   }
   if ((s = copy_out_slices(ctx, u_slices, N)) != KD_OK) return s;
@@ -891,7 +820,7 @@ kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase,
     KD_LAUNCH(learned_to_fine(x + 2L * off * nc, K, P, ctx->ws_f.X, pf, Kf, Pf, cnt, ctx->st), "to fine");
     FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, nfine, cnt, dt, t0);
     if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;
-    KD_LAUNCH(fine_launch_steps(pf, a, S, true, false, ctx->st), "fine steps");
+    KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false), "fine steps");
     KD_LAUNCH(fine_to_learned(ctx->ws_f.X, pf, Kf, Pf, y + 2L * off * nc, K, P, cnt, ctx->st), "to learned");
     KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   }

@@ -50,6 +50,13 @@ struct GridTables {
   void* sing;  // T[n]
 };
 
+// Per-slice parameters of a batch whose fields belong to different problems (batched
+// instances): flow amplitude, kz, Rm and the step dt of field b; flow is FLOW_*.
+struct SliceParams {
+  double amp, kz, Rm, dt;
+  int flow, pad;
+};
+
 // Everything a fine-step kernel needs about one batched propagation.
 struct FineArgs {
   int n, K, P;
@@ -69,6 +76,8 @@ struct FineArgs {
   const void* sing;
   const void* phases;  // Galloway-Proctor flow phases [batch][phase_steps][4 stages][4] (precision T)
   int phase_steps;     // steps covered by the phase table
+  const SliceParams* sp;  // optional [batch] per-slice parameters (NULL: the scalars above);
+                          // with sp the phase table is read for every field (flow = FLOW_GP)
 };
 
 }  // namespace kd

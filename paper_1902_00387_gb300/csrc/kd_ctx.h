@@ -1,0 +1,120 @@
+// Library-internal view of the context of include/kd.h and the helpers shared by the
+// C-ABI translation units (kd_abi.cu, kd_tune.cu, kd_sweep.cu).
+#pragma once
+#include <cuda_bf16.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kd.h"
+#include "kd_fine.h"
+
+namespace kdi {
+
+struct Tables {
+  int n = 0, prec = -1;
+  void* tw = nullptr;
+  void* cosg = nullptr;
+  void* sing = nullptr;
+};
+
+struct FineWs {
+  long cap = 0;
+  int n = 0, prec = 0;
+  void* X = nullptr;
+  void* R2 = nullptr;
+  void* R3 = nullptr;
+  void* R4 = nullptr;
+  void* M = nullptr;
+  void* W = nullptr;
+  void* ph = nullptr;      // flow-phase table
+  size_t ph_bytes = 0;
+};
+
+inline size_t csize(int prec) { return prec == KD_C128 ? 16 : 8; }
+
+}  // namespace kdi
+
+struct kd_ctx {
+  kd_params p;
+  kd::FinePlan plan[2];        // launch plans of the fine (0) and coarse (1) grid
+  cudaStream_t st = nullptr;
+  int device = 0;
+  kdi::Tables tab_f, tab_c;
+  kdi::FineWs ws_f, ws_c;
+  // Parareal / serial buffers
+  long cap_slices = 0;
+  double* U = nullptr;
+  double* Fv = nullptr;
+  double* Gv = nullptr;
+  double* Uprev = nullptr;    // previous iterate (increment form of the fine sweep)
+  void* ph_c = nullptr;       // coarse flow-phase table of all slices
+  size_t ph_c_bytes = 0;
+  double* t0f = nullptr;
+  double* t0c = nullptr;
+  double* partials = nullptr;
+  double* scal = nullptr;     // device scalars (sigma, fit)
+  double* Ebuf = nullptr;
+  void* full_tmp = nullptr;   // full-grid FP64 staging [max(N+1, batch)][3][n][n]
+  size_t full_tmp_bytes = 0;
+  double* host_scal = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<void*> allocs;
+  std::string err;
+  long long launches = 0;     // kernels launched by this context
+  int cK = 0, cP = 0;         // coarse mode set k in [-cK, cP - cK)^2
+  // learned coarse propagator (kd_learned_*)
+  int l_nphase = 0;
+  double l_sliceT = 0.0;
+  __nv_bfloat16* l_W = nullptr;   // [nphase][2 nc][nc] BF16 stacked operators
+  float* l_W0 = nullptr;          // [nphase][2 nc][nc] FP32 classical-propagator matrices
+  std::vector<int> l_valid;       // phase operator passed validation against the classical one
+  float* l_x = nullptr;           // sweep vectors [2][nc] complex
+  int fallback = 0;
+  // optional event timing of the fine column / row kernels
+  int prof = 0;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pkid;
+  size_t pev_used = 0;
+  double prof_ms[2] = {0.0, 0.0};
+  long long prof_n[2] = {0, 0};
+};
+
+
+namespace kdi {
+
+kd_status fail(kd_ctx* c, kd_status s, const std::string& m);
+kd_status cuda_fail(kd_ctx* c, cudaError_t e, const char* where);
+
+#define KD_CUDA(call, where)                                 \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return kdi::cuda_fail(ctx, e_, where); \
+  } while (0)
+
+#define KD_LAUNCH(expr, where)                                                          \
+  do {                                                                                  \
+    int r_ = (expr);                                                                    \
+    if (r_ < 0) return kdi::fail(ctx, KD_ECUDA, std::string(where) + ": launch failed"); \
+    ctx->launches += r_ > 0 ? r_ : 1;                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) return kdi::cuda_fail(ctx, e_, where);                       \
+  } while (0)
+
+bool valid_n(int n);
+inline int kept(int n) { return 2 * (n / 3) + 1; }
+inline long compact_len(int n) { return 3L * kept(n) * kept(n); }  // complex entries per field
+int steps_for(double dT, double dt);
+kd_status dalloc(kd_ctx* ctx, void** p, size_t bytes, const char* what);
+void dfree(kd_ctx* ctx, void* p);
+kd_status make_tables(kd_ctx* ctx, Tables& t, int n, int prec);
+kd_status ensure_ws(kd_ctx* ctx, FineWs& w, int n, int prec, long batch);
+kd::FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int n, long batch, double dt,
+                       const double* t0);
+// point a.phases at a table of the workspace large enough for `nsteps` steps
+kd_status with_phases(kd_ctx* ctx, FineWs& w, kd::FineArgs& a, int nsteps);
+// fine steps on grid g (0 fine, 1 coarse) with the context's plan for that grid
+int run_fine(kd_ctx* ctx, int g, int prec, const kd::FineArgs& a, int nsteps, bool prologue, bool store_last,
+             const kd::LaunchProbe* probe = nullptr, const int* active = nullptr);
+
+}  // namespace kdi

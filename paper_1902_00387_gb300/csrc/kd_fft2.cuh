@@ -94,8 +94,19 @@ struct FFT2 {
   __host__ __device__ static constexpr int out_pos_base(int r) { return R2 * (r / R2) + R1 * (r % R2); }
 };
 
+// Shared twiddles of fft2_3, laid out [q][a] = w_N^(a q) (q < R1, a < R2) so that the
+// lanes of a transform read consecutive words.  tw[e] = exp(-2 pi i e / N).
+template <typename T, int N>
+__device__ __forceinline__ void fft2_tables(cx<T>* s_tw, const cx<T>* tw) {
+  constexpr int R2 = Split<N>::R2;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int q = i / R2, a = i - q * R2;
+    s_tw[i] = tw[(a * q) & (N - 1)];
+  }
+}
+
 // Three-component transform.  S(c, q, a2) returns the shared-memory slot of matrix
-// element (q, a2) of component c for this thread's transform.  tw[e] = exp(-2 pi i e / N).
+// element (q, a2) of component c for this thread's transform; tw: fft2_tables.
 // Ends with the results in registers; the caller must __syncthreads() before the
 // shared exchange buffers are written again.
 template <typename T, int N, int DIR, class Slot>
@@ -108,7 +119,7 @@ __device__ __forceinline__ void fft2_3(cx<T> (&v)[3][Split<N>::R1], int a, const
     for (int q = 0; q < R1; ++q) {
       cx<T> y = v[c][bitrev<R1>(q)];
       if (q != 0) {
-        const cx<T> w = tw[(a * q) & (N - 1)];
+        const cx<T> w = tw[q * R2 + a];
         y = cmul(y, DIR < 0 ? w : mk(w.x, -w.y));
       }
       *S(c, q, a) = y;

@@ -20,9 +20,26 @@ template <int N>
 struct F3 {
   static constexpr int T = N / 16, RM = N / 256, NB2 = 16 / RM;
   static constexpr int NPAD = N + N / 16;
+  // twiddles re-laid for conflict-free reads: pass 3 [k][j] (16 x T), pass 2 [k][b mod 16]
+  static constexpr int TWS = N + 16 * RM;
 };
 
-// S(c, i): shared slot of element i (already padded by the caller's layout) of component c
+// Fill the shared twiddle tables of fft3_3 from tw[e] = exp(-2 pi i e / N).
+template <typename T, int N>
+__device__ __forceinline__ void fft3_tables(cx<T>* s_tw, const cx<T>* tw) {
+  constexpr int TT = F3<N>::T, RM = F3<N>::RM;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int k = i / TT, j = i - k * TT;
+    s_tw[i] = tw[k * j];                               // pass 3: w^(k j)
+  }
+  for (int i = threadIdx.x; i < 16 * RM; i += blockDim.x) {
+    const int k = i / 16, bm = i - k * 16;
+    s_tw[N + i] = tw[k * bm * (N / (16 * RM))];        // pass 2: w^(k (b mod 16) N / (16 RM))
+  }
+}
+
+// S(c, i): shared slot of element i (already padded by the caller's layout) of component c;
+// tw: the tables written by fft3_tables
 template <typename T, int N, int DIR, class Slot>
 __device__ __forceinline__ void fft3_3(cx<T> (&v)[3][16], int j, const cx<T>* tw, Slot S) {
   constexpr int TT = F3<N>::T, RM = F3<N>::RM, NB2 = F3<N>::NB2;
@@ -51,7 +68,7 @@ __device__ __forceinline__ void fft3_3(cx<T> (&v)[3][16], int j, const cx<T>* tw
     cx<T> w[RM];
 #pragma unroll
     for (int k = 1; k < RM; ++k) {
-      const cx<T> t = tw[k * bm * (N / (16 * RM))];
+      const cx<T> t = tw[N + k * 16 + bm];
       w[k] = DIR < 0 ? t : mk(t.x, -t.y);
     }
     const int idxD = (b >> 4) * 16 * RM + bm;
@@ -70,7 +87,7 @@ __device__ __forceinline__ void fft3_3(cx<T> (&v)[3][16], int j, const cx<T>* tw
   cx<T> w[16];
 #pragma unroll
   for (int k = 1; k < 16; ++k) {
-    const cx<T> t = tw[k * j];
+    const cx<T> t = tw[k * TT + j];
     w[k] = DIR < 0 ? t : mk(t.x, -t.y);
   }
 #pragma unroll

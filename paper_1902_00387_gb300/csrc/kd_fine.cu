@@ -2,7 +2,8 @@
 // Parareal, Sec. 3 Eq. 8 and Sec. 4), all slices of a batch advanced by every launch.
 //
 // This file holds the flow-phase table and the dispatch to the kernel families
-// (kd_fine2.cu for n <= 256, kd_fine3.cu for n = 512, 1024).  One right-hand-side
+// (kd_fine2.cuh for n <= 256, kd_fine3.cuh for n = 512, 1024, instantiated per
+// precision and grid in kd_fine2_*.cu / kd_fine3_*.cu).  One right-hand-side
 // evaluation nabla_k x (u x b) followed by one IMEX stage is two kernels:
 //   column kernel : mixed M (ky rows, x columns) -> inverse FFT in y -> u x b on the
 //                   grid (u analytic, Sec. 2.1 / 2.2) -> forward FFT in y -> keep
@@ -30,15 +31,28 @@ __constant__ double c_stage[4] = {0.0, 0.5, 2.0 / 3.0, 0.5};
 
 // Flow phases of every (field, step, stage), in double, rounded to T:
 // t = t0[b] + s dt + c_j dt, then (cos(cos t), sin(cos t), cos(sin t), sin(sin t)).
+// With per-slice parameters dt is the field's own, and fields under a steady flow get
+// the constant phases (1, 0, 1, 0).
 template <typename T>
-__global__ void phase_kernel(const double* t0, int batch, int nsteps, double dt, T* out) {
+__global__ void phase_kernel(const double* t0, int batch, int nsteps, double dt, const SliceParams* sp, T* out) {
   const long total = (long)batch * nsteps * 4;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int j = (int)(i & 3);
     const long bs = i >> 2;
     const int s = (int)(bs % nsteps);
     const long b = bs / nsteps;
-    const double t = t0[b] + s * dt + c_stage[j] * dt;
+    double dtb = dt;
+    if (sp) {
+      if (sp[b].flow != FLOW_GP) {
+        out[i * 4 + 0] = T(1);
+        out[i * 4 + 1] = T(0);
+        out[i * 4 + 2] = T(1);
+        out[i * 4 + 3] = T(0);
+        continue;
+      }
+      dtb = sp[b].dt;
+    }
+    const double t = t0[b] + s * dtb + c_stage[j] * dtb;
     const double px = cos(t), py = sin(t);
     out[i * 4 + 0] = (T)cos(px);
     out[i * 4 + 1] = (T)sin(px);
@@ -52,28 +66,78 @@ size_t phase_table_bytes(int prec, long batch, int nsteps) {
 }
 
 int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st) {
-  if (a.flow != FLOW_GP || nsteps <= 0 || a.batch <= 0) return 0;
+  if ((a.flow != FLOW_GP && !a.sp) || nsteps <= 0 || a.batch <= 0) return 0;
   const long total = (long)a.batch * nsteps * 4;
   long g = (total + 255) / 256;
   if (g > 65535L * 16) g = 65535L * 16;
   if (prec == 0)
-    phase_kernel<float><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, (float*)a.phases);
+    phase_kernel<float><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, (float*)a.phases);
   else
-    phase_kernel<double><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, (double*)a.phases);
+    phase_kernel<double><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, (double*)a.phases);
   return 1;
 }
 
-cudaError_t fine_prepare(int prec) {
-  cudaError_t e = fine2_prepare(prec);
-  return e != cudaSuccess ? e : fine3_prepare(prec);
+template <typename T>
+static cudaError_t prepare_all() {
+  cudaError_t e;
+  if ((e = fine2_prep<T, 16>()) != cudaSuccess) return e;
+  if ((e = fine2_prep<T, 32>()) != cudaSuccess) return e;
+  if ((e = fine2_prep<T, 64>()) != cudaSuccess) return e;
+  if ((e = fine2_prep<T, 128>()) != cudaSuccess) return e;
+  if ((e = fine2_prep<T, 256>()) != cudaSuccess) return e;
+  if ((e = fine3_prep<T, 512>()) != cudaSuccess) return e;
+  return fine3_prep<T, 1024>();
+}
+
+cudaError_t fine_prepare(int prec) { return prec == 0 ? prepare_all<float>() : prepare_all<double>(); }
+
+template <typename T>
+static bool variants_T(int n, int* ncol, int* nrow) {
+  switch (n) {
+    case 16: fine2_variants<T, 16>(ncol, nrow); return true;
+    case 32: fine2_variants<T, 32>(ncol, nrow); return true;
+    case 64: fine2_variants<T, 64>(ncol, nrow); return true;
+    case 128: fine2_variants<T, 128>(ncol, nrow); return true;
+    case 256: fine2_variants<T, 256>(ncol, nrow); return true;
+    case 512: fine3_variants<T, 512>(ncol, nrow); return true;
+    case 1024: fine3_variants<T, 1024>(ncol, nrow); return true;
+  }
+  return false;
+}
+
+bool fine_variants(int n, int prec, int* ncol, int* nrow) {
+  return prec == 0 ? variants_T<float>(n, ncol, nrow) : variants_T<double>(n, ncol, nrow);
+}
+
+template <typename T>
+static int run_T(const FineArgs& a, const StepCfg& cfg) {
+  switch (a.n) {
+    case 16: return fine2_run<T, 16>(a, cfg);
+    case 32: return fine2_run<T, 32>(a, cfg);
+    case 64: return fine2_run<T, 64>(a, cfg);
+    case 128: return fine2_run<T, 128>(a, cfg);
+    case 256: return fine2_run<T, 256>(a, cfg);
+    case 512: return fine3_run<T, 512>(a, cfg);
+    case 1024: return fine3_run<T, 1024>(a, cfg);
+  }
+  return -1;
+}
+
+int fine_run(int prec, const FineArgs& a, const StepCfg& cfg) {
+  const int nph = launch_phases(prec, a, cfg.nsteps, cfg.st);
+  const int r = prec == 0 ? run_T<float>(a, cfg) : run_T<double>(a, cfg);
+  return r < 0 ? r : r + nph;
 }
 
 int fine_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
                       const LaunchProbe* pr) {
-  const int nph = launch_phases(prec, a, nsteps, st);
-  const int r = a.n <= 256 ? fine2_launch_steps(prec, a, nsteps, prologue, store_last, st, pr)
-                           : fine3_launch_steps(prec, a, nsteps, prologue, store_last, st, pr);
-  return r < 0 ? r : r + nph;
+  StepCfg cfg;
+  cfg.nsteps = nsteps;
+  cfg.prologue = prologue;
+  cfg.store_last = store_last;
+  cfg.probe = pr;
+  cfg.st = st;
+  return fine_run(prec, a, cfg);
 }
 
 }  // namespace kd

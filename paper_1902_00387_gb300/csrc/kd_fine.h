@@ -12,27 +12,58 @@ struct LaunchProbe {
   void* user;
 };
 
+// Launch plan of the fine kernels: index of the column-kernel and row-kernel variant
+// (tile shape, stage-update style) among those instantiated for the grid and precision;
+// {0, 0} is the default.  Chosen per (n, precision, batch) by the autotuner.
+struct FinePlan {
+  int col = 0;
+  int row = 0;
+};
+
+// One enqueue of fine steps.
+struct StepCfg {
+  int nsteps = 0;
+  bool prologue = true;     // start with the inverse x transform of X (needed unless M holds it)
+  bool store_last = false;  // leave M filled for the state after the last step
+  // host [nsteps]: fields advanced at step s, a prefix of the batch (fields ordered by
+  // decreasing step count); NULL: every field takes every step
+  const int* active = nullptr;
+  const LaunchProbe* probe = nullptr;
+  FinePlan plan;
+  cudaStream_t st = nullptr;
+};
+
 // ---- kd_fine.cu
 cudaError_t fine_prepare(int prec);
 // bytes of the flow-phase table FineArgs::phases for `batch` fields and `nsteps` steps
 size_t phase_table_bytes(int prec, long batch, int nsteps);
-// fill FineArgs::phases (Galloway-Proctor only); returns kernels launched
+// fill FineArgs::phases (Galloway-Proctor, or any batch with per-slice parameters);
+// returns kernels launched
 int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
-// ---- kd_fine3.cu (register-FFT kernels, n = 512, 1024)
-cudaError_t fine3_prepare(int prec);
-int fine3_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
-                       const LaunchProbe* probe);
-// ---- kd_fine2.cu (register-FFT kernels, n <= 256)
-cudaError_t fine2_prepare(int prec);
-int fine2_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last, cudaStream_t st,
-                       const LaunchProbe* probe);
-// Enqueue `nsteps` RK443 steps on the compact state a.X (after filling the phase
-// table a.phases, which must hold phase_table_bytes(prec, a.batch, nsteps)).  prologue: start with the
-// inverse x transform of X (needed unless M already holds it).  store_last: leave M
-// filled for the state after the last step.  Returns the number of kernels launched
-// (negative on an unsupported grid size).
+// number of column / row variants instantiated for (n, prec); false if n is unsupported
+bool fine_variants(int n, int prec, int* ncol, int* nrow);
+// Enqueue cfg.nsteps RK443 steps on the compact state a.X after filling the phase table
+// a.phases (which must hold phase_table_bytes(prec, a.batch, nsteps)).  Returns the
+// number of kernels launched (negative on an unsupported grid size).
+int fine_run(int prec, const FineArgs& a, const StepCfg& cfg);
+// the same with the default plan and every field taking every step
 int fine_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last,
                       cudaStream_t st, const LaunchProbe* probe = nullptr);
+
+// ---- kd_fine2_*.cu (register-FFT kernels, n <= 256) and kd_fine3_*.cu (n = 512, 1024):
+// explicit instantiations per (T, N)
+template <typename T, int N>
+int fine2_run(const FineArgs& a, const StepCfg& cfg);
+template <typename T, int N>
+cudaError_t fine2_prep();
+template <typename T, int N>
+void fine2_variants(int* ncol, int* nrow);
+template <typename T, int N>
+int fine3_run(const FineArgs& a, const StepCfg& cfg);
+template <typename T, int N>
+cudaError_t fine3_prep();
+template <typename T, int N>
+void fine3_variants(int* ncol, int* nrow);
 
 // ---- kd_ops.cu (layout conversions, Parareal update, norms)
 // full [batch][3][n][n] (precision pin) -> compact [batch][3][P][P] (precision pout)

@@ -1,0 +1,4 @@
+// Instantiations of the n <= 256 fine kernels (kd_fine2.cuh): float, n = 128.
+#include "kd_fine2.cuh"
+
+KD_FINE2_INSTANTIATE(float, 128)

@@ -1,0 +1,5 @@
+// Instantiations of the n = 512, 1024 fine kernels (kd_fine3.cuh): double, n = 512 1024.
+#include "kd_fine3.cuh"
+
+KD_FINE3_INSTANTIATE(double, 512)
+KD_FINE3_INSTANTIATE(double, 1024)

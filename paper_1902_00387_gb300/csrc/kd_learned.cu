@@ -68,7 +68,7 @@ int learned_gather(const double* U, const double* Uprev, int Kf, int Pf, float* 
                    cudaStream_t st) {
   const long total = (long)batch * 3 * P * P;
   k_lgather<<<grid1(total), TB, 0, st>>>(U, Uprev, Kf, Pf, x, K, P, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void __launch_bounds__(TB) k_lupdate(const double* Fv, const float* y, int K, int P, double* U, int Kf,
@@ -144,7 +144,7 @@ int learned_to_fine(const float* x, int K, int P, void* X, int prec, int Kf, int
     k_l2f<float><<<grid1(total), TB, 0, st>>>(x, K, P, (cx<float>*)X, Kf, Pf, total);
   else
     k_l2f<double><<<grid1(total), TB, 0, st>>>(x, K, P, (cx<double>*)X, Kf, Pf, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int fine_to_learned(const void* X, int prec, int Kf, int Pf, float* y, int K, int P, long batch, cudaStream_t st) {
@@ -153,7 +153,7 @@ int fine_to_learned(const void* X, int prec, int Kf, int Pf, float* y, int K, in
     k_f2l<float><<<grid1(total), TB, 0, st>>>((const cx<float>*)X, Kf, Pf, y, K, P, total);
   else
     k_f2l<double><<<grid1(total), TB, 0, st>>>((const cx<double>*)X, Kf, Pf, y, K, P, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_f32_f64(const float* x, double* d, long n2) {
@@ -163,7 +163,7 @@ __global__ void k_f32_f64(const float* x, double* d, long n2) {
 
 int learned_f32_to_f64(const float* x, double* d, long n_complex, cudaStream_t st) {
   k_f32_f64<<<grid1(2 * n_complex), TB, 0, st>>>(x, d, 2 * n_complex);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_f64_f32(const double* d, float* x, long n2) {
@@ -173,7 +173,7 @@ __global__ void k_f64_f32(const double* d, float* x, long n2) {
 
 int learned_f64_to_f32(const double* d, float* x, long n_complex, cudaStream_t st) {
   k_f64_f32<<<grid1(2 * n_complex), TB, 0, st>>>(d, x, 2 * n_complex);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_units(double* d, int nc, int j0, long total) {
@@ -188,7 +188,7 @@ __global__ void k_units(double* d, int nc, int j0, long total) {
 int learned_unit_vectors(double* d, int nc, int j0, int count, cudaStream_t st) {
   const long total = (long)count * nc;
   k_units<<<grid1(total), TB, 0, st>>>(d, nc, j0, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_columns(const double* g64, int nc, int ld, int j0, int count, float* W, long total) {
@@ -205,7 +205,7 @@ __global__ void k_columns(const double* g64, int nc, int ld, int j0, int count, 
 int learned_columns(const double* g64, int nc, int ld, int j0, int count, float* W, cudaStream_t st) {
   const long total = (long)nc * count;
   k_columns<<<grid1(total), TB, 0, st>>>(g64, nc, ld, j0, count, W, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // -------------------------------------------------------------------- GEMV
@@ -265,7 +265,7 @@ int learned_gemv(const __nv_bfloat16* W, const float* x, float* y, int nc, int l
   if (ld % 8 != 0 || ld < nc || batch <= 0) return -1;
   dim3 grid((unsigned)((nc + GV_WARPS - 1) / GV_WARPS), (unsigned)batch);
   k_gemv<<<grid, GV_WARPS * 32, 2 * ld * sizeof(float), st>>>(W, x, y, nc, ld);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // -------------------------------------------------------------------- GEMM
@@ -378,7 +378,7 @@ int gemm_bf16_tn(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int 
   if (K % 8 != 0 || M <= 0 || N <= 0) return -1;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   k_gemm_tn<<<grid, 256, 0, st>>>(A, Bt, C, M, N, K, ldc);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // ---------------------------------------------------------------- training
@@ -401,7 +401,7 @@ __global__ void k_pack_x(const float* x, int m, int nc, int ld, __nv_bfloat16* X
 int learned_pack_x(const float* x, int m, int nc, int ld, __nv_bfloat16* Xs, __nv_bfloat16* XtT, cudaStream_t st) {
   const long total = (long)m * ld;
   k_pack_x<<<grid1(total), TB, 0, st>>>(x, m, nc, ld, Xs, XtT, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_transpose_y(const float* y, int m, int nc, float* yT, long total) {
@@ -416,7 +416,7 @@ __global__ void k_transpose_y(const float* y, int m, int nc, float* yT, long tot
 int learned_transpose_y(const float* y, int m, int nc, float* yT, cudaStream_t st) {
   const long total = (long)m * nc;
   k_transpose_y<<<grid1(total), TB, 0, st>>>(y, m, nc, yT, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void __launch_bounds__(TB) k_residual(const float* C1, const float* yT, int m, int nc,
@@ -498,7 +498,7 @@ __global__ void k_momentum(float* W, const float* W0, const float* C2, float* v,
 int learned_momentum(float* W, const float* W0, const float* C2, float* v, __nv_bfloat16* Wbf, long count,
                      float scale, float wd, float eta, float mu, cudaStream_t st) {
   k_momentum<<<grid1(count), TB, 0, st>>>(W, W0, C2, v, Wbf, count, scale, wd, eta, mu);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_grad(const float* W, const float* W0, const float* C2, float* grad, long count, float scale,
@@ -512,7 +512,7 @@ __global__ void k_grad(const float* W, const float* W0, const float* C2, float* 
 int learned_grad(const float* W, const float* W0, const float* C2, float* grad, long count, float scale, float wd,
                  cudaStream_t st) {
   k_grad<<<grid1(count), TB, 0, st>>>(W, W0, C2, grad, count, scale, wd);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_f2bf(const float* x, __nv_bfloat16* y, long count) {
@@ -522,7 +522,7 @@ __global__ void k_f2bf(const float* x, __nv_bfloat16* y, long count) {
 
 int f32_to_bf16(const float* x, __nv_bfloat16* y, long count, cudaStream_t st) {
   k_f2bf<<<grid1(count), TB, 0, st>>>(x, y, count);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void __launch_bounds__(TB) k_sum(const double* p, int count, double* out) {
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(TB) k_sum(const double* p, int count, double* 
 
 int sum_partials(const double* p, int count, double* out, cudaStream_t st) {
   k_sum<<<1, TB, 0, st>>>(p, count, out);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void __launch_bounds__(TB) k_diff_norms(const float* a, const float* b, long count, double* partials) {

@@ -68,21 +68,21 @@ static int f2c(const void* full, void* comp, long batch, int n, cudaStream_t st)
   const int K = n / 3, P = 2 * K + 1;
   const long total = batch * 3 * (long)P * P;
   k_full_to_compact<Ti, To><<<grid_for(total), 256, 0, st>>>((const cx<Ti>*)full, (cx<To>*)comp, total, n, K, P);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 template <typename Ti, typename To>
 static int c2f(const void* comp, void* full, long batch, int n, cudaStream_t st) {
   const int K = n / 3, P = 2 * K + 1;
   const long total = batch * 3 * (long)n * n;
   k_compact_to_full<Ti, To><<<grid_for(total), 256, 0, st>>>((const cx<Ti>*)comp, (cx<To>*)full, total, n, K, P);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 template <typename Ti, typename To>
 static int rs(const void* src, int ns, void* dst, int nd, long batch, cudaStream_t st) {
   const int Ks = ns / 3, Kd = nd / 3;
   const long total = batch * 3 * (long)(2 * Kd + 1) * (2 * Kd + 1);
   k_resample<Ti, To><<<grid_for(total), 256, 0, st>>>((const cx<Ti>*)src, Ks, 2 * Ks + 1, (cx<To>*)dst, Kd, 2 * Kd + 1, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int full_to_compact(int pin, const void* full, int pout, void* comp, long batch, int n, cudaStream_t st) {
@@ -130,7 +130,7 @@ int delta_in(int pout, const double* U, double* Uprev, void* X, long total, int 
     k_delta_in<float><<<grid_for(total), 256, 0, st>>>((const cx<double>*)U, (cx<double>*)Uprev, (cx<float>*)X, total, first);
   else
     k_delta_in<double><<<grid_for(total), 256, 0, st>>>((const cx<double>*)U, (cx<double>*)Uprev, (cx<double>*)X, total, first);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int accum_out(int pin, const void* X, double* Fv, long total, int first, cudaStream_t st) {
@@ -138,7 +138,7 @@ int accum_out(int pin, const void* X, double* Fv, long total, int first, cudaStr
     k_accum_out<float><<<grid_for(total), 256, 0, st>>>((const cx<float>*)X, (cx<double>*)Fv, total, first);
   else
     k_accum_out<double><<<grid_for(total), 256, 0, st>>>((const cx<double>*)X, (cx<double>*)Fv, total, first);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_diff(const double* U, const double* Uprev, double* d, long total) {
@@ -148,7 +148,7 @@ __global__ void k_diff(const double* U, const double* Uprev, double* d, long tot
 
 int diff_kernel(const double* U, const double* Uprev, double* d, long total, cudaStream_t st) {
   k_diff<<<grid_for(2 * total), 256, 0, st>>>(U, Uprev, d, total);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // ------------------------------------------------------------ parareal update
@@ -248,7 +248,7 @@ __global__ void k_finish_sigma(const double* partials, int nb, double* out) {
 
 int finish_sigma(const double* partials, int nblocks, double* out, cudaStream_t st) {
   k_finish_sigma<<<1, 256, 0, st>>>(partials, nblocks, out);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // ---------------------------------------------------------------- energies
@@ -269,7 +269,7 @@ __global__ void k_energy(const cx<double>* f, long len, double* E) {
 int energy_kernel(const double* fields, long len, int count, double* E, cudaStream_t st) {
   if (count <= 0) return 0;
   k_energy<<<count, 256, 0, st>>>((const cx<double>*)fields, len, E);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_growth_fit(const double* E, int count, double dt, double fit_from, double* out) {
@@ -300,7 +300,7 @@ __global__ void k_growth_fit(const double* E, int count, double dt, double fit_f
 
 int growth_fit(const double* E, int count, double dt, double fit_from, double* out, cudaStream_t st) {
   k_growth_fit<<<1, 32, 0, st>>>(E, count, dt, fit_from, out);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 __global__ void k_fill_times(double* dst, int count, double t0, double dT) {
@@ -311,7 +311,7 @@ __global__ void k_fill_times(double* dst, int count, double t0, double dT) {
 int fill_times(double* dst, int count, double t0, double dT, cudaStream_t st) {
   if (count <= 0) return 0;
   k_fill_times<<<nblk(count, 256), 256, 0, st>>>(dst, count, t0, dT);
-  return (int)cudaGetLastError();
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace kd

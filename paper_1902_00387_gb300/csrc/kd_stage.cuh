@@ -2,6 +2,8 @@
 // u(x, y, t) (Sec. 2.1 / 2.2), the cross product u x b, the spectral curl
 // i k3 x w_hat, and the IMEX RK443 stage update with diagonal implicit diffusion.
 #pragma once
+#include <type_traits>
+
 #include "kd_common.cuh"
 
 namespace kd {
@@ -29,6 +31,34 @@ __device__ __forceinline__ Phase<T> load_phase(const FineArgs& a, long b, int st
     p.spy = T(0);
   }
   return p;
+}
+
+// Flow amplitude of field b.
+template <typename T>
+__device__ __forceinline__ T flow_amp(const FineArgs& a, long b) {
+  return a.sp ? (T)a.sp[b].amp : (T)a.amp;
+}
+
+// Per-field coefficients of the stage update: dt, kz and 1 / Rm in precision T.
+template <typename T>
+struct StageCoef {
+  T dt, kz, inv_rm;
+};
+
+template <typename T>
+__device__ __forceinline__ StageCoef<T> stage_coef(const FineArgs& a, long b) {
+  StageCoef<T> q;
+  if (a.sp) {
+    const SliceParams& p = a.sp[b];
+    q.dt = (T)p.dt;
+    q.kz = (T)p.kz;
+    q.inv_rm = T(1) / (T)p.Rm;
+  } else {
+    q.dt = (T)a.dt;
+    q.kz = (T)a.kz;
+    q.inv_rm = T(1) / (T)a.Rm;
+  }
+  return q;
 }
 
 // w = u x b at the grid point with cos/sin of x and y given;
@@ -67,17 +97,17 @@ __device__ __forceinline__ StageArrays<T> stage_arrays(const FineArgs& a) {
 
 // One IMEX RK443 stage at spectral point s (index into the compact arrays) for the
 // three components: w_hat (already scaled by 1/n^2) -> F = i k3 x w_hat -> new stage
-// value (returned in w).  mode = stage 0..3.
-template <typename T>
-__device__ __forceinline__ void stage_update(const FineArgs& a, const StageArrays<T>& sa, int mode, long s0,
-                                             long cstride, T fkx, T fky, cx<T>& w0, cx<T>& w1, cx<T>& w2) {
-  const T dt = (T)a.dt;
-  const T kz = (T)a.kz;
+// value (returned in w).  MODE = stage 0..3.
+template <int MODE, typename T>
+__device__ __forceinline__ void stage_update(const StageCoef<T>& q, const StageArrays<T>& sa, long s0, long cstride,
+                                             T fkx, T fky, cx<T>& w0, cx<T>& w1, cx<T>& w2) {
+  const T dt = q.dt;
+  const T kz = q.kz;
   cx<T> F[3];
   F[0] = mul_i(w2 * fky - w1 * kz);
   F[1] = mul_i(w0 * kz - w2 * fkx);
   F[2] = mul_i(w1 * fkx - w0 * fky);
-  const T lam = (fkx * fkx + fky * fky + kz * kz) * (T(1) / (T)a.Rm);
+  const T lam = (fkx * fkx + fky * fky + kz * kz) * q.inv_rm;
   const T inv_d = T(1) / (T(1) + dt * T(0.5) * lam);
   const T dl = dt * lam;
   cx<T>* __restrict__ X = sa.X;
@@ -89,19 +119,19 @@ __device__ __forceinline__ void stage_update(const FineArgs& a, const StageArray
   for (int c = 0; c < 3; ++c) {
     const long s = s0 + c * cstride;
     const cx<T> f = F[c];
-    if (mode == 0) {
+    if (MODE == 0) {
       const cx<T> x0 = X[s];
       const cx<T> x1 = (x0 + f * (dt * T(0.5))) * inv_d;
       R2[s] = x0 + f * (dt * T(11.0 / 18.0)) - x1 * (dl * T(1.0 / 6.0));
       R3[s] = x0 + f * (dt * T(5.0 / 6.0)) + x1 * (dl * T(0.5));
       R4[s] = x0 + f * (dt * T(0.25)) - x1 * (dl * T(1.5));
       out[c] = x1;
-    } else if (mode == 1) {
+    } else if (MODE == 1) {
       const cx<T> x2 = (R2[s] + f * (dt * T(1.0 / 18.0))) * inv_d;
       R3[s] = R3[s] - f * (dt * T(5.0 / 6.0)) - x2 * (dl * T(0.5));
       R4[s] = R4[s] + f * (dt * T(1.75)) + x2 * (dl * T(1.5));
       out[c] = x2;
-    } else if (mode == 2) {
+    } else if (MODE == 2) {
       const cx<T> x3 = (R3[s] + f * (dt * T(0.5))) * inv_d;
       R4[s] = R4[s] + f * (dt * T(0.75)) - x3 * (dl * T(0.5));
       out[c] = x3;
@@ -114,6 +144,18 @@ __device__ __forceinline__ void stage_update(const FineArgs& a, const StageArray
   w0 = out[0];
   w1 = out[1];
   w2 = out[2];
+}
+
+// Call f(std::integral_constant<int, m>) for the runtime stage index m = 0..3, so that
+// the stage update of a loop body is specialised for its stage.
+template <class F>
+__device__ __forceinline__ void with_stage(int mode, F&& f) {
+  switch (mode) {
+    case 0: f(std::integral_constant<int, 0>()); break;
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    default: f(std::integral_constant<int, 3>()); break;
+  }
 }
 
 }  // namespace kd

@@ -132,6 +132,7 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   q += 2 * mixed;
   a.phases = phase ? q : nullptr;
   a.phase_steps = nsteps;
+  a.sp = nullptr;
   a.tw = tw;
   a.cosg = cg;
   a.sing = sg;

@@ -22,6 +22,7 @@ KD_C64, KD_C128 = 0, 1
 KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
 KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
 KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
+KD_GRID_FINE, KD_GRID_COARSE = 0, 1
 KD_MAX_SLICES = 1024
 KD_MAX_ITERS = 256
 
@@ -49,11 +50,30 @@ class kd_parareal_stats(ctypes.Structure):
                 ("fallback_used", ctypes.c_int), ("n_launches", ctypes.c_longlong)]
 
 
+class kd_instance(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int), ("n", ctypes.c_int), ("kz", ctypes.c_double), ("Rm", ctypes.c_double),
+                ("dt_fine", ctypes.c_double), ("n_coarse", ctypes.c_int), ("dt_coarse", ctypes.c_double)]
+
+
+class kd_instance_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("k_con", ctypes.c_int), ("n_fine_steps", ctypes.c_int),
+                ("n_coarse_steps", ctypes.c_int), ("dt_fine_used", ctypes.c_double),
+                ("dt_coarse_used", ctypes.c_double), ("sigma", ctypes.c_double * KD_MAX_ITERS),
+                ("growth_rate", ctypes.c_double)]
+
+
+class kd_sweep_stats(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_fine", ctypes.c_double),
+                ("ms_coarse", ctypes.c_double), ("n_launches", ctypes.c_longlong),
+                ("fine_dof_steps", ctypes.c_double)]
+
+
 _lib = None
 EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
            "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
-           "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply"]
+           "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
+           "kd_get_plan", "kd_autotune", "kd_sweep_run"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -82,6 +102,13 @@ def load():
         "kd_learned_eval": (I, [P, P, P, P, I, P, P]),
         "kd_learned_loss_grad": (I, [P, P, P, ctypes.c_float, P, P, I, ctypes.POINTER(D), P]),
         "kd_learned_apply": (I, [P, P, P, I, I]),
+        "kd_plan_variants": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "kd_set_plan": (I, [P, I, I, I]),
+        "kd_get_plan": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "kd_autotune": (I, [P, I, I, I, ctypes.c_char_p, ctypes.POINTER(D)]),
+        "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
+                             ctypes.POINTER(P), ctypes.POINTER(kd_instance_result), ctypes.POINTER(kd_sweep_stats),
+                             P, ctypes.c_char_p]),
         "kd_launch_count": (ctypes.c_longlong, [P]),
         "kd_profile": (I, [P, I]),
         "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
@@ -272,6 +299,59 @@ def kd_learned_loss_grad(ctx, W, W0, weight_decay, x, y, n, grad):
 
 def kd_learned_apply(ctx, x, y, phase, n):
     return _check(ctx, load().kd_learned_apply(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), int(phase), int(n)))
+
+
+def kd_plan_variants(ctx, grid=KD_GRID_FINE):
+    """(number of column variants, number of row variants) of a grid."""
+    c, r = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().kd_plan_variants(ctx, int(grid), ctypes.byref(c), ctypes.byref(r)))
+    return c.value, r.value
+
+
+def kd_set_plan(ctx, grid, col, row):
+    return _check(ctx, load().kd_set_plan(ctx, int(grid), int(col), int(row)))
+
+
+def kd_get_plan(ctx, grid=KD_GRID_FINE):
+    c, r = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().kd_get_plan(ctx, int(grid), ctypes.byref(c), ctypes.byref(r)))
+    return c.value, r.value
+
+
+def kd_autotune(ctx, grid, batch, nsteps=2, cache_path=None):
+    """Autotune a grid's plan; returns the chosen plan's ms per step (-1 if read from the cache)."""
+    ms = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(ctx, load().kd_autotune(ctx, int(grid), int(batch), int(nsteps), path, ctypes.byref(ms)))
+    return ms.value
+
+
+def make_instance(flow, n, kz, Rm, dt_fine, n_coarse, dt_coarse):
+    return kd_instance(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(n_coarse), float(dt_coarse))
+
+
+def kd_sweep_run(instances, b0, T, n_slices, k_max, tol, u_final=None, tune_cache=None, stream=None):
+    """Batched Parareal over independent instances.  b0 / u_final: lists of complex128
+    [3][n_i][n_i] buffers (numpy arrays or tensors, host or device; u_final entries may be
+    None).  Returns (status, results list, stats)."""
+    lib = load()
+    m = len(instances)
+    arr = (kd_instance * m)(*instances)
+    keep = list(b0) + [u for u in (u_final or []) if u is not None]
+    b_ptrs = (ctypes.c_void_p * m)(*[_any_ptr(b, "complex128") for b in b0])
+    u_ptrs = None
+    if u_final is not None:
+        u_ptrs = (ctypes.c_void_p * m)(*[_any_ptr(u, "complex128") if u is not None else None for u in u_final])
+    res = (kd_instance_result * m)()
+    st = kd_sweep_stats()
+    err = ctypes.create_string_buffer(256)
+    strm = _current_stream() if stream is None else stream
+    s = lib.kd_sweep_run(arr, m, b_ptrs, float(T), int(n_slices), int(k_max), float(tol),
+                         tune_cache.encode() if tune_cache else None, u_ptrs, res, ctypes.byref(st), strm, err)
+    del keep
+    if s not in (KD_OK, KD_ENOTCONV):
+        raise KdError(s, err.value.decode())
+    return s, list(res), st
 
 
 def kd_launch_count(ctx):

@@ -55,24 +55,27 @@ def test_version_and_argument_validation_without_gpu(lib):
 
 
 def test_struct_layout_matches_header(lib, tmp_path):
-    """ctypes mirrors of kd_params / kd_parareal_stats have the C compiler's layout."""
+    """Every ctypes mirror of a header struct has the C compiler's size and field offsets."""
     import shutil
     import subprocess
     import paper_1902_00387_gb300 as kd
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
+    structs = [kd.kd_params, kd.kd_parareal_stats, kd.kd_instance, kd.kd_instance_result, kd.kd_sweep_stats]
+    exprs, want = [], []
+    for st in structs:
+        name = st.__name__
+        exprs.append("sizeof(%s)" % name)
+        want.append(ctypes.sizeof(st))
+        for fname, _ in st._fields_:
+            exprs.append("offsetof(%s, %s)" % (name, fname))
+            want.append(getattr(st, fname).offset)
     probe = tmp_path / "probe.c"
-    probe.write_text(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "kd.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kd_params), offsetof(kd_params, n_coarse), offsetof(kd_params, fine_form),'
-        ' sizeof(kd_parareal_stats), offsetof(kd_parareal_stats, sigma), offsetof(kd_parareal_stats, growth_rate),'
-        ' offsetof(kd_parareal_stats, fallback_used), offsetof(kd_parareal_stats, n_launches)); return 0;}\n')
+    body = "".join('printf("%%zu\\n", (size_t)%s);' % e for e in exprs)
+    probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kd.h"\nint main(void){' + body +
+                     ' return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [ctypes.sizeof(kd.kd_params), kd.kd_params.n_coarse.offset, kd.kd_params.fine_form.offset,
-            ctypes.sizeof(kd.kd_parareal_stats),
-            kd.kd_parareal_stats.sigma.offset, kd.kd_parareal_stats.growth_rate.offset,
-            kd.kd_parareal_stats.fallback_used.offset, kd.kd_parareal_stats.n_launches.offset]
-    assert got == want
+    assert got == want, [(e, g, w) for e, g, w in zip(exprs, got, want) if g != w]

@@ -29,10 +29,12 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def run_fine(kd, flow, n, kz, Rm, dt, prec, b, t0, nsteps):
+def run_fine(kd, flow, n, kz, Rm, dt, prec, b, t0, nsteps, plan=None):
     import torch
     ctx = kd.kd_create(kd.make_params(flow, n, kz, Rm, dt, prec))
     try:
+        if plan is not None:
+            kd.kd_set_plan(ctx, kd.KD_GRID_FINE, *plan)
         dtype = torch.complex128 if prec == kd.KD_C128 else torch.complex64
         x = torch.tensor(b, dtype=dtype, device="cuda")
         y = torch.empty_like(x)
@@ -76,6 +78,70 @@ def test_large_grids_fp32(kd, n):
     out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, [2.0], 2)
     ref = O.propagate(b[0], O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm), 2.0, dt, 2)
     assert rel(out[0], ref) < TOL32
+
+
+@pytest.mark.parametrize("n", [32, 128, 256, 512])
+def test_every_launch_plan_matches_oracle(kd, n):
+    """Every instantiated (column, row) kernel variant: same oracle parity, and the same
+    values as the default plan to FP32 round-off (the variants change tiles and where
+    the stage update runs, not the arithmetic)."""
+    kz, Rm, dt = 0.57, 100.0, 5e-3
+    seeds = [31, 32, 33] if n <= 256 else [31]
+    t0 = [0.3, 1.1, 2.9][:len(seeds)]
+    b = I.initial_batch(n, kz, seeds)
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64))
+    try:
+        ncol, nrow = kd.kd_plan_variants(ctx, kd.KD_GRID_FINE)
+    finally:
+        kd.kd_destroy(ctx)
+    assert ncol >= 2 and nrow >= 4
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    refs = [O.propagate(b[i], p, t0[i], dt, 2) for i in range(len(seeds))]
+    base = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, t0, 2, plan=(0, 0))
+    for c in range(ncol):
+        for r in range(nrow):
+            out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, t0, 2, plan=(c, r))
+            for i in range(len(seeds)):
+                assert rel(out[i], refs[i]) < TOL32, (c, r, i)
+                assert rel(out[i], base[i]) < 1e-6, (c, r, i)
+
+
+def test_plan_api_validation(kd):
+    ctx = kd.kd_create(kd.make_params(O.ROBERTS, 64, 1.0, 8.0, 1e-2, kd.KD_C64))
+    try:
+        ncol, nrow = kd.kd_plan_variants(ctx, kd.KD_GRID_FINE)
+        kd.kd_set_plan(ctx, kd.KD_GRID_FINE, ncol - 1, nrow - 1)
+        assert kd.kd_get_plan(ctx, kd.KD_GRID_FINE) == (ncol - 1, nrow - 1)
+        for bad in ((ncol, 0), (0, nrow), (-1, 0)):
+            with pytest.raises(kd.KdError):
+                kd.kd_set_plan(ctx, kd.KD_GRID_FINE, *bad)
+        with pytest.raises(kd.KdError):
+            kd.kd_set_plan(ctx, 7, 0, 0)
+    finally:
+        kd.kd_destroy(ctx)
+
+
+def test_autotune_picks_a_plan_and_caches_it(kd, tmp_path):
+    import json
+    cache = str(tmp_path / "tune.json")
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, 128, 0.57, 100.0, 5e-3, kd.KD_C64))
+    try:
+        ms = kd.kd_autotune(ctx, kd.KD_GRID_FINE, 16, 2, cache)
+        assert ms > 0
+        plan = kd.kd_get_plan(ctx, kd.KD_GRID_FINE)
+        data = json.load(open(cache))
+        ent = [e for e in data["entries"] if e["n"] == 128 and e["batch"] == 16]
+        assert len(ent) == 1 and (ent[0]["col"], ent[0]["row"]) == plan
+        # a second context reads the plan from the cache without timing
+        kd.kd_set_plan(ctx, kd.KD_GRID_FINE, 0, 0)
+        assert kd.kd_autotune(ctx, kd.KD_GRID_FINE, 13, 2, cache) == -1.0   # 13 -> key 16
+        assert kd.kd_get_plan(ctx, kd.KD_GRID_FINE) == plan
+        # a second key is appended, the first kept
+        kd.kd_autotune(ctx, kd.KD_GRID_FINE, 40, 1, cache)
+        keys = sorted(e["batch"] for e in json.load(open(cache))["entries"])
+        assert keys == [16, 64]
+    finally:
+        kd.kd_destroy(ctx)
 
 
 def test_roberts_slice_fp64_config1(kd):

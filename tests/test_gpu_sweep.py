@@ -1,0 +1,116 @@
+"""Batched sweep of independent Parareal instances (kd_sweep_run): per-instance parity
+with the CPU oracle's Parareal and serial fine solutions, with instances of different
+grids, flows, kz, Rm and step counts in one call."""
+import math
+
+import numpy as np
+import pytest
+
+import kd_inputs as I
+from oracle import kd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    return kd
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+# (flow, n, kz, Rm, dt_fine, n_coarse, dt_coarse): two grids, both flows, uneven steps
+INSTANCES = [
+    (O.GALLOWAY_PROCTOR, 32, 0.57, 100.0, 0.02, 16, 0.05),
+    (O.ROBERTS, 32, 1.0, 8.0, 0.025, 16, 0.05),
+    (O.GALLOWAY_PROCTOR, 32, 1.3, 400.0, 0.0125, 16, 0.025),
+    (O.ROBERTS, 16, 0.4, 60.0, 0.05, 16, 0.1),
+    (O.GALLOWAY_PROCTOR, 16, 0.9, 20.0, 0.04, 16, 0.1),
+]
+T, N = 2.0, 4
+
+
+def oracle_parareal(inst, b0, k_max, tol):
+    flow, n, kz, Rm, dt, nc, dtc = inst
+    prob = O.Problem(flow, n, kz, Rm)
+    dT = T / N
+    S, Sc = math.ceil(dT / dt - 1e-9), math.ceil(dT / dtc - 1e-9)
+    fine = lambda u, i: O.propagate(u, prob, i * dT, dT / S, S)
+    coarse = lambda u, i: O.coarse_propagate(u, prob, nc, i * dT, dT / Sc, Sc)
+    return O.parareal(b0, fine, coarse, N, k_max, tol), O.serial_fine(b0, fine, N)
+
+
+def run_sweep(kd, insts, seeds, k_max, tol, tune_cache=None):
+    ins = [kd.make_instance(*x) for x in insts]
+    b0 = [I.initial_field(x[1], x[2], s).astype(np.complex128) for x, s in zip(insts, seeds)]
+    out = [np.zeros_like(b) for b in b0]
+    status, res, st = kd.kd_sweep_run(ins, b0, T, N, k_max, tol, u_final=out, tune_cache=tune_cache)
+    return status, res, st, b0, out
+
+
+def test_sweep_matches_oracle_per_instance(kd):
+    seeds = [101, 102, 103, 104, 105]
+    status, res, st, b0, out = run_sweep(kd, INSTANCES, seeds, N, 1e-9)
+    assert st.n_groups == 2
+    for i, inst in enumerate(INSTANCES):
+        par, ser = oracle_parareal(inst, b0[i], N, 1e-9)
+        r = res[i]
+        # defects of the first iterations are set by the method, not by rounding
+        ks = min(r.k_con, par["k_con"], 3)
+        for k in range(ks):
+            if par["sigma"][k] > 1e-4:
+                assert abs(r.sigma[k] - par["sigma"][k]) < 1e-3 * par["sigma"][k], (i, k, r.sigma[k], par["sigma"][k])
+        # the final state is the serial fine solution at FP32 accuracy
+        assert rel(out[i], ser[-1]) < 2e-5, (i, rel(out[i], ser[-1]))
+        assert r.n_fine_steps == math.ceil((T / N) / inst[4] - 1e-9)
+
+
+def test_sweep_iterates_match_oracle_iterates(kd):
+    """k_max = 2 stops early: the state is the oracle's second Parareal iterate."""
+    seeds = [201, 202, 203, 204, 205]
+    status, res, st, b0, out = run_sweep(kd, INSTANCES, seeds, 2, 0.0)
+    assert status == kd.KD_ENOTCONV
+    for i, inst in enumerate(INSTANCES):
+        par, _ = oracle_parareal(inst, b0[i], 2, 0.0)
+        assert res[i].k_con == 2 and res[i].status == kd.KD_ENOTCONV
+        assert rel(out[i], par["U"][-1]) < 2e-5, (i, rel(out[i], par["U"][-1]))
+
+
+def test_sweep_single_instance_equals_parareal_run_order_of_magnitude(kd):
+    """One GP instance alone: the sweep converges to the same tolerance as
+    kd_parareal_run in the increment form, and both give the serial fine state."""
+    inst = INSTANCES[0]
+    status, res, st, b0, out = run_sweep(kd, [inst], [301], 16, 1e-6)
+    assert status == kd.KD_OK and res[0].status == kd.KD_OK
+    _, ser = oracle_parareal(inst, b0[0], 1, 0.0)
+    assert rel(out[0], ser[-1]) < 2e-5
+    assert res[0].sigma[res[0].k_con - 1] <= 1e-6
+
+
+def test_sweep_with_autotuned_plan(kd, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    seeds = [401, 402, 403, 404, 405]
+    status, res, st, b0, out = run_sweep(kd, INSTANCES, seeds, N, 1e-9, tune_cache=cache)
+    for i, inst in enumerate(INSTANCES):
+        _, ser = oracle_parareal(inst, b0[i], 1, 0.0)
+        assert rel(out[i], ser[-1]) < 2e-5
+    import json
+    assert len(json.load(open(cache))["entries"]) == 2    # one fine plan per group
+
+
+def test_sweep_argument_errors(kd):
+    ins = [kd.make_instance(*INSTANCES[0])]
+    b0 = [I.initial_field(32, 0.57, 1).astype(np.complex128)]
+    with pytest.raises(kd.KdError):
+        kd.kd_sweep_run(ins, b0, T, 0, 4, 1e-6)
+    bad = [kd.make_instance(O.ROBERTS, 48, 1.0, 8.0, 0.01, 16, 0.1)]
+    with pytest.raises(kd.KdError):
+        kd.kd_sweep_run(bad, b0, T, N, 4, 1e-6)
