@@ -271,6 +271,137 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------ batched sweep of independent instances
+SWEEP_WL = {
+    "workload": "rm_kz_sweep_parareal_32_slices",
+    "slices": 32, "T": 8 * math.pi, "tol": 1e-6, "k_max": 32, "seed0": 1000,
+    "recipe": "flow Roberts (even seed) / Galloway-Proctor (odd); Rm log-uniform [50, 3200]; n = 64 sqrt(Rm/50) "
+              "rounded in log2 to [64, 512]; kz uniform [0.2, 1.5]; GP dt = 0.128/n, Roberts dt = 1.6/n; "
+              "n_coarse = n/2; coarse dt = min(20 dt (GP) or 10 dt (Roberts), 2/n_coarse)",
+}
+
+
+def sweep_instances(kd, count, seed0):
+    """The sweep's instances (parameters from kd_inputs.sweep_instance) and seeds."""
+    import kd_inputs
+    out = []
+    for i in range(count):
+        seed = seed0 + i
+        q = kd_inputs.sweep_instance(seed)
+        n, flow = q["n"], q["flow"]
+        if flow == kd.KD_FLOW_GALLOWAY_PROCTOR:
+            dt, ratio = 0.128 / n, 20
+        else:
+            dt, ratio = 1.6 / n, 10
+        nc = n // 2
+        dtc = min(ratio * dt, 2.0 / nc)     # explicit stability of the coarse grid
+        out.append((seed, kd.make_instance(flow, n, q["kz"], q["Rm"], dt, nc, dtc), q))
+    return out
+
+
+def run_sweep(args):
+    """Config 3: `--sweep-count` independent Parareal instances per rank in one
+    kd_sweep_run call per step (ranks take disjoint seed ranges: weak scaling)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    W = dict(SWEEP_WL, count_per_rank=args.sweep_count)
+    N, T = W["slices"], W["T"]
+    insts = sweep_instances(kd, args.sweep_count, W["seed0"] + rank * args.sweep_count)
+    b0_host = [torch.tensor(kd_inputs.initial_field(q.n, q.kz, seed)).pin_memory() for seed, q, _ in insts]
+    b0_dev = [b.cuda() for b in b0_host]
+    u_dev = [torch.zeros_like(b) for b in b0_dev]
+    u_host = [torch.zeros_like(b).pin_memory() for b in b0_host]
+    ins = [q for _, q, _ in insts]
+    cache = os.path.join(tempfile.gettempdir(), "kd_tune_cache.json")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve(b0, out):
+        s, res, st = kd.kd_sweep_run(ins, b0, T, N, W["k_max"], W["tol"], u_final=out, tune_cache=cache)
+        return s, res, st
+
+    for _ in range(args.warmup):
+        solve(b0_dev, u_dev)
+
+    def timed(b0, out, steps, clocks=None):
+        res = []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        t = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            res.append(solve(b0, out))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        ck = clocks.stop() if clocks else None
+        if world > 1:
+            tt = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = tt.item()
+        return el, res, ck
+
+    el, res, clk = timed(b0_dev, u_dev, args.steps, ClockSampler(local))
+    s, results, st = res[-1]
+    # serial-fine-equivalent work of one solve: every instance's N x S fine steps
+    units = sum(3 * q.n ** 2 * N * r.n_fine_steps for q, r in zip(ins, results))
+    value = units * world * args.steps / el / 1e6
+    # fine work actually done and its two-pass algorithmic bytes
+    fine_bytes = 0.0
+    for q, r in zip(ins, results):
+        cb, rb = col_row_bytes(q.n, 1)
+        per_slice_step = 4 * (cb + rb)
+        fine_bytes += sum(N - min(k - 1, N - 1) for k in range(1, r.k_con + 1)) * r.n_fine_steps * per_slice_step
+    hbm_peak, peak_kind = peaks()
+    achieved = fine_bytes / (st.ms_fine / 1e3) / 1e9
+    el_e2e, _, _ = timed(b0_host, u_host, max(1, args.steps // 2))
+    e2e_value = units * world * max(1, args.steps // 2) / el_e2e / 1e6
+    nbytes = sum(b.numel() * 16 for b in b0_host)
+    ks = [r.k_con for r in results]
+    by_n = {}
+    for q, r in zip(ins, results):
+        by_n.setdefault(q.n, []).append(r.k_con)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 fine / f64 update", "data": "synthetic",
+        "config": dict(W, l2="flushed between steps (512 MB write)",
+                       parallelism="instances x slices in one batched launch per grid; ranks take disjoint seeds"),
+        "instances_by_n": {str(k): len(v) for k, v in sorted(by_n.items())},
+        "k_con_by_n": {str(k): v for k, v in sorted(by_n.items())},
+        "converged": sum(1 for r in results if r.status == kd.KD_OK), "k_con_max": max(ks),
+        "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse, "total": st.ms_total},
+        "fine_mdof_steps_per_s": st.fine_dof_steps / (st.ms_fine / 1e3) / 1e6,
+        "roofline": {"bound": "hbm", "kernel": "fine phase (column + row kernels, increment gather/scatter)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_kind": peak_kind},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(st.n_launches) * args.steps,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -288,8 +419,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal", choices=["parareal", "learned"],
-                    help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2")
+    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep"],
+                    help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
+                         "sweep: batched independent instances (Rm / kz sweep)")
+    ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -297,6 +430,9 @@ def main():
         return
     if args.config == "learned":
         run_learned(args)
+        return
+    if args.config == "sweep":
+        run_sweep(args)
         return
 
     import numpy as np

@@ -1,6 +1,6 @@
 // Classical coarse propagator G (Sec. 3.2, Sec. 5.2: the same equations on the coarse
 // N_C grid with the coarse step) as one persistent thread-block cluster per field for
-// coarse sets of side <= 64,
+// coarse sets of side <= 88 (coarse grids up to 128),
 // fused with the Fourier restriction of the fine input and, in the Parareal sweep,
 // with the FP64 update U_{n+1} = F + (G_new - G_old) and the defect of Eq. 9.
 //
@@ -69,7 +69,14 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   cx<T>* buf = (cx<T>*)smem_raw;                  // [2][3][LH][L]
   T* s_ph = (T*)(buf + 2 * 3 * LH * L);           // [nsteps][4][4] when staged
   const int bufsz = 3 * LH * L;
-  const double* Un = a.Un + (long)b * 2 * 3 * Pf * Pf;
+  const long lenf2 = 2L * 3 * Pf * Pf;            // doubles per fine compact field
+  const long slot = a.map ? (long)a.map[b] : (long)b;
+  const double* Un = a.Un + slot * lenf2;
+  const double* Uprev = a.Uprev ? a.Uprev + (a.map ? slot * lenf2 : 0) : nullptr;
+  const double* Fv = a.Fv ? a.Fv + (a.map ? slot * lenf2 : 0) : nullptr;
+  double* Unext = a.Unext ? a.Unext + (a.map ? (slot + 1) * lenf2 : 0) : nullptr;
+  double* sig = a.sigma_out ? a.sigma_out + (a.map ? 3L * b : 0) : nullptr;
+  const int nsteps = a.steps ? a.steps[b] : a.nsteps;
   for (int i = threadIdx.x; i < 2 * bufsz; i += CCB) buf[i] = mk(T(0), T(0));
   const bool stage_ph = a.phases && a.nsteps * 16 <= a.phase_smem;
   const T* ph_g = a.phases ? (const T*)a.phases + (long)b * a.nsteps * 16 : nullptr;
@@ -80,7 +87,8 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   const int M = hr * P;
   cx<T> x0[MPT][3], r2[MPT][3], r3[MPT][3], r4[MPT][3];
   T lam_dt[MPT], inv_d[MPT], fkx[MPT], fky[MPT];
-  const T kz = (T)a.kz, dt = (T)a.dt;
+  const T kz = a.sp ? (T)a.sp[b].kz : (T)a.kz, dt = a.sp ? (T)a.sp[b].dt : (T)a.dt;
+  const T inv_rm = T(1) / (a.sp ? (T)a.sp[b].Rm : (T)a.Rm);
 #pragma unroll
   for (int i = 0; i < MPT; ++i) {
     const int m = threadIdx.x + CCB * i;
@@ -88,7 +96,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
     const int iy = y0 + ly;
     fkx[i] = (T)(ix - K);
     fky[i] = (T)(iy - K);
-    const T lam = (fkx[i] * fkx[i] + fky[i] * fky[i] + kz * kz) * (T(1) / (T)a.Rm);
+    const T lam = (fkx[i] * fkx[i] + fky[i] * fky[i] + kz * kz) * inv_rm;
     lam_dt[i] = dt * lam;
     inv_d[i] = T(1) / (T(1) + dt * T(0.5) * lam);
 #pragma unroll
@@ -96,8 +104,8 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
       cx<T> v = mk(T(0), T(0));
       if (m < M) {
         const long src = ((long)c * Pf + (iy + Kf - K)) * Pf + (ix + Kf - K);
-        if (a.Uprev)
-          v = mk((T)(Un[2 * src] - a.Uprev[2 * src]), (T)(Un[2 * src + 1] - a.Uprev[2 * src + 1]));
+        if (Uprev)
+          v = mk((T)(Un[2 * src] - Uprev[2 * src]), (T)(Un[2 * src + 1] - Uprev[2 * src + 1]));
         else
           v = mk((T)Un[2 * src], (T)Un[2 * src + 1]);
       }
@@ -126,9 +134,9 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   }
   cluster.sync();
 
-  const T A = (T)a.amp;
+  const T A = a.sp ? (T)a.sp[b].amp : (T)a.amp;
   int cur = 0;
-  for (int s = 0; s < a.nsteps; ++s) {
+  for (int s = 0; s < nsteps; ++s) {
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       Phase<T> ph;
@@ -251,22 +259,22 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
       ux = gx;
       uy = gy;
     } else {
-      ux = a.Fv[2 * fi] + (gx - ox);
-      uy = a.Fv[2 * fi + 1] + (gy - oy);
+      ux = Fv[2 * fi] + (gx - ox);
+      uy = Fv[2 * fi + 1] + (gy - oy);
     }
-    if (ic >= 0 && a.mode != COARSE_INCR) {
+    if (ic >= 0 && a.mode != COARSE_INCR && a.Gold) {
       a.Gold[2 * ic] = gx;
       a.Gold[2 * ic + 1] = gy;
     }
-    if (a.sigma_out) {
-      const double dx = ux - a.Unext[2 * fi], dy = uy - a.Unext[2 * fi + 1];
+    if (sig) {
+      const double dx = ux - Unext[2 * fi], dy = uy - Unext[2 * fi + 1];
       acc_d += dx * dx + dy * dy;
       acc_n += ux * ux + uy * uy;
     }
-    a.Unext[2 * fi] = ux;
-    a.Unext[2 * fi + 1] = uy;
+    Unext[2 * fi] = ux;
+    Unext[2 * fi + 1] = uy;
   }
-  if (a.sigma_out) {
+  if (sig) {
     for (int o = 16; o > 0; o >>= 1) {
       acc_d += __shfl_down_sync(0xffffffffu, acc_d, o);
       acc_n += __shfl_down_sync(0xffffffffu, acc_n, o);
@@ -289,19 +297,20 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
     }
   }
   cluster.sync();   // partial sums delivered; peers' buffers no longer read
-  if (a.sigma_out && rank == 0 && threadIdx.x == 0) {
+  if (sig && rank == 0 && threadIdx.x == 0) {
     double d = 0.0, n = 0.0;
     for (int r = 0; r < CS; ++r) {
       d += cl_d[r];
       n += cl_n[r];
     }
-    a.sigma_out[0] = sqrt(d) / sqrt(n);
-    a.sigma_out[1] = d;
-    a.sigma_out[2] = n;
+    sig[0] = sqrt(d) / sqrt(n);
+    sig[1] = d;
+    sig[2] = n;
   }
 }
 
-// cluster split of a P-row coarse square: CS blocks of H rows (H <= 8 for P <= 64)
+// cluster split of a P-row coarse square: CS blocks of H rows (H <= 8 for P <= 64,
+// H <= 11 for P <= 88)
 static void cluster_shape(int P, int* CS, int* H) {
   int cs = (P + 5) / 6;
   if (cs > 8) cs = 8;
@@ -323,14 +332,30 @@ static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots) {
   return base + (size_t)slots * es;
 }
 
-bool coarse_conv_supported(int P) { return P >= 1 && P <= 64; }
-
-cudaError_t coarse_prepare(int prec) {
-  int slots = 0;
-  const int bytes = (int)cluster_smem(prec, 64, 512, &slots);
-  return prec == 0 ? cudaFuncSetAttribute(coarse_cluster_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                   : cudaFuncSetAttribute(coarse_cluster_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// modes per thread needed for a P-row square (0: unsupported)
+static int modes_per_thread(int P) {
+  int CS, H;
+  cluster_shape(P, &CS, &H);
+  if (H * P <= 2 * CCB) return 2;
+  if (H * P <= 4 * CCB) return 4;
+  return 0;
 }
+
+bool coarse_conv_supported(int P) { return P >= 1 && modes_per_thread(P) > 0; }
+
+template <typename T>
+static cudaError_t prepare_T() {
+  int slots = 0;
+  const int prec = sizeof(T) == 4 ? 0 : 1;
+  int P = 64;
+  while (coarse_conv_supported(P + 1)) ++P;   // largest supported square
+  const int bytes = (int)cluster_smem(prec, P, 512, &slots);
+  cudaError_t e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t coarse_prepare(int prec) { return prec == 0 ? prepare_T<float>() : prepare_T<double>(); }
 
 template <typename T>
 static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
@@ -351,7 +376,9 @@ static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H) == cudaSuccess ? 1 : -1;
+  const cudaError_t e = modes_per_thread(a.Pc) == 2 ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H)
+                                                    : cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 4>, a, CS, H);
+  return e == cudaSuccess ? 1 : -1;
 }
 
 int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st) {

@@ -25,11 +25,18 @@ struct CoarseArgs {
   const double* Fv;     // COARSE_UPDATE: fine values F(U_n), fine compact FP64
   double* Gold;         // coarse values of the previous sweep (read, then replaced)
   double* Unext;        // U_{n+1}, fine compact FP64 (written)
-  double* sigma_out;    // if not NULL: sigma, |U - U_old|^2, |U|^2 of Unext (3 doubles)
+  double* sigma_out;    // if not NULL: sigma, |U - U_old|^2, |U|^2 of Unext (3 doubles per field)
   int phase_smem;       // (internal) phase values the cluster kernel may stage in shared memory
+  // Batched instances (all optional): per-field parameters (kz, Rm, dt, amplitude; the
+  // phase table then covers every field), per-field step counts (<= nsteps; the phase
+  // table stride stays nsteps) and per-field slots: field b reads Un / Uprev / Fv at slot
+  // map[b] (stride 3 Pf^2 complex) and writes slot map[b] + 1 of Unext.
+  const SliceParams* sp;
+  const int* steps;
+  const int* map;
 };
 
-bool coarse_conv_supported(int P);   // coarse set side P <= 64
+bool coarse_conv_supported(int P);   // coarse set side P <= 88
 cudaError_t coarse_prepare(int prec);
 // One thread-block cluster per field; returns 1 (kernels launched) or -1 if unsupported.
 int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st);

@@ -9,8 +9,12 @@
 //    (FineArgs::sp); at step s only the prefix of fields that still have steps is
 //    launched.  Increment form: the batch holds U - Uprev and Fv accumulates F of it.
 //  - serial step: slice by slice, the restricted increments of all active members form
-//    one coarse batch (ordered by decreasing coarse step count), advanced by the same
-//    kernels on the coarse grid; U_{n+1} = Fv_n + prolong(G(restrict(U_n - Uprev_n))).
+//    one coarse batch, U_{n+1} = Fv_n + prolong(G(restrict(U_n - Uprev_n))): for coarse
+//    sets of side <= 88 one persistent cluster launch per slice (restriction, every
+//    coarse step and the FP64 update fused, each field with its own step count),
+//    otherwise the fine-step kernels on the coarse grid (fields ordered by decreasing
+//    coarse step count, launched as a shrinking prefix) between a restriction and an
+//    update kernel.
 //  - defect (Eq. 9) per member from deterministic per-block partial sums.
 // Members leave the iteration when their defect reaches tol.  Slices n < k - 1 are exact
 // after k iterations and are skipped, as in kd_parareal_run.
@@ -24,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "kd_coarse.h"
 #include "kd_ctx.h"
 
 using namespace kd;
@@ -185,6 +190,10 @@ struct GroupBufs {
   double *t0f = nullptr, *t0c = nullptr;
   int *emap = nullptr, *cmap = nullptr;
   double *partials = nullptr, *sigma = nullptr, *E = nullptr, *fit = nullptr;
+  double* sig3 = nullptr;      // cluster path: (sigma, diff, norm) per field
+  int* stepsc = nullptr;       // cluster path: coarse steps per field
+  void* phc = nullptr;         // cluster path: coarse phase table of every slice
+  size_t phc_bytes = 0;
 };
 
 kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int k_max, double tol,
@@ -201,7 +210,9 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
       (s = dalloc(ctx, (void**)&g.Fv, slots * len * 16, "sweep F values")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.Up, slots * len * 16, "sweep previous iterate")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.spf, (size_t)m * N * sizeof(SliceParams), "slice params")) != KD_OK ||
-      (s = dalloc(ctx, (void**)&g.spc, (size_t)m * sizeof(SliceParams), "coarse params")) != KD_OK ||
+      (s = dalloc(ctx, (void**)&g.spc, (size_t)m * N * sizeof(SliceParams), "coarse params")) != KD_OK ||
+      (s = dalloc(ctx, (void**)&g.sig3, (size_t)m * 3 * 8, "cluster defects")) != KD_OK ||
+      (s = dalloc(ctx, (void**)&g.stepsc, (size_t)m * 4, "coarse steps")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.t0f, (size_t)m * N * 8, "slice times")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.t0c, (size_t)m * N * 8, "coarse times")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.emap, (size_t)m * N * 4, "fine map")) != KD_OK ||
@@ -302,51 +313,95 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
       lo = first + 1;
     }
     if (lo < N) {
-      spc.resize(na);
-      for (int j = 0; j < na; ++j) spc[j] = slice_params(mem[Ac[j]].in, mem[Ac[j]].dtc);
-      KD_CUDA(cudaMemcpyAsync(g.spc, spc.data(), na * sizeof(SliceParams), cudaMemcpyHostToDevice, ctx->st),
-              "coarse params");
+      // per-slice copies of the members' coarse parameters, maps and start times ([slice][member])
+      spc.resize((long)na * N);
       cmap.assign((long)na * N, 0);
       t0c.assign((long)na * N, 0.0);
       for (int sl = 0; sl < N; ++sl)
         for (int j = 0; j < na; ++j) {
+          spc[(long)sl * na + j] = slice_params(mem[Ac[j]].in, mem[Ac[j]].dtc);
           cmap[(long)sl * na + j] = slot(Ac[j], sl);
           t0c[(long)sl * na + j] = sl * dT;
         }
+      KD_CUDA(cudaMemcpyAsync(g.spc, spc.data(), (size_t)na * N * sizeof(SliceParams), cudaMemcpyHostToDevice,
+                              ctx->st), "coarse params");
       KD_CUDA(cudaMemcpyAsync(g.cmap, cmap.data(), (size_t)na * N * 4, cudaMemcpyHostToDevice, ctx->st), "coarse map");
       KD_CUDA(cudaMemcpyAsync(g.t0c, t0c.data(), (size_t)na * N * 8, cudaMemcpyHostToDevice, ctx->st), "coarse times");
       const int Scmax = mem[Ac[0]].Sc;
-      act_c.assign(Scmax, 0);
-      for (int st = 0; st < Scmax; ++st) {
-        int c = 0;
-        while (c < na && mem[Ac[c]].Sc > st) ++c;
-        act_c[st] = c;
-      }
-      for (int sl = lo; sl < N; ++sl) {
-        const int* cm = g.cmap + (long)sl * na;
-        k_restrict_map<float><<<grid1((long)na * lenc), 256, 0, ctx->st>>>(
-            (const cx<double>*)g.U, k >= 1 ? (const cx<double>*)g.Up : nullptr, cm, Kf, Pf, (cx<float>*)ctx->ws_c.X, Kc,
-            Pc, na);
-        KD_LAUNCH(0, "restrict");
-        FineArgs ac = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, na, mem[Ac[0]].dtc, g.t0c + (long)sl * na);
-        ac.flow = KD_FLOW_GALLOWAY_PROCTOR;
-        ac.sp = g.spc;
-        if ((s = with_phases(ctx, ctx->ws_c, ac, Scmax)) != KD_OK) return s;
-        KD_LAUNCH(run_fine(ctx, 1, KD_C64, ac, Scmax, true, false, nullptr, act_c.data()), "coarse steps");
-        const bool last = k >= 1 && sl == N - 1;
-        k_update_map<float><<<dim3(kUpdBlocks, na), 256, 0, ctx->st>>>(
-            k >= 1 ? (const cx<double>*)g.Fv : nullptr, (const cx<float>*)ctx->ws_c.X, cm, (cx<double>*)g.U, Kf, Pf,
-            Kc, Pc, last ? g.partials : nullptr);
-        KD_LAUNCH(0, "update");
+      if (coarse_conv_supported(Pc)) {
+        std::vector<int> stc(na);
+        for (int j = 0; j < na; ++j) stc[j] = mem[Ac[j]].Sc;
+        KD_CUDA(cudaMemcpyAsync(g.stepsc, stc.data(), na * 4, cudaMemcpyHostToDevice, ctx->st), "coarse steps");
+        const size_t need = phase_table_bytes(KD_C64, (long)na * N, Scmax);
+        if (g.phc_bytes < need) {
+          dfree(ctx, g.phc);
+          g.phc = nullptr;
+          g.phc_bytes = 0;
+          if ((s = dalloc(ctx, &g.phc, need, "coarse phase table")) != KD_OK) return s;
+          g.phc_bytes = need;
+        }
+        FineArgs pa = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, (long)na * N, mem[Ac[0]].dtc, g.t0c);
+        pa.flow = KD_FLOW_GALLOWAY_PROCTOR;
+        pa.sp = g.spc;
+        pa.phases = g.phc;
+        KD_LAUNCH(launch_phases(KD_C64, pa, Scmax, ctx->st), "coarse phases");
+        for (int sl = lo; sl < N; ++sl) {
+          CoarseArgs c;
+          memset(&c, 0, sizeof(c));
+          c.Kc = Kc;
+          c.Pc = Pc;
+          c.Kf = Kf;
+          c.Pf = Pf;
+          c.flow = KD_FLOW_GALLOWAY_PROCTOR;
+          c.nsteps = Scmax;
+          c.phases = (const float*)g.phc + (size_t)sl * na * Scmax * 16;
+          c.Un = g.U;
+          c.Uprev = k >= 1 ? g.Up : nullptr;
+          c.Fv = k >= 1 ? g.Fv : nullptr;
+          c.Unext = g.U;
+          c.mode = k >= 1 ? COARSE_INCR : COARSE_INIT;
+          c.sigma_out = (k >= 1 && sl == N - 1) ? g.sig3 : nullptr;
+          c.sp = g.spc + (long)sl * na;
+          c.steps = g.stepsc;
+          c.map = g.cmap + (long)sl * na;
+          KD_LAUNCH(coarse_conv_launch(KD_C64, c, na, ctx->st), "coarse solve");
+        }
+      } else {
+        act_c.assign(Scmax, 0);
+        for (int st = 0; st < Scmax; ++st) {
+          int c = 0;
+          while (c < na && mem[Ac[c]].Sc > st) ++c;
+          act_c[st] = c;
+        }
+        for (int sl = lo; sl < N; ++sl) {
+          const int* cm = g.cmap + (long)sl * na;
+          k_restrict_map<float><<<grid1((long)na * lenc), 256, 0, ctx->st>>>(
+              (const cx<double>*)g.U, k >= 1 ? (const cx<double>*)g.Up : nullptr, cm, Kf, Pf,
+              (cx<float>*)ctx->ws_c.X, Kc, Pc, na);
+          KD_LAUNCH(0, "restrict");
+          FineArgs ac = fine_args(ctx, ctx->ws_c, ctx->tab_c, nc, na, mem[Ac[0]].dtc, g.t0c + (long)sl * na);
+          ac.flow = KD_FLOW_GALLOWAY_PROCTOR;
+          ac.sp = g.spc + (long)sl * na;
+          if ((s = with_phases(ctx, ctx->ws_c, ac, Scmax)) != KD_OK) return s;
+          KD_LAUNCH(run_fine(ctx, 1, KD_C64, ac, Scmax, true, false, nullptr, act_c.data()), "coarse steps");
+          const bool last = k >= 1 && sl == N - 1;
+          k_update_map<float><<<dim3(kUpdBlocks, na), 256, 0, ctx->st>>>(
+              k >= 1 ? (const cx<double>*)g.Fv : nullptr, (const cx<float>*)ctx->ws_c.X, cm, (cx<double>*)g.U, Kf,
+              Pf, Kc, Pc, last ? g.partials : nullptr);
+          KD_LAUNCH(0, "update");
+        }
       }
     }
     KD_CUDA(cudaEventRecord(e2, ctx->st), "event");
-    std::vector<double> sig(na, 0.0);
-    if (k >= 1) {
+    std::vector<double> sig(na, 0.0), sig3(3 * na, 0.0);
+    const bool from_cluster = k >= 1 && first < N - 1 && coarse_conv_supported(Pc);
+    if (k >= 1 && !from_cluster) {
       k_sigma_map<<<(na + 127) / 128, 128, 0, ctx->st>>>(g.partials, kUpdBlocks, g.sigma, na);
       KD_LAUNCH(0, "defect");
       KD_CUDA(cudaMemcpyAsync(sig.data(), g.sigma, na * 8, cudaMemcpyDeviceToHost, ctx->st), "defect copy");
     }
+    if (from_cluster)
+      KD_CUDA(cudaMemcpyAsync(sig3.data(), g.sig3, 3 * na * 8, cudaMemcpyDeviceToHost, ctx->st), "defect copy");
     KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
     float mf = 0.f, mc = 0.f;
     cudaEventElapsedTime(&mf, e0, e1);
@@ -354,6 +409,8 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
     gt.fine += mf;
     gt.coarse += mc;
     if (k == 0) continue;
+    if (from_cluster)
+      for (int j = 0; j < na; ++j) sig[j] = sig3[3 * j];
     for (int j = 0; j < na; ++j) {
       Member& mb = mem[Ac[j]];
       mb.k = k;
