@@ -262,6 +262,11 @@ kd_status kd_plan_variants(kd_ctx* ctx, int grid, int* n_col, int* n_row);
 kd_status kd_set_plan(kd_ctx* ctx, int grid, int col, int row);
 kd_status kd_get_plan(kd_ctx* ctx, int grid, int* col, int* row);
 
+/* Launch the fine step's kernels as programmatic dependent launches (enable = 1, the
+ * default): each kernel may start while its predecessor drains and waits on the device
+ * before it reads the predecessor's output.  enable = 0 uses ordinary launches. */
+kd_status kd_set_dependent_launch(kd_ctx* ctx, int enable);
+
 /* Autotune the plan of a grid for batches of `batch` fields: if `cache_path` (may be
  * NULL) names a JSON file holding an entry for (device name, n, precision, batch rounded
  * up to a power of two), that entry's plan is used; otherwise every (col, row) pair is

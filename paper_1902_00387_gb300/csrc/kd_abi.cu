@@ -232,6 +232,7 @@ int run_fine(kd_ctx* ctx, int g, int prec, const FineArgs& a, int nsteps, bool p
   cfg.active = active;
   cfg.probe = probe;
   cfg.plan = ctx->plan[g];
+  cfg.pdl = ctx->pdl != 0;
   cfg.st = ctx->st;
   return fine_run(prec, a, cfg);
 }

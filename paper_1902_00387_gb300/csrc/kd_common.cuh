@@ -38,6 +38,16 @@ __host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> mul_i(cx<T> a) { return mk(-a.y, a.x); }
 
+// Programmatic dependent launch (kernels launched with the attribute
+// cudaLaunchAttributeProgrammaticStreamSerialization may start while their predecessor in
+// the stream drains): griddep_wait() returns once the predecessor has completed and its
+// memory is visible (immediately for an ordinary launch); griddep_launch_dependents() lets
+// the successor be scheduled.  A kernel reads its predecessor's outputs only after
+// griddep_wait() and calls griddep_launch_dependents() only after its own wait, so data
+// written two launches back is complete before the wait as well.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // Flow identifiers (match include/kd.h).
 enum { FLOW_ROBERTS = 0, FLOW_GP = 1, FLOW_NONE = 2 };
 

@@ -38,6 +38,7 @@ inline size_t csize(int prec) { return prec == KD_C128 ? 16 : 8; }
 struct kd_ctx {
   kd_params p;
   kd::FinePlan plan[2];        // launch plans of the fine (0) and coarse (1) grid
+  int pdl = 1;                 // fine-step kernels as programmatic dependent launches
   cudaStream_t st = nullptr;
   int device = 0;
   kdi::Tables tab_f, tab_c;

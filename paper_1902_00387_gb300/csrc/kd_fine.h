@@ -30,6 +30,7 @@ struct StepCfg {
   const int* active = nullptr;
   const LaunchProbe* probe = nullptr;
   FinePlan plan;
+  bool pdl = false;         // launch the step kernels as programmatic dependent launches
   cudaStream_t st = nullptr;
 };
 

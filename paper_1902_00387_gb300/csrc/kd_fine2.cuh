@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(Col2<T, N, XT>::BLOCK, Col2<T, N, XT>::MIN_BLO
 
   cx<T> v[3][R1];
   const cx<T>* M = (const cx<T>*)a.M;
+  griddep_wait();    // M is the predecessor's output
 #pragma unroll
   for (int k = 0; k < R1; ++k) {
     const int yy = lane + R2 * k;
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(Col2<T, N, XT>::BLOCK, Col2<T, N, XT>::MIN_BLO
     cross_u<T>(A, ph, cxg, sxg, s_cos[y], s_sin[y], v[0][r], v[1][r], v[2][r]);
   }
   out_to_in<T, N>(v);
+  griddep_launch_dependents();
   __syncthreads();   // exchange buffers are reused
   fft2_3<T, N, -1>(v, lane, s_tw, slot);           // y -> ky
 
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row
   auto hslot = [&](int c, int r, int ix) { return S + (c * RT + r) * LROW + ix; };
 
   cx<T> v[3][R1];
+  griddep_wait();    // W (and, for the prologue, X) come from the predecessors
   if (mode == 4) {
     const cx<T>* X = (const cx<T>*)a.X;
     const long sbase = ((b * 3) * P + iy) * (long)P + K;
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row
       __syncthreads();   // exchange reads of the forward transform are done
     }
   }
+  griddep_launch_dependents();
   fft2_3<T, N, +1>(v, lane, s_tw, slot);           // kx -> x
   if (!valid) return;
   cx<T>* Mo = (cx<T>*)a.M;
@@ -268,123 +272,4 @@ __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row
   }
 }
 
-template <typename T, int N, int XT>
-static cudaError_t prepare_col2() {
-  return cudaFuncSetAttribute(col2_kernel<T, N, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Col2<T, N, XT>::smem);
-}
-
-template <typename T, int N, int RT, bool STAGED>
-static cudaError_t prepare_row2() {
-  return cudaFuncSetAttribute(row2_kernel<T, N, RT, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Row2<T, N, RT, STAGED ? 128 : 168>::smem);
-}
-
-template <typename T, int N, int XT>
-static void launch_col2(const FineArgs& a, int s, int j, cudaStream_t st) {
-  using C = Col2<T, N, XT>;
-  const unsigned gc = (unsigned)(((long)a.batch * N + XT - 1) / XT);
-  col2_kernel<T, N, XT><<<gc, C::BLOCK, C::smem, st>>>(a, s, j);
-}
-
-template <typename T, int N, int RT, bool STAGED>
-static void launch_row2(const FineArgs& a, int mode, int store, cudaStream_t st) {
-  using R = Row2<T, N, RT, STAGED ? 128 : 168>;
-  const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
-  row2_kernel<T, N, RT, STAGED><<<gr, R::BLOCK, R::smem, st>>>(a, mode, store);
-}
-
-// Kernel entry points of one (T, N) for the plan's variants.
-template <typename T, int N>
-struct Fine2Set {
-  using Sh = Shapes2<T, N>;
-  static constexpr bool WIDE = sizeof(T) == 4;   // complex64: every candidate shape
-  static int ncol() { return WIDE ? 2 : 1; }
-  static int nrow() { return WIDE ? 4 : 1; }
-  static cudaError_t prepare() {
-    cudaError_t e;
-    if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
-    if ((e = prepare_row2<T, N, Sh::rt(0), true>()) != cudaSuccess) return e;
-    if (WIDE) {
-      if ((e = prepare_col2<T, N, Sh::xt(1)>()) != cudaSuccess) return e;
-      if ((e = prepare_row2<T, N, Sh::rt(1), true>()) != cudaSuccess) return e;
-      if ((e = prepare_row2<T, N, Sh::rt(0), false>()) != cudaSuccess) return e;
-      if ((e = prepare_row2<T, N, Sh::rt(1), false>()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
-  static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st) {
-    if (WIDE && v == 1)
-      launch_col2<T, N, Sh::xt(1)>(a, s, j, st);
-    else
-      launch_col2<T, N, Sh::xt(0)>(a, s, j, st);
-  }
-  static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st) {
-    if (!WIDE) v = 0;
-    switch (v) {
-      case 1: launch_row2<T, N, Sh::rt(1), true>(a, mode, store, st); break;
-      case 2: launch_row2<T, N, Sh::rt(0), false>(a, mode, store, st); break;
-      case 3: launch_row2<T, N, Sh::rt(1), false>(a, mode, store, st); break;
-      default: launch_row2<T, N, Sh::rt(0), true>(a, mode, store, st); break;
-    }
-  }
-};
-
-// The step loop shared by both kernel families (Set: Fine2Set or Fine3Set).
-template <class Set>
-static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
-  const FinePlan pl = cfg.plan;
-  const int cv = pl.col >= 0 && pl.col < Set::ncol() ? pl.col : 0;
-  const int rv = pl.row >= 0 && pl.row < Set::nrow() ? pl.row : 0;
-  int launches = 0;
-  if (cfg.prologue) {
-    Set::row(rv, a0, 4, 1, cfg.st);
-    ++launches;
-  }
-  FineArgs a = a0;
-  for (int s = 0; s < cfg.nsteps; ++s) {
-    if (cfg.active) {
-      a.batch = cfg.active[s];
-      if (a.batch <= 0) break;
-    }
-    for (int j = 0; j < 4; ++j) {
-      if (cfg.probe) cfg.probe->before(cfg.probe->user, 0);
-      Set::col(cv, a, s, j, cfg.st);
-      if (cfg.probe) cfg.probe->after(cfg.probe->user, 0);
-      const int store = (s == cfg.nsteps - 1 && j == 3) ? (cfg.store_last ? 1 : 0) : 1;
-      if (cfg.probe) cfg.probe->before(cfg.probe->user, 1);
-      Set::row(rv, a, j, store, cfg.st);
-      if (cfg.probe) cfg.probe->after(cfg.probe->user, 1);
-      launches += 2;
-    }
-  }
-  return launches;
-}
-
 }  // namespace kd
-
-namespace kd {
-
-template <typename T, int N>
-int fine2_run(const FineArgs& a, const StepCfg& cfg) {
-  return run_steps<Fine2Set<T, N>>(a, cfg);
-}
-
-template <typename T, int N>
-cudaError_t fine2_prep() {
-  return Fine2Set<T, N>::prepare();
-}
-
-template <typename T, int N>
-void fine2_variants(int* ncol, int* nrow) {
-  *ncol = Fine2Set<T, N>::ncol();
-  *nrow = Fine2Set<T, N>::nrow();
-}
-
-}  // namespace kd
-
-// Explicit instantiation of one (T, N) in the including translation unit.
-#define KD_FINE2_INSTANTIATE(T, N)                                        \
-  template int kd::fine2_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
-  template cudaError_t kd::fine2_prep<T, N>();                             \
-  template void kd::fine2_variants<T, N>(int*, int*);

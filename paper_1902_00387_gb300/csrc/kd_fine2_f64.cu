@@ -1,5 +1,5 @@
 // Instantiations of the n <= 256 fine kernels (kd_fine2.cuh): double, n = 16 32 64 128 256.
-#include "kd_fine2.cuh"
+#include "kd_fine_sets.cuh"
 
 KD_FINE2_INSTANTIATE(double, 16)
 KD_FINE2_INSTANTIATE(double, 32)

@@ -1,4 +1,4 @@
 // Instantiations of the n = 512, 1024 fine kernels (kd_fine3.cuh): float, n = 512.
-#include "kd_fine3.cuh"
+#include "kd_fine_sets.cuh"
 
 KD_FINE3_INSTANTIATE(float, 512)

@@ -1,0 +1,284 @@
+// Launch plans of the fine step: the kernel variants of every (precision, grid) and the
+// step loop (kd_fine.h: fine_run).  Included by the instantiation units kd_fine2_*.cu
+// and kd_fine3_*.cu.
+//
+// complex64 variants (complex128 has variant 0 only):
+//   n <= 256  column: 0, 1 = four-step kernels with XT0, XT0/2 columns per block;
+//                     2 = three-pass kernel with 8 values per thread (n = 128, 256)
+//             row:    0..3 = four-step kernels, (RT0 | RT0/2 rows) x (staged | registers);
+//                     4, 5 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
+//   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
+//                     2 = persistent prefetching kernel; 3 = 8 values per thread (n = 512)
+//             row:    0..3 = three-pass, 16 values, (RT0 | RT0/2) x (staged | registers);
+//                     4 = persistent prefetching kernel (in registers);
+//                     5, 6 = 8 values per thread, staged | registers (n = 512)
+#pragma once
+#include "kd_fine3.cuh"
+
+namespace kd {
+
+// Launch `k` on stream st; with pdl the launch may overlap its predecessor's tail
+// (programmatic dependent launch; the kernels synchronise with griddep_wait()).
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <typename T, int N, int XT>
+static cudaError_t prepare_col2() {
+  return cudaFuncSetAttribute(col2_kernel<T, N, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Col2<T, N, XT>::smem);
+}
+
+template <typename T, int N, int RT, bool STAGED>
+static cudaError_t prepare_row2() {
+  return cudaFuncSetAttribute(row2_kernel<T, N, RT, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Row2<T, N, RT, STAGED ? 128 : 168>::smem);
+}
+
+template <typename T, int N, int XT>
+static void launch_col2(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = Col2<T, N, XT>;
+  const unsigned gc = (unsigned)(((long)a.batch * N + XT - 1) / XT);
+  launch_k(col2_kernel<T, N, XT>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <typename T, int N, int RT, bool STAGED>
+static void launch_row2(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+  using R = Row2<T, N, RT, STAGED ? 128 : 168>;
+  const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
+  launch_k(row2_kernel<T, N, RT, STAGED>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
+}
+
+template <typename T, int N, int XT, int R>
+static cudaError_t prepare_col3() {
+  return cudaFuncSetAttribute(col3_kernel<T, N, XT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Col3<T, N, XT, R>::smem);
+}
+
+template <typename T, int N, int RT, bool STAGED, int R>
+static cudaError_t prepare_row3() {
+  return cudaFuncSetAttribute(row3_kernel<T, N, RT, STAGED, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Row3<T, N, RT, STAGED ? 128 : 168, R>::smem);
+}
+
+template <typename T, int N, int XT, int R>
+static void launch_col3(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = Col3<T, N, XT, R>;
+  const unsigned gc = (unsigned)(((long)a.batch * N + XT - 1) / XT);
+  launch_k(col3_kernel<T, N, XT, R>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <typename T, int N, int RT, bool STAGED, int R>
+static void launch_row3(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+  using G = Row3<T, N, RT, STAGED ? 128 : 168, R>;
+  const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
+  launch_k(row3_kernel<T, N, RT, STAGED, R>, gr, G::BLOCK, G::smem, st, pdl, a, mode, store);
+}
+
+// 8-values-per-thread shapes: 256-thread blocks
+template <int N>
+struct Shapes8 {
+  static constexpr int TPT = N / 8;
+  static constexpr int XT = 256 / TPT, RT = 256 / TPT;
+};
+
+template <typename T, int N>
+struct Fine2Set {
+  using Sh = Shapes2<T, N>;
+  static constexpr bool WIDE = sizeof(T) == 4;
+  static constexpr bool R8 = WIDE && (N == 128 || N == 256);
+  static int ncol() { return WIDE ? (R8 ? 3 : 2) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 6 : 4) : 1; }
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
+    if ((e = prepare_row2<T, N, Sh::rt(0), true>()) != cudaSuccess) return e;
+    if (WIDE) {
+      if ((e = prepare_col2<T, N, Sh::xt(1)>()) != cudaSuccess) return e;
+      if ((e = prepare_row2<T, N, Sh::rt(1), true>()) != cudaSuccess) return e;
+      if ((e = prepare_row2<T, N, Sh::rt(0), false>()) != cudaSuccess) return e;
+      if ((e = prepare_row2<T, N, Sh::rt(1), false>()) != cudaSuccess) return e;
+    }
+    if constexpr (R8) {
+      if ((e = prepare_col3<T, N, Shapes8<N>::XT, 8>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Shapes8<N>::RT, true, 8>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Shapes8<N>::RT, false, 8>()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (R8) {
+      if (v == 2) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
+    }
+    if (WIDE && v == 1)
+      launch_col2<T, N, Sh::xt(1)>(a, s, j, st, pdl);
+    else
+      launch_col2<T, N, Sh::xt(0)>(a, s, j, st, pdl);
+  }
+  static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+    if (!WIDE) v = 0;
+    if constexpr (R8) {
+      if (v == 4) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
+      if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
+    }
+    switch (v) {
+      case 1: launch_row2<T, N, Sh::rt(1), true>(a, mode, store, st, pdl); break;
+      case 2: launch_row2<T, N, Sh::rt(0), false>(a, mode, store, st, pdl); break;
+      case 3: launch_row2<T, N, Sh::rt(1), false>(a, mode, store, st, pdl); break;
+      default: launch_row2<T, N, Sh::rt(0), true>(a, mode, store, st, pdl); break;
+    }
+  }
+};
+
+template <typename T, int N>
+struct Fine3Set {
+  using Sh = Shapes3<T, N>;
+  static constexpr bool WIDE = sizeof(T) == 4;
+  static constexpr bool R8 = WIDE && N == 512;
+  static int ncol() { return WIDE ? (R8 ? 4 : 3) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 7 : 5) : 1; }
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = prepare_col3<T, N, Sh::xt(0), 16>()) != cudaSuccess) return e;
+    if ((e = prepare_row3<T, N, Sh::rt(0), true, 16>()) != cudaSuccess) return e;
+    if (WIDE) {
+      if ((e = prepare_col3<T, N, Sh::xt(1), 16>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Sh::rt(1), true, 16>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Sh::rt(0), false, 16>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Sh::rt(1), false, 16>()) != cudaSuccess) return e;
+      if ((e = cudaFuncSetAttribute(col3p_kernel<T, N, Sh::XT0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col3P<T, N, Sh::XT0>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(row3p_kernel<T, N, Sh::RT0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Row3P<T, N, Sh::RT0>::smem)) != cudaSuccess)
+        return e;
+    }
+    if constexpr (R8) {
+      if ((e = prepare_col3<T, N, Shapes8<N>::XT, 8>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Shapes8<N>::RT, true, 8>()) != cudaSuccess) return e;
+      if ((e = prepare_row3<T, N, Shapes8<N>::RT, false, 8>()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (R8) {
+      if (v == 3) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
+    }
+    if (WIDE && v == 2) {
+      using C = Col3P<T, N, Sh::XT0>;
+      launch_k(col3p_kernel<T, N, Sh::XT0>, persistent_grid((long)a.batch * N / Sh::XT0), C::BLOCK, C::smem, st, pdl,
+               a, s, j);
+    } else if (WIDE && v == 1) {
+      launch_col3<T, N, Sh::xt(1), 16>(a, s, j, st, pdl);
+    } else {
+      launch_col3<T, N, Sh::xt(0), 16>(a, s, j, st, pdl);
+    }
+  }
+  static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+    if (!WIDE) v = 0;
+    if constexpr (R8) {
+      if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
+      if (v == 6) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
+    }
+    if (v == 4 && mode == 4) v = 0;   // the prologue runs on the tiled kernel
+    if (v == 4) {
+      using G = Row3P<T, N, Sh::RT0>;
+      const long tiles = ((long)a.batch * a.P + Sh::RT0 - 1) / Sh::RT0;
+      launch_k(row3p_kernel<T, N, Sh::RT0>, persistent_grid(tiles), G::BLOCK, G::smem, st, pdl, a, mode, store);
+      return;
+    }
+    switch (v) {
+      case 1: launch_row3<T, N, Sh::rt(1), true, 16>(a, mode, store, st, pdl); break;
+      case 2: launch_row3<T, N, Sh::rt(0), false, 16>(a, mode, store, st, pdl); break;
+      case 3: launch_row3<T, N, Sh::rt(1), false, 16>(a, mode, store, st, pdl); break;
+      default: launch_row3<T, N, Sh::rt(0), true, 16>(a, mode, store, st, pdl); break;
+    }
+  }
+};
+
+// The step loop shared by both kernel families.
+template <class Set>
+static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
+  const FinePlan pl = cfg.plan;
+  const int cv = pl.col >= 0 && pl.col < Set::ncol() ? pl.col : 0;
+  const int rv = pl.row >= 0 && pl.row < Set::nrow() ? pl.row : 0;
+  int launches = 0;
+  if (cfg.prologue) {
+    Set::row(rv, a0, 4, 1, cfg.st, cfg.pdl);
+    ++launches;
+  }
+  FineArgs a = a0;
+  for (int s = 0; s < cfg.nsteps; ++s) {
+    if (cfg.active) {
+      a.batch = cfg.active[s];
+      if (a.batch <= 0) break;
+    }
+    for (int j = 0; j < 4; ++j) {
+      if (cfg.probe) cfg.probe->before(cfg.probe->user, 0);
+      Set::col(cv, a, s, j, cfg.st, cfg.pdl);
+      if (cfg.probe) cfg.probe->after(cfg.probe->user, 0);
+      const int store = (s == cfg.nsteps - 1 && j == 3) ? (cfg.store_last ? 1 : 0) : 1;
+      if (cfg.probe) cfg.probe->before(cfg.probe->user, 1);
+      Set::row(rv, a, j, store, cfg.st, cfg.pdl);
+      if (cfg.probe) cfg.probe->after(cfg.probe->user, 1);
+      launches += 2;
+    }
+  }
+  return launches;
+}
+
+template <typename T, int N>
+int fine2_run(const FineArgs& a, const StepCfg& cfg) {
+  return run_steps<Fine2Set<T, N>>(a, cfg);
+}
+
+template <typename T, int N>
+cudaError_t fine2_prep() {
+  return Fine2Set<T, N>::prepare();
+}
+
+template <typename T, int N>
+void fine2_variants(int* ncol, int* nrow) {
+  *ncol = Fine2Set<T, N>::ncol();
+  *nrow = Fine2Set<T, N>::nrow();
+}
+
+template <typename T, int N>
+int fine3_run(const FineArgs& a, const StepCfg& cfg) {
+  return run_steps<Fine3Set<T, N>>(a, cfg);
+}
+
+template <typename T, int N>
+cudaError_t fine3_prep() {
+  return Fine3Set<T, N>::prepare();
+}
+
+template <typename T, int N>
+void fine3_variants(int* ncol, int* nrow) {
+  *ncol = Fine3Set<T, N>::ncol();
+  *nrow = Fine3Set<T, N>::nrow();
+}
+
+}  // namespace kd
+
+// Explicit instantiation of one (T, N) in the including translation unit.
+#define KD_FINE2_INSTANTIATE(T, N)                                        \
+  template int kd::fine2_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
+  template cudaError_t kd::fine2_prep<T, N>();                             \
+  template void kd::fine2_variants<T, N>(int*, int*);
+#define KD_FINE3_INSTANTIATE(T, N)                                        \
+  template int kd::fine3_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
+  template cudaError_t kd::fine3_prep<T, N>();                             \
+  template void kd::fine3_variants<T, N>(int*, int*);

@@ -192,6 +192,12 @@ kd_status kd_get_plan(kd_ctx* ctx, int grid, int* col, int* row) {
   return KD_OK;
 }
 
+kd_status kd_set_dependent_launch(kd_ctx* ctx, int enable) {
+  if (!ctx) return KD_EINVAL;
+  ctx->pdl = enable ? 1 : 0;
+  return KD_OK;
+}
+
 kd_status kd_autotune(kd_ctx* ctx, int grid, int batch, int nsteps, const char* cache_path, double* ms_per_step) {
   if (!ctx) return KD_EINVAL;
   int n, prec;

@@ -73,7 +73,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
            "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
-           "kd_get_plan", "kd_autotune", "kd_sweep_run"]
+           "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -104,6 +104,7 @@ def load():
         "kd_learned_apply": (I, [P, P, P, I, I]),
         "kd_plan_variants": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "kd_set_plan": (I, [P, I, I, I]),
+        "kd_set_dependent_launch": (I, [P, I]),
         "kd_get_plan": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "kd_autotune": (I, [P, I, I, I, ctypes.c_char_p, ctypes.POINTER(D)]),
         "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
@@ -310,6 +311,10 @@ def kd_plan_variants(ctx, grid=KD_GRID_FINE):
 
 def kd_set_plan(ctx, grid, col, row):
     return _check(ctx, load().kd_set_plan(ctx, int(grid), int(col), int(row)))
+
+
+def kd_set_dependent_launch(ctx, enable):
+    return _check(ctx, load().kd_set_dependent_launch(ctx, int(bool(enable))))
 
 
 def kd_get_plan(ctx, grid=KD_GRID_FINE):

@@ -80,7 +80,7 @@ def test_large_grids_fp32(kd, n):
     assert rel(out[0], ref) < TOL32
 
 
-@pytest.mark.parametrize("n", [32, 128, 256, 512])
+@pytest.mark.parametrize("n", [32, 128, 256, 512, 1024])
 def test_every_launch_plan_matches_oracle(kd, n):
     """Every instantiated (column, row) kernel variant: same oracle parity, and the same
     values as the default plan to FP32 round-off (the variants change tiles and where
