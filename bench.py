@@ -271,6 +271,97 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------- large run (config 5)
+LARGE_WL = {
+    "workload": "gp_cp_1024x1024_parareal_256_slices",
+    "flow": "galloway-proctor", "n": 1024, "kz": 0.57, "Rm": 1e4, "dt_fine_max": 1e-3, "T": 2 * math.pi * 32,
+    "slices": 256, "n_coarse": 512, "tol": 1e-6, "k_max": 32, "prec_fine": "complex64", "prec_coarse": "complex64",
+    "update": "float64", "fine_form": "increment", "coarse": "classical (the learned operator is not trained here)",
+}
+
+
+def run_large(args):
+    """Config 5: one Parareal solve of the GP 1024^2 problem with 256 slices resident on
+    one GPU, against serial fine stepping with the same kernels; growth rate from the
+    log-energy fit; fine-kernel roofline from a separately timed batched step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    W = LARGE_WL
+    n, N, T = W["n"], W["slices"], W["T"]
+    dtc = min(20 * W["dt_fine_max"], 2.0 / W["n_coarse"])     # coarse-grid stability (R15)
+    p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], W["dt_fine_max"], kd.KD_C64,
+                       n_coarse=W["n_coarse"], dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
+    ctx = kd.kd_create(p)
+    kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 2, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
+    kd.kd_autotune(ctx, kd.KD_GRID_COARSE, 1, 4, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
+    plan_f, plan_c = kd.kd_get_plan(ctx, kd.KD_GRID_FINE), kd.kd_get_plan(ctx, kd.KD_GRID_COARSE)
+    b0 = torch.tensor(kd_inputs.initial_field(n, W["kz"], 1000), device="cuda")
+    u = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = ev(), ev()
+    e0.record()
+    s, st = kd.kd_parareal_run(ctx, b0, T, N, W["k_max"], W["tol"], u)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    S = st.n_fine_steps
+    ser = torch.zeros_like(u)
+    e0, e1 = ev(), ev()
+    e0.record()
+    kd.kd_fine_serial(ctx, b0, T, N, ser)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_ser = e0.elapsed_time(e1)
+    err = (torch.linalg.norm(u[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
+    gr_ser = kd.kd_growth_rate(ctx, ser, N + 1, T, 0.5 * T)
+    del ser, u
+    torch.cuda.empty_cache()
+    # fine-kernel roofline: two steps of all 256 slices, every launch timed with events
+    x = torch.tensor(kd_inputs.initial_batch(n, W["kz"], range(8)), dtype=torch.complex64, device="cuda")
+    x = x.repeat(N // 8, 1, 1, 1)
+    t0 = torch.arange(N, dtype=torch.float64, device="cuda") * (T / N)
+    kd.kd_fine_batched(ctx, x, x, t0, 1, N)
+    kd.kd_profile(ctx, 1)
+    kd.kd_fine_batched(ctx, x, x, t0, 2, N)
+    prof_ms, prof_n = kd.kd_profile_read(ctx)
+    kd.kd_profile(ctx, 0)
+    cb, rb = col_row_bytes(n, N)
+    step_bytes = 4 * (cb + rb)
+    achieved = (cb * prof_n[0] + rb * prof_n[1]) / ((prof_ms[0] + prof_ms[1]) / 1e3) / 1e9
+    kid = 0 if prof_ms[0] >= prof_ms[1] else 1
+    k_ach = ((cb, rb)[kid] * prof_n[kid]) / (prof_ms[kid] / 1e3) / 1e9
+    hbm_peak, peak_kind = peaks()
+    units = 3 * n * n * N * S
+    out = {
+        "metric": METRIC, "value": units / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 fine / f64 update", "data": "synthetic",
+        "config": dict(W, dt_coarse=dtc, fine_steps_per_slice=S, coarse_steps_per_slice=st.n_coarse_steps,
+                       fine_plan=list(plan_f), coarse_plan=list(plan_c)),
+        "time_to_solution_ms": ms, "serial_fine_ms": ms_ser, "speedup_vs_serial_fine": ms_ser / ms,
+        "k_con": st.k_con, "converged": bool(st.converged), "sigma": list(st.sigma[:st.k_con]),
+        "err_vs_serial_fine": err, "growth_rate": st.growth_rate, "growth_rate_serial_fine": gr_ser,
+        "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
+        "fine_step": {"ms_per_step_all_slices": (prof_ms[0] + prof_ms[1]) / 2, "two_pass_bytes_per_step": step_bytes,
+                      "achieved_gbs": achieved, "frac": achieved / hbm_peak},
+        "roofline": {"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid], "achieved": k_ach,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": k_ach / hbm_peak, "traffic": None,
+                     "peak_kind": peak_kind, "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid])},
+        "clocks": clk, "gpu_launches": int(st.n_launches),
+    }
+    print(json.dumps(out), flush=True)
+    kd.kd_destroy(ctx)
+
+
 # ------------------------------------------------ batched sweep of independent instances
 SWEEP_WL = {
     "workload": "rm_kz_sweep_parareal_32_slices",
@@ -419,9 +510,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep"],
+    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large"],
                     help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
-                         "sweep: batched independent instances (Rm / kz sweep)")
+                         "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices")
     ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -433,6 +524,9 @@ def main():
         return
     if args.config == "sweep":
         run_sweep(args)
+        return
+    if args.config == "large":
+        run_large(args)
         return
 
     import numpy as np
@@ -459,6 +553,8 @@ def main():
                             n_coarse=WL["n_coarse"], dt_coarse=WL["dt_coarse_max"], prec_coarse=kd.KD_C64,
                             fine_form=kd.KD_FINE_INCREMENT)
     ctx = kd.kd_create(params, stream.cuda_stream)
+    tune_ms = kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 3, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
+    plan = kd.kd_get_plan(ctx, kd.KD_GRID_FINE)
     b0_host = torch.tensor(kd_inputs.initial_field(n, WL["kz"], 1000 + rank)).pin_memory()
     b0_dev = b0_host.to("cuda")
     u_dev = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
@@ -494,13 +590,20 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, res, ck
 
-    # ---- main timed region: device-resident inputs, kernel profile of the fine sweep on
+    # ---- main timed region: device-resident inputs, no instrumentation
     launches0 = kd.kd_launch_count(ctx)
-    kd.kd_profile(ctx, 1)
     ms, stats, clk = timed(lambda: solve(b0_dev, u_dev), args.steps, ClockSampler(local))
+    launches = kd.kd_launch_count(ctx) - launches0
+    # ---- kernel timing for the roofline: the same solve with every fine launch bracketed
+    # by CUDA events on the context stream (separate from the timed region: the events
+    # serialise the dependent launches)
+    prof_steps = 2
+    kd.kd_profile(ctx, 1)
+    for _ in range(prof_steps):
+        solve(b0_dev, u_dev)
+    torch.cuda.synchronize()
     prof_ms, prof_n = kd.kd_profile_read(ctx)
     kd.kd_profile(ctx, 0)
-    launches = kd.kd_launch_count(ctx) - launches0
     total_ms = sum(ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -536,13 +639,13 @@ def main():
     S = st.n_fine_steps
     # fine-sweep batches over one solve: slices k-1..N-1 in iteration k
     batches = [N - min(k - 1, N - 1) for k in range(1, st.k_con + 1)]
-    col_b = sum(col_row_bytes(n, b)[0] * 4 * S for b in batches) * args.steps
-    row_b = sum(col_row_bytes(n, b)[1] * 4 * S for b in batches) * args.steps
+    col_b = sum(col_row_bytes(n, b)[0] * 4 * S for b in batches) * prof_steps
+    row_b = sum(col_row_bytes(n, b)[1] * 4 * S for b in batches) * prof_steps
     kid = 0 if prof_ms[0] >= prof_ms[1] else 1
     kbytes = (col_b, row_b)[kid]
     achieved = kbytes / (prof_ms[kid] / 1e3) / 1e9
     fine_units = 3 * n * n * S * sum(batches) * args.steps
-    fine_rate = fine_units / ((prof_ms[0] + prof_ms[1]) / 1e3) / 1e6
+    fine_rate = fine_units / (sum(x.ms_fine for x in stats) / 1e3) / 1e6
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -558,7 +661,8 @@ def main():
         "vs_baseline": None, "dtype": "c64 fine / f64 update", "data": "synthetic",
         "config": dict(WL, fine_steps_per_slice=S, coarse_steps_per_slice=st.n_coarse_steps,
                        l2="flushed between steps (512 MB write)", parallelism="time slices in one launch; "
-                       "ranks solve independent instances"),
+                       "ranks solve independent instances", fine_plan=list(plan),
+                       fine_plan_ms_per_step=tune_ms),
         "time_to_solution_ms": ms_per_step, "serial_fine_ms": serial_ms,
         "speedup_vs_serial_fine": serial_ms / ms_per_step, "k_con": st.k_con,
         "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "growth_rate": st.growth_rate,

@@ -1,10 +1,15 @@
-"""Small, repeatable fine-propagator launch for profiling one kernel with ncu.
+"""Small, repeatable launches for profiling with ncu.
 
-    python -m paper_1902_00387_gb300.profile_case --n 128 --batch 64 --steps 2
+    python -m paper_1902_00387_gb300.profile_case --n 128 --batch 64 --steps 2 [--plan 0,3]
 
 builds the library if needed, propagates `batch` seeded Galloway-Proctor fields by
 `steps` fine steps once to warm up and once more (the launches to capture), and
 prints the device time of the second call.
+
+    python -m paper_1902_00387_gb300.profile_case --parareal
+
+runs one Parareal solve of the GP 128^2, 64-slice workload of bench.py (plan
+autotuned first), for a launch list of a whole solve.
 """
 import argparse
 import os
@@ -23,6 +28,8 @@ def main():
     ap.add_argument("--kz", type=float, default=0.57)
     ap.add_argument("--Rm", type=float, default=100.0)
     ap.add_argument("--dt", type=float, default=5e-3)
+    ap.add_argument("--plan", default=None, help="column,row variant of the fine kernels")
+    ap.add_argument("--parareal", action="store_true")
     args = ap.parse_args()
     import torch
 
@@ -32,8 +39,31 @@ def main():
     import paper_1902_00387_gb300 as kd
     kd.load()
     torch.cuda.init()
+    if args.parareal:
+        import math
+        n, N, T = 128, 64, 2 * math.pi * 8
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, 0.57, 100.0, 5e-3, kd.KD_C64, n_coarse=64,
+                           dt_coarse=0.04, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
+        ctx = kd.kd_create(p)
+        if args.plan:
+            kd.kd_set_plan(ctx, kd.KD_GRID_FINE, *(int(v) for v in args.plan.split(",")))
+        else:
+            kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 2)
+        b0 = torch.tensor(kd_inputs.initial_field(n, 0.57, 1000), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s, st = kd.kd_parareal_run(ctx, b0, T, N, 64, 1e-6)
+        e1.record()
+        torch.cuda.synchronize()
+        print("parareal GP 128^2 x 64 slices: %.1f ms, k_con %d, plan %s" % (e0.elapsed_time(e1), st.k_con,
+                                                                            kd.kd_get_plan(ctx)))
+        kd.kd_destroy(ctx)
+        return
     p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64)
     ctx = kd.kd_create(p)
+    if args.plan:
+        c, r = (int(v) for v in args.plan.split(","))
+        kd.kd_set_plan(ctx, kd.KD_GRID_FINE, c, r)
     x = torch.tensor(kd_inputs.initial_batch(args.n, args.kz, range(args.batch)), dtype=torch.complex64,
                      device="cuda")
     t0 = torch.arange(args.batch, dtype=torch.float64, device="cuda") * 0.785
