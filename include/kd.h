@@ -247,6 +247,46 @@ kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int
 kd_status kd_fine_batched_static(const kd_params* params, const void* b_in, void* b_out, const double* t0,
                                  int nsteps, int batch, void* cuda_stream);
 
+/* Growth rate by power iteration of the fine propagator over [t0, t0 + tau] (Sec. 1: the
+ * leading eigenvalue for a steady flow, the leading Floquet multiplier for a time-periodic
+ * one with tau = its period): b <- M b / |M b| from b0 (complex128 [3][n][n], host or
+ * device), rate_k = ln(|M b| / |b|) / tau, until |rate_k - rate_{k-1}| <= tol or max_iter
+ * iterations.  The fine steps are ceil(tau / dt_fine) steps of the context's fine
+ * precision; norms are FP64.  rate: the last estimate; iters (may be NULL): iterations
+ * taken; b_out (may be NULL): the normalised final vector (complex128 [3][n][n]).
+ * Synchronous.  KD_ENOTCONV if tol was not reached (outputs still written),
+ * KD_ENONFINITE on a zero or non-finite norm. */
+kd_status kd_growth_power(kd_ctx* ctx, const double* b0, double t0, double tau, int max_iter, double tol,
+                          double* rate, int* iters, double* b_out);
+
+/* ------------------------------------------------------------------------------------
+ * Slice blocks for Parareal over several ranks (the paper's time communicator, Sec. 4.1
+ * Algorithms 1-3): rank r owns the contiguous slices [lo, lo + n_local) of n_slices.  The
+ * host drives the iteration and moves one boundary state per sweep between ranks:
+ *
+ *   kd_block_init(ctx, lo, n_local, T, n_slices)
+ *   rank 0: kd_block_set_initial(ctx, b0)
+ *   k = 0:  rank > 0 receives U_lo -> kd_block_set_boundary;  kd_block_sweep(ctx, 0, NULL);
+ *           kd_block_get_boundary -> send U_hi to rank + 1
+ *   k >= 1: kd_block_fine(ctx, k) (parallel step, no communication); receive U_lo and
+ *           kd_block_set_boundary (rank > 0); kd_block_sweep(ctx, k, &sigma) (the rank
+ *           holding the last slice gets the Eq. 9 defect); send U_hi; broadcast sigma.
+ *
+ * The arithmetic is that of kd_parareal_run with fine_form KD_FINE_INCREMENT (required);
+ * one rank holding all slices reproduces it.  Boundary states are FP64 compact fields of
+ * kd_block_boundary_bytes() bytes (host or device buffers).  States are returned by
+ * kd_block_get_state (local index 0..n_local, complex128 [3][n][n]).  Synchronous.  The
+ * learned coarse propagator is used where it passed validation, without the fallback
+ * rule of kd_parareal_run. */
+kd_status kd_block_init(kd_ctx* ctx, int lo, int n_local, double T, int n_slices);
+size_t kd_block_boundary_bytes(kd_ctx* ctx);
+kd_status kd_block_set_initial(kd_ctx* ctx, const double* b0);
+kd_status kd_block_set_boundary(kd_ctx* ctx, const double* u_lo);
+kd_status kd_block_get_boundary(kd_ctx* ctx, double* u_hi);
+kd_status kd_block_fine(kd_ctx* ctx, int k);
+kd_status kd_block_sweep(kd_ctx* ctx, int k, double* sigma);
+kd_status kd_block_get_state(kd_ctx* ctx, int local_index, double* u);
+
 /* ------------------------------------------------------------------------------------
  * Launch plans and the autotuner.
  *

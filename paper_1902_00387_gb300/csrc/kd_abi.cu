@@ -382,7 +382,7 @@ kd_status learned_step(kd_ctx* ctx, int i, bool init, bool last) {
   const int n = ctx->p.n, Kf = n / 3, Pf = 2 * Kf + 1;
   const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P;
   const long len = compact_len(n);
-  const int ph = i % ctx->l_nphase;
+  const int ph = (ctx->blk_lo + i) % ctx->l_nphase;   // phase of the global slice index
   float* x = ctx->l_x;
   float* y = ctx->l_x + 2 * nc;
   KD_LAUNCH(learned_gather(ctx->U + 2 * i * len, init ? nullptr : ctx->Uprev + 2 * i * len, Kf, Pf, x, K, P, 1,
@@ -400,7 +400,7 @@ kd_status learned_step(kd_ctx* ctx, int i, bool init, bool last) {
 
 bool use_learned(const kd_ctx* ctx, int i) {
   return ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback && ctx->l_nphase > 0 &&
-         ctx->l_valid[i % ctx->l_nphase];
+         ctx->l_valid[(ctx->blk_lo + i) % ctx->l_nphase];
 }
 
 // Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
@@ -603,9 +603,10 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
       return fail(ctx, KD_EINVAL, "kd_parareal_run: slice length differs from the learned operators' slice");
   }
   ctx->fallback = 0;
+  ctx->blk_lo = 0;
   const long len = compact_len(n), lenc = 3L * ctx->cP * ctx->cP;
-  KD_LAUNCH(fill_times(ctx->t0f, N + 1, 0.0, dT, ctx->st), "times");
-  KD_LAUNCH(fill_times(ctx->t0c, N + 1, 0.0, dT, ctx->st), "times");
+  KD_LAUNCH(fill_slice_times(ctx->t0f, N + 1, 0, dT, ctx->st), "times");
+  KD_LAUNCH(fill_slice_times(ctx->t0c, N + 1, 0, dT, ctx->st), "times");
 
   KD_CUDA(cudaEventRecord(ctx->ev[0], ctx->st), "event");
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
@@ -719,7 +720,7 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
   if ((s = ensure_slices(ctx, N)) != KD_OK) return s;
   if ((s = ensure_ws(ctx, ctx->ws_f, n, pf, 1)) != KD_OK) return s;
   const long len = compact_len(n);
-  KD_LAUNCH(fill_times(ctx->t0f, N + 1, 0.0, dT, ctx->st), "times");
+  KD_LAUNCH(fill_slice_times(ctx->t0f, N + 1, 0, dT, ctx->st), "times");
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
   for (int i = 0; i < N; ++i) {
     KD_LAUNCH(compact_resample(KD_C128, ctx->U + 2 * i * len, n, pf, ctx->ws_f.X, n, 1, ctx->st), "to fine");

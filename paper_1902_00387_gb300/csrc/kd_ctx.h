@@ -72,6 +72,9 @@ struct kd_ctx {
   std::vector<int> l_valid;       // phase operator passed validation against the classical one
   float* l_x = nullptr;           // sweep vectors [2][nc] complex
   int fallback = 0;
+  // slice block of a multi-rank run (kd_block_*): global index of local slice 0 and sizes
+  int blk_lo = 0, blk_n = 0, blk_N = 0, blk_S = 0, blk_Sc = 0;
+  double blk_dt = 0.0, blk_dtc = 0.0;
   // optional event timing of the fine column / row kernels
   int prof = 0;
   std::vector<cudaEvent_t> pev;
@@ -114,6 +117,16 @@ kd::FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int 
                        const double* t0);
 // point a.phases at a table of the workspace large enough for `nsteps` steps
 kd_status with_phases(kd_ctx* ctx, FineWs& w, kd::FineArgs& a, int nsteps);
+// Parareal building blocks (kd_abi.cu) on local slice indices of the context's slice
+// arrays U / Fv / Uprev / Gv (slice i starts at t0f[i]):
+kd_status ensure_slices(kd_ctx* ctx, long N);
+kd_status coarse_phases(kd_ctx* ctx, int N, int Sc, double dtc);
+kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool last);
+kd_status learned_step(kd_ctx* ctx, int i, bool init, bool last);
+bool use_learned(const kd_ctx* ctx, int i);
+kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter);
+kd_status copy_in_b0(kd_ctx* ctx, const double* b0);
+kd_status ensure_full_tmp(kd_ctx* ctx, size_t bytes);
 // fine steps on grid g (0 fine, 1 coarse) with the context's plan for that grid
 int run_fine(kd_ctx* ctx, int g, int prec, const kd::FineArgs& a, int nsteps, bool prologue, bool store_last,
              const kd::LaunchProbe* probe = nullptr, const int* active = nullptr);

@@ -99,5 +99,7 @@ int accum_out(int pin, const void* X, double* Fv, long total, int first, cudaStr
 int diff_kernel(const double* U, const double* Uprev, double* d, long total, cudaStream_t st);
 // dst[i] = t0 + i * dT
 int fill_times(double* dst, int count, double t0, double dT, cudaStream_t st);
+// dst[i] = (first + i) * dT: start times of slices first, first + 1, ...
+int fill_slice_times(double* dst, int count, int first, double dT, cudaStream_t st);
 
 }  // namespace kd

@@ -308,6 +308,16 @@ __global__ void k_fill_times(double* dst, int count, double t0, double dT) {
   if (i < count) dst[i] = t0 + i * dT;
 }
 
+__global__ void k_fill_slice_times(double* dst, int count, int first, double dT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (double)(first + i) * dT;
+}
+
+int fill_slice_times(double* dst, int count, int first, double dT, cudaStream_t st) {
+  k_fill_slice_times<<<nblk(count, 256), 256, 0, st>>>(dst, count, first, dT);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int fill_times(double* dst, int count, double t0, double dT, cudaStream_t st) {
   if (count <= 0) return 0;
   k_fill_times<<<nblk(count, 256), 256, 0, st>>>(dst, count, t0, dT);

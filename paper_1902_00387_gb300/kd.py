@@ -73,7 +73,9 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
            "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
-           "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch"]
+           "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
+           "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
+           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -110,6 +112,15 @@ def load():
         "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
                              ctypes.POINTER(P), ctypes.POINTER(kd_instance_result), ctypes.POINTER(kd_sweep_stats),
                              P, ctypes.c_char_p]),
+        "kd_growth_power": (I, [P, P, D, D, I, D, ctypes.POINTER(D), ctypes.POINTER(I), P]),
+        "kd_block_init": (I, [P, I, I, D, I]),
+        "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
+        "kd_block_set_initial": (I, [P, P]),
+        "kd_block_set_boundary": (I, [P, P]),
+        "kd_block_get_boundary": (I, [P, P]),
+        "kd_block_fine": (I, [P, I]),
+        "kd_block_sweep": (I, [P, I, ctypes.POINTER(D)]),
+        "kd_block_get_state": (I, [P, I, P]),
         "kd_launch_count": (ctypes.c_longlong, [P]),
         "kd_profile": (I, [P, I]),
         "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
@@ -357,6 +368,58 @@ def kd_sweep_run(instances, b0, T, n_slices, k_max, tol, u_final=None, tune_cach
     if s not in (KD_OK, KD_ENOTCONV):
         raise KdError(s, err.value.decode())
     return s, list(res), st
+
+
+def kd_growth_power(ctx, b0, t0, tau, max_iter, tol, b_out=None):
+    """Power-iteration growth rate; returns (status, rate, iterations)."""
+    rate, its = ctypes.c_double(), ctypes.c_int()
+    s = load().kd_growth_power(ctx, _any_ptr(b0, "complex128"), float(t0), float(tau), int(max_iter), float(tol),
+                               ctypes.byref(rate), ctypes.byref(its), _any_ptr(b_out, "complex128"))
+    _check(ctx, s, allow=(KD_ENOTCONV,))
+    return s, rate.value, its.value
+
+
+def kd_block_init(ctx, lo, n_local, T, n_slices):
+    return _check(ctx, load().kd_block_init(ctx, int(lo), int(n_local), float(T), int(n_slices)))
+
+
+def kd_block_boundary_bytes(ctx):
+    return int(load().kd_block_boundary_bytes(ctx))
+
+
+def kd_block_set_initial(ctx, b0):
+    return _check(ctx, load().kd_block_set_initial(ctx, _any_ptr(b0, "complex128")))
+
+
+def _f64_ptr(x):
+    if isinstance(x, np.ndarray):
+        return _ptr(x, "float64", device=False)
+    return _ptr(x, "float64", device=False)
+
+
+def kd_block_set_boundary(ctx, u_lo):
+    """u_lo: float64 buffer of kd_block_boundary_bytes(ctx) bytes (host or device)."""
+    return _check(ctx, load().kd_block_set_boundary(ctx, _f64_ptr(u_lo)))
+
+
+def kd_block_get_boundary(ctx, u_hi):
+    return _check(ctx, load().kd_block_get_boundary(ctx, _f64_ptr(u_hi)))
+
+
+def kd_block_fine(ctx, k):
+    return _check(ctx, load().kd_block_fine(ctx, int(k)))
+
+
+def kd_block_sweep(ctx, k):
+    """Serial sweep of iteration k over the block; returns the defect (0 unless this
+    block holds the last slice and k >= 1)."""
+    sig = ctypes.c_double()
+    _check(ctx, load().kd_block_sweep(ctx, int(k), ctypes.byref(sig)))
+    return sig.value
+
+
+def kd_block_get_state(ctx, i, u):
+    return _check(ctx, load().kd_block_get_state(ctx, int(i), _any_ptr(u, "complex128")))
 
 
 def kd_launch_count(ctx):

@@ -1,0 +1,112 @@
+"""Parareal over several ranks: the paper's time communicator (Sec. 4.1, Algorithms 1-3).
+
+Rank r owns the contiguous slices [lo_r, hi_r) of N.  Iteration 0 is the serial coarse
+sweep passed from rank to rank; in iteration k >= 1 every rank takes its parallel step
+(fine propagation of its slices, no communication), then the serial sweep runs through
+the ranks: rank r receives U_{lo_r} from rank r - 1, sweeps its block and sends U_{hi_r}
+to rank r + 1.  The rank holding the last slice measures the defect of Eq. 9 and
+broadcasts it (8 bytes); every rank stops at the same iteration.
+
+The per-rank work is done by a block object (the library's kd_block_* calls in
+`LibBlock`); messages go through a communicator object (`TorchDistComm` for
+torch.distributed, one GPU per rank over NCCL or host tensors over gloo).  This module
+holds only the schedule: no arithmetic of the method.
+"""
+import math
+
+
+def block_of(rank, world, n_slices):
+    """Contiguous block [lo, hi) of slices owned by `rank` (sizes differ by at most one)."""
+    lo = rank * n_slices // world
+    hi = (rank + 1) * n_slices // world
+    return lo, hi
+
+
+class TorchDistComm:
+    """Point-to-point boundary messages and the defect broadcast over torch.distributed."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+
+    def send(self, buf, dst):
+        self.dist.send(buf, dst, group=self.group)
+
+    def recv(self, buf, src):
+        self.dist.recv(buf, src, group=self.group)
+
+    def bcast_scalar(self, value, root, like):
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64, device=like.device)
+        self.dist.broadcast(t, root, group=self.group)
+        return float(t.item())
+
+
+class LibBlock:
+    """A rank's slice block on its GPU through the library (kd_block_*)."""
+
+    def __init__(self, kd, ctx, device="cuda"):
+        self.kd, self.ctx, self.device = kd, ctx, device
+
+    def init(self, lo, n_local, T, n_slices):
+        self.kd.kd_block_init(self.ctx, lo, n_local, T, n_slices)
+
+    def make_buffer(self):
+        import torch
+        return torch.empty(self.kd.kd_block_boundary_bytes(self.ctx) // 8, dtype=torch.float64, device=self.device)
+
+    def set_initial(self, b0):
+        self.kd.kd_block_set_initial(self.ctx, b0)
+
+    def set_boundary(self, buf):
+        self.kd.kd_block_set_boundary(self.ctx, buf)
+
+    def get_boundary(self, buf):
+        self.kd.kd_block_get_boundary(self.ctx, buf)
+
+    def fine(self, k):
+        self.kd.kd_block_fine(self.ctx, k)
+
+    def sweep(self, k):
+        return self.kd.kd_block_sweep(self.ctx, k)
+
+
+def parareal_pipeline(block, comm, rank, world, b0, T, n_slices, k_max, tol):
+    """Run Parareal for `rank` of `world`.  `b0` is used on rank 0 only.  Returns the
+    rank's block bounds, the iteration count and the defect history (the same on every
+    rank).  Raises FloatingPointError on a non-finite defect."""
+    if world < 1 or not 0 <= rank < world or n_slices < world:
+        raise ValueError("need 0 <= rank < world <= n_slices")
+    lo, hi = block_of(rank, world, n_slices)
+    block.init(lo, hi - lo, T, n_slices)
+    if rank == 0:
+        block.set_initial(b0)
+    buf = block.make_buffer()
+    last = world - 1
+
+    def sweep(k):
+        if rank > 0:
+            comm.recv(buf, rank - 1)
+            block.set_boundary(buf)
+        s = block.sweep(k)
+        if rank < last:
+            block.get_boundary(buf)
+            comm.send(buf, rank + 1)
+        return s
+
+    sweep(0)
+    sigmas = []
+    k_con = k_max
+    converged = False
+    for k in range(1, k_max + 1):
+        block.fine(k)
+        s = comm.bcast_scalar(sweep(k), last, buf)
+        sigmas.append(s)
+        if not math.isfinite(s):
+            raise FloatingPointError("non-finite Parareal defect at iteration %d" % k)
+        if s <= tol:
+            k_con, converged = k, True
+            break
+    return {"lo": lo, "hi": hi, "k_con": k_con if converged else min(k_max, len(sigmas)), "converged": converged,
+            "sigma": sigmas}

@@ -1,0 +1,90 @@
+"""Direct growth rate on the GPU (kd_growth_power): power iteration of the fine
+propagator against the oracle's Floquet power iteration (Galloway-Proctor, Table 1) and
+the leading eigenvalue of the oracle's sparse linear operator (Roberts)."""
+import math
+
+import numpy as np
+import pytest
+
+import kd_inputs as I
+from oracle import kd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    return kd
+
+
+def test_gp_floquet_rate_matches_oracle_and_table1(kd):
+    # Table 1: GP, Rm = 3, kx = 0.57 (our kz), 16 modes -> 0.15; one period = 1257 steps
+    n, kz, Rm, S = 16, 0.57, 3.0, 1257
+    dt = 2 * math.pi / S
+    b = I.initial_field(n, kz, 1)
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    g = []
+    x = b.copy()
+    for _ in range(6):
+        nx = O.propagate(x, p, 0.0, dt, S)
+        g.append(math.log(O.l2(nx) / O.l2(x)) / (2 * math.pi))
+        x = nx / O.l2(nx)
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C128))
+    try:
+        out = np.zeros_like(b)
+        s, rate, its = kd.kd_growth_power(ctx, b, 0.0, 2 * math.pi, 6, 0.0, out)
+    finally:
+        kd.kd_destroy(ctx)
+    assert its == 6
+    assert abs(rate - g[-1]) < 1e-11, (rate, g[-1])
+    assert float("%.2g" % rate) == 0.15
+    assert np.linalg.norm(out - x) < 1e-10                 # same normalised vector
+
+
+def test_roberts_rate_matches_leading_eigenvalue(kd):
+    import scipy.sparse.linalg as sla
+    n, kz, Rm = 32, 1.0, 8.0
+    w = sla.eigs(O.linear_operator(O.Problem(O.ROBERTS, n, kz, Rm)).tocsc(), k=3, sigma=0.3,
+                 return_eigenvectors=False, tol=1e-13)
+    gamma = max(w.real)
+    ctx = kd.kd_create(kd.make_params(O.ROBERTS, n, kz, Rm, 0.01, kd.KD_C64))
+    try:
+        s, rate, its = kd.kd_growth_power(ctx, I.initial_field(n, kz, 3), 0.0, 2.0, 60, 1e-8)
+    finally:
+        kd.kd_destroy(ctx)
+    assert s == kd.KD_OK, (rate, its)
+    assert abs(rate - gamma) < 1e-4, (rate, gamma)          # growth-rate tolerance
+
+
+def test_gp_fp32_rate_matches_fp64(kd):
+    """The FP32 propagator gives the FP64 growth rate to 1e-4 (Rm = 100, 64^2)."""
+    n, kz, Rm = 64, 0.57, 100.0
+    dt = 2 * math.pi / 1257
+    b = I.initial_field(n, kz, 9)
+    rates = []
+    for prec in (kd.KD_C64, kd.KD_C128):
+        ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, prec))
+        try:
+            s, r, its = kd.kd_growth_power(ctx, b, 0.0, 2 * math.pi, 30, 1e-9)
+            rates.append(r)
+        finally:
+            kd.kd_destroy(ctx)
+    assert abs(rates[0] - rates[1]) < 1e-4, rates
+
+
+def test_growth_argument_errors(kd):
+    ctx = kd.kd_create(kd.make_params(O.ROBERTS, 16, 1.0, 8.0, 0.01, kd.KD_C64))
+    try:
+        b = I.initial_field(16, 1.0, 1)
+        with pytest.raises(kd.KdError):
+            kd.kd_growth_power(ctx, b, 0.0, 0.0, 5, 1e-6)
+        with pytest.raises(kd.KdError):
+            kd.kd_growth_power(ctx, b, 0.0, 1.0, 0, 1e-6)
+    finally:
+        kd.kd_destroy(ctx)

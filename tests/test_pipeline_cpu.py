@@ -1,0 +1,137 @@
+"""Multi-rank Parareal schedule (paper_1902_00387_gb300.pipeline) on CPU ranks over gloo,
+with oracle-backed slice blocks: every rank's slice states, the iteration count and the
+defect history equal the single-process oracle Parareal bit for bit."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import kd_inputs as I
+from oracle import kd_oracle as O
+
+N_SLICES, T, N_GRID = 6, 1.2, 16
+
+
+class OracleBlock:
+    """A rank's slices with the oracle's propagators (Eq. 8 in the evaluation order
+    F(U^k_n) + (G(U^{k+1}_n) - G(U^k_n)))."""
+
+    def __init__(self, prob, dt, dtc, nc):
+        self.prob, self.dt, self.dtc, self.nc = prob, dt, dtc, nc
+
+    def init(self, lo, n_local, T, n_slices):
+        import math
+        self.lo, self.nl, self.N = lo, n_local, n_slices
+        self.dT = T / n_slices
+        self.S = math.ceil(self.dT / self.dt - 1e-9)
+        self.Sc = math.ceil(self.dT / self.dtc - 1e-9)
+        self.U = [None] * (n_local + 1)
+        self.F = [None] * n_local
+        self.G = [None] * n_local
+
+    def fine_op(self, u, n):
+        return O.propagate(u, self.prob, n * self.dT, self.dT / self.S, self.S)
+
+    def coarse_op(self, u, n):
+        return O.coarse_propagate(u, self.prob, self.nc, n * self.dT, self.dT / self.Sc, self.Sc)
+
+    def make_buffer(self):
+        import torch
+        return torch.zeros(2 * 3 * N_GRID * N_GRID, dtype=torch.float64)
+
+    def set_initial(self, b0):
+        self.U[0] = np.array(b0, np.complex128)
+
+    def set_boundary(self, buf):
+        self.U[0] = buf.numpy().view(np.complex128).reshape(3, N_GRID, N_GRID).copy()
+
+    def get_boundary(self, buf):
+        import torch
+        buf.copy_(torch.from_numpy(np.ascontiguousarray(self.U[self.nl]).view(np.float64).ravel()))
+
+    def fine(self, k):
+        for i in range(self.nl):
+            self.F[i] = self.fine_op(self.U[i], self.lo + i)
+
+    def sweep(self, k):
+        prev = None if self.U[self.nl] is None else self.U[self.nl].copy()
+        for i in range(self.nl):
+            g = self.coarse_op(self.U[i], self.lo + i)
+            self.U[i + 1] = g.copy() if k == 0 else self.F[i] + (g - self.G[i])
+            self.G[i] = g
+        if k >= 1 and self.lo + self.nl == self.N:
+            return O.l2(self.U[self.nl] - prev) / O.l2(self.U[self.nl])
+        return 0.0
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, k_max, tol, outdir):
+    import torch.distributed as dist
+    from paper_1902_00387_gb300 import pipeline
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        prob = O.Problem(O.ROBERTS, N_GRID, 1.0, 8.0)
+        blk = OracleBlock(prob, 0.02, 0.1, 16)
+        b0 = I.initial_field(N_GRID, 1.0, 5)
+        res = pipeline.parareal_pipeline(blk, pipeline.TorchDistComm(), rank, world, b0, T, N_SLICES, k_max, tol)
+        np.savez(os.path.join(outdir, "rank%d.npz" % rank), U=np.stack(blk.U), lo=res["lo"], hi=res["hi"],
+                 k_con=res["k_con"], sigma=np.array(res["sigma"]))
+    finally:
+        dist.destroy_process_group()
+
+
+def _run(world, k_max, tol, tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(world, port, k_max, tol, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    return [dict(np.load(os.path.join(str(tmp_path), "rank%d.npz" % r))) for r in range(world)]
+
+
+def _reference(k_max, tol):
+    prob = O.Problem(O.ROBERTS, N_GRID, 1.0, 8.0)
+    blk = OracleBlock(prob, 0.02, 0.1, 16)
+    blk.init(0, N_SLICES, T, N_SLICES)
+    b0 = I.initial_field(N_GRID, 1.0, 5)
+    return O.parareal(b0, blk.fine_op, blk.coarse_op, N_SLICES, k_max, tol)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_pipeline_equals_single_process_parareal(world, tmp_path):
+    out = _run(world, 3, 0.0, tmp_path)
+    ref = _reference(3, 0.0)
+    for r, o in enumerate(out):
+        lo, hi = int(o["lo"]), int(o["hi"])
+        assert (lo, hi) == (r * N_SLICES // world, (r + 1) * N_SLICES // world)
+        assert np.array_equal(o["U"], np.stack(ref["U"][lo:hi + 1]))   # bit for bit
+        assert np.array_equal(o["sigma"], np.array(ref["sigma"]))
+        assert int(o["k_con"]) == 3
+
+
+def test_pipeline_stops_at_tolerance_on_every_rank(tmp_path):
+    tol = 1e-6
+    ref = _reference(N_SLICES, tol)
+    out = _run(2, N_SLICES, tol, tmp_path)
+    assert ref["k_con"] < N_SLICES
+    for o in out:
+        assert int(o["k_con"]) == ref["k_con"]
+        assert np.array_equal(o["sigma"], np.array(ref["sigma"]))
+
+
+def test_block_bounds_cover_the_slices():
+    from paper_1902_00387_gb300.pipeline import block_of
+    for N in (1, 5, 64, 257):
+        for world in range(1, min(N, 9) + 1):
+            blocks = [block_of(r, world, N) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == N
+            assert all(a[1] == b[0] for a, b in zip(blocks, blocks[1:]))
+            sizes = [hi - lo for lo, hi in blocks]
+            assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 1
