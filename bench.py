@@ -493,6 +493,23 @@ def run_sweep(args):
         dist.destroy_process_group()
 
 
+# FP32 arithmetic rate from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops
+# (fused multiply-add) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def conv_roofline(n, S, batches, steps, stats):
+    """ALU roofline of the convolution-form fine propagator: ~180 flops per kept mode and
+    stage (two neighbour pairs of cross products with the 4 flow modes, curl, stage update),
+    i.e. 720 P^2 flops per slice-step, over the fine phase's device time."""
+    P = 2 * (n // 3) + 1
+    flops = 720.0 * P * P * S * sum(batches) * steps
+    tf = flops / (sum(x.ms_fine for x in stats) / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "coarse_cluster_kernel<float, 4> as the fine convolution operator",
+            "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS,
+            "traffic": None, "peak_kind": "derived from unit counts and the 2.07 GHz clock"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -514,6 +531,9 @@ def main():
                     help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
                          "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices")
     ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
+    ap.add_argument("--fine-operator", default="fft", choices=["fft", "conv"],
+                    help="fft: the pseudo-spectral fine step (the workload's definition); conv: the same operator "
+                         "as the exact spectral convolution in one persistent launch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -549,9 +569,10 @@ def main():
     stream = torch.cuda.current_stream()
 
     n, N, T = WL["n"], WL["slices"], WL["T"]
+    fine_op = kd.KD_FINE_CONV if args.fine_operator == "conv" else kd.KD_FINE_FFT
     params = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C64,
                             n_coarse=WL["n_coarse"], dt_coarse=WL["dt_coarse_max"], prec_coarse=kd.KD_C64,
-                            fine_form=kd.KD_FINE_INCREMENT)
+                            fine_form=kd.KD_FINE_INCREMENT, fine_operator=fine_op)
     ctx = kd.kd_create(params, stream.cuda_stream)
     tune_ms = kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 3, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
     plan = kd.kd_get_plan(ctx, kd.KD_GRID_FINE)
@@ -643,7 +664,7 @@ def main():
     row_b = sum(col_row_bytes(n, b)[1] * 4 * S for b in batches) * prof_steps
     kid = 0 if prof_ms[0] >= prof_ms[1] else 1
     kbytes = (col_b, row_b)[kid]
-    achieved = kbytes / (prof_ms[kid] / 1e3) / 1e9
+    achieved = kbytes / (prof_ms[kid] / 1e3) / 1e9 if prof_ms[kid] > 0 else 0.0
     fine_units = 3 * n * n * S * sum(batches) * args.steps
     fine_rate = fine_units / (sum(x.ms_fine for x in stats) / 1e3) / 1e6
 
@@ -661,17 +682,18 @@ def main():
         "vs_baseline": None, "dtype": "c64 fine / f64 update", "data": "synthetic",
         "config": dict(WL, fine_steps_per_slice=S, coarse_steps_per_slice=st.n_coarse_steps,
                        l2="flushed between steps (512 MB write)", parallelism="time slices in one launch; "
-                       "ranks solve independent instances", fine_plan=list(plan),
+                       "ranks solve independent instances", fine_plan=list(plan), fine_operator=args.fine_operator,
                        fine_plan_ms_per_step=tune_ms),
         "time_to_solution_ms": ms_per_step, "serial_fine_ms": serial_ms,
         "speedup_vs_serial_fine": serial_ms / ms_per_step, "k_con": st.k_con,
         "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "growth_rate": st.growth_rate,
         "fine_mdof_steps_per_s": fine_rate,
         "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
-        "roofline": {"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
-                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": None, "peak_kind": peak_kind,
-                     "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]},
+        "roofline": ({"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
+                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                      "traffic": None, "peak_kind": peak_kind,
+                      "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]}
+                     if args.fine_operator == "fft" else conv_roofline(n, S, batches, args.steps, stats)),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 16, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -57,6 +57,11 @@ enum { KD_COARSE_CLASSICAL = 0, KD_COARSE_LEARNED = 1 };
  * Both are the same iteration in exact arithmetic; DIRECT keeps the bitwise
  * finite-termination property (after k iterations slices 0..k equal kd_fine_serial). */
 enum { KD_FINE_DIRECT = 0, KD_FINE_INCREMENT = 1 };
+/* Evaluation of the explicit term by the fine propagator.  The flow has Fourier modes
+ * |q| = 1 only, so with the 2/3 rule the pseudo-spectral product u x b has no aliasing
+ * and equals the spectral convolution sum_q u_hat(q) x b_hat(k - q) exactly; the two
+ * operators differ by round-off. */
+enum { KD_FINE_FFT = 0, KD_FINE_CONV = 1 };
 
 #define KD_MAX_SLICES 1024
 #define KD_MAX_ITERS 256
@@ -79,6 +84,10 @@ typedef struct {
                           the learned operator AND by the classical coarse propagator ("same
                           truncation"); 0: the dealiased set of the n_coarse grid */
   int fine_form;       /* KD_FINE_DIRECT or KD_FINE_INCREMENT (kd_parareal_run) */
+  int fine_operator;   /* KD_FINE_FFT (pseudo-spectral: FFT, u x b on the grid, FFT) or
+                          KD_FINE_CONV: the same discrete operator evaluated as the exact
+                          4-mode spectral convolution in a persistent cluster kernel (one
+                          launch for all steps; grids n <= 128) */
 } kd_params;
 
 /* Create a context for one problem.  `cuda_stream` is a cudaStream_t (may be NULL).

@@ -293,6 +293,9 @@ kd_status check_params(const kd_params* p, std::string& why) {
   if (p->coarse_kind == KD_COARSE_LEARNED && (p->learned_modes == 0 || p->fine_form != KD_FINE_INCREMENT))
     return why = "the learned coarse propagator needs learned_modes > 0 and fine_form KD_FINE_INCREMENT", KD_EINVAL;
   if (p->fine_form != KD_FINE_DIRECT && p->fine_form != KD_FINE_INCREMENT) return why = "bad fine_form", KD_EINVAL;
+  if (p->fine_operator != KD_FINE_FFT && p->fine_operator != KD_FINE_CONV) return why = "bad fine_operator", KD_EINVAL;
+  if (p->fine_operator == KD_FINE_CONV && !coarse_conv_supported(2 * (p->n / 3) + 1))
+    return why = "fine_operator KD_FINE_CONV needs n <= 128", KD_EINVAL;
   return KD_OK;
 }
 
@@ -403,6 +406,28 @@ bool use_learned(const kd_ctx* ctx, int i) {
          ctx->l_valid[(ctx->blk_lo + i) % ctx->l_nphase];
 }
 
+// Fine propagator in the spectral-convolution form (KD_FINE_CONV): `batch` FP64 compact
+// fields `in` (fine set) -> `out` (may alias), nsteps steps of dt from t0[b], all in one
+// persistent cluster launch with arithmetic in the fine precision.
+kd_status conv_fine(kd_ctx* ctx, const double* in, double* out, long batch, int nsteps, double dt, const double* t0) {
+  const int n = ctx->p.n, pf = ctx->p.prec_fine;
+  FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, dt, t0);
+  kd_status s = with_phases(ctx, ctx->ws_f, a, nsteps);
+  if (s != KD_OK) return s;
+  KD_LAUNCH(launch_phases(pf, a, nsteps, ctx->st), "fine phases");
+  CoarseArgs c = coarse_args(ctx, nsteps, dt);
+  c.Kc = n / 3;
+  c.Pc = kept(n);
+  c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? a.phases : nullptr;
+  c.Un = in;
+  c.mode = COARSE_OUT;
+  c.g64 = out;
+  KD_LAUNCH(coarse_conv_launch(pf, c, (int)batch, ctx->st), "fine convolution steps");
+  return KD_OK;
+}
+
+bool conv_op(const kd_ctx* ctx) { return ctx->p.fine_operator == KD_FINE_CONV; }
+
 // Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
 // increment form Fv[n] += F(U[n] - Uprev[n]) (iter > 1).
 kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
@@ -411,6 +436,18 @@ kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) 
   if (b <= 0) return KD_OK;
   const long len = compact_len(n);
   const bool incr = ctx->p.fine_form == KD_FINE_INCREMENT;
+  if (conv_op(ctx)) {
+    if (!incr) return conv_fine(ctx, ctx->U + 2 * first * len, ctx->Fv + 2 * first * len, b, S, dt, ctx->t0f + first);
+    kd_status s0 = ensure_full_tmp(ctx, (size_t)b * len * 16);
+    if (s0 != KD_OK) return s0;
+    double* tmp = (double*)ctx->full_tmp;
+    KD_LAUNCH(delta_in(KD_C128, ctx->U + 2 * first * len, ctx->Uprev + 2 * first * len, tmp, b * len,
+                       iter == 1 ? 1 : 0, ctx->st),
+              "increment");
+    if ((s0 = conv_fine(ctx, tmp, tmp, b, S, dt, ctx->t0f + first)) != KD_OK) return s0;
+    KD_LAUNCH(accum_out(KD_C128, tmp, ctx->Fv + 2 * first * len, b * len, iter == 1 ? 1 : 0, ctx->st), "accumulate");
+    return KD_OK;
+  }
   if (incr)
     KD_LAUNCH(delta_in(pf, ctx->U + 2 * first * len, ctx->Uprev + 2 * first * len, ctx->ws_f.X, b * len,
                        iter == 1 ? 1 : 0, ctx->st),
@@ -482,6 +519,7 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   if (e == cudaSuccess) e = fine_prepare(params->prec_fine);
   if (e == cudaSuccess) e = fine_prepare(params->prec_coarse);
   if (e == cudaSuccess) e = coarse_prepare(params->prec_coarse);
+  if (e == cudaSuccess && params->fine_operator == KD_FINE_CONV) e = coarse_prepare(params->prec_fine);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e != cudaSuccess) {
     fprintf(stderr, "kd_create: %s\n", cudaGetErrorString(e));
@@ -526,6 +564,14 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
   const int n = ctx->p.n, pf = ctx->p.prec_fine;
   kd_status s = ensure_ws(ctx, ctx->ws_f, n, pf, batch);
   if (s != KD_OK) return s;
+  if (conv_op(ctx)) {
+    if ((s = ensure_full_tmp(ctx, (size_t)batch * compact_len(n) * 16)) != KD_OK) return s;
+    double* tmp = (double*)ctx->full_tmp;
+    KD_LAUNCH(full_to_compact(pf, b_in, KD_C128, tmp, batch, n, ctx->st), "pack");
+    if (nsteps > 0 && (s = conv_fine(ctx, tmp, tmp, batch, nsteps, ctx->p.dt_fine, t0)) != KD_OK) return s;
+    KD_LAUNCH(compact_to_full(KD_C128, tmp, pf, b_out, batch, n, ctx->st), "unpack");
+    return KD_OK;
+  }
   KD_LAUNCH(full_to_compact(pf, b_in, pf, ctx->ws_f.X, batch, n, ctx->st), "pack");
   FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, ctx->p.dt_fine, t0);
   if ((s = with_phases(ctx, ctx->ws_f, a, nsteps)) != KD_OK) return s;
@@ -723,6 +769,11 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
   KD_LAUNCH(fill_slice_times(ctx->t0f, N + 1, 0, dT, ctx->st), "times");
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
   for (int i = 0; i < N; ++i) {
+    if (conv_op(ctx)) {
+      if ((s = conv_fine(ctx, ctx->U + 2 * i * len, ctx->U + 2 * (i + 1) * len, 1, S, dt, ctx->t0f + i)) != KD_OK)
+        return s;
+      continue;
+    }
     KD_LAUNCH(compact_resample(KD_C128, ctx->U + 2 * i * len, n, pf, ctx->ws_f.X, n, 1, ctx->st), "to fine");
     FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, 1, dt, ctx->t0f + i);
     if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;

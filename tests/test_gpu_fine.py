@@ -246,3 +246,34 @@ def test_coarse_propagator_matches_oracle(kd):
     for i, t in enumerate((0.0, 0.7)):
         ref = O.coarse_propagate(b[i], prob, nc, t, dtc, 6)
         assert rel(out[i], ref) < 1e-13
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_convolution_fine_operator_matches_oracle(kd, n, prec):
+    """KD_FINE_CONV: the explicit term as the exact spectral convolution in one persistent
+    launch; the same discrete operator as the FFT route (oracle pin: both routes agree to
+    1e-13), so parity with the oracle at the precision's tolerance."""
+    import torch
+    P = kd.KD_C64 if prec == "c64" else kd.KD_C128
+    kz, Rm, dt = 0.57, 100.0, 5e-3
+    b = I.initial_batch(n, kz, [41, 42, 43])
+    t0 = [0.0, 0.6, 2.2]
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, P, fine_operator=kd.KD_FINE_CONV))
+    try:
+        dtype = torch.complex64 if P == kd.KD_C64 else torch.complex128
+        x = torch.tensor(b, dtype=dtype, device="cuda")
+        y = torch.empty_like(x)
+        kd.kd_fine_batched(ctx, x, y, torch.tensor(t0, dtype=torch.float64, device="cuda"), 4, 3, P)
+        torch.cuda.synchronize()
+        out = y.cpu().numpy().astype(np.complex128)
+    finally:
+        kd.kd_destroy(ctx)
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i in range(3):
+        assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 4)) < (TOL32 if P == kd.KD_C64 else 1e-12)
+
+
+def test_convolution_fine_operator_rejected_above_128(kd):
+    with pytest.raises(kd.KdError):
+        kd.kd_create(kd.make_params(O.ROBERTS, 256, 1.0, 8.0, 1e-2, kd.KD_C64, fine_operator=kd.KD_FINE_CONV))

@@ -191,3 +191,28 @@ def test_invalid_arguments_are_rejected(kd):
             kd.kd_parareal_run(ctx, I.initial_field(32, 1.0, 0), -1.0, 4, 3, 1e-6)
     finally:
         kd.kd_destroy(ctx)
+
+
+def test_parareal_with_convolution_fine_operator(kd):
+    """The whole Parareal run with KD_FINE_CONV agrees with the FFT fine operator to FP32
+    accuracy, takes the same iterations, and reproduces its own serial fine run."""
+    n, kz, Rm, T, N = 32, 0.57, 100.0, 2.0, 8
+    b0 = I.initial_field(n, kz, 19)
+    outs, ks = [], []
+    for op in (kd.KD_FINE_FFT, kd.KD_FINE_CONV):
+        p = kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, 5e-3, kd.KD_C64, n_coarse=32, dt_coarse=0.025,
+                           prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT, fine_operator=op)
+        ctx = kd.kd_create(p)
+        try:
+            u = np.zeros((N + 1, 3, n, n), np.complex128)
+            s, st = kd.kd_parareal_run(ctx, b0, T, N, N, 1e-6, u)
+            ser = np.zeros_like(u)
+            kd.kd_fine_serial(ctx, b0, T, N, ser)
+        finally:
+            kd.kd_destroy(ctx)
+        assert s == kd.KD_OK
+        assert np.linalg.norm(u[-1] - ser[-1]) / np.linalg.norm(ser[-1]) < 1e-5
+        outs.append(u)
+        ks.append(st.k_con)
+    assert ks[0] == ks[1]
+    assert np.linalg.norm(outs[1][-1] - outs[0][-1]) / np.linalg.norm(outs[0][-1]) < 2e-5
