@@ -146,6 +146,17 @@ typedef struct {
 kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices, int k_max,
                           double tol, double* u_slices, kd_parareal_stats* stats);
 
+/* Pipelined iterations of kd_parareal_run (default chunks = 0: off): the parallel step of
+ * iteration k + 1 runs in `chunks` slice chunks on a low-priority stream and overlaps the
+ * serial sweep of iteration k, which runs on a high-priority stream; chunk j starts once
+ * the sweep has passed its last slice, and the next sweep waits for each chunk before its
+ * first slice.  The parallel step is computed before the defect of iteration k is known
+ * and discarded if the run stops there.  The results are those of the unpipelined order
+ * bit for bit.  It pays when a chunk's fine work is few launches (KD_FINE_CONV); with the
+ * FFT operator every chunk repeats all the step launches on a smaller batch.  KD_EINVAL
+ * for chunks outside [0, 16]. */
+kd_status kd_set_overlap(kd_ctx* ctx, int chunks);
+
 /* Serial fine solution at the slice boundaries, U_{n+1} = F(U_n) with each slice
  * restarted at t_n = n dT exactly as in kd_parareal_run (the solution Parareal
  * converges to, Sec. 3.1).  Same arguments and step rule as kd_parareal_run.

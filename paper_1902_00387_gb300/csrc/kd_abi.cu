@@ -428,6 +428,16 @@ kd_status conv_fine(kd_ctx* ctx, const double* in, double* out, long batch, int 
 
 bool conv_op(const kd_ctx* ctx) { return ctx->p.fine_operator == KD_FINE_CONV; }
 
+kd_status ensure_conv_tmp(kd_ctx* ctx, size_t bytes) {
+  if (ctx->conv_tmp_bytes >= bytes) return KD_OK;
+  dfree(ctx, ctx->conv_tmp);
+  ctx->conv_tmp = nullptr;
+  ctx->conv_tmp_bytes = 0;
+  kd_status s = dalloc(ctx, &ctx->conv_tmp, bytes, "convolution staging");
+  if (s == KD_OK) ctx->conv_tmp_bytes = bytes;
+  return s;
+}
+
 // Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
 // increment form Fv[n] += F(U[n] - Uprev[n]) (iter > 1).
 kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
@@ -438,9 +448,9 @@ kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) 
   const bool incr = ctx->p.fine_form == KD_FINE_INCREMENT;
   if (conv_op(ctx)) {
     if (!incr) return conv_fine(ctx, ctx->U + 2 * first * len, ctx->Fv + 2 * first * len, b, S, dt, ctx->t0f + first);
-    kd_status s0 = ensure_full_tmp(ctx, (size_t)b * len * 16);
+    kd_status s0 = ensure_conv_tmp(ctx, (size_t)b * len * 16);
     if (s0 != KD_OK) return s0;
-    double* tmp = (double*)ctx->full_tmp;
+    double* tmp = (double*)ctx->conv_tmp;
     KD_LAUNCH(delta_in(KD_C128, ctx->U + 2 * first * len, ctx->Uprev + 2 * first * len, tmp, b * len,
                        iter == 1 ? 1 : 0, ctx->st),
               "increment");
@@ -488,6 +498,148 @@ kd_status copy_out_slices(kd_ctx* ctx, double* u_slices, int N) {
   return KD_OK;
 }
 
+// ---------------------------------------------------------------- pipelined Parareal
+struct Chunk {
+  int lo, hi;
+};
+
+// [first, N) split into at most m nearly equal chunks
+std::vector<Chunk> chunks_of(int first, int N, int m) {
+  std::vector<Chunk> out;
+  const int total = N - first;
+  const int c = total < m ? total : m;
+  for (int j = 0; j < c; ++j) out.push_back({first + j * total / c, first + (j + 1) * total / c});
+  return out;
+}
+
+// One serial sweep of iteration k on ctx->st.  Before slice i it waits for the fine chunk
+// of iteration k holding i (events F, in the order of `wait`); after slice i it releases
+// the chunks of iteration k + 1 whose last slice is i (events E, order of `rel`): from
+// then on the sweep no longer reads their U / Uprev / Fv, and their U_n^k are final.
+kd_status pipelined_sweep(kd_ctx* ctx, int k, int N, int Sc, double dtc, const std::vector<Chunk>& wait,
+                          const std::vector<Chunk>& rel) {
+  cudaEvent_t* E = &ctx->pev2[0];
+  cudaEvent_t* F = &ctx->pev2[kMaxChunks];
+  const int n = ctx->p.n;
+  const long len = compact_len(n), lenc = 3L * ctx->cP * ctx->cP;
+  const int first = k == 0 ? 0 : (k - 1 < N - 1 ? k - 1 : N - 1);
+  size_t wj = 0, rj = 0;
+  kd_status s;
+  for (int i = first; i < N; ++i) {
+    while (wj < wait.size() && wait[wj].lo <= i) KD_CUDA(cudaStreamWaitEvent(ctx->st, F[wj++], 0), "wait fine");
+    const bool last = k >= 1 && i == N - 1;
+    if (k == 0) {
+      if ((s = use_learned(ctx, i) ? learned_step(ctx, i, true, false) : coarse_step(ctx, i, Sc, dtc, true, false)) !=
+          KD_OK)
+        return s;
+    } else if (i == first) {
+      int nb = parareal_update(ctx->Fv + 2 * i * len, ctx->Gv + 2 * i * lenc, KD_C128, ctx->Gv + 2 * i * lenc,
+                               ctx->U + 2 * (i + 1) * len, n, ctx->cK, ctx->cP, 0, last ? ctx->partials : nullptr,
+                               ctx->st);
+      if (nb < 0) return fail(ctx, KD_ECUDA, "parareal update launch failed");
+      ctx->launches += 1;
+      if (last) KD_LAUNCH(finish_sigma(ctx->partials, nb, ctx->scal, ctx->st), "sigma");
+    } else if ((s = use_learned(ctx, i) ? learned_step(ctx, i, false, last)
+                                        : coarse_step(ctx, i, Sc, dtc, false, last)) != KD_OK) {
+      return s;
+    }
+    while (rj < rel.size() && rel[rj].hi - 1 <= i) KD_CUDA(cudaEventRecord(E[rj++], ctx->st), "release");
+  }
+  while (rj < rel.size()) KD_CUDA(cudaEventRecord(E[rj++], ctx->st), "release");
+  return KD_OK;
+}
+
+// The fine chunks of iteration k on st2, each after its release event; records F per chunk
+// and the span events ts / te.
+kd_status pipelined_fine(kd_ctx* ctx, int k, int S, double dt, const std::vector<Chunk>& ck, cudaEvent_t ts,
+                         cudaEvent_t te) {
+  cudaEvent_t* E = &ctx->pev2[0];
+  cudaEvent_t* F = &ctx->pev2[kMaxChunks];
+  cudaStream_t saved = ctx->st;
+  ctx->st = ctx->st2;
+  kd_status s = KD_OK;
+  for (size_t j = 0; j < ck.size() && s == KD_OK; ++j) {
+    cudaError_t e = cudaStreamWaitEvent(ctx->st2, E[j], 0);
+    if (e == cudaSuccess && j == 0) e = cudaEventRecord(ts, ctx->st2);
+    if (e != cudaSuccess) {
+      s = cuda_fail(ctx, e, "fine chunk wait");
+      break;
+    }
+    s = fine_sweep(ctx, ck[j].lo, ck[j].hi, S, dt, k);
+    if (s == KD_OK && (e = cudaEventRecord(F[j], ctx->st2)) != cudaSuccess) s = cuda_fail(ctx, e, "fine chunk done");
+  }
+  if (s == KD_OK) {
+    cudaError_t e = cudaEventRecord(te, ctx->st2);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "fine span");
+  }
+  ctx->st = saved;
+  return s;
+}
+
+// Iterations of kd_parareal_run with the fine sweep of iteration k + 1 overlapping the
+// serial sweep of iteration k (speculatively: it only writes Fv / Uprev, which a stop
+// after iteration k leaves unused).  Same values as the unpipelined order.
+kd_status parareal_pipelined(kd_ctx* ctx, int N, int S, int Sc, double dt, double dtc, int k_max, double tol,
+                             std::vector<double>& sig, int& k_done, int& conv, float& ms_fine, float& ms_coarse) {
+  const int m = ctx->overlap < kMaxChunks ? ctx->overlap : kMaxChunks;
+  cudaEvent_t fs[2] = {ctx->pev2[2 * kMaxChunks], ctx->pev2[2 * kMaxChunks + 1]};
+  cudaEvent_t fe[2] = {ctx->pev2[2 * kMaxChunks + 2], ctx->pev2[2 * kMaxChunks + 3]};
+  cudaEvent_t cs = ctx->pev2[2 * kMaxChunks + 4], ce = ctx->pev2[2 * kMaxChunks + 5];
+  kd_status s;
+  auto first_of = [&](int k) { return k - 1 < N - 1 ? k - 1 : N - 1; };
+  // size the buffers both streams use for the largest chunk now: a reallocation later
+  // would free memory the other stream may still be using
+  {
+    const int n = ctx->p.n;
+    FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, N, dt, ctx->t0f);
+    if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;
+    if (conv_op(ctx) && (s = ensure_conv_tmp(ctx, (size_t)N * compact_len(n) * 16)) != KD_OK) return s;
+    if (!coarse_conv_supported(ctx->cP) && (s = ensure_full_tmp(ctx, (size_t)compact_len(n) * 16)) != KD_OK) return s;
+  }
+  std::vector<Chunk> cur = chunks_of(0, N, m);
+  // iterate 0 releases the chunks of iteration 1
+  KD_CUDA(cudaEventRecord(cs, ctx->st), "event");
+  if ((s = pipelined_sweep(ctx, 0, N, Sc, dtc, {}, k_max >= 1 ? cur : std::vector<Chunk>())) != KD_OK) return s;
+  KD_CUDA(cudaEventRecord(ce, ctx->st), "event");
+  if (k_max >= 1 && (s = pipelined_fine(ctx, 1, S, dt, cur, fs[1], fe[1])) != KD_OK) return s;
+  KD_CUDA(cudaEventSynchronize(ce), "sync");
+  {
+    float m0 = 0.f;
+    cudaEventElapsedTime(&m0, cs, ce);
+    ms_coarse += m0;
+  }
+  for (int k = 1; k <= k_max; ++k) {
+    const std::vector<Chunk> next = k < k_max ? chunks_of(first_of(k + 1), N, m) : std::vector<Chunk>();
+    KD_CUDA(cudaEventRecord(cs, ctx->st), "event");
+    if ((s = pipelined_sweep(ctx, k, N, Sc, dtc, cur, next)) != KD_OK) return s;
+    KD_CUDA(cudaMemcpyAsync(ctx->host_scal, ctx->scal, 8, cudaMemcpyDeviceToHost, ctx->st), "sigma copy");
+    KD_CUDA(cudaEventRecord(ce, ctx->st), "event");
+    if (k < k_max && (s = pipelined_fine(ctx, k + 1, S, dt, next, fs[(k + 1) & 1], fe[(k + 1) & 1])) != KD_OK)
+      return s;
+    KD_CUDA(cudaEventSynchronize(ce), "sync");
+    float m1 = 0.f, m2 = 0.f;
+    cudaEventElapsedTime(&m1, fs[k & 1], fe[k & 1]);
+    cudaEventElapsedTime(&m2, cs, ce);
+    ms_fine += m1;
+    ms_coarse += m2;
+    cur = next;
+    const double sigma = ctx->host_scal[0];
+    sig.push_back(sigma);
+    k_done = k;
+    if (!isfinite(sigma)) return fail(ctx, KD_ENONFINITE, "kd_parareal_run: non-finite defect");
+    if (sigma <= tol) {
+      conv = 1;
+      break;
+    }
+    if (ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback &&
+        ((k >= 2 && sigma > sig[k - 2]) || (k_max > 1 && k >= k_max / 2)))
+      ctx->fallback = 1;
+  }
+  KD_CUDA(cudaStreamSynchronize(ctx->st2), "sync");   // speculative fine chunks finished
+  if (ctx->prof) prof_flush(ctx);
+  return KD_OK;
+}
+
 }  // namespace kdi
 
 extern "C" {
@@ -521,6 +673,15 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   if (e == cudaSuccess) e = coarse_prepare(params->prec_coarse);
   if (e == cudaSuccess && params->fine_operator == KD_FINE_CONV) e = coarse_prepare(params->prec_fine);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, prio_lo);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->st_hi, cudaStreamNonBlocking, prio_hi);
+  for (int i = 0; i < 2 * kMaxChunks + 6 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) ctx->pev2.push_back(ev);
+  }
   if (e != cudaSuccess) {
     fprintf(stderr, "kd_create: %s\n", cudaGetErrorString(e));
     delete ctx;
@@ -551,6 +712,15 @@ kd_status kd_destroy(kd_ctx* ctx) {
     if (p) cudaFree(p);
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->st2) {
+    cudaStreamSynchronize(ctx->st2);
+    cudaStreamDestroy(ctx->st2);
+  }
+  if (ctx->st_hi) {
+    cudaStreamSynchronize(ctx->st_hi);
+    cudaStreamDestroy(ctx->st_hi);
+  }
+  for (cudaEvent_t e : ctx->pev2) cudaEventDestroy(e);
   if (ctx->host_scal) cudaFreeHost(ctx->host_scal);
   delete ctx;
   return KD_OK;
@@ -565,8 +735,8 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
   kd_status s = ensure_ws(ctx, ctx->ws_f, n, pf, batch);
   if (s != KD_OK) return s;
   if (conv_op(ctx)) {
-    if ((s = ensure_full_tmp(ctx, (size_t)batch * compact_len(n) * 16)) != KD_OK) return s;
-    double* tmp = (double*)ctx->full_tmp;
+    if ((s = ensure_conv_tmp(ctx, (size_t)batch * compact_len(n) * 16)) != KD_OK) return s;
+    double* tmp = (double*)ctx->conv_tmp;
     KD_LAUNCH(full_to_compact(pf, b_in, KD_C128, tmp, batch, n, ctx->st), "pack");
     if (nsteps > 0 && (s = conv_fine(ctx, tmp, tmp, batch, nsteps, ctx->p.dt_fine, t0)) != KD_OK) return s;
     KD_LAUNCH(compact_to_full(KD_C128, tmp, pf, b_out, batch, n, ctx->st), "unpack");
@@ -658,6 +828,24 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
   if ((s = coarse_phases(ctx, N, Sc, dtc)) != KD_OK) return s;
   float ms_fine = 0.f, ms_coarse = 0.f;
+  int k_done = 0, conv = 0;
+  std::vector<double> sig;
+  if (ctx->overlap > 0 && N >= 2) {
+    // the sweeps run on the high-priority stream, ordered after the caller's stream
+    cudaStream_t user = ctx->st;
+    KD_CUDA(cudaEventRecord(ctx->ev[1], user), "event");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_hi, ctx->ev[1], 0), "event");
+    ctx->st = ctx->st_hi;
+    s = parareal_pipelined(ctx, N, S, Sc, dt, dtc, k_max, tol, sig, k_done, conv, ms_fine, ms_coarse);
+    cudaEventRecord(ctx->ev[1], ctx->st_hi);
+    ctx->st = user;
+    cudaStreamWaitEvent(user, ctx->ev[1], 0);
+    if (s != KD_OK) {
+      cudaStreamSynchronize(ctx->st2);
+      if (stats && s == KD_ENONFINITE) stats->k_con = k_done;
+      return s;
+    }
+  } else {
   // iterate 0: serial coarse sweep
   KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
   for (int i = 0; i < N; ++i)
@@ -671,8 +859,6 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     cudaEventElapsedTime(&m, ctx->ev[2], ctx->ev[3]);
     ms_coarse += m;
   }
-  int k_done = 0, conv = 0;
-  std::vector<double> sig;
   for (int k = 1; k <= k_max; ++k) {
     // parallel step over the slices that can still change: n >= k - 1
     // (the last slice is always swept so that sigma is measured)
@@ -721,6 +907,7 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     if (ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback &&
         ((k >= 2 && sigma > sig[k - 2]) || (k_max > 1 && k >= k_max / 2)))
       ctx->fallback = 1;
+  }
   }
   // energies and growth rate of the final iterate
   KD_LAUNCH(energy_kernel(ctx->U, len, N + 1, ctx->Ebuf, ctx->st), "energy");

@@ -39,6 +39,14 @@ struct kd_ctx {
   kd_params p;
   kd::FinePlan plan[2];        // launch plans of the fine (0) and coarse (1) grid
   int pdl = 1;                 // fine-step kernels as programmatic dependent launches
+  // pipelined Parareal: the fine sweep of iteration k + 1 runs in `overlap` slice chunks on
+  // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)
+  int overlap = 0;
+  cudaStream_t st2 = nullptr;      // fine chunks (lowest priority)
+  cudaStream_t st_hi = nullptr;    // serial sweeps (highest priority)
+  std::vector<cudaEvent_t> pev2;   // chunk release / fine-done / timing events
+  void* conv_tmp = nullptr;        // FP64 staging of the convolution fine operator
+  size_t conv_tmp_bytes = 0;
   cudaStream_t st = nullptr;
   int device = 0;
   kdi::Tables tab_f, tab_c;
@@ -86,6 +94,8 @@ struct kd_ctx {
 
 
 namespace kdi {
+
+constexpr int kMaxChunks = 16;   // slice chunks of the pipelined fine sweep
 
 kd_status fail(kd_ctx* c, kd_status s, const std::string& m);
 kd_status cuda_fail(kd_ctx* c, cudaError_t e, const char* where);

@@ -192,6 +192,13 @@ kd_status kd_get_plan(kd_ctx* ctx, int grid, int* col, int* row) {
   return KD_OK;
 }
 
+kd_status kd_set_overlap(kd_ctx* ctx, int chunks) {
+  if (!ctx) return KD_EINVAL;
+  if (chunks < 0 || chunks > kMaxChunks) return fail(ctx, KD_EINVAL, "kd_set_overlap: chunks must be in [0, 16]");
+  ctx->overlap = chunks;
+  return KD_OK;
+}
+
 kd_status kd_set_dependent_launch(kd_ctx* ctx, int enable) {
   if (!ctx) return KD_EINVAL;
   ctx->pdl = enable ? 1 : 0;

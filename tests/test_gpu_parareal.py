@@ -216,3 +216,28 @@ def test_parareal_with_convolution_fine_operator(kd):
         ks.append(st.k_con)
     assert ks[0] == ks[1]
     assert np.linalg.norm(outs[1][-1] - outs[0][-1]) / np.linalg.norm(outs[0][-1]) < 2e-5
+
+
+@pytest.mark.parametrize("form", ["direct", "increment"])
+@pytest.mark.parametrize("chunks", [1, 3, 16])
+def test_pipelined_iterations_equal_unpipelined(kd, form, chunks):
+    """The fine sweep of iteration k + 1 overlapping the serial sweep of iteration k gives
+    the same slice states and defects bit for bit as the unpipelined order."""
+    n, kz, Rm, T, N = 32, 0.57, 100.0, 3.0, 13
+    b0 = I.initial_field(n, kz, 23)
+    res = []
+    for ov in (0, chunks):
+        p = kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, 5e-3, kd.KD_C64, n_coarse=32, dt_coarse=0.025,
+                           prec_coarse=kd.KD_C64,
+                           fine_form=kd.KD_FINE_INCREMENT if form == "increment" else kd.KD_FINE_DIRECT)
+        ctx = kd.kd_create(p)
+        try:
+            kd.kd_set_overlap(ctx, ov)
+            u = np.zeros((N + 1, 3, n, n), np.complex128)
+            s, st = kd.kd_parareal_run(ctx, b0, T, N, 5, 0.0, u)
+            res.append((u, list(st.sigma[:st.k_con]), st.k_con))
+        finally:
+            kd.kd_destroy(ctx)
+    assert res[0][2] == res[1][2] == 5
+    assert res[0][1] == res[1][1]
+    assert np.array_equal(res[0][0], res[1][0])
