@@ -146,6 +146,14 @@ typedef struct {
 kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices, int k_max,
                           double tol, double* u_slices, kd_parareal_stats* stats);
 
+/* Thread blocks per cluster of the persistent coarse solver (coarse sets up to 88 modes
+ * a side): 0 = the default (a batch of fields that fits the GPU in clusters of 16: ~3 rows
+ * per block, up to 16 blocks; larger batches: ~6 rows per block, at most 8), else 1..8 (1..16 where the
+ * device allows non-portable cluster sizes) when the rows of a block fit its
+ * modes-per-thread budget.  Fewer blocks mean cheaper cluster
+ * barriers and more work per block.  KD_EINVAL if the coarse set does not fit. */
+kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks);
+
 /* Pipelined iterations of kd_parareal_run (default chunks = 0: off): the parallel step of
  * iteration k + 1 runs in `chunks` slice chunks on a low-priority stream and overlaps the
  * serial sweep of iteration k, which runs on a high-priority stream; chunk j starts once

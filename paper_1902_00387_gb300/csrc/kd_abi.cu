@@ -330,6 +330,7 @@ CoarseArgs coarse_args(const kd_ctx* ctx, int steps, double dtc) {
   c.Rm = ctx->p.Rm;
   c.dt = dtc;
   c.nsteps = steps;
+  c.cluster = ctx->coarse_cluster;
   return c;
 }
 

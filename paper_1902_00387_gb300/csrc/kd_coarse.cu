@@ -311,9 +311,13 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
 
 // cluster split of a P-row coarse square: CS blocks of H rows (H <= 8 for P <= 64,
 // H <= 11 for P <= 88)
-static void cluster_shape(int P, int* CS, int* H) {
-  int cs = (P + 5) / 6;
-  if (cs > 8) cs = 8;
+// clusters of more than 8 blocks need the non-portable size opt-in (granted in prepare)
+static int g_max_cluster = 8;
+
+static void cluster_shape(int P, int* CS, int* H, int req = 0) {
+  int cs = req > 0 ? req : (P + 5) / 6;
+  if (cs > g_max_cluster) cs = g_max_cluster;
+  if (req == 0 && cs > 8) cs = 8;
   if (cs < 1) cs = 1;
   *H = (P + cs - 1) / cs;
   *CS = cs;
@@ -321,10 +325,10 @@ static void cluster_shape(int P, int* CS, int* H) {
 
 constexpr int kMaxPhaseSlots = 8192;   // staged flow phases (512 steps x 4 stages x 4)
 
-static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots) {
+static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots, int req = 0) {
   const int L = P + 2;
   int CS, H;
-  cluster_shape(P, &CS, &H);
+  cluster_shape(P, &CS, &H, req);
   const size_t es = prec == 0 ? 4 : 8;
   const size_t base = (size_t)2 * 3 * (H + 2) * L * 2 * es;
   const int slots = nsteps * 16 <= kMaxPhaseSlots ? nsteps * 16 : 0;
@@ -333,9 +337,9 @@ static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots) {
 }
 
 // modes per thread needed for a P-row square (0: unsupported)
-static int modes_per_thread(int P) {
+static int modes_per_thread(int P, int req = 0) {
   int CS, H;
-  cluster_shape(P, &CS, &H);
+  cluster_shape(P, &CS, &H, req);
   if (H * P <= 2 * CCB) return 2;
   if (H * P <= 4 * CCB) return 4;
   return 0;
@@ -343,26 +347,66 @@ static int modes_per_thread(int P) {
 
 bool coarse_conv_supported(int P) { return P >= 1 && modes_per_thread(P) > 0; }
 
+bool coarse_cluster_fits(int P, int cs) {
+  return P >= 1 && cs >= 0 && cs <= g_max_cluster && (cs == 0 || cs <= P) && modes_per_thread(P, cs) > 0;
+}
+
 template <typename T>
 static cudaError_t prepare_T() {
   int slots = 0;
   const int prec = sizeof(T) == 4 ? 0 : 1;
-  int P = 64;
-  while (coarse_conv_supported(P + 1)) ++P;   // largest supported square
-  const int bytes = (int)cluster_smem(prec, P, 512, &slots);
+  int bytes = 0;   // the largest shared-memory need over every supported square and cluster size
+  for (int P = 1; P <= 128; ++P)
+    for (int cs = 0; cs <= 8; ++cs)
+      if (coarse_cluster_fits(P, cs)) {
+        const int b = (int)cluster_smem(prec, P, 512, &slots, cs);
+        if (b > bytes) bytes = b;
+      }
   cudaError_t e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  // 16-block clusters where the device grants them
+  if (cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess)
+    g_max_cluster = 16;
+  cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t coarse_prepare(int prec) { return prec == 0 ? prepare_T<float>() : prepare_T<double>(); }
 
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 132;
+  }
+  return sms;
+}
+
+// Default cluster size: the per-stage time is a fixed barrier / latency part plus a part
+// proportional to the rows of a block, so a few fields take the largest clusters that all
+// fit on the GPU at once (~3 rows per block, up to 16 blocks); larger batches keep ~6 rows
+// per block (at most 8) so that more clusters run concurrently.
+static int auto_cluster(int P, int batch) {
+  if (g_max_cluster >= 16 && batch * 16 <= sm_count()) {
+    const int cs = (P + 2) / 3 < 16 ? (P + 2) / 3 : 16;
+    if (cs > 8 && coarse_cluster_fits(P, cs)) return cs;
+  }
+  return 0;
+}
+
 template <typename T>
 static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   CoarseArgs a = a0;
+  const int req = a.cluster > 0 && coarse_cluster_fits(a.Pc, a.cluster) ? a.cluster : auto_cluster(a.Pc, batch);
   int CS, H, slots;
-  cluster_shape(a.Pc, &CS, &H);
-  const size_t sm = cluster_smem(sizeof(T) == 4 ? 0 : 1, a.Pc, a.nsteps, &slots);
+  cluster_shape(a.Pc, &CS, &H, req);
+  const size_t sm = cluster_smem(sizeof(T) == 4 ? 0 : 1, a.Pc, a.nsteps, &slots, req);
   a.phase_smem = slots;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CS * batch), 1, 1);
@@ -376,8 +420,9 @@ static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = modes_per_thread(a.Pc) == 2 ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H)
-                                                    : cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 4>, a, CS, H);
+  const cudaError_t e = modes_per_thread(a.Pc, req) == 2
+                            ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H)
+                            : cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 4>, a, CS, H);
   return e == cudaSuccess ? 1 : -1;
 }
 

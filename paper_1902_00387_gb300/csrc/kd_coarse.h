@@ -34,9 +34,12 @@ struct CoarseArgs {
   const SliceParams* sp;
   const int* steps;
   const int* map;
+  int cluster;          // thread blocks per cluster (0: the default for Pc)
 };
 
 bool coarse_conv_supported(int P);   // coarse set side P <= 88
+// whether a cluster of `cs` blocks can hold a P-row square (cs = 0: the default)
+bool coarse_cluster_fits(int P, int cs);
 cudaError_t coarse_prepare(int prec);
 // One thread-block cluster per field; returns 1 (kernels launched) or -1 if unsupported.
 int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st);

@@ -42,6 +42,7 @@ struct kd_ctx {
   // pipelined Parareal: the fine sweep of iteration k + 1 runs in `overlap` slice chunks on
   // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)
   int overlap = 0;
+  int coarse_cluster = 0;          // blocks per cluster of the coarse solver (0: default)
   cudaStream_t st2 = nullptr;      // fine chunks (lowest priority)
   cudaStream_t st_hi = nullptr;    // serial sweeps (highest priority)
   std::vector<cudaEvent_t> pev2;   // chunk release / fine-done / timing events

@@ -145,8 +145,8 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   else
     k_static_tables<double><<<tb, 256, 0, st>>>(n, (double*)tw, (double*)cg, (double*)sg);
   if (cudaGetLastError() != cudaSuccess) return KD_ECUDA;
-  if (full_to_compact(prec, b_in, prec, a.X, batch, n, st) != 0) return KD_ECUDA;
+  if (full_to_compact(prec, b_in, prec, a.X, batch, n, st) < 0) return KD_ECUDA;
   if (nsteps > 0 && fine_launch_steps(prec, a, nsteps, true, false, st) < 0) return KD_ECUDA;
-  if (compact_to_full(prec, a.X, prec, b_out, batch, n, st) != 0) return KD_ECUDA;
+  if (compact_to_full(prec, a.X, prec, b_out, batch, n, st) < 0) return KD_ECUDA;
   return cudaGetLastError() == cudaSuccess ? KD_OK : KD_ECUDA;
 }

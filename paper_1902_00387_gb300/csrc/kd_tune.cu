@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "kd_coarse.h"
 #include "kd_ctx.h"
 
 using namespace kd;
@@ -189,6 +190,14 @@ kd_status kd_get_plan(kd_ctx* ctx, int grid, int* col, int* row) {
     return fail(ctx, KD_EINVAL, "kd_get_plan: bad argument");
   *col = ctx->plan[grid].col;
   *row = ctx->plan[grid].row;
+  return KD_OK;
+}
+
+kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks) {
+  if (!ctx) return KD_EINVAL;
+  if (!coarse_cluster_fits(ctx->cP, blocks))
+    return fail(ctx, KD_EINVAL, "kd_set_coarse_cluster: the coarse set does not fit clusters of that size");
+  ctx->coarse_cluster = blocks;
   return KD_OK;
 }
 

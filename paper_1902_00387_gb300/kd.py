@@ -77,7 +77,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
-           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_set_overlap"]
+           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_set_overlap", "kd_set_coarse_cluster"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -110,6 +110,7 @@ def load():
         "kd_set_plan": (I, [P, I, I, I]),
         "kd_set_dependent_launch": (I, [P, I]),
         "kd_set_overlap": (I, [P, I]),
+        "kd_set_coarse_cluster": (I, [P, I]),
         "kd_get_plan": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "kd_autotune": (I, [P, I, I, I, ctypes.c_char_p, ctypes.POINTER(D)]),
         "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
@@ -326,6 +327,10 @@ def kd_plan_variants(ctx, grid=KD_GRID_FINE):
 
 def kd_set_plan(ctx, grid, col, row):
     return _check(ctx, load().kd_set_plan(ctx, int(grid), int(col), int(row)))
+
+
+def kd_set_coarse_cluster(ctx, blocks):
+    return _check(ctx, load().kd_set_coarse_cluster(ctx, int(blocks)))
 
 
 def kd_set_overlap(ctx, chunks):
