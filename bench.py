@@ -271,6 +271,62 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------- stepper work versus accuracy (Sec. 5.1)
+STEPPERS_WL = {
+    "workload": "gp_cp_128x128_stepper_work_vs_accuracy", "flow": "galloway-proctor", "n": 128, "kz": 0.57,
+    "Rm": 100.0, "T": 2 * math.pi / 8, "batch": 64, "reference": "RK443, dt = T/4096, complex128",
+    "dts": [0.04, 0.02, 0.01, 0.005, 0.0025, 0.00125],
+}
+
+
+def run_steppers(args):
+    """The paper's stepper study (Sec. 5.1): relative error at T of RK111, RK222 and RK443
+    against a reference run, and the device time of the batched FP32 fine propagation
+    (64 fields), per step size."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    W = STEPPERS_WL
+    n, T, B = W["n"], W["T"], W["batch"]
+    b = kd_inputs.initial_batch(n, W["kz"], range(B))
+    t0 = torch.zeros(B, dtype=torch.float64, device="cuda")
+
+    def run(sch, dt_max, prec):
+        steps = math.ceil(T / dt_max - 1e-9)     # equal steps that end exactly at T
+        ctx = kd.kd_create(kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], T / steps, prec,
+                                          fine_scheme=sch))
+        try:
+            dtype = torch.complex64 if prec == kd.KD_C64 else torch.complex128
+            x = torch.tensor(b, dtype=dtype, device="cuda")
+            y = torch.empty_like(x)
+            kd.kd_fine_batched(ctx, x, y, t0, steps, B, prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            kd.kd_fine_batched(ctx, x, y, t0, steps, B, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            return y.to(torch.complex128), e0.elapsed_time(e1), steps
+        finally:
+            kd.kd_destroy(ctx)
+
+    ref, _, _ = run(kd.KD_RK443, T / 4096, kd.KD_C128)
+    rows = []
+    for name, sch, stages in (("RK111", kd.KD_RK111, 1), ("RK222", kd.KD_RK222, 2), ("RK443", kd.KD_RK443, 4)):
+        for dt in W["dts"]:
+            y, ms, steps = run(sch, dt, kd.KD_C64)
+            err = (torch.linalg.norm(y - ref) / torch.linalg.norm(ref)).item()
+            rows.append({"scheme": name, "dt": T / steps, "steps": steps, "rhs_evals": steps * stages,
+                         "rel_error": err if math.isfinite(err) else None, "ms": ms})
+    print(json.dumps({"config": W, "metric": "relative error at T vs device time (64 fields, complex64)",
+                      "rows": rows}), flush=True)
+
+
 # ------------------------------------------------------------- large run (config 5)
 LARGE_WL = {
     "workload": "gp_cp_1024x1024_parareal_256_slices",
@@ -527,7 +583,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large"],
+    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large", "steppers"],
                     help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
                          "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices")
     ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
@@ -547,6 +603,9 @@ def main():
         return
     if args.config == "large":
         run_large(args)
+        return
+    if args.config == "steppers":
+        run_steppers(args)
         return
 
     import numpy as np

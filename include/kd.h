@@ -62,6 +62,9 @@ enum { KD_FINE_DIRECT = 0, KD_FINE_INCREMENT = 1 };
  * and equals the spectral convolution sum_q u_hat(q) x b_hat(k - q) exactly; the two
  * operators differ by round-off. */
 enum { KD_FINE_FFT = 0, KD_FINE_CONV = 1 };
+/* IMEX Runge-Kutta scheme of the fine step (Sec. 4, Sec. 5.1): Ascher-Ruuth-Spiteri
+ * (4,4,3), (2,2,2) or (1,1,1); the coarse propagator always steps with RK443. */
+enum { KD_RK443 = 0, KD_RK222 = 1, KD_RK111 = 2 };
 
 #define KD_MAX_SLICES 1024
 #define KD_MAX_ITERS 256
@@ -87,7 +90,8 @@ typedef struct {
   int fine_operator;   /* KD_FINE_FFT (pseudo-spectral: FFT, u x b on the grid, FFT) or
                           KD_FINE_CONV: the same discrete operator evaluated as the exact
                           4-mode spectral convolution in a persistent cluster kernel (one
-                          launch for all steps; grids n <= 128) */
+                          launch for all steps; grids n <= 128; RK443 only) */
+  int fine_scheme;     /* KD_RK443 (default), KD_RK222 or KD_RK111 */
 } kd_params;
 
 /* Create a context for one problem.  `cuda_stream` is a cudaStream_t (may be NULL).

@@ -160,6 +160,8 @@ FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int n, l
   a.phases = nullptr;
   a.phase_steps = 0;
   a.sp = nullptr;
+  // the fine workspace steps with the fine scheme; the coarse propagator is RK443
+  a.scheme = &w == &ctx->ws_f ? ctx->p.fine_scheme : SCHEME_RK443;
   return a;
 }
 
@@ -296,6 +298,10 @@ kd_status check_params(const kd_params* p, std::string& why) {
   if (p->fine_operator != KD_FINE_FFT && p->fine_operator != KD_FINE_CONV) return why = "bad fine_operator", KD_EINVAL;
   if (p->fine_operator == KD_FINE_CONV && !coarse_conv_supported(2 * (p->n / 3) + 1))
     return why = "fine_operator KD_FINE_CONV needs n <= 128", KD_EINVAL;
+  if (p->fine_scheme != KD_RK443 && p->fine_scheme != KD_RK222 && p->fine_scheme != KD_RK111)
+    return why = "bad fine_scheme", KD_EINVAL;
+  if (p->fine_operator == KD_FINE_CONV && p->fine_scheme != KD_RK443)
+    return why = "fine_operator KD_FINE_CONV steps with RK443 only", KD_EINVAL;
   return KD_OK;
 }
 

@@ -88,6 +88,12 @@ struct FineArgs {
   int phase_steps;     // steps covered by the phase table
   const SliceParams* sp;  // optional [batch] per-slice parameters (NULL: the scalars above);
                           // with sp the phase table is read for every field (flow = FLOW_GP)
+  int scheme;             // IMEX scheme of the fine step: SCHEME_RK443 / RK222 / RK111
 };
+
+// IMEX Runge-Kutta schemes of the fine step (match include/kd.h KD_RK*) and their stage
+// counts.
+enum { SCHEME_RK443 = 0, SCHEME_RK222 = 1, SCHEME_RK111 = 2 };
+__host__ __device__ constexpr int scheme_stages(int sch) { return sch == SCHEME_RK443 ? 4 : (sch == SCHEME_RK222 ? 2 : 1); }
 
 }  // namespace kd

@@ -26,15 +26,18 @@
 
 namespace kd {
 
-// Stage times c_j of the explicit evaluations F_j (RK443).
-__constant__ double c_stage[4] = {0.0, 0.5, 2.0 / 3.0, 0.5};
+// Stage times c_j of the explicit evaluations F_j of RK443, RK222 and RK111.
+__constant__ double c_stage[3][4] = {{0.0, 0.5, 2.0 / 3.0, 0.5},
+                                     {0.0, 0.29289321881345247560, 0.0, 0.0},
+                                     {0.0, 0.0, 0.0, 0.0}};
 
 // Flow phases of every (field, step, stage), in double, rounded to T:
 // t = t0[b] + s dt + c_j dt, then (cos(cos t), sin(cos t), cos(sin t), sin(sin t)).
 // With per-slice parameters dt is the field's own, and fields under a steady flow get
 // the constant phases (1, 0, 1, 0).
 template <typename T>
-__global__ void phase_kernel(const double* t0, int batch, int nsteps, double dt, const SliceParams* sp, T* out) {
+__global__ void phase_kernel(const double* t0, int batch, int nsteps, double dt, const SliceParams* sp, int sch,
+                             T* out) {
   const long total = (long)batch * nsteps * 4;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int j = (int)(i & 3);
@@ -52,7 +55,7 @@ __global__ void phase_kernel(const double* t0, int batch, int nsteps, double dt,
       }
       dtb = sp[b].dt;
     }
-    const double t = t0[b] + s * dtb + c_stage[j] * dtb;
+    const double t = t0[b] + s * dtb + c_stage[sch][j] * dtb;
     const double px = cos(t), py = sin(t);
     out[i * 4 + 0] = (T)cos(px);
     out[i * 4 + 1] = (T)sin(px);
@@ -71,9 +74,9 @@ int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st) {
   long g = (total + 255) / 256;
   if (g > 65535L * 16) g = 65535L * 16;
   if (prec == 0)
-    phase_kernel<float><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, (float*)a.phases);
+    phase_kernel<float><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, a.scheme, (float*)a.phases);
   else
-    phase_kernel<double><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, (double*)a.phases);
+    phase_kernel<double><<<(unsigned)g, 256, 0, st>>>(a.t0, a.batch, nsteps, a.dt, a.sp, a.scheme, (double*)a.phases);
   return 1;
 }
 

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(Col2<T, N, XT>::BLOCK, Col2<T, N, XT>::MIN_BLO
 // stage arrays, independent loads), and the new stage values are read back in the
 // layout of the inverse transform.  Otherwise the update runs on the registers the
 // forward transform left (lanes hold consecutive kx, so the accesses still coalesce).
-template <typename T, int N, int RT, bool STAGED>
+template <typename T, int N, int RT, bool STAGED, int SCH = SCHEME_RK443>
 __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row2<T, N, RT, STAGED ? 128 : 168>::MIN_BLOCKS)
     row2_kernel(FineArgs a, int mode, int store_m) {
   using G = Row2<T, N, RT, STAGED ? 128 : 168>;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row
           const long gb = grow / P;
           const int giy = (int)(grow - gb * P);
           cx<T> w0 = *hslot(0, r, ix), w1 = *hslot(1, r, ix), w2 = *hslot(2, r, ix);
-          stage_update<MODE, T>(stage_coef<T>(a, gb), sa, ((gb * 3) * P + giy) * (long)P + ix, (long)P * P,
+          stage_update_s<SCH, MODE, T>(stage_coef<T>(a, gb), sa, ((gb * 3) * P + giy) * (long)P + ix, (long)P * P,
                                 (T)(ix - K), (T)(giy - K), w0, w1, w2);
           *hslot(0, r, ix) = w0;
           *hslot(1, r, ix) = w1;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(Row2<T, N, RT, STAGED ? 128 : 168>::BLOCK, Row
           const int kx = xx < N / 2 ? xx : xx - N;
           if (valid && kx >= -K && kx <= K) {
             cx<T> w0 = v[0][r] * inv_n2, w1 = v[1][r] * inv_n2, w2 = v[2][r] * inv_n2;
-            stage_update<MODE, T>(q, sa, s0 + kx, (long)P * P, (T)kx, fky, w0, w1, w2);
+            stage_update_s<SCH, MODE, T>(q, sa, s0 + kx, (long)P * P, (T)kx, fky, w0, w1, w2);
             v[0][r] = w0;
             v[1][r] = w1;
             v[2][r] = w2;

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(Col3<T, N, XT, R>::BLOCK, Col3<T, N, XT, R>::M
 
 // mode 0..3: stage update from W; mode 4: prologue (inverse x transform of X).
 // STAGED as in row2_kernel; otherwise lane j updates its kept modes j + q T in registers.
-template <typename T, int N, int RT, bool STAGED, int R>
+template <typename T, int N, int RT, bool STAGED, int R, int SCH = SCHEME_RK443>
 __global__ void __launch_bounds__(Row3<T, N, RT, STAGED ? 128 : 168, R>::BLOCK,
                                   Row3<T, N, RT, STAGED ? 128 : 168, R>::MIN_BLOCKS)
     row3_kernel(FineArgs a, int mode, int store_m) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(Row3<T, N, RT, STAGED ? 128 : 168, R>::BLOCK,
           const long gb = grow / P;
           const int giy = (int)(grow - gb * P);
           cx<T> w0 = *hslot(0, r, ix), w1 = *hslot(1, r, ix), w2 = *hslot(2, r, ix);
-          stage_update<MODE, T>(stage_coef<T>(a, gb), sa, ((gb * 3) * P + giy) * (long)P + ix, (long)P * P,
+          stage_update_s<SCH, MODE, T>(stage_coef<T>(a, gb), sa, ((gb * 3) * P + giy) * (long)P + ix, (long)P * P,
                                 (T)(ix - K), (T)(giy - K), w0, w1, w2);
           *hslot(0, r, ix) = w0;
           *hslot(1, r, ix) = w1;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(Row3<T, N, RT, STAGED ? 128 : 168, R>::BLOCK,
           const int kx = xx < N / 2 ? xx : xx - N;
           if (valid && kx >= -K && kx <= K) {
             cx<T> w0 = v[0][q] * inv_n2, w1 = v[1][q] * inv_n2, w2 = v[2][q] * inv_n2;
-            stage_update<MODE, T>(sc, sa, s0 + kx, (long)P * P, (T)kx, fky, w0, w1, w2);
+            stage_update_s<SCH, MODE, T>(sc, sa, s0 + kx, (long)P * P, (T)kx, fky, w0, w1, w2);
             v[0][q] = w0;
             v[1][q] = w1;
             v[2][q] = w2;

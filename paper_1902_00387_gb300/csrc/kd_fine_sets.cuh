@@ -41,9 +41,9 @@ static cudaError_t prepare_col2() {
                               (int)Col2<T, N, XT>::smem);
 }
 
-template <typename T, int N, int RT, bool STAGED>
+template <typename T, int N, int RT, bool STAGED, int SCH = SCHEME_RK443>
 static cudaError_t prepare_row2() {
-  return cudaFuncSetAttribute(row2_kernel<T, N, RT, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(row2_kernel<T, N, RT, STAGED, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Row2<T, N, RT, STAGED ? 128 : 168>::smem);
 }
 
@@ -54,11 +54,11 @@ static void launch_col2(const FineArgs& a, int s, int j, cudaStream_t st, bool p
   launch_k(col2_kernel<T, N, XT>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
 }
 
-template <typename T, int N, int RT, bool STAGED>
+template <typename T, int N, int RT, bool STAGED, int SCH = SCHEME_RK443>
 static void launch_row2(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
   using R = Row2<T, N, RT, STAGED ? 128 : 168>;
   const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
-  launch_k(row2_kernel<T, N, RT, STAGED>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
+  launch_k(row2_kernel<T, N, RT, STAGED, SCH>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
 }
 
 template <typename T, int N, int XT, int R>
@@ -67,9 +67,9 @@ static cudaError_t prepare_col3() {
                               (int)Col3<T, N, XT, R>::smem);
 }
 
-template <typename T, int N, int RT, bool STAGED, int R>
+template <typename T, int N, int RT, bool STAGED, int R, int SCH = SCHEME_RK443>
 static cudaError_t prepare_row3() {
-  return cudaFuncSetAttribute(row3_kernel<T, N, RT, STAGED, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(row3_kernel<T, N, RT, STAGED, R, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Row3<T, N, RT, STAGED ? 128 : 168, R>::smem);
 }
 
@@ -80,11 +80,11 @@ static void launch_col3(const FineArgs& a, int s, int j, cudaStream_t st, bool p
   launch_k(col3_kernel<T, N, XT, R>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
 }
 
-template <typename T, int N, int RT, bool STAGED, int R>
+template <typename T, int N, int RT, bool STAGED, int R, int SCH = SCHEME_RK443>
 static void launch_row3(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
   using G = Row3<T, N, RT, STAGED ? 128 : 168, R>;
   const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
-  launch_k(row3_kernel<T, N, RT, STAGED, R>, gr, G::BLOCK, G::smem, st, pdl, a, mode, store);
+  launch_k(row3_kernel<T, N, RT, STAGED, R, SCH>, gr, G::BLOCK, G::smem, st, pdl, a, mode, store);
 }
 
 // 8-values-per-thread shapes: 256-thread blocks
@@ -105,6 +105,8 @@ struct Fine2Set {
     cudaError_t e;
     if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
     if ((e = prepare_row2<T, N, Sh::rt(0), true>()) != cudaSuccess) return e;
+    if ((e = prepare_row2<T, N, Sh::rt(0), true, SCHEME_RK222>()) != cudaSuccess) return e;
+    if ((e = prepare_row2<T, N, Sh::rt(0), true, SCHEME_RK111>()) != cudaSuccess) return e;
     if (WIDE) {
       if ((e = prepare_col2<T, N, Sh::xt(1)>()) != cudaSuccess) return e;
       if ((e = prepare_row2<T, N, Sh::rt(1), true>()) != cudaSuccess) return e;
@@ -129,6 +131,9 @@ struct Fine2Set {
   }
   static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
     if (!WIDE) v = 0;
+    // the lower-order schemes run on the default row kernel (prologue included)
+    if (a.scheme == SCHEME_RK222) return launch_row2<T, N, Sh::rt(0), true, SCHEME_RK222>(a, mode, store, st, pdl);
+    if (a.scheme == SCHEME_RK111) return launch_row2<T, N, Sh::rt(0), true, SCHEME_RK111>(a, mode, store, st, pdl);
     if constexpr (R8) {
       if (v == 4) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
       if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
@@ -153,6 +158,8 @@ struct Fine3Set {
     cudaError_t e;
     if ((e = prepare_col3<T, N, Sh::xt(0), 16>()) != cudaSuccess) return e;
     if ((e = prepare_row3<T, N, Sh::rt(0), true, 16>()) != cudaSuccess) return e;
+    if ((e = prepare_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK222>()) != cudaSuccess) return e;
+    if ((e = prepare_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK111>()) != cudaSuccess) return e;
     if (WIDE) {
       if ((e = prepare_col3<T, N, Sh::xt(1), 16>()) != cudaSuccess) return e;
       if ((e = prepare_row3<T, N, Sh::rt(1), true, 16>()) != cudaSuccess) return e;
@@ -188,6 +195,8 @@ struct Fine3Set {
   }
   static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
     if (!WIDE) v = 0;
+    if (a.scheme == SCHEME_RK222) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK222>(a, mode, store, st, pdl);
+    if (a.scheme == SCHEME_RK111) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK111>(a, mode, store, st, pdl);
     if constexpr (R8) {
       if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
       if (v == 6) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
@@ -220,16 +229,17 @@ static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
     ++launches;
   }
   FineArgs a = a0;
+  const int stages = scheme_stages(a0.scheme);
   for (int s = 0; s < cfg.nsteps; ++s) {
     if (cfg.active) {
       a.batch = cfg.active[s];
       if (a.batch <= 0) break;
     }
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < stages; ++j) {
       if (cfg.probe) cfg.probe->before(cfg.probe->user, 0);
       Set::col(cv, a, s, j, cfg.st, cfg.pdl);
       if (cfg.probe) cfg.probe->after(cfg.probe->user, 0);
-      const int store = (s == cfg.nsteps - 1 && j == 3) ? (cfg.store_last ? 1 : 0) : 1;
+      const int store = (s == cfg.nsteps - 1 && j == stages - 1) ? (cfg.store_last ? 1 : 0) : 1;
       if (cfg.probe) cfg.probe->before(cfg.probe->user, 1);
       Set::row(rv, a, j, store, cfg.st, cfg.pdl);
       if (cfg.probe) cfg.probe->after(cfg.probe->user, 1);

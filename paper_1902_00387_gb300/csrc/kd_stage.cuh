@@ -146,6 +146,68 @@ __device__ __forceinline__ void stage_update(const StageCoef<T>& q, const StageA
   w2 = out[2];
 }
 
+// Ascher-Ruuth-Spiteri (2,2,2) and (1,1,1) in the same accumulator form as RK443 above:
+// stage j evaluates F_j at X_j, forms X_{j+1} = (Q_{j+1} + dt H_{j+1,j} F_j) / (1 + dt g lam)
+// with Q_1 = X_0 and Q_i = R_i, and adds its terms to the later accumulators
+// R_i += dt H_ij F_j - dt A_{i,j+1} lam X_{j+1} (R_i = X_0 + ... from stage 0).  Both are
+// stiffly accurate: the last stage value is the new state.
+//   RK222: g = 1 - 1/sqrt(2), d = 1 - 1/(2g); A = [[g], [1-g, g]], H = [[g], [d, 1-d]]
+//   RK111: A = [[1]], H = [[1]]
+struct Tab222 {
+  static constexpr double g = 0.29289321881345247560;    // 1 - 1/sqrt(2)
+  static constexpr double d = -0.70710678118654752440;   // 1 - 1/(2 g)
+};
+
+template <int SCH, int MODE, typename T>
+__device__ __forceinline__ void stage_update_tab(const StageCoef<T>& q, const StageArrays<T>& sa, long s0,
+                                                 long cstride, T fkx, T fky, cx<T>& w0, cx<T>& w1, cx<T>& w2) {
+  const T dt = q.dt;
+  const T kz = q.kz;
+  cx<T> F[3];
+  F[0] = mul_i(w2 * fky - w1 * kz);
+  F[1] = mul_i(w0 * kz - w2 * fkx);
+  F[2] = mul_i(w1 * fkx - w0 * fky);
+  const T lam = (fkx * fkx + fky * fky + kz * kz) * q.inv_rm;
+  const T gam = SCH == SCHEME_RK222 ? T(Tab222::g) : T(1);
+  const T inv_d = T(1) / (T(1) + dt * gam * lam);
+  const T dl = dt * lam;
+  cx<T>* __restrict__ X = sa.X;
+  cx<T>* __restrict__ R2 = sa.R2;
+  cx<T> out[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long s = s0 + c * cstride;
+    const cx<T> f = F[c];
+    if (SCH == SCHEME_RK111) {
+      const cx<T> x1 = (X[s] + f * dt) * inv_d;
+      X[s] = x1;
+      out[c] = x1;
+    } else if (MODE == 0) {
+      const cx<T> x0 = X[s];
+      const cx<T> x1 = (x0 + f * (dt * gam)) * inv_d;
+      R2[s] = x0 + f * (dt * T(Tab222::d)) - x1 * (dl * (T(1) - gam));
+      out[c] = x1;
+    } else {
+      const cx<T> x2 = (R2[s] + f * (dt * (T(1) - T(Tab222::d)))) * inv_d;
+      X[s] = x2;
+      out[c] = x2;
+    }
+  }
+  w0 = out[0];
+  w1 = out[1];
+  w2 = out[2];
+}
+
+// Stage update of scheme SCH (RK443: stage_update above).
+template <int SCH, int MODE, typename T>
+__device__ __forceinline__ void stage_update_s(const StageCoef<T>& q, const StageArrays<T>& sa, long s0,
+                                               long cstride, T fkx, T fky, cx<T>& w0, cx<T>& w1, cx<T>& w2) {
+  if constexpr (SCH == SCHEME_RK443)
+    stage_update<MODE, T>(q, sa, s0, cstride, fkx, fky, w0, w1, w2);
+  else
+    stage_update_tab<SCH, MODE, T>(q, sa, s0, cstride, fkx, fky, w0, w1, w2);
+}
+
 // Call f(std::integral_constant<int, m>) for the runtime stage index m = 0..3, so that
 // the stage update of a loop body is specialised for its stage.
 template <class F>

@@ -59,7 +59,7 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   const int n = p->n, prec = p->prec_fine;
   const bool n_ok = n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
   if (!n_ok || p->flow < 0 || p->flow > 2 || (prec != KD_C64 && prec != KD_C128) || !(p->Rm > 0) ||
-      !(p->dt_fine > 0) || !isfinite(p->kz)) {
+      !(p->dt_fine > 0) || !isfinite(p->kz) || p->fine_scheme < KD_RK443 || p->fine_scheme > KD_RK111) {
     fprintf(stderr, "kd_fine_batched_static: invalid parameters\n");
     return KD_EINVAL;
   }
@@ -133,6 +133,7 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   a.phases = phase ? q : nullptr;
   a.phase_steps = nsteps;
   a.sp = nullptr;
+  a.scheme = p->fine_scheme;
   a.tw = tw;
   a.cosg = cg;
   a.sing = sg;

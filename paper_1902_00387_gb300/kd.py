@@ -22,6 +22,7 @@ KD_C64, KD_C128 = 0, 1
 KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
 KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
 KD_FINE_FFT, KD_FINE_CONV = 0, 1
+KD_RK443, KD_RK222, KD_RK111 = 0, 1, 2
 KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
 KD_GRID_FINE, KD_GRID_COARSE = 0, 1
 KD_MAX_SLICES = 1024
@@ -40,7 +41,7 @@ class kd_params(ctypes.Structure):
                 ("Rm", ctypes.c_double), ("dt_fine", ctypes.c_double), ("prec_fine", ctypes.c_int),
                 ("n_coarse", ctypes.c_int), ("dt_coarse", ctypes.c_double), ("prec_coarse", ctypes.c_int),
                 ("coarse_kind", ctypes.c_int), ("learned_modes", ctypes.c_int), ("fine_form", ctypes.c_int),
-                ("fine_operator", ctypes.c_int)]
+                ("fine_operator", ctypes.c_int), ("fine_scheme", ctypes.c_int)]
 
 
 class kd_parareal_stats(ctypes.Structure):
@@ -141,11 +142,11 @@ def load():
 
 def make_params(flow, n, kz, Rm, dt_fine, prec_fine=KD_C64, n_coarse=None, dt_coarse=None,
                 prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL, fine_form=KD_FINE_DIRECT, learned_modes=0,
-                fine_operator=KD_FINE_FFT):
+                fine_operator=KD_FINE_FFT, fine_scheme=KD_RK443):
     return kd_params(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(prec_fine),
                      int(n_coarse if n_coarse else max(16, n // 2)),
                      float(dt_coarse if dt_coarse else dt_fine), int(prec_fine if prec_coarse is None else prec_coarse),
-                     int(coarse_kind), int(learned_modes), int(fine_form), int(fine_operator))
+                     int(coarse_kind), int(learned_modes), int(fine_form), int(fine_operator), int(fine_scheme))
 
 
 def _ptr(x, dtype=None, device=True):

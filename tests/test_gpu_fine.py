@@ -1,5 +1,7 @@
 """Parity of the CUDA fine propagator (kd_fine_batched, kd_coarse) with the CPU FP64
 oracle, element by element, through the C ABI."""
+import math
+
 import numpy as np
 import pytest
 
@@ -277,3 +279,56 @@ def test_convolution_fine_operator_matches_oracle(kd, n, prec):
 def test_convolution_fine_operator_rejected_above_128(kd):
     with pytest.raises(kd.KdError):
         kd.kd_create(kd.make_params(O.ROBERTS, 256, 1.0, 8.0, 1e-2, kd.KD_C64, fine_operator=kd.KD_FINE_CONV))
+
+
+@pytest.mark.parametrize("scheme", ["RK222", "RK111"])
+@pytest.mark.parametrize("n,prec", [(32, "c128"), (64, "c128"), (128, "c64"), (512, "c64")])
+def test_lower_order_schemes_match_oracle(kd, scheme, n, prec):
+    """ARS (2,2,2) and (1,1,1) fine steps (Sec. 4, 5.1) against the oracle's tableaux."""
+    import torch
+    sch = {"RK222": kd.KD_RK222, "RK111": kd.KD_RK111}[scheme]
+    tab = {"RK222": O.RK222, "RK111": O.RK111}[scheme]
+    P = kd.KD_C64 if prec == "c64" else kd.KD_C128
+    kz, Rm, dt = 0.57, 100.0, 4e-3
+    seeds = [51, 52] if n <= 128 else [51]
+    t0 = [0.2, 1.3][:len(seeds)]
+    b = I.initial_batch(n, kz, seeds)
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, P, fine_scheme=sch))
+    try:
+        dtype = torch.complex64 if P == kd.KD_C64 else torch.complex128
+        x = torch.tensor(b, dtype=dtype, device="cuda")
+        y = torch.empty_like(x)
+        kd.kd_fine_batched(ctx, x, y, torch.tensor(t0, dtype=torch.float64, device="cuda"), 5, len(seeds), P)
+        torch.cuda.synchronize()
+        out = y.cpu().numpy().astype(np.complex128)
+    finally:
+        kd.kd_destroy(ctx)
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i in range(len(seeds)):
+        ref = O.propagate(b[i], p, t0[i], dt, 5, tab=tab)
+        assert rel(out[i], ref) < (TOL32 if P == kd.KD_C64 else 1e-12), (scheme, n, i)
+
+
+def test_scheme_orders_on_gpu(kd):
+    """Observed orders of the three schemes in FP64 on the GPU: 1, 2 and 3."""
+    import torch
+    n, kz, Rm, T = 32, 0.57, 20.0, 0.4
+    b = I.initial_batch(n, kz, [61])
+    t0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def run(sch, dt):
+        ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C128, fine_scheme=sch))
+        try:
+            x = torch.tensor(b, dtype=torch.complex128, device="cuda")
+            y = torch.empty_like(x)
+            kd.kd_fine_batched(ctx, x, y, t0, int(round(T / dt)), 1, kd.KD_C128)
+            torch.cuda.synchronize()
+            return y.cpu().numpy()
+        finally:
+            kd.kd_destroy(ctx)
+
+    ref = run(kd.KD_RK443, T / 640)
+    for sch, order in ((kd.KD_RK111, 1), (kd.KD_RK222, 2), (kd.KD_RK443, 3)):
+        e = [np.linalg.norm(run(sch, T / m) - ref) for m in (20, 40, 80)]
+        rates = [math.log2(e[0] / e[1]), math.log2(e[1] / e[2])]
+        assert abs(rates[-1] - order) < 0.25, (sch, rates)
