@@ -4,8 +4,9 @@
 Workload (one "step" = one complete Parareal solve through the C ABI): the
 Galloway-Proctor circularly polarised flow on a 128 x 128 grid, kz = 0.57, Rm = 100,
 fine dt <= 5e-3 over T = 2 pi * 8 split into 64 slices (158 RK443 steps of pi/632
-per slice), complex64 fine propagator, classical coarse propagator on the 64 x 64
-grid (20 steps of pi/80 per slice), FP64 update and convergence defect, the fine and
+per slice), complex64 fine propagator, classical coarse propagator on the same grid
+with a 3x larger step (51 steps per slice; the measured optimum of the coarse-grid sweep,
+`--config coarse-sweep`), FP64 update and convergence defect, the fine and
 coarse values evaluated on FP64 increments (F and G are linear in b), stopping at
 sigma <= 1e-6 (Eq. 9).
 
@@ -39,7 +40,7 @@ if ROOT not in sys.path:
 WL = {
     "workload": "gp_cp_128x128_parareal_64_slices",
     "flow": "galloway-proctor", "n": 128, "kz": 0.57, "Rm": 100.0, "dt_fine_max": 5e-3,
-    "T": 2 * math.pi * 8, "slices": 64, "n_coarse": 64, "dt_coarse_max": 0.04, "tol": 1e-6,
+    "T": 2 * math.pi * 8, "slices": 64, "n_coarse": 128, "dt_coarse_max": 2.0 / 128, "tol": 1e-6,
     "k_max": 64, "prec_fine": "complex64", "prec_coarse": "complex64", "update": "float64",
     "fine_form": "increment",
 }
@@ -327,6 +328,57 @@ def run_steppers(args):
                       "rows": rows}), flush=True)
 
 
+# --------------------------------------------------------- coarse-grid sweep (Sec. 5.2)
+def run_coarse_sweep(args):
+    """The paper's coarse-resolution study (Sec. 5.2, fig. 6) on the config-2 problem:
+    Parareal iterations and time to 1e-6 for N_C = 16, 32, 64, 128 (coarse step at the
+    stability limit of each coarse grid, min(20 dt, 2 / N_C), reading R15), against the
+    serial fine time with the same kernels."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    n, N, T = WL["n"], WL["slices"], WL["T"]
+    b0 = torch.tensor(kd_inputs.initial_field(n, WL["kz"], 1000), device="cuda")
+    rows = []
+    serial = None
+    for nc in (16, 32, 64, 128):
+        dtc = min(20 * WL["dt_fine_max"], 2.0 / nc)
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C64,
+                           n_coarse=nc, dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
+        ctx = kd.kd_create(p)
+        try:
+            kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 2)
+            if serial is None:
+                ser = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+                kd.kd_fine_serial(ctx, b0, T, N, ser)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                kd.kd_fine_serial(ctx, b0, T, N, ser)
+                e1.record()
+                torch.cuda.synchronize()
+                serial = e0.elapsed_time(e1)
+            kd.kd_parareal_run(ctx, b0, T, N, WL["k_max"], WL["tol"])
+            ms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s, st = kd.kd_parareal_run(ctx, b0, T, N, WL["k_max"], WL["tol"])
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            rows.append({"n_coarse": nc, "dt_coarse": st.dt_coarse_used, "coarse_steps": st.n_coarse_steps,
+                         "k_con": st.k_con, "converged": bool(st.converged), "ms": min(ms),
+                         "fine_ms": st.ms_fine, "coarse_ms": st.ms_coarse, "speedup_vs_serial_fine": serial / min(ms)})
+        finally:
+            kd.kd_destroy(ctx)
+    print(json.dumps({"config": dict(WL, study="n_coarse sweep"), "serial_fine_ms": serial, "rows": rows}),
+          flush=True)
+
+
 # ------------------------------------------------------------- large run (config 5)
 LARGE_WL = {
     "workload": "gp_cp_1024x1024_parareal_256_slices",
@@ -583,7 +635,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large", "steppers"],
+    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large", "steppers", "coarse-sweep"],
                     help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
                          "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices")
     ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
@@ -606,6 +658,9 @@ def main():
         return
     if args.config == "steppers":
         run_steppers(args)
+        return
+    if args.config == "coarse-sweep":
+        run_coarse_sweep(args)
         return
 
     import numpy as np
