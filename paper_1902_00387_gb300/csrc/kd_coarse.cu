@@ -54,10 +54,11 @@ __device__ __forceinline__ UHat<T> uhat(T A, const Phase<T>& p) {
 // below, double-buffered: a stage reads buffer `cur`, writes its new rows into `nxt`
 // locally and its first / last row into the neighbours' halo rows of `nxt` through
 // distributed shared memory, then one cluster barrier makes `nxt` current.
-constexpr int CCB = 256;   // threads per block of the cluster kernel
+constexpr int CCB = 256;   // threads per block of the cluster kernel (MPT = 2, 4)
+constexpr int CCB1 = 512;  // threads per block with one mode per thread
 
-template <typename T, int MPT>
-__global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int CS, int H) {
+template <typename T, int MPT, int NT = CCB>
+__global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS, int H) {
   cgrp::cluster_group cluster = cgrp::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = a.Kc, P = a.Pc, L = P + 2, LH = H + 2;
@@ -77,11 +78,11 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   double* Unext = a.Unext ? a.Unext + (a.map ? (slot + 1) * lenf2 : 0) : nullptr;
   double* sig = a.sigma_out ? a.sigma_out + (a.map ? 3L * b : 0) : nullptr;
   const int nsteps = a.steps ? a.steps[b] : a.nsteps;
-  for (int i = threadIdx.x; i < 2 * bufsz; i += CCB) buf[i] = mk(T(0), T(0));
+  for (int i = threadIdx.x; i < 2 * bufsz; i += NT) buf[i] = mk(T(0), T(0));
   const bool stage_ph = a.phases && a.nsteps * 16 <= a.phase_smem;
   const T* ph_g = a.phases ? (const T*)a.phases + (long)b * a.nsteps * 16 : nullptr;
   if (stage_ph)
-    for (int i = threadIdx.x; i < a.nsteps * 16; i += CCB) s_ph[i] = ph_g[i];
+    for (int i = threadIdx.x; i < a.nsteps * 16; i += NT) s_ph[i] = ph_g[i];
   __syncthreads();
 
   const int M = hr * P;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   const T inv_rm = T(1) / (a.sp ? (T)a.sp[b].Rm : (T)a.Rm);
 #pragma unroll
   for (int i = 0; i < MPT; ++i) {
-    const int m = threadIdx.x + CCB * i;
+    const int m = threadIdx.x + NT * i;
     const int ly = m < M ? m / P : 0, ix = m < M ? m % P : 0;
     const int iy = y0 + ly;
     fkx[i] = (T)(ix - K);
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   cluster.sync();   // every block has zeroed its buffers before peers write halos
 #pragma unroll
   for (int i = 0; i < MPT; ++i) {
-    const int m = threadIdx.x + CCB * i;
+    const int m = threadIdx.x + NT * i;
     if (m < M)
 #pragma unroll
       for (int c = 0; c < 3; ++c) put(0, m / P, m % P, c, x0[i][c]);
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
       const cx<T>* Xs = buf + cur * bufsz;
 #pragma unroll
       for (int i = 0; i < MPT; ++i) {
-        const int m = threadIdx.x + CCB * i;
+        const int m = threadIdx.x + NT * i;
         if (m >= M) continue;
         const int ly = m / P + 1, ix = m % P + 1;
         cx<T> w[3] = {mk(T(0), T(0)), mk(T(0), T(0)), mk(T(0), T(0))};
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
   const cx<T>* Xf = buf + cur * bufsz;
   if (a.mode == COARSE_OUT) {
     double* g = a.g64 + (long)b * 2 * 3 * P * P;
-    for (int i = threadIdx.x; i < 3 * M; i += CCB) {
+    for (int i = threadIdx.x; i < 3 * M; i += NT) {
       const int c = i / M, r = i - c * M;
       const int ly = r / P, ix = r % P;
       const cx<T> v = Xf[(c * LH + ly + 1) * L + ix + 1];
@@ -229,12 +230,12 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
     return;
   }
   // fused Parareal update over the fine rows ky in this block's share of [-Kf, Kf]
-  __shared__ double red_d[CCB / 32], red_n[CCB / 32];
+  __shared__ double red_d[NT / 32], red_n[NT / 32];
   __shared__ double cl_d[16], cl_n[16];
   const int fr0 = (Pf * rank) / CS, fr1 = (Pf * (rank + 1)) / CS;   // fine rows of this block
   const int Mf = (fr1 - fr0) * Pf;
   double acc_d = 0.0, acc_n = 0.0;
-  for (int i = threadIdx.x; i < 3 * Mf; i += CCB) {
+  for (int i = threadIdx.x; i < 3 * Mf; i += NT) {
     const int c = i / Mf, r = i - c * Mf;
     const int fy = fr0 + r / Pf, fx = r % Pf;
     const int ky = fy - Kf, kx = fx - Kf;
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(CCB) coarse_cluster_kernel(CoarseArgs a, int C
     __syncthreads();
     if (threadIdx.x == 0) {
       double d = 0.0, n = 0.0;
-      for (int w = 0; w < CCB / 32; ++w) {
+      for (int w = 0; w < NT / 32; ++w) {
         d += red_d[w];
         n += red_n[w];
       }
@@ -337,9 +338,13 @@ static size_t cluster_smem(int prec, int P, int nsteps, int* phase_slots, int re
 }
 
 // modes per thread needed for a P-row square (0: unsupported)
+// modes per thread of a block (1: CCB1 threads; 2, 4: CCB threads); 0 if the rows of a
+// block do not fit
 static int modes_per_thread(int P, int req = 0) {
   int CS, H;
   cluster_shape(P, &CS, &H, req);
+  if (H * P <= CCB) return 2;
+  if (H * P <= CCB1) return 1;
   if (H * P <= 2 * CCB) return 2;
   if (H * P <= 4 * CCB) return 4;
   return 0;
@@ -366,10 +371,14 @@ static cudaError_t prepare_T() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 1, CCB1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
   // 16-block clusters where the device grants them
   if (cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
           cudaSuccess &&
       cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(coarse_cluster_kernel<T, 1, CCB1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
           cudaSuccess)
     g_max_cluster = 16;
   cudaGetLastError();
@@ -410,7 +419,8 @@ static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   a.phase_smem = slots;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CS * batch), 1, 1);
-  cfg.blockDim = dim3(CCB, 1, 1);
+  const int mpt = modes_per_thread(a.Pc, req);
+  cfg.blockDim = dim3(mpt == 1 ? CCB1 : CCB, 1, 1);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -420,9 +430,9 @@ static int launch_cluster(const CoarseArgs& a0, int batch, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = modes_per_thread(a.Pc, req) == 2
-                            ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H)
-                            : cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 4>, a, CS, H);
+  const cudaError_t e = mpt == 1   ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 1, CCB1>, a, CS, H)
+                       : mpt == 2 ? cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 2>, a, CS, H)
+                                  : cudaLaunchKernelEx(&cfg, coarse_cluster_kernel<T, 4>, a, CS, H);
   return e == cudaSuccess ? 1 : -1;
 }
 

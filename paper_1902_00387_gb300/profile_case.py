@@ -42,8 +42,8 @@ def main():
     if args.parareal:
         import math
         n, N, T = 128, 64, 2 * math.pi * 8
-        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, 0.57, 100.0, 5e-3, kd.KD_C64, n_coarse=64,
-                           dt_coarse=0.04, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, 0.57, 100.0, 5e-3, kd.KD_C64, n_coarse=128,
+                           dt_coarse=2.0 / 128, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
         ctx = kd.kd_create(p)
         if args.plan:
             kd.kd_set_plan(ctx, kd.KD_GRID_FINE, *(int(v) for v in args.plan.split(",")))
