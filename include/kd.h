@@ -171,8 +171,9 @@ kd_status kd_set_overlap(kd_ctx* ctx, int chunks);
 
 /* Serial fine solution at the slice boundaries, U_{n+1} = F(U_n) with each slice
  * restarted at t_n = n dT exactly as in kd_parareal_run (the solution Parareal
- * converges to, Sec. 3.1).  Same arguments and step rule as kd_parareal_run.
- * Synchronous. */
+ * converges to, Sec. 3.1).  Same arguments and step rule as kd_parareal_run.  The fine
+ * kernels run with a launch plan autotuned for one field (once per context; the
+ * batched plan of kd_set_plan / kd_autotune is left unchanged).  Synchronous. */
 kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int n_slices,
                          double* u_slices);
 

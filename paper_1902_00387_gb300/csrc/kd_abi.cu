@@ -960,6 +960,16 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
   if ((s = ensure_slices(ctx, N)) != KD_OK) return s;
   if ((s = ensure_ws(ctx, ctx->ws_f, n, pf, 1)) != KD_OK) return s;
   const long len = compact_len(n);
+  // one field at a time is a different launch shape from the batched sweeps: tune it once
+  if (!conv_op(ctx) && !ctx->plan_serial_ok) {
+    const FinePlan saved = ctx->plan[0];
+    if ((s = kd_autotune(ctx, KD_GRID_FINE, 1, 2, nullptr, nullptr)) != KD_OK) return s;
+    ctx->plan_serial = ctx->plan[0];
+    ctx->plan[0] = saved;
+    ctx->plan_serial_ok = 1;
+  }
+  const FinePlan batched = ctx->plan[0];
+  ctx->plan[0] = ctx->plan_serial;
   KD_LAUNCH(fill_slice_times(ctx->t0f, N + 1, 0, dT, ctx->st), "times");
   if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
   for (int i = 0; i < N; ++i) {
@@ -974,6 +984,7 @@ kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double*
     KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false), "fine steps");
     KD_LAUNCH(compact_resample(pf, ctx->ws_f.X, n, KD_C128, ctx->U + 2 * (i + 1) * len, n, 1, ctx->st), "from fine");
   }
+  ctx->plan[0] = batched;
   if ((s = copy_out_slices(ctx, u_slices, N)) != KD_OK) return s;
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   return KD_OK;

@@ -38,6 +38,8 @@ inline size_t csize(int prec) { return prec == KD_C128 ? 16 : 8; }
 struct kd_ctx {
   kd_params p;
   kd::FinePlan plan[2];        // launch plans of the fine (0) and coarse (1) grid
+  kd::FinePlan plan_serial;    // fine-grid plan for one field at a time (kd_fine_serial)
+  int plan_serial_ok = 0;
   int pdl = 1;                 // fine-step kernels as programmatic dependent launches
   // pipelined Parareal: the fine sweep of iteration k + 1 runs in `overlap` slice chunks on
   // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)

@@ -141,6 +141,44 @@ __device__ __forceinline__ void fft2_3(cx<T> (&v)[3][Split<N>::R1], int a, const
   }
 }
 
+// One-component transform (the component-split kernels): the same passes as fft2_3 with
+// S(q, a2) the slot of matrix element (q, a2) of this thread's transform.
+template <typename T, int N, int DIR, class Slot>
+__device__ __forceinline__ void fft2_1(cx<T> (&v)[Split<N>::R1], int a, const cx<T>* tw, Slot S) {
+  constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2, J = R1 / R2;
+  dft_dif<T, R1, DIR>(v);
+#pragma unroll
+  for (int q = 0; q < R1; ++q) {
+    cx<T> y = v[bitrev<R1>(q)];
+    if (q != 0) {
+      const cx<T> w = tw[q * R2 + a];
+      y = cmul(y, DIR < 0 ? w : mk(w.x, -w.y));
+    }
+    *S(q, a) = y;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int q = a + R2 * j;
+    cx<T> u[R2];
+#pragma unroll
+    for (int a2 = 0; a2 < R2; ++a2) u[a2] = *S(q, a2);
+    dft_dif<T, R2, DIR>(u);
+#pragma unroll
+    for (int p = 0; p < R2; ++p) v[j * R2 + p] = u[bitrev<R2>(p)];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void out_to_in_1(cx<T> (&v)[Split<N>::R1]) {
+  constexpr int R1 = Split<N>::R1;
+  cx<T> t[R1];
+#pragma unroll
+  for (int k = 0; k < R1; ++k) t[k] = v[FFT2<N>::in_from_out(k)];
+#pragma unroll
+  for (int k = 0; k < R1; ++k) v[k] = t[k];
+}
+
 // Re-order registers from the output layout of one transform to the input layout of
 // the next (same lane): in[k] = out[in_from_out(k)].
 template <typename T, int N>

@@ -4,15 +4,18 @@
 //
 // complex64 variants (complex128 has variant 0 only):
 //   n <= 256  column: 0, 1 = four-step kernels with XT0, XT0/2 columns per block;
-//                     2 = three-pass kernel with 8 values per thread (n = 128, 256)
+//                     2 = component-split four-step kernel (one component per thread);
+//                     3 = three-pass kernel with 8 values per thread (n = 128, 256)
 //             row:    0..3 = four-step kernels, (RT0 | RT0/2 rows) x (staged | registers);
-//                     4, 5 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
+//                     4, 5 = component-split kernels with 8 | 4 rows per block;
+//                     6, 7 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
 //   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
 //                     2 = persistent prefetching kernel; 3 = 8 values per thread (n = 512)
 //             row:    0..3 = three-pass, 16 values, (RT0 | RT0/2) x (staged | registers);
 //                     4 = persistent prefetching kernel (in registers);
 //                     5, 6 = 8 values per thread, staged | registers (n = 512)
 #pragma once
+#include "kd_fine2c.cuh"
 #include "kd_fine3.cuh"
 
 namespace kd {
@@ -94,13 +97,35 @@ struct Shapes8 {
   static constexpr int XT = 256 / TPT, RT = 256 / TPT;
 };
 
+template <typename T, int N, int XT>
+static void launch_col2c(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = Col2C<T, N, XT>;
+  const unsigned gc = (unsigned)(((long)a.batch * N + XT - 1) / XT);
+  launch_k(col2c_kernel<T, N, XT>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <typename T, int N, int RT>
+static void launch_row2c(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+  using R = Row2C<T, N, RT>;
+  const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
+  launch_k(row2c_kernel<T, N, RT>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
+}
+
+// component-split shapes
+template <int N>
+struct ShapesC {
+  static constexpr int XT = N <= 64 ? 32 : 16;
+  static constexpr int RT0 = 8, RT1 = 4;
+};
+
 template <typename T, int N>
 struct Fine2Set {
   using Sh = Shapes2<T, N>;
+  using ShC = ShapesC<N>;
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && (N == 128 || N == 256);
-  static int ncol() { return WIDE ? (R8 ? 3 : 2) : 1; }
-  static int nrow() { return WIDE ? (R8 ? 6 : 4) : 1; }
+  static int ncol() { return WIDE ? (R8 ? 4 : 3) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 8 : 6) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
@@ -113,6 +138,17 @@ struct Fine2Set {
       if ((e = prepare_row2<T, N, Sh::rt(0), false>()) != cudaSuccess) return e;
       if ((e = prepare_row2<T, N, Sh::rt(1), false>()) != cudaSuccess) return e;
     }
+    if constexpr (WIDE) {
+      if ((e = cudaFuncSetAttribute(col2c_kernel<T, N, ShC::XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col2C<T, N, ShC::XT>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(row2c_kernel<T, N, ShC::RT0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Row2C<T, N, ShC::RT0>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(row2c_kernel<T, N, ShC::RT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Row2C<T, N, ShC::RT1>::smem)) != cudaSuccess)
+        return e;
+    }
     if constexpr (R8) {
       if ((e = prepare_col3<T, N, Shapes8<N>::XT, 8>()) != cudaSuccess) return e;
       if ((e = prepare_row3<T, N, Shapes8<N>::RT, true, 8>()) != cudaSuccess) return e;
@@ -121,8 +157,11 @@ struct Fine2Set {
     return cudaSuccess;
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (WIDE) {
+      if (v == 2) return launch_col2c<T, N, ShC::XT>(a, s, j, st, pdl);
+    }
     if constexpr (R8) {
-      if (v == 2) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
+      if (v == 3) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
     }
     if (WIDE && v == 1)
       launch_col2<T, N, Sh::xt(1)>(a, s, j, st, pdl);
@@ -134,9 +173,13 @@ struct Fine2Set {
     // the lower-order schemes run on the default row kernel (prologue included)
     if (a.scheme == SCHEME_RK222) return launch_row2<T, N, Sh::rt(0), true, SCHEME_RK222>(a, mode, store, st, pdl);
     if (a.scheme == SCHEME_RK111) return launch_row2<T, N, Sh::rt(0), true, SCHEME_RK111>(a, mode, store, st, pdl);
+    if constexpr (WIDE) {
+      if (v == 4) return launch_row2c<T, N, ShC::RT0>(a, mode, store, st, pdl);
+      if (v == 5) return launch_row2c<T, N, ShC::RT1>(a, mode, store, st, pdl);
+    }
     if constexpr (R8) {
-      if (v == 4) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
-      if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
+      if (v == 6) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
+      if (v == 7) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
     }
     switch (v) {
       case 1: launch_row2<T, N, Sh::rt(1), true>(a, mode, store, st, pdl); break;
