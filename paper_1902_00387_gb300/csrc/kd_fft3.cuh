@@ -111,6 +111,52 @@ __device__ __forceinline__ void fft3r(cx<T> (&v)[3][R], int j, const cx<T>* tw, 
   }
 }
 
+// One-component three-pass transform (the component-split kernels): S(i) is the slot of
+// padded index i of this thread's component.
+template <typename T, int N, int R, int DIR, class Slot>
+__device__ __forceinline__ void fft3r_1(cx<T> (&v)[R], int j, const cx<T>* tw, Slot S) {
+  using F = F3<N, R>;
+  constexpr int TT = F::T, RM = F::RM, NB2 = F::NB2;
+  dft_dif<T, R, DIR>(v);
+#pragma unroll
+  for (int q = 0; q < R; ++q) *S(F::pad(j * R + q)) = v[bitrev<R>(q)];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB2; ++i) {
+    const int b = j + i * TT;
+#pragma unroll
+    for (int k = 0; k < RM; ++k) v[i * RM + k] = *S(F::pad(b + k * (N / RM)));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB2; ++i) {
+    const int b = j + i * TT;
+    const int bm = b % R;
+    cx<T>* vv = &v[i * RM];
+#pragma unroll
+    for (int k = 1; k < RM; ++k) {
+      const cx<T> t = tw[N + k * R + bm];
+      vv[k] = cmul(vv[k], DIR < 0 ? t : mk(t.x, -t.y));
+    }
+    dft_dif<T, RM, DIR>(vv);
+    const int idxD = (b / R) * R * RM + bm;
+#pragma unroll
+    for (int q = 0; q < RM; ++q) *S(F::pad(idxD + q * R)) = vv[bitrev<RM>(q)];
+  }
+  __syncthreads();
+  cx<T> u[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) u[k] = *S(F::pad(j + k * TT));
+#pragma unroll
+  for (int k = 1; k < R; ++k) {
+    const cx<T> t = tw[k * TT + j];
+    u[k] = cmul(u[k], DIR < 0 ? t : mk(t.x, -t.y));
+  }
+  dft_dif<T, R, DIR>(u);
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = u[bitrev<R>(q)];
+}
+
 // The 16-values-per-thread transform of the n = 512, 1024 kernels.
 template <typename T, int N, int DIR, class Slot>
 __device__ __forceinline__ void fft3_3(cx<T> (&v)[3][16], int j, const cx<T>* tw, Slot S) {

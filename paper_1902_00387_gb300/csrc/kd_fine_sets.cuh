@@ -10,13 +10,16 @@
 //                     4, 5 = component-split kernels with 8 | 4 rows per block;
 //                     6, 7 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
 //   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
-//                     2 = persistent prefetching kernel; 3 = 8 values per thread (n = 512)
+//                     2 = persistent prefetching kernel; 3 = component-split kernel;
+//                     4 = 8 values per thread (n = 512)
 //             row:    0..3 = three-pass, 16 values, (RT0 | RT0/2) x (staged | registers);
 //                     4 = persistent prefetching kernel (in registers);
-//                     5, 6 = 8 values per thread, staged | registers (n = 512)
+//                     5, 6 = component-split kernels with RT0 | RT0/2 rows per block;
+//                     7, 8 = 8 values per thread, staged | registers (n = 512)
 #pragma once
 #include "kd_fine2c.cuh"
 #include "kd_fine3.cuh"
+#include "kd_fine3c.cuh"
 
 namespace kd {
 
@@ -190,13 +193,28 @@ struct Fine2Set {
   }
 };
 
+template <typename T, int N, int XT>
+static void launch_col3c(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = Col3C<T, N, XT>;
+  const unsigned gc = (unsigned)(((long)a.batch * N + XT - 1) / XT);
+  launch_k(col3c_kernel<T, N, XT>, gc, C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <typename T, int N, int RT>
+static void launch_row3c(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+  using R = Row3C<T, N, RT>;
+  const unsigned gr = (unsigned)(((long)a.batch * a.P + RT - 1) / RT);
+  launch_k(row3c_kernel<T, N, RT>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
+}
+
 template <typename T, int N>
 struct Fine3Set {
   using Sh = Shapes3<T, N>;
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
-  static int ncol() { return WIDE ? (R8 ? 4 : 3) : 1; }
-  static int nrow() { return WIDE ? (R8 ? 7 : 5) : 1; }
+  static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
+  static int ncol() { return WIDE ? (R8 ? 5 : 4) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 9 : 7) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_col3<T, N, Sh::xt(0), 16>()) != cudaSuccess) return e;
@@ -215,6 +233,17 @@ struct Fine3Set {
                                     (int)Row3P<T, N, Sh::RT0>::smem)) != cudaSuccess)
         return e;
     }
+    if constexpr (WIDE) {
+      if ((e = cudaFuncSetAttribute(col3c_kernel<T, N, XTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col3C<T, N, XTC>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(row3c_kernel<T, N, RTC0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Row3C<T, N, RTC0>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(row3c_kernel<T, N, RTC1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Row3C<T, N, RTC1>::smem)) != cudaSuccess)
+        return e;
+    }
     if constexpr (R8) {
       if ((e = prepare_col3<T, N, Shapes8<N>::XT, 8>()) != cudaSuccess) return e;
       if ((e = prepare_row3<T, N, Shapes8<N>::RT, true, 8>()) != cudaSuccess) return e;
@@ -223,8 +252,11 @@ struct Fine3Set {
     return cudaSuccess;
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (WIDE) {
+      if (v == 3) return launch_col3c<T, N, XTC>(a, s, j, st, pdl);
+    }
     if constexpr (R8) {
-      if (v == 3) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
+      if (v == 4) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
     }
     if (WIDE && v == 2) {
       using C = Col3P<T, N, Sh::XT0>;
@@ -240,9 +272,13 @@ struct Fine3Set {
     if (!WIDE) v = 0;
     if (a.scheme == SCHEME_RK222) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK222>(a, mode, store, st, pdl);
     if (a.scheme == SCHEME_RK111) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK111>(a, mode, store, st, pdl);
+    if constexpr (WIDE) {
+      if (v == 5) return launch_row3c<T, N, RTC0>(a, mode, store, st, pdl);
+      if (v == 6) return launch_row3c<T, N, RTC1>(a, mode, store, st, pdl);
+    }
     if constexpr (R8) {
-      if (v == 5) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
-      if (v == 6) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
+      if (v == 7) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
+      if (v == 8) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
     }
     if (v == 4 && mode == 4) v = 0;   // the prologue runs on the tiled kernel
     if (v == 4) {
