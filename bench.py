@@ -379,6 +379,70 @@ def run_coarse_sweep(args):
           flush=True)
 
 
+# ------------------------------------------- coarse-resolution study, Roberts (Sec. 5.2)
+ROBERTS_SWEEP_WL = {
+    "workload": "roberts_rm512_nf160_parareal_10_slices_nc_sweep",
+    "flow": "roberts", "n": 160, "kz": 2.87, "Rm": 512.0, "dt_fine": 1e-2, "T": 50.0, "slices": 10,
+    "n_coarse": [20, 40, 60, 80, 100, 120, 160], "dt_coarse": "dt_fine * N_F / N_C (the stability limit ~1.6 / N)",
+    "tol": 1e-6, "k_max": 10, "prec_fine": "complex64", "prec_coarse": "complex64", "update": "float64",
+    "fine_form": "increment", "fine_operator": "conv (N_F = 160 is not a power of two)",
+}
+
+
+def run_roberts_coarse_sweep(args):
+    """The paper's coarse-resolution study at its own parameters (Sec. 5.2, fig. 6 and
+    Table 1's Roberts row): Rm = 512, kz = 2.87, N_F = 160, delta t = 1e-2, N_P = 10
+    slices, the coarse step at the stability limit of each coarse grid; Parareal
+    iterations and time to the tolerance against the serial fine run, one GPU."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    W = ROBERTS_SWEEP_WL
+    n, N, T = W["n"], W["slices"], W["T"]
+    b0 = torch.tensor(kd_inputs.initial_field(n, W["kz"], 1000), device="cuda")
+
+    def timed(f, reps=3):
+        f()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = f()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best, out
+
+    rows, serial = [], None
+    for nc in W["n_coarse"]:
+        dtc = W["dt_fine"] * n / nc
+        p = kd.make_params(kd.KD_FLOW_ROBERTS, n, W["kz"], W["Rm"], W["dt_fine"], kd.KD_C64, n_coarse=nc,
+                           dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT,
+                           fine_operator=kd.KD_FINE_CONV)
+        ctx = kd.kd_create(p)
+        try:
+            if serial is None:
+                ser = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+                serial, _ = timed(lambda: kd.kd_fine_serial(ctx, b0, T, N, ser))
+                ser_last = ser[-1].clone()
+            out = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
+            ms, (s, st) = timed(lambda: kd.kd_parareal_run(ctx, b0, T, N, W["k_max"], W["tol"], out))
+            err = float(torch.linalg.vector_norm(out[-1] - ser_last) / torch.linalg.vector_norm(ser_last))
+            rows.append({"n_coarse": nc, "dt_coarse": st.dt_coarse_used, "coarse_steps": st.n_coarse_steps,
+                         "k_con": st.k_con, "converged": bool(st.converged), "ms": ms, "fine_ms": st.ms_fine,
+                         "coarse_ms": st.ms_coarse, "speedup_vs_serial_fine": serial / ms,
+                         "err_vs_serial_fine": err,
+                         "sigma": [float(st.sigma[i]) for i in range(min(st.k_con, W["k_max"]))]})
+        finally:
+            kd.kd_destroy(ctx)
+    print(json.dumps({"config": dict(W, study="n_coarse sweep"), "serial_fine_ms": serial, "rows": rows}),
+          flush=True)
+
+
 # ------------------------------------------------------------- large run (config 5)
 LARGE_WL = {
     "workload": "gp_cp_1024x1024_parareal_256_slices",
@@ -635,9 +699,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal", choices=["parareal", "learned", "sweep", "large", "steppers", "coarse-sweep"],
+    ap.add_argument("--config", default="parareal",
+                    choices=["parareal", "learned", "sweep", "large", "steppers", "coarse-sweep",
+                             "coarse-sweep-roberts"],
                     help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
-                         "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices")
+                         "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices; "
+                         "steppers: RK111 / RK222 / RK443 accuracy per work; coarse-sweep: N_C study on the GP "
+                         "128^2 problem; coarse-sweep-roberts: N_C study at Rm 512, N_F 160")
     ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
     ap.add_argument("--fine-operator", default="fft", choices=["fft", "conv"],
                     help="fft: the pseudo-spectral fine step (the workload's definition); conv: the same operator "
@@ -661,6 +729,9 @@ def main():
         return
     if args.config == "coarse-sweep":
         run_coarse_sweep(args)
+        return
+    if args.config == "coarse-sweep-roberts":
+        run_roberts_coarse_sweep(args)
         return
 
     import numpy as np

@@ -72,12 +72,14 @@ enum { KD_RK443 = 0, KD_RK222 = 1, KD_RK111 = 2 };
 /* Problem and discretisation parameters (Sec. 2, Sec. 4, Table 1). */
 typedef struct {
   int flow;            /* KD_FLOW_*; NONE (u = 0) leaves pure diffusion */
-  int n;               /* fine grid side: 16, 32, 64, 128, 256, 512 or 1024 */
+  int n;               /* fine grid side: 16, 32, 64, 128, 256, 512 or 1024; with
+                          KD_FINE_CONV any even side in [16, 190] (Table 1's N_F = 160) */
   double kz;           /* wavenumber along the invariant direction (the paper's kx for GP) */
   double Rm;           /* magnetic Reynolds number (Eq. 2), > 0 */
   double dt_fine;      /* fine step delta t (upper bound; see kd_parareal_run) */
   int prec_fine;       /* KD_C64 or KD_C128 arithmetic of the fine propagator */
-  int n_coarse;        /* coarse grid side N_C (power of two, 16 <= N_C <= n) */
+  int n_coarse;        /* coarse grid side N_C, 16 <= N_C <= n: a power of two, or an even
+                          side whose dealiased set the cluster solver holds (N_C <= 190) */
   double dt_coarse;    /* coarse step Delta t (upper bound) */
   int prec_coarse;     /* KD_C64 or KD_C128 arithmetic of the classical coarse propagator */
   int coarse_kind;     /* KD_COARSE_CLASSICAL or KD_COARSE_LEARNED (needs kd_learned_init and
@@ -90,7 +92,8 @@ typedef struct {
   int fine_operator;   /* KD_FINE_FFT (pseudo-spectral: FFT, u x b on the grid, FFT) or
                           KD_FINE_CONV: the same discrete operator evaluated as the exact
                           4-mode spectral convolution in a persistent cluster kernel (one
-                          launch for all steps; grids n <= 128; RK443 only) */
+                          launch for all steps; even n <= 190, i.e. at most 127 kept modes
+                          a side; RK443 only) */
   int fine_scheme;     /* KD_RK443 (default), KD_RK222 or KD_RK111 */
 } kd_params;
 

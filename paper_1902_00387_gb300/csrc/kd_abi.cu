@@ -74,8 +74,8 @@ kd_status make_tables(kd_ctx* ctx, Tables& t, int n, int prec) {
     cg[e] = cos(a);
     sg[e] = sin(a);
   }
-  // exact values where the angle is a multiple of pi/2
-  for (int e = 0; e < n; e += n / 4) {
+  // exact values where the angle is a multiple of pi/2 (sides divisible by 4)
+  for (int e = 0; n % 4 == 0 && e < n; e += n / 4) {
     const int q = (e / (n / 4)) & 3;
     const double c = q == 0 ? 1.0 : q == 2 ? -1.0 : 0.0;
     const double s = q == 1 ? 1.0 : q == 3 ? -1.0 : 0.0;
@@ -281,8 +281,12 @@ int steps_for(double dT, double dt) {
 kd_status check_params(const kd_params* p, std::string& why) {
   if (!p) return why = "params is NULL", KD_EINVAL;
   if (p->flow < 0 || p->flow > 2) return why = "flow must be 0, 1 or 2", KD_EINVAL;
-  if (!valid_n(p->n)) return why = "n must be a power of two in [16, 1024]", KD_EINVAL;
-  if (!valid_n(p->n_coarse) || p->n_coarse > p->n) return why = "n_coarse must be a power of two in [16, n]", KD_EINVAL;
+  // grids that are not powers of two are checked in kd_create against the cluster solver
+  if (p->n < 16 || p->n > 1024 || (p->n & 1)) return why = "n must be even and in [16, 1024]", KD_EINVAL;
+  if (p->n_coarse < 16 || p->n_coarse > p->n || (p->n_coarse & 1))
+    return why = "n_coarse must be even and in [16, n]", KD_EINVAL;
+  if (!valid_n(p->n) && p->fine_operator != KD_FINE_CONV)
+    return why = "n must be a power of two in [16, 1024] (other sides need fine_operator KD_FINE_CONV)", KD_EINVAL;
   if (!(p->Rm > 0) || !isfinite(p->Rm)) return why = "Rm must be finite and > 0", KD_EINVAL;
   if (!isfinite(p->kz)) return why = "kz must be finite", KD_EINVAL;
   if (!(p->dt_fine > 0) || !(p->dt_coarse > 0)) return why = "time steps must be > 0", KD_EINVAL;
@@ -296,8 +300,7 @@ kd_status check_params(const kd_params* p, std::string& why) {
     return why = "the learned coarse propagator needs learned_modes > 0 and fine_form KD_FINE_INCREMENT", KD_EINVAL;
   if (p->fine_form != KD_FINE_DIRECT && p->fine_form != KD_FINE_INCREMENT) return why = "bad fine_form", KD_EINVAL;
   if (p->fine_operator != KD_FINE_FFT && p->fine_operator != KD_FINE_CONV) return why = "bad fine_operator", KD_EINVAL;
-  if (p->fine_operator == KD_FINE_CONV && !coarse_conv_supported(2 * (p->n / 3) + 1))
-    return why = "fine_operator KD_FINE_CONV needs n <= 128", KD_EINVAL;
+
   if (p->fine_scheme != KD_RK443 && p->fine_scheme != KD_RK222 && p->fine_scheme != KD_RK111)
     return why = "bad fine_scheme", KD_EINVAL;
   if (p->fine_operator == KD_FINE_CONV && p->fine_scheme != KD_RK443)
@@ -418,9 +421,11 @@ bool use_learned(const kd_ctx* ctx, int i) {
 // persistent cluster launch with arithmetic in the fine precision.
 kd_status conv_fine(kd_ctx* ctx, const double* in, double* out, long batch, int nsteps, double dt, const double* t0) {
   const int n = ctx->p.n, pf = ctx->p.prec_fine;
-  FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, dt, t0);
-  kd_status s = with_phases(ctx, ctx->ws_f, a, nsteps);
+  // the fine workspace only carries the flow-phase table here
+  kd_status s = ensure_ws(ctx, ctx->ws_f, n, pf, 1);
   if (s != KD_OK) return s;
+  FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, dt, t0);
+  if ((s = with_phases(ctx, ctx->ws_f, a, nsteps)) != KD_OK) return s;
   KD_LAUNCH(launch_phases(pf, a, nsteps, ctx->st), "fine phases");
   CoarseArgs c = coarse_args(ctx, nsteps, dt);
   c.Kc = n / 3;
@@ -693,6 +698,19 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
     fprintf(stderr, "kd_create: %s\n", cudaGetErrorString(e));
     delete ctx;
     return KD_ECUDA;
+  }
+  // grid sides the cluster solver must hold (known once its kernels are set up)
+  {
+    std::string bad;
+    if (params->fine_operator == KD_FINE_CONV && !coarse_conv_supported(kept(params->n)))
+      bad = "fine_operator KD_FINE_CONV: the kept set of n does not fit the cluster solver (n <= 192)";
+    else if (!valid_n(params->n_coarse) && !coarse_conv_supported(ctx->cP))
+      bad = "n_coarse that is not a power of two needs a coarse set that fits the cluster solver";
+    if (!bad.empty()) {
+      fprintf(stderr, "kd_create: %s\n", bad.c_str());
+      kd_destroy(ctx);
+      return KD_EINVAL;
+    }
   }
   if ((s = make_tables(ctx, ctx->tab_f, params->n, params->prec_fine)) != KD_OK ||
       (s = make_tables(ctx, ctx->tab_c, params->n_coarse, params->prec_coarse)) != KD_OK ||
@@ -1074,6 +1092,16 @@ kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase,
       th[i] = phase[off + i] * ctx->l_sliceT;
     }
     KD_CUDA(cudaMemcpyAsync(t0, th.data(), cnt * 8, cudaMemcpyHostToDevice, ctx->st), "times");
+    if (conv_op(ctx)) {
+      // the convolution operator on FP64 compact fields
+      if ((s = ensure_conv_tmp(ctx, (size_t)cnt * compact_len(nfine) * 16)) != KD_OK) return s;
+      KD_LAUNCH(learned_to_fine(x + 2L * off * nc, K, P, ctx->conv_tmp, KD_C128, Kf, Pf, cnt, ctx->st), "to fine");
+      if ((s = conv_fine(ctx, (const double*)ctx->conv_tmp, (double*)ctx->conv_tmp, cnt, S, dt, t0)) != KD_OK)
+        return s;
+      KD_LAUNCH(fine_to_learned(ctx->conv_tmp, KD_C128, Kf, Pf, y + 2L * off * nc, K, P, cnt, ctx->st), "to learned");
+      KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+      continue;
+    }
     if ((s = ensure_ws(ctx, ctx->ws_f, nfine, pf, cnt)) != KD_OK) return s;
     KD_LAUNCH(learned_to_fine(x + 2L * off * nc, K, P, ctx->ws_f.X, pf, Kf, Pf, cnt, ctx->st), "to fine");
     FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, nfine, cnt, dt, t0);

@@ -1,6 +1,7 @@
 // Classical coarse propagator G (Sec. 3.2, Sec. 5.2: the same equations on the coarse
 // N_C grid with the coarse step) as one persistent thread-block cluster per field for
-// coarse sets of side <= 88 (coarse grids up to 128),
+// coarse sets of side <= 88 (coarse grids up to 128) with portable clusters, and up to
+// 127 (grids up to 190) with 16-block clusters,
 // fused with the Fourier restriction of the fine input and, in the Parareal sweep,
 // with the FP64 update U_{n+1} = F + (G_new - G_old) and the defect of Eq. 9.
 //
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
 }
 
 // cluster split of a P-row coarse square: CS blocks of H rows (H <= 8 for P <= 64,
-// H <= 11 for P <= 88)
+// H <= 11 for P <= 88; 16 blocks of H <= 8 rows for P <= 127)
 // clusters of more than 8 blocks need the non-portable size opt-in (granted in prepare)
 static int g_max_cluster = 8;
 
@@ -350,29 +351,22 @@ static int modes_per_thread(int P, int req = 0) {
   return 0;
 }
 
-bool coarse_conv_supported(int P) { return P >= 1 && modes_per_thread(P) > 0; }
-
 bool coarse_cluster_fits(int P, int cs) {
   return P >= 1 && cs >= 0 && cs <= g_max_cluster && (cs == 0 || cs <= P) && modes_per_thread(P, cs) > 0;
 }
 
+// smallest cluster larger than the default that holds a P-row square (0: none)
+static int min_fitting_cluster(int P) {
+  for (int cs = 9; cs <= g_max_cluster; ++cs)
+    if (coarse_cluster_fits(P, cs)) return cs;
+  return 0;
+}
+
+// the default shape, or (squares above 88 rows) the smallest larger cluster that holds them
+bool coarse_conv_supported(int P) { return P >= 1 && (modes_per_thread(P) > 0 || min_fitting_cluster(P) > 0); }
+
 template <typename T>
 static cudaError_t prepare_T() {
-  int slots = 0;
-  const int prec = sizeof(T) == 4 ? 0 : 1;
-  int bytes = 0;   // the largest shared-memory need over every supported square and cluster size
-  for (int P = 1; P <= 128; ++P)
-    for (int cs = 0; cs <= 8; ++cs)
-      if (coarse_cluster_fits(P, cs)) {
-        const int b = (int)cluster_smem(prec, P, 512, &slots, cs);
-        if (b > bytes) bytes = b;
-      }
-  cudaError_t e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 1, CCB1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
   // 16-block clusters where the device grants them
   if (cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
           cudaSuccess &&
@@ -382,7 +376,20 @@ static cudaError_t prepare_T() {
           cudaSuccess)
     g_max_cluster = 16;
   cudaGetLastError();
-  return cudaSuccess;
+  int slots = 0;
+  const int prec = sizeof(T) == 4 ? 0 : 1;
+  int bytes = 0;   // the largest shared-memory need over every supported square and cluster size
+  for (int P = 1; P <= 128; ++P)
+    for (int cs = 0; cs <= g_max_cluster; ++cs)
+      if (coarse_cluster_fits(P, cs)) {
+        const int b = (int)cluster_smem(prec, P, 512, &slots, cs);
+        if (b > bytes) bytes = b;
+      }
+  cudaError_t e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(coarse_cluster_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(coarse_cluster_kernel<T, 1, CCB1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t coarse_prepare(int prec) { return prec == 0 ? prepare_T<float>() : prepare_T<double>(); }
@@ -406,7 +413,7 @@ static int auto_cluster(int P, int batch) {
     const int cs = (P + 2) / 3 < 16 ? (P + 2) / 3 : 16;
     if (cs > 8 && coarse_cluster_fits(P, cs)) return cs;
   }
-  return 0;
+  return modes_per_thread(P) > 0 ? 0 : min_fitting_cluster(P);
 }
 
 template <typename T>

@@ -37,7 +37,7 @@ struct CoarseArgs {
   int cluster;          // thread blocks per cluster (0: the default for Pc)
 };
 
-bool coarse_conv_supported(int P);   // coarse set side P <= 88
+bool coarse_conv_supported(int P);   // coarse set side P <= 88 (P <= 127 with 16-block clusters)
 // whether a cluster of `cs` blocks can hold a P-row square (cs = 0: the default)
 bool coarse_cluster_fits(int P, int cs);
 cudaError_t coarse_prepare(int prec);

@@ -140,6 +140,10 @@ bool use_learned(const kd_ctx* ctx, int i);
 kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter);
 kd_status copy_in_b0(kd_ctx* ctx, const double* b0);
 kd_status ensure_full_tmp(kd_ctx* ctx, size_t bytes);
+// the convolution-form fine operator (fine_operator KD_FINE_CONV) on FP64 compact fields
+bool conv_op(const kd_ctx* ctx);
+kd_status ensure_conv_tmp(kd_ctx* ctx, size_t bytes);
+kd_status conv_fine(kd_ctx* ctx, const double* in, double* out, long batch, int nsteps, double dt, const double* t0);
 // fine steps on grid g (0 fine, 1 coarse) with the context's plan for that grid
 int run_fine(kd_ctx* ctx, int g, int prec, const kd::FineArgs& a, int nsteps, bool prologue, bool store_last,
              const kd::LaunchProbe* probe = nullptr, const int* active = nullptr);

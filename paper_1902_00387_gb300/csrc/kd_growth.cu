@@ -79,32 +79,41 @@ extern "C" kd_status kd_growth_power(kd_ctx* ctx, const double* b0, double t0, d
   if (!b0 || !rate) return fail(ctx, KD_EINVAL, "kd_growth_power: NULL buffer");
   if (!(tau > 0) || !isfinite(tau) || !isfinite(t0)) return fail(ctx, KD_EINVAL, "kd_growth_power: tau must be > 0");
   if (max_iter < 1 || !(tol >= 0)) return fail(ctx, KD_EINVAL, "kd_growth_power: max_iter >= 1, tol >= 0");
-  const int n = ctx->p.n, pf = ctx->p.prec_fine;
+  const int n = ctx->p.n;
+  const bool conv = conv_op(ctx);
+  // the vector: fine-precision compact state of the FFT operator, FP64 for the convolution one
+  const int pf = conv ? KD_C128 : ctx->p.prec_fine;
   const long len = compact_len(n);
   const int S = steps_for(tau, ctx->p.dt_fine);
   const double dt = tau / S;
   kd_status s;
-  if ((s = ensure_ws(ctx, ctx->ws_f, n, pf, 1)) != KD_OK) return s;
+  if ((s = ensure_ws(ctx, ctx->ws_f, n, ctx->p.prec_fine, 1)) != KD_OK) return s;
   if ((s = ensure_full_tmp(ctx, 3UL * n * n * 16)) != KD_OK) return s;
+  if (conv && (s = ensure_conv_tmp(ctx, (size_t)len * 16)) != KD_OK) return s;
+  void* X = conv ? ctx->conv_tmp : ctx->ws_f.X;
   KD_CUDA(cudaMemcpyAsync(ctx->full_tmp, b0, 3UL * n * n * 16, cudaMemcpyDefault, ctx->st), "copy b0");
-  KD_LAUNCH(full_to_compact(KD_C128, ctx->full_tmp, pf, ctx->ws_f.X, 1, n, ctx->st), "pack");
+  KD_LAUNCH(full_to_compact(KD_C128, ctx->full_tmp, pf, X, 1, n, ctx->st), "pack");
   // scal[8] = |b|^2, scal[9] = |M b|^2; partials in ctx->partials; t0 of the field in scal[10]
   double* n0 = ctx->scal + 8;
   double* n1 = ctx->scal + 9;
   double* tdev = ctx->scal + 10;
   KD_CUDA(cudaMemcpyAsync(tdev, &t0, 8, cudaMemcpyHostToDevice, ctx->st), "t0");
-  KD_LAUNCH(norm2(pf, ctx->ws_f.X, len, ctx->partials, n0, ctx->st), "norm");
-  KD_LAUNCH(normalise(pf, ctx->ws_f.X, len, n0, ctx->st), "normalise");
+  KD_LAUNCH(norm2(pf, X, len, ctx->partials, n0, ctx->st), "norm");
+  KD_LAUNCH(normalise(pf, X, len, n0, ctx->st), "normalise");
   FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, 1, dt, tdev);
   if ((s = with_phases(ctx, ctx->ws_f, a, S)) != KD_OK) return s;
   double prev = NAN, cur = NAN;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
-    KD_LAUNCH(norm2(pf, ctx->ws_f.X, len, ctx->partials, n0, ctx->st), "norm");
-    KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false), "fine steps");
-    KD_LAUNCH(norm2(pf, ctx->ws_f.X, len, ctx->partials, n1, ctx->st), "norm");
+    KD_LAUNCH(norm2(pf, X, len, ctx->partials, n0, ctx->st), "norm");
+    if (conv) {
+      if ((s = conv_fine(ctx, (const double*)X, (double*)X, 1, S, dt, tdev)) != KD_OK) return s;
+    } else {
+      KD_LAUNCH(run_fine(ctx, 0, pf, a, S, true, false), "fine steps");
+    }
+    KD_LAUNCH(norm2(pf, X, len, ctx->partials, n1, ctx->st), "norm");
     KD_CUDA(cudaMemcpyAsync(ctx->host_scal, n0, 16, cudaMemcpyDeviceToHost, ctx->st), "norm copy");
-    KD_LAUNCH(normalise(pf, ctx->ws_f.X, len, n1, ctx->st), "normalise");
+    KD_LAUNCH(normalise(pf, X, len, n1, ctx->st), "normalise");
     KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
     const double a0 = ctx->host_scal[0], a1 = ctx->host_scal[1];
     if (!(a0 > 0) || !(a1 > 0) || !isfinite(a0) || !isfinite(a1))
@@ -117,7 +126,7 @@ extern "C" kd_status kd_growth_power(kd_ctx* ctx, const double* b0, double t0, d
   *rate = cur;
   if (iters) *iters = it;
   if (b_out) {
-    KD_LAUNCH(compact_to_full(pf, ctx->ws_f.X, KD_C128, ctx->full_tmp, 1, n, ctx->st), "unpack");
+    KD_LAUNCH(compact_to_full(pf, X, KD_C128, ctx->full_tmp, 1, n, ctx->st), "unpack");
     KD_CUDA(cudaMemcpyAsync(b_out, ctx->full_tmp, 3UL * n * n * 16, cudaMemcpyDefault, ctx->st), "copy out");
     KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   }

@@ -28,7 +28,8 @@ __global__ void k_full_to_compact(const cx<Ti>* full, cx<To>* comp, long total, 
     const long bc = i / ((long)P * P);
     const int r = (int)(i - bc * P * P);
     const int iy = r / P, ix = r - iy * P;
-    const int y = (iy - K) & (n - 1), x = (ix - K) & (n - 1);
+    // FFT order: wavenumber k < 0 sits at index k + n (any even n)
+    const int y = iy >= K ? iy - K : iy - K + n, x = ix >= K ? ix - K : ix - K + n;
     comp[i] = from_d<To>(to_d(full[(bc * n + y) * n + x]));
   }
 }

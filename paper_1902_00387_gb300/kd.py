@@ -144,7 +144,7 @@ def make_params(flow, n, kz, Rm, dt_fine, prec_fine=KD_C64, n_coarse=None, dt_co
                 prec_coarse=None, coarse_kind=KD_COARSE_CLASSICAL, fine_form=KD_FINE_DIRECT, learned_modes=0,
                 fine_operator=KD_FINE_FFT, fine_scheme=KD_RK443):
     return kd_params(int(flow), int(n), float(kz), float(Rm), float(dt_fine), int(prec_fine),
-                     int(n_coarse if n_coarse else max(16, n // 2)),
+                     int(n_coarse if n_coarse else max(16, n // 4 * 2)),   # even, about n / 2
                      float(dt_coarse if dt_coarse else dt_fine), int(prec_fine if prec_coarse is None else prec_coarse),
                      int(coarse_kind), int(learned_modes), int(fine_form), int(fine_operator), int(fine_scheme))
 

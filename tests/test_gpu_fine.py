@@ -250,12 +250,14 @@ def test_coarse_propagator_matches_oracle(kd):
         assert rel(out[i], ref) < 1e-13
 
 
-@pytest.mark.parametrize("n", [32, 64, 128])
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 160, 190])
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_convolution_fine_operator_matches_oracle(kd, n, prec):
     """KD_FINE_CONV: the explicit term as the exact spectral convolution in one persistent
     launch; the same discrete operator as the FFT route (oracle pin: both routes agree to
-    1e-13), so parity with the oracle at the precision's tolerance."""
+    1e-13), so parity with the oracle at the precision's tolerance.  Sides that are not
+    powers of two (96, Table 1's 160, the largest 190 with 127 kept modes a side) take
+    16-block clusters."""
     import torch
     P = kd.KD_C64 if prec == "c64" else kd.KD_C128
     kz, Rm, dt = 0.57, 100.0, 5e-3
@@ -276,9 +278,38 @@ def test_convolution_fine_operator_matches_oracle(kd, n, prec):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 4)) < (TOL32 if P == kd.KD_C64 else 1e-12)
 
 
-def test_convolution_fine_operator_rejected_above_128(kd):
+@pytest.mark.parametrize("n,op", [(256, "conv"), (192, "conv"), (96, "fft"), (160, "fft"), (97, "conv"),
+                                  (14, "conv")])
+def test_unsupported_grid_sides_rejected(kd, n, op):
+    """The convolution operator holds at most 127 kept modes a side (n <= 190); the FFT
+    operator needs a power of two; every side is even and >= 16."""
+    f = kd.KD_FINE_CONV if op == "conv" else kd.KD_FINE_FFT
     with pytest.raises(kd.KdError):
-        kd.kd_create(kd.make_params(O.ROBERTS, 256, 1.0, 8.0, 1e-2, kd.KD_C64, fine_operator=kd.KD_FINE_CONV))
+        kd.kd_create(kd.make_params(O.ROBERTS, n, 1.0, 8.0, 1e-2, kd.KD_C64, n_coarse=16, fine_operator=f))
+
+
+@pytest.mark.parametrize("n,nc", [(160, 80), (96, 48), (128, 80)])
+def test_coarse_propagator_on_uneven_coarse_grid(kd, n, nc):
+    """The classical G on a coarse grid that is not a power of two (Table 1: N_F = 160,
+    N_C = 80) against the oracle's coarse propagator, FP64."""
+    import torch
+    kz, Rm, dtc = 2.87, 512.0, 2e-2
+    op = kd.KD_FINE_FFT if n == 128 else kd.KD_FINE_CONV
+    b = I.initial_batch(n, kz, [71, 72])
+    ctx = kd.kd_create(kd.make_params(O.ROBERTS, n, kz, Rm, 1e-2, kd.KD_C128, n_coarse=nc, dt_coarse=dtc,
+                                      prec_coarse=kd.KD_C128, fine_operator=op))
+    try:
+        x = torch.tensor(b, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        t0 = torch.tensor([0.0, 0.4], dtype=torch.float64, device="cuda")
+        kd.kd_coarse(ctx, x, y, t0, 7, 2)
+        torch.cuda.synchronize()
+        out = y.cpu().numpy()
+    finally:
+        kd.kd_destroy(ctx)
+    prob = O.Problem(O.ROBERTS, n, kz, Rm)
+    for i, t in enumerate((0.0, 0.4)):
+        assert rel(out[i], O.coarse_propagate(b[i], prob, nc, t, dtc, 7)) < 1e-12, i
 
 
 @pytest.mark.parametrize("scheme", ["RK222", "RK111"])

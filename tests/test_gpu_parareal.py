@@ -218,6 +218,31 @@ def test_parareal_with_convolution_fine_operator(kd):
     assert np.linalg.norm(outs[1][-1] - outs[0][-1]) / np.linalg.norm(outs[0][-1]) < 2e-5
 
 
+def test_parareal_table1_roberts_grids_match_oracle(kd):
+    """Parareal on Table 1's Roberts grids (N_F = 160, N_C = 80, delta t = 1e-2,
+    Delta t = 2e-2; neither side a power of two), FP64 on both sides, iterates equal to
+    the oracle's Parareal."""
+    n, nc, kz, Rm, T, N, kmax = 160, 80, 2.87, 512.0, 0.8, 4, 2
+    b0 = I.initial_field(n, kz, 23)
+    p = kd.make_params(O.ROBERTS, n, kz, Rm, 1e-2, kd.KD_C128, n_coarse=nc, dt_coarse=2e-2,
+                       prec_coarse=kd.KD_C128, fine_operator=kd.KD_FINE_CONV)
+    ctx = kd.kd_create(p)
+    try:
+        out = np.zeros((N + 1, 3, n, n), np.complex128)
+        status, st = kd.kd_parareal_run(ctx, b0, T, N, kmax, 0.0, out)
+    finally:
+        kd.kd_destroy(ctx)
+    assert status == kd.KD_ENOTCONV and st.k_con == kmax
+    prob = O.Problem(O.ROBERTS, n, kz, Rm)
+    fine, coarse, S, Sc = oracle_ops(prob, nc, T, N, 1e-2, 2e-2)
+    assert (st.n_fine_steps, st.n_coarse_steps) == (S, Sc) == (20, 10)
+    ref = O.parareal(b0, fine, coarse, N, kmax, 0.0)
+    for i in range(N + 1):
+        assert rel(out[i], ref["U"][i]) < 1e-11, i
+    for k in range(kmax):
+        assert abs(st.sigma[k] - ref["sigma"][k]) <= 1e-8 * ref["sigma"][k]
+
+
 @pytest.mark.parametrize("form", ["direct", "increment"])
 @pytest.mark.parametrize("chunks", [1, 3, 16])
 def test_pipelined_iterations_equal_unpipelined(kd, form, chunks):
