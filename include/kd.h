@@ -161,6 +161,20 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices,
  * barriers and more work per block.  KD_EINVAL if the coarse set does not fit. */
 kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks);
 
+/* How the blocks of a coarse-solver cluster exchange the halo rows after each of the
+ * 4 stages of an RK443 step (the classical G, Sec. 3.2 / 5.2, and the KD_FINE_CONV
+ * operator).  KD_SYNC_CLUSTER (default): the first and last rows are stored into the
+ * neighbours' halo rows through distributed shared memory, then a cluster-wide barrier.
+ * KD_SYNC_P2P: each block pushes those rows with st.async, counted on the receiver's
+ * mbarrier, and waits only for its own halos (bounded wait; a halo that never arrives
+ * makes the outputs NaN, which the callers report as KD_ENONFINITE).  KD_SYNC_PULL: no
+ * halo copies; the cluster barrier is split (arrive after a stage's stores, wait before
+ * the first and last rows of the next stage, the rows between computed meanwhile) and the
+ * neighbours' rows are read in place.  All give identical results bit for bit.  KD_EINVAL
+ * for another mode. */
+enum { KD_SYNC_CLUSTER = 0, KD_SYNC_P2P = 1, KD_SYNC_PULL = 2 };
+kd_status kd_set_coarse_sync(kd_ctx* ctx, int mode);
+
 /* Pipelined iterations of kd_parareal_run (default chunks = 0: off): the parallel step of
  * iteration k + 1 runs in `chunks` slice chunks on a low-priority stream and overlaps the
  * serial sweep of iteration k, which runs on a high-priority stream; chunk j starts once

@@ -340,6 +340,7 @@ CoarseArgs coarse_args(const kd_ctx* ctx, int steps, double dtc) {
   c.dt = dtc;
   c.nsteps = steps;
   c.cluster = ctx->coarse_cluster;
+  c.halo = ctx->coarse_sync == KD_SYNC_P2P ? 1 : ctx->coarse_sync == KD_SYNC_PULL ? 2 : 0;
   return c;
 }
 

@@ -35,12 +35,19 @@ struct CoarseArgs {
   const int* steps;
   const int* map;
   int cluster;          // thread blocks per cluster (0: the default for Pc)
+  int halo;             // halo exchange per stage: 0 halo stores + cluster barrier; 1 point-to-
+                        // point (st.async counted on the receiver's mbarrier); 2 pull (the
+                        // neighbours' rows read in place after a split cluster barrier)
 };
 
 bool coarse_conv_supported(int P);   // coarse set side P <= 88 (P <= 127 with 16-block clusters)
 // whether a cluster of `cs` blocks can hold a P-row square (cs = 0: the default)
 bool coarse_cluster_fits(int P, int cs);
 cudaError_t coarse_prepare(int prec);
+// the kernels of the alternative halo exchanges (CoarseArgs::halo 1, 2; kd_coarse_alt.cu)
+cudaError_t coarse_alt_allow_nonportable(int prec);
+cudaError_t coarse_alt_set_smem(int prec, int bytes);
+cudaError_t coarse_alt_launch(int prec, const cudaLaunchConfig_t& cfg, int mpt, const CoarseArgs& a, int CS, int H);
 // One thread-block cluster per field; returns 1 (kernels launched) or -1 if unsupported.
 int coarse_conv_launch(int prec, const CoarseArgs& a, int batch, cudaStream_t st);
 

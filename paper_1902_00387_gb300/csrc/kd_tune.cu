@@ -201,6 +201,14 @@ kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks) {
   return KD_OK;
 }
 
+kd_status kd_set_coarse_sync(kd_ctx* ctx, int mode) {
+  if (!ctx) return KD_EINVAL;
+  if (mode != KD_SYNC_CLUSTER && mode != KD_SYNC_P2P && mode != KD_SYNC_PULL)
+    return fail(ctx, KD_EINVAL, "kd_set_coarse_sync: mode must be KD_SYNC_CLUSTER, KD_SYNC_P2P or KD_SYNC_PULL");
+  ctx->coarse_sync = mode;
+  return KD_OK;
+}
+
 kd_status kd_set_overlap(kd_ctx* ctx, int chunks) {
   if (!ctx) return KD_EINVAL;
   if (chunks < 0 || chunks > kMaxChunks) return fail(ctx, KD_EINVAL, "kd_set_overlap: chunks must be in [0, 16]");

@@ -23,6 +23,7 @@ KD_COARSE_CLASSICAL, KD_COARSE_LEARNED = 0, 1
 KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
 KD_FINE_FFT, KD_FINE_CONV = 0, 1
 KD_RK443, KD_RK222, KD_RK111 = 0, 1, 2
+KD_SYNC_CLUSTER, KD_SYNC_P2P, KD_SYNC_PULL = 0, 1, 2
 KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
 KD_GRID_FINE, KD_GRID_COARSE = 0, 1
 KD_MAX_SLICES = 1024
@@ -78,7 +79,8 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
-           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_set_overlap", "kd_set_coarse_cluster"]
+           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -112,6 +114,7 @@ def load():
         "kd_set_dependent_launch": (I, [P, I]),
         "kd_set_overlap": (I, [P, I]),
         "kd_set_coarse_cluster": (I, [P, I]),
+        "kd_set_coarse_sync": (I, [P, I]),
         "kd_get_plan": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "kd_autotune": (I, [P, I, I, I, ctypes.c_char_p, ctypes.POINTER(D)]),
         "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
@@ -332,6 +335,11 @@ def kd_set_plan(ctx, grid, col, row):
 
 def kd_set_coarse_cluster(ctx, blocks):
     return _check(ctx, load().kd_set_coarse_cluster(ctx, int(blocks)))
+
+
+def kd_set_coarse_sync(ctx, mode):
+    """KD_SYNC_CLUSTER (default), KD_SYNC_P2P or KD_SYNC_PULL halo exchange of the coarse solver."""
+    return _check(ctx, load().kd_set_coarse_sync(ctx, int(mode)))
 
 
 def kd_set_overlap(ctx, chunks):

@@ -10,6 +10,11 @@ prints the device time of the second call.
 
 runs one Parareal solve of the GP 128^2, 64-slice workload of bench.py (plan
 autotuned first), for a launch list of a whole solve.
+
+    python -m paper_1902_00387_gb300.profile_case --coarse --n 128 --n-coarse 128 --steps 51 [--cluster 16] [--sync 0|1]
+
+runs the classical coarse propagator (one thread-block cluster, kd_coarse) on one field
+twice and prints the device time per RK443 stage of the second call.
 """
 import argparse
 import os
@@ -30,6 +35,10 @@ def main():
     ap.add_argument("--dt", type=float, default=5e-3)
     ap.add_argument("--plan", default=None, help="column,row variant of the fine kernels")
     ap.add_argument("--parareal", action="store_true")
+    ap.add_argument("--coarse", action="store_true")
+    ap.add_argument("--n-coarse", type=int, default=128)
+    ap.add_argument("--cluster", type=int, default=0, help="blocks per cluster of the coarse solver (0: default)")
+    ap.add_argument("--sync", type=int, default=0, help="coarse halo exchange: 0 cluster barrier, 1 point-to-point")
     args = ap.parse_args()
     import torch
 
@@ -57,6 +66,28 @@ def main():
         torch.cuda.synchronize()
         print("parareal GP 128^2 x 64 slices: %.1f ms, k_con %d, plan %s" % (e0.elapsed_time(e1), st.k_con,
                                                                             kd.kd_get_plan(ctx)))
+        kd.kd_destroy(ctx)
+        return
+    if args.coarse:
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64,
+                           n_coarse=args.n_coarse, dt_coarse=2.0 / args.n_coarse, prec_coarse=kd.KD_C64)
+        ctx = kd.kd_create(p)
+        if args.cluster:
+            kd.kd_set_coarse_cluster(ctx, args.cluster)
+        kd.kd_set_coarse_sync(ctx, args.sync)
+        x = torch.tensor(kd_inputs.initial_batch(args.n, args.kz, [7]), dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        t0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        kd.kd_coarse(ctx, x, y, t0, args.steps, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        kd.kd_coarse(ctx, x, y, t0, args.steps, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        print("coarse N_C=%d steps=%d cluster=%d sync=%d: %.3f ms, %.3f us per stage" % (
+            args.n_coarse, args.steps, args.cluster, args.sync, e0.elapsed_time(e1),
+            e0.elapsed_time(e1) * 1000 / (4 * args.steps)))
         kd.kd_destroy(ctx)
         return
     p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64)
