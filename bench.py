@@ -669,6 +669,13 @@ def run_sweep(args):
 # (fused multiply-add) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# DRAM traffic of the dominant kernel at the headline workload: dram__bytes_read.sum +
+# dram__bytes_write.sum of row2_kernel<float, 128, 8, 0, 0> (row variant 3, the plan the
+# autotuner picks), averaged over the 4 stage launches of one fine step of 64 fields, L2
+# left warm as in the solve (profiles/fine_row2_traffic_gp128_b64.md).  Reported only
+# when the bench runs that kernel.
+ROW_TRAFFIC = {"n": 128, "batch": 64, "row_variant": 3, "bytes_per_launch": 26471552}
+
 
 def conv_roofline(n, S, batches, steps, stats):
     """ALU roofline of the convolution-form fine propagator: ~180 flops per kept mode and
@@ -876,7 +883,11 @@ def main():
         "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
         "roofline": ({"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
                       "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                      "traffic": None, "peak_kind": peak_kind,
+                      "traffic": (ROW_TRAFFIC["bytes_per_launch"]
+                                  if kid == 1 and n == ROW_TRAFFIC["n"] and N == ROW_TRAFFIC["batch"]
+                                  and plan[1] == ROW_TRAFFIC["row_variant"] else None),
+                      "traffic_unit": "bytes per launch (ncu, L2 warm)",
+                      "algorithmic_bytes_per_launch": kbytes / max(1, prof_n[kid]), "peak_kind": peak_kind,
                       "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]}
                      if args.fine_operator == "fft" else conv_roofline(n, S, batches, args.steps, stats)),
         "clocks": clk,
