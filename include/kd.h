@@ -309,6 +309,39 @@ kd_status kd_fine_batched_static(const kd_params* params, const void* b_in, void
 kd_status kd_growth_power(kd_ctx* ctx, const double* b0, double t0, double tau, int max_iter, double tol,
                           double* rate, int* iters, double* b_out);
 
+/* Leading eigenvalues of the fine propagator M over [t0, t0 + tau] by restarted Arnoldi
+ * (Sec. 1: the growth rate is Re lambda of the leading eigenvalue for a steady flow,
+ * ln|mu| / period of the leading Floquet multiplier for a time-periodic one).  Unlike the
+ * power iteration it converges for a small gap between the leading |mu| and finds complex
+ * multipliers (oscillating modes).  A Krylov space of dimension m is built from b0
+ * (complex128 [3][n][n], host or device; its dealiased part) with FP64 basis vectors and
+ * Gram-Schmidt done twice; the Ritz values of largest modulus are accepted when the
+ * relative residual |H[m][m-1]| |y[m-1]| / |theta| of each of the nev leading ones is
+ * <= tol; otherwise the run restarts from the sum of their Ritz vectors, at most
+ * `restarts` times.  M is ceil(tau / dt_fine) fine steps of the context's operator and
+ * precision.
+ *   mu    : out, double[nev][2], the multipliers (re, im) by decreasing modulus; for a
+ *           steady flow lambda = log(mu) / tau (principal branch: take tau with
+ *           |Im lambda| tau < pi)
+ *   rate  : out (may be NULL), double[nev], ln|mu| / tau
+ *   iters : out (may be NULL), restarts used
+ *   b_out : out (may be NULL), complex128 [3][n][n], the leading Ritz vector (unit norm)
+ * 2 <= m <= KD_ARNOLDI_MAX_M, 1 <= nev < m, restarts >= 1, tol >= 0, else KD_EINVAL.
+ * Synchronous; allocates (m + 1) compact FP64 fields for the call.  KD_ENOTCONV if tol
+ * was not reached (outputs hold the last estimates), KD_ENONFINITE on a zero or
+ * non-finite vector. */
+#define KD_ARNOLDI_MAX_M 64
+kd_status kd_growth_arnoldi(kd_ctx* ctx, const double* b0, double t0, double tau, int m, int nev, int restarts,
+                            double tol, double* mu, double* rate, int* iters, double* b_out);
+
+/* The host routine that kd_growth_arnoldi uses for its small dense eigenproblem, exposed
+ * for checking: eigenvalues of an m x m complex upper Hessenberg matrix h (row-major,
+ * interleaved re / im; entries below the subdiagonal must be zero) by the shifted QR
+ * algorithm, into eig[m][2] in the order of the Schur form's diagonal; vec (may be NULL):
+ * the unit eigenvectors as columns of an m x m complex matrix (row-major, interleaved).
+ * No GPU involved.  KD_EINVAL for bad arguments, KD_ENOTCONV if QR did not converge. */
+kd_status kd_hessenberg_eig(int m, const double* h, double* eig, double* vec);
+
 /* ------------------------------------------------------------------------------------
  * Slice blocks for Parareal over several ranks (the paper's time communicator, Sec. 4.1
  * Algorithms 1-3): rank r owns the contiguous slices [lo, lo + n_local) of n_slices.  The

@@ -79,7 +79,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
-           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_set_overlap", "kd_set_coarse_cluster",
            "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
@@ -121,6 +121,8 @@ def load():
                              ctypes.POINTER(P), ctypes.POINTER(kd_instance_result), ctypes.POINTER(kd_sweep_stats),
                              P, ctypes.c_char_p]),
         "kd_growth_power": (I, [P, P, D, D, I, D, ctypes.POINTER(D), ctypes.POINTER(I), P]),
+        "kd_growth_arnoldi": (I, [P, P, D, D, I, I, I, D, P, P, ctypes.POINTER(I), P]),
+        "kd_hessenberg_eig": (I, [I, P, P, P]),
         "kd_block_init": (I, [P, I, I, D, I]),
         "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
         "kd_block_set_initial": (I, [P, P]),
@@ -399,6 +401,33 @@ def kd_growth_power(ctx, b0, t0, tau, max_iter, tol, b_out=None):
                                ctypes.byref(rate), ctypes.byref(its), _any_ptr(b_out, "complex128"))
     _check(ctx, s, allow=(KD_ENOTCONV,))
     return s, rate.value, its.value
+
+
+def kd_growth_arnoldi(ctx, b0, t0, tau, m, nev, restarts, tol, b_out=None):
+    """Restarted Arnoldi on the fine propagator over [t0, t0 + tau]; returns (status,
+    multipliers (complex numpy array [nev], by decreasing modulus), rates ln|mu| / tau,
+    restarts used)."""
+    mu = np.zeros(2 * int(nev), np.float64)
+    rate = np.zeros(int(nev), np.float64)
+    its = ctypes.c_int()
+    s = load().kd_growth_arnoldi(ctx, _any_ptr(b0, "complex128"), float(t0), float(tau), int(m), int(nev),
+                                 int(restarts), float(tol), mu.ctypes.data, rate.ctypes.data, ctypes.byref(its),
+                                 _any_ptr(b_out, "complex128"))
+    _check(ctx, s, allow=(KD_ENOTCONV,))
+    return s, mu[0::2] + 1j * mu[1::2], rate, its.value
+
+
+def kd_hessenberg_eig(h, vectors=False):
+    """Eigenvalues (and unit eigenvectors as columns) of a complex upper Hessenberg matrix
+    by the library's host QR routine (no GPU)."""
+    h = np.ascontiguousarray(h, dtype=np.complex128)
+    m = h.shape[0]
+    eig = np.zeros(m, np.complex128)
+    vec = np.zeros((m, m), np.complex128) if vectors else None
+    s = load().kd_hessenberg_eig(m, h.ctypes.data, eig.ctypes.data, vec.ctypes.data if vectors else None)
+    if s != KD_OK:
+        raise KdError(s, "kd_hessenberg_eig failed")
+    return (eig, vec) if vectors else eig
 
 
 def kd_block_init(ctx, lo, n_local, T, n_slices):
