@@ -334,6 +334,22 @@ kd_status kd_growth_power(kd_ctx* ctx, const double* b0, double t0, double tau, 
 kd_status kd_growth_arnoldi(kd_ctx* ctx, const double* b0, double t0, double tau, int m, int nev, int restarts,
                             double tol, double* mu, double* rate, int* iters, double* b_out);
 
+/* The BF16 GEMM of the learned operator's training (Sec. 3.2's learned G; the forward
+ * product W X and the gradient product (W X - Y) X^T): C[M][N] = A[M][K] Bt[N][K]^T with
+ * A and Bt row-major BF16 (K innermost, K a multiple of 8, base addresses 16-byte
+ * aligned), C row-major FP32 with row
+ * stride ldc >= N; all device pointers.  KD_GEMM_TCGEN05 (default for training): 5th-
+ * generation tensor cores, tcgen05.mma into a tensor-memory accumulator, 128 x 128 tiles;
+ * KD_GEMM_MMA_SYNC: the warp-level mma.sync kernel.  Synchronous on cuda_stream (NULL =
+ * legacy default stream).  KD_EINVAL for bad arguments, KD_ECUDA on a launch failure or a
+ * bounded wait inside the kernel that ran out. */
+enum { KD_GEMM_TCGEN05 = 0, KD_GEMM_MMA_SYNC = 1 };
+kd_status kd_gemm_bf16_tn(const void* A, const void* Bt, float* C, int M, int N, int K, int ldc, int engine,
+                          void* cuda_stream);
+
+/* Engine of the GEMMs in kd_learned_train / kd_learned_loss_grad (default KD_GEMM_TCGEN05). */
+kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine);
+
 /* The host routine that kd_growth_arnoldi uses for its small dense eigenproblem, exposed
  * for checking: eigenvalues of an m x m complex upper Hessenberg matrix h (row-major,
  * interleaved re / im; entries below the subdiagonal must be zero) by the shifted QR

@@ -1121,6 +1121,7 @@ namespace {
 struct TrainBufs {
   float *xp = nullptr, *yp = nullptr, *yT = nullptr, *C1 = nullptr, *C2 = nullptr;
   __nv_bfloat16 *Xs = nullptr, *XtT = nullptr, *A2 = nullptr, *Wbf = nullptr;
+  int* err = nullptr;   // set by the tensor-core GEMM if one of its bounded waits ran out
 };
 
 kd_status train_bufs(kd_ctx* ctx, TrainBufs& b, int mp, int nc) {
@@ -1137,11 +1138,28 @@ kd_status train_bufs(kd_ctx* ctx, TrainBufs& b, int mp, int nc) {
   if ((s = dalloc(ctx, (void**)&b.XtT, m2 * nc * 2, "x^T operand")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&b.A2, 2 * (size_t)nc * m2 * 2, "residual operand")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&b.Wbf, 2 * (size_t)nc * ld * 2, "bf16 weights")) != KD_OK) return s;
+  if ((s = dalloc(ctx, (void**)&b.err, 16, "gemm status")) != KD_OK) return s;
+  KD_CUDA(cudaMemsetAsync(b.err, 0, 16, ctx->st), "memset");
   return KD_OK;
 }
 
+// C = A Bt^T on the engine the context selects (kd_set_learned_gemm)
+int train_gemm(const kd_ctx* ctx, const TrainBufs& b, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
+               int M, int N, int K, int ldc) {
+  return ctx->gemm_engine == KD_GEMM_MMA_SYNC ? gemm_bf16_tn(A, Bt, C, M, N, K, ldc, ctx->st)
+                                              : gemm_bf16_tn_tc(A, Bt, C, M, N, K, ldc, b.err, ctx->st);
+}
+
+// KD_ECUDA if a tensor-core GEMM of this training reported a timed-out wait
+kd_status check_gemm(kd_ctx* ctx, const TrainBufs& b) {
+  int e = 0;
+  KD_CUDA(cudaMemcpyAsync(&e, b.err, 4, cudaMemcpyDeviceToHost, ctx->st), "gemm status");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  return e ? fail(ctx, KD_ECUDA, "tensor-core GEMM: a bounded wait ran out") : KD_OK;
+}
+
 void free_train_bufs(kd_ctx* ctx, TrainBufs& b) {
-  void* all[] = {b.xp, b.yp, b.yT, b.C1, b.C2, b.Xs, b.XtT, b.A2, b.Wbf};
+  void* all[] = {b.xp, b.yp, b.yT, b.C1, b.C2, b.Xs, b.XtT, b.A2, b.Wbf, b.err};
   for (void* p : all) dfree(ctx, p);
   b = TrainBufs();
 }
@@ -1168,12 +1186,12 @@ kd_status load_pairs(kd_ctx* ctx, TrainBufs& b, const float* x, const float* y, 
 // forward GEMM, residual (loss sum -> out[0]) and gradient GEMM (-> b.C2) for W in b.Wbf
 kd_status forward_backward(kd_ctx* ctx, TrainBufs& b, int mp, int nc, double* loss_dev) {
   const int ld = (nc + 7) & ~7;
-  KD_LAUNCH(gemm_bf16_tn(b.Wbf, b.Xs, b.C1, 2 * nc, 2 * mp, ld, 2 * mp, ctx->st), "forward gemm");
+  KD_LAUNCH(train_gemm(ctx, b, b.Wbf, b.Xs, b.C1, 2 * nc, 2 * mp, ld, 2 * mp), "forward gemm");
   const int nb = learned_residual(b.C1, b.yT, mp, nc, b.A2, ctx->partials, ctx->st);
   if (nb < 0) return fail(ctx, KD_ECUDA, "residual launch failed");
   ctx->launches += 1;
   KD_LAUNCH(sum_partials(ctx->partials, nb, loss_dev, ctx->st), "loss");
-  KD_LAUNCH(gemm_bf16_tn(b.A2, b.XtT, b.C2, 2 * nc, nc, 2 * mp, ld, ctx->st), "gradient gemm");
+  KD_LAUNCH(train_gemm(ctx, b, b.A2, b.XtT, b.C2, 2 * nc, nc, 2 * mp, ld), "gradient gemm");
   return KD_OK;
 }
 
@@ -1252,6 +1270,7 @@ kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const in
         loss_out[(size_t)p * epochs + e] = byp[p].empty() ? 0.0 : h[2 * ((size_t)p * epochs + e)] / byp[p].size();
   }
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  if ((s = check_gemm(ctx, b)) != KD_OK) return s;
   free_train_bufs(ctx, b);
   dfree(ctx, Wm);
   dfree(ctx, m1);
@@ -1295,6 +1314,7 @@ kd_status kd_learned_loss_grad(kd_ctx* ctx, const float* W, const float* W0, flo
   KD_CUDA(cudaMemcpyAsync(h, ctx->scal + 8, 32, cudaMemcpyDeviceToHost, ctx->st), "loss");
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   *loss_out = h[0] / n + weight_decay * h[2];
+  if ((s = check_gemm(ctx, b)) != KD_OK) return s;
   free_train_bufs(ctx, b);
   dfree(ctx, Wp);
   dfree(ctx, W0p);

@@ -45,6 +45,7 @@ struct kd_ctx {
   // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)
   int overlap = 0;
   int coarse_cluster = 0;          // blocks per cluster of the coarse solver (0: default)
+  int gemm_engine = 0;             // learned-operator training GEMM: KD_GEMM_TCGEN05 (0) or KD_GEMM_MMA_SYNC
   int coarse_sync = 0;             // coarse solver halo exchange: KD_SYNC_CLUSTER (0) or KD_SYNC_P2P
   cudaStream_t st2 = nullptr;      // fine chunks (lowest priority)
   cudaStream_t st_hi = nullptr;    // serial sweeps (highest priority)

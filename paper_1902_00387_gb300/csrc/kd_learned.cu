@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __nv_bfloat16* __restrict
 
 int gemm_bf16_tn(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int M, int N, int K, int ldc,
                  cudaStream_t st) {
-  if (K % 8 != 0 || M <= 0 || N <= 0) return -1;
+  if (K % 8 != 0 || M <= 0 || N <= 0 || (((uintptr_t)A) & 15) || (((uintptr_t)Bt) & 15)) return -1;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   k_gemm_tn<<<grid, 256, 0, st>>>(A, Bt, C, M, N, K, ldc);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

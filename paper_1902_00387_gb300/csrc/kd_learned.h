@@ -41,6 +41,10 @@ int learned_gemv(const __nv_bfloat16* W, const float* x, float* y, int nc, int l
 // contiguous (K a multiple of 8); tensor-core mma, FP32 accumulate.
 int gemm_bf16_tn(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int M, int N, int K, int ldc,
                  cudaStream_t st);
+// The same product on the tcgen05 tensor cores (kd_gemm_tc.cu): TMEM accumulator, 128-byte
+// swizzled K-major operand tiles; *err (device int) is set if a bounded wait ran out.
+int gemm_bf16_tn_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int M, int N, int K, int ldc,
+                    int* err, cudaStream_t st);
 
 // training helpers (m pairs, nc complex unknowns)
 // Xs[2m][ld]  rows n: Re x_n, rows m + n: Im x_n (zero beyond nc)  (forward B operand)

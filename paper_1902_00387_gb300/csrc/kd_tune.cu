@@ -201,6 +201,14 @@ kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks) {
   return KD_OK;
 }
 
+kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine) {
+  if (!ctx) return KD_EINVAL;
+  if (engine != KD_GEMM_TCGEN05 && engine != KD_GEMM_MMA_SYNC)
+    return fail(ctx, KD_EINVAL, "kd_set_learned_gemm: engine must be KD_GEMM_TCGEN05 or KD_GEMM_MMA_SYNC");
+  ctx->gemm_engine = engine;
+  return KD_OK;
+}
+
 kd_status kd_set_coarse_sync(kd_ctx* ctx, int mode) {
   if (!ctx) return KD_EINVAL;
   if (mode != KD_SYNC_CLUSTER && mode != KD_SYNC_P2P && mode != KD_SYNC_PULL)

@@ -24,6 +24,7 @@ KD_FINE_DIRECT, KD_FINE_INCREMENT = 0, 1
 KD_FINE_FFT, KD_FINE_CONV = 0, 1
 KD_RK443, KD_RK222, KD_RK111 = 0, 1, 2
 KD_SYNC_CLUSTER, KD_SYNC_P2P, KD_SYNC_PULL = 0, 1, 2
+KD_GEMM_TCGEN05, KD_GEMM_MMA_SYNC = 0, 1
 KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
 KD_GRID_FINE, KD_GRID_COARSE = 0, 1
 KD_MAX_SLICES = 1024
@@ -79,7 +80,8 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
-           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
+           "kd_set_learned_gemm", "kd_set_overlap", "kd_set_coarse_cluster",
            "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
@@ -123,6 +125,8 @@ def load():
         "kd_growth_power": (I, [P, P, D, D, I, D, ctypes.POINTER(D), ctypes.POINTER(I), P]),
         "kd_growth_arnoldi": (I, [P, P, D, D, I, I, I, D, P, P, ctypes.POINTER(I), P]),
         "kd_hessenberg_eig": (I, [I, P, P, P]),
+        "kd_gemm_bf16_tn": (I, [P, P, P, I, I, I, I, I, P]),
+        "kd_set_learned_gemm": (I, [P, I]),
         "kd_block_init": (I, [P, I, I, D, I]),
         "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
         "kd_block_set_initial": (I, [P, P]),
@@ -415,6 +419,26 @@ def kd_growth_arnoldi(ctx, b0, t0, tau, m, nev, restarts, tol, b_out=None):
                                  _any_ptr(b_out, "complex128"))
     _check(ctx, s, allow=(KD_ENOTCONV,))
     return s, mu[0::2] + 1j * mu[1::2], rate, its.value
+
+
+def kd_gemm_bf16_tn(A, Bt, C, engine=KD_GEMM_TCGEN05, stream=None):
+    """C = A Bt^T for BF16 device tensors A [M][K], Bt [N][K] (K % 8 == 0) into the FP32
+    device tensor C [M][>= N]; synchronous."""
+    import torch
+    if A.dtype != torch.bfloat16 or Bt.dtype != torch.bfloat16 or C.dtype != torch.float32:
+        raise TypeError("A, Bt must be bfloat16 and C float32")
+    M, K = A.shape
+    N = Bt.shape[0]
+    if Bt.shape[1] != K or C.shape[0] != M or C.shape[1] < N:
+        raise ValueError("shape mismatch")
+    st = _current_stream() if stream is None else stream
+    s = load().kd_gemm_bf16_tn(_ptr(A), _ptr(Bt), _ptr(C), int(M), int(N), int(K), int(C.stride(0)), int(engine), st)
+    if s != KD_OK:
+        raise KdError(s, "kd_gemm_bf16_tn failed")
+
+
+def kd_set_learned_gemm(ctx, engine):
+    return _check(ctx, load().kd_set_learned_gemm(ctx, int(engine)))
 
 
 def kd_hessenberg_eig(h, vectors=False):
