@@ -29,6 +29,8 @@
 
 #include <stdio.h>
 
+#include <mutex>
+
 #include "../../include/kd.h"
 #include "kd_learned.h"
 
@@ -422,17 +424,25 @@ extern "C" kd_status kd_gemm_bf16_tn(const void* A, const void* Bt, float* C, in
     if (gemm_bf16_tn((const __nv_bfloat16*)A, (const __nv_bfloat16*)Bt, C, M, N, K, ldc, st) < 0) return KD_ECUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? KD_OK : KD_ECUDA;
   }
+  // the status word of the kernel's bounded waits: one per device for the process lifetime
+  static int* err_of[64] = {nullptr};
+  static std::mutex err_mutex;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KD_ECUDA;
   int* err = nullptr;
-  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return KD_ENOMEM;
+  {
+    std::lock_guard<std::mutex> lock(err_mutex);
+    if (!err_of[dev] && cudaMalloc(&err_of[dev], sizeof(int)) != cudaSuccess) {
+      err_of[dev] = nullptr;
+      return KD_ENOMEM;
+    }
+    err = err_of[dev];
+  }
   int e = 0;
-  kd_status s = KD_OK;
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
       gemm_bf16_tn_tc((const __nv_bfloat16*)A, (const __nv_bfloat16*)Bt, C, M, N, K, ldc, err, st) < 0 ||
       cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
-    s = KD_ECUDA;
-  else if (e)
-    s = KD_ECUDA;
-  cudaFree(err);
-  return s;
+    return KD_ECUDA;
+  return e ? KD_ECUDA : KD_OK;
 }

@@ -15,6 +15,11 @@ autotuned first), for a launch list of a whole solve.
 
 runs the classical coarse propagator (one thread-block cluster, kd_coarse) on one field
 twice and prints the device time per RK443 stage of the second call.
+
+    python -m paper_1902_00387_gb300.profile_case --gemm 4096,4096,4096 [--engine 0|1]
+
+runs the BF16 training GEMM (kd_gemm_bf16_tn; engine 0 tcgen05, 1 mma.sync) on seeded
+operands twice and prints the TFLOP/s of the second call.
 """
 import argparse
 import os
@@ -39,6 +44,8 @@ def main():
     ap.add_argument("--n-coarse", type=int, default=128)
     ap.add_argument("--cluster", type=int, default=0, help="blocks per cluster of the coarse solver (0: default)")
     ap.add_argument("--sync", type=int, default=0, help="coarse halo exchange: 0 cluster barrier, 1 point-to-point")
+    ap.add_argument("--gemm", default=None, help="M,N,K of a BF16 GEMM to run")
+    ap.add_argument("--engine", type=int, default=0, help="GEMM engine: 0 tcgen05, 1 mma.sync")
     args = ap.parse_args()
     import torch
 
@@ -67,6 +74,21 @@ def main():
         print("parareal GP 128^2 x 64 slices: %.1f ms, k_con %d, plan %s" % (e0.elapsed_time(e1), st.k_con,
                                                                             kd.kd_get_plan(ctx)))
         kd.kd_destroy(ctx)
+        return
+    if args.gemm:
+        M, N, K = (int(v) for v in args.gemm.split(","))
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        Bt = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        kd.kd_gemm_bf16_tn(A, Bt, C, args.engine)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        kd.kd_gemm_bf16_tn(A, Bt, C, args.engine)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print("gemm %dx%dx%d engine %d: %.3f ms, %.1f TFLOP/s" % (M, N, K, args.engine, ms, 2.0 * M * N * K / ms / 1e9))
         return
     if args.coarse:
         p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64,
