@@ -7,7 +7,8 @@
 //
 // The explicit term is evaluated as the exact spectral convolution
 //     w_hat(k) = sum_q u_hat(q, t) x b_hat(k - q),   q in {(+-1, 0), (0, +-1)},
-// followed by the curl i k3 x w_hat on the dealiased set.  The flow has only those
+// followed by the curl i k3 x w_hat on the dealiased set (two complex products per
+// neighbour: the flows' modes satisfy u_y = -+ i u_z at q = +-x, u_z = -+ i u_x at q = +-y).  The flow has only those
 // four Fourier modes and n/3 + 1 < n/2, so the pseudo-spectral product of the fine
 // kernels has no aliasing and this is the same discrete operator (equal to round-off).
 //

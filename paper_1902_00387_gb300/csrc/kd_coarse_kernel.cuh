@@ -288,18 +288,26 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
           if (o < 0) continue;
           const bool edge = ((first_mask | last_mask) >> i) & 1u;
           if (split && (edge ? 0 : 1) != (pass == 0 ? 1 : 0)) continue;
+          // u_hat of the flows of Sec. 2 (see uhat): u_y(+-x) = -+ i u_z(+-x) and
+          // u_z(+-y) = -+ i u_x(+-y), so each neighbour's cross product takes two complex
+          // products: with z = u_z(q), x neighbour b = b_hat(k - q), q = +-x:
+          //   w += (z (-b_y -+ i b_z), z b_x, +- i z b_x);
+          // with v = u_x(q), y neighbour c = b_hat(k - q), q = +-y:
+          //   w += (+- i v c_y, v (-c_z -+ i c_x), v c_y)
           cx<T> w[3] = {mk(T(0), T(0)), mk(T(0), T(0)), mk(T(0), T(0))};
 #pragma unroll
           for (int sgn = 0; sgn < 2; ++sgn) {
             const int ox = o + (sgn == 0 ? -1 : 1);   // x neighbour ix -+ 1
             const cx<T> bx = Xs[ox], by = Xs[LH * L + ox], bz = Xs[2 * LH * L + ox];
-            const cx<T> uy = u.py[sgn], uz = u.pz[sgn];
-            w[0] = w[0] + cmul(uy, bz) - cmul(uz, by);
-            w[1] = w[1] + cmul(uz, bx);
-            w[2] = w[2] - cmul(uy, bx);
-            // y neighbour ly -+ 1
+            const cx<T> z = u.pz[sgn];
+            const cx<T> p = cmul(z, bx);
+            const cx<T> s0 = sgn == 0 ? mk(bz.y - by.x, -by.y - bz.x) : mk(-by.x - bz.y, bz.x - by.y);
+            w[0] = w[0] + cmul(z, s0);
+            w[1] = w[1] + p;
+            w[2] = sgn == 0 ? w[2] + mul_i(p) : w[2] - mul_i(p);
+            // y neighbour ly -+ 1 (in the neighbour block's rows when pulling them)
             cx<T> cxv, cyv, czv;
-            const bool far = sgn == 0 ? ((first_mask >> i) & 1u) : ((last_mask >> i) & 1u);
+            const bool far = pull && (sgn == 0 ? ((first_mask >> i) & 1u) : ((last_mask >> i) & 1u));
             if (far) {
               const cx<T>* Y = sgn == 0 ? Xup : Xdn;
               cxv = Y[o];
@@ -311,10 +319,12 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
               cyv = Xs[LH * L + oy];
               czv = Xs[2 * LH * L + oy];
             }
-            const cx<T> ux = u.qx[sgn], uz2 = u.qz[sgn];
-            w[0] = w[0] - cmul(uz2, cyv);
-            w[1] = w[1] + cmul(uz2, cxv) - cmul(ux, czv);
-            w[2] = w[2] + cmul(ux, cyv);
+            const cx<T> v = u.qx[sgn];
+            const cx<T> r = cmul(v, cyv);
+            const cx<T> s1 = sgn == 0 ? mk(cxv.y - czv.x, -czv.y - cxv.x) : mk(-czv.x - cxv.y, cxv.x - czv.y);
+            w[0] = sgn == 0 ? w[0] + mul_i(r) : w[0] - mul_i(r);
+            w[1] = w[1] + cmul(v, s1);
+            w[2] = w[2] + r;
           }
           cx<T> F[3];
           F[0] = mul_i(w[2] * fky[i] - w[1] * kz);
