@@ -678,11 +678,12 @@ ROW_TRAFFIC = {"n": 128, "batch": 64, "row_variant": 3, "bytes_per_launch": 2647
 
 
 def conv_roofline(n, S, batches, steps, stats):
-    """ALU roofline of the convolution-form fine propagator: ~180 flops per kept mode and
-    stage (two neighbour pairs of cross products with the 4 flow modes, curl, stage update),
-    i.e. 720 P^2 flops per slice-step, over the fine phase's device time."""
+    """ALU roofline of the convolution-form fine propagator: ~135 flops per kept mode and
+    stage (the cross products with the 4 flow modes as 8 complex products and their sums,
+    ~80; curl, ~18; stage update, ~36), i.e. 540 P^2 flops per slice-step, over the fine
+    phase's device time."""
     P = 2 * (n // 3) + 1
-    flops = 720.0 * P * P * S * sum(batches) * steps
+    flops = 540.0 * P * P * S * sum(batches) * steps
     tf = flops / (sum(x.ms_fine for x in stats) / 1e3) / 1e12
     return {"bound": "alu", "kernel": "coarse_cluster_kernel<float, 4> as the fine convolution operator",
             "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS,
