@@ -262,6 +262,15 @@ kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int
 kd_status kd_learned_loss_grad(kd_ctx* ctx, const float* W, const float* W0, float weight_decay, const float* x,
                                const float* y, int n, double* loss_out, float* grad_out);
 
+/* Checkpoint of the learned operators: copy W_phase out (BF16 [2 nc][nc], host or
+ * device) with its usability flag (valid: 1 when kd_learned_eval found it no worse than
+ * the classical propagator; may be NULL), or load one in, e.g. from a previous run, with
+ * the flag the caller gives (the Parareal sweep uses W_phase only when it is set).  The
+ * padding of the internal rows stays zero.  Synchronous.  KD_EINVAL before
+ * kd_learned_init or for a phase outside [0, n_phase). */
+kd_status kd_learned_get(kd_ctx* ctx, int phase, void* W, int* valid);
+kd_status kd_learned_set(kd_ctx* ctx, int phase, const void* W, int valid);
+
 /* y_i = W_phase x_i for n learned vectors (device).  Asynchronous. */
 kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int n);
 

@@ -1332,6 +1332,32 @@ kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int
   return KD_OK;
 }
 
+kd_status kd_learned_get(kd_ctx* ctx, int phase, void* W, int* valid) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0 || phase < 0 || phase >= ctx->l_nphase || !W)
+    return fail(ctx, KD_EINVAL, "kd_learned_get: bad arguments");
+  const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
+  KD_CUDA(cudaMemcpy2DAsync(W, (size_t)nc * 2, ctx->l_W + (size_t)phase * 2 * nc * ld, (size_t)ld * 2, (size_t)nc * 2,
+                            2 * (size_t)nc, cudaMemcpyDefault, ctx->st),
+          "operator out");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  if (valid) *valid = ctx->l_valid[phase];
+  return KD_OK;
+}
+
+kd_status kd_learned_set(kd_ctx* ctx, int phase, const void* W, int valid) {
+  if (!ctx) return KD_EINVAL;
+  if (ctx->l_nphase == 0 || phase < 0 || phase >= ctx->l_nphase || !W)
+    return fail(ctx, KD_EINVAL, "kd_learned_set: bad arguments");
+  const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
+  KD_CUDA(cudaMemcpy2DAsync(ctx->l_W + (size_t)phase * 2 * nc * ld, (size_t)ld * 2, W, (size_t)nc * 2, (size_t)nc * 2,
+                            2 * (size_t)nc, cudaMemcpyDefault, ctx->st),
+          "operator in");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  ctx->l_valid[phase] = valid ? 1 : 0;
+  return KD_OK;
+}
+
 kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, double* err_learned,
                           double* err_classical) {
   if (!ctx) return KD_EINVAL;

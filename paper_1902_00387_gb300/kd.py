@@ -81,7 +81,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
            "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
-           "kd_set_learned_gemm", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_set_overlap", "kd_set_coarse_cluster",
            "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
@@ -127,6 +127,8 @@ def load():
         "kd_hessenberg_eig": (I, [I, P, P, P]),
         "kd_gemm_bf16_tn": (I, [P, P, P, I, I, I, I, I, P]),
         "kd_set_learned_gemm": (I, [P, I]),
+        "kd_learned_get": (I, [P, I, P, ctypes.POINTER(I)]),
+        "kd_learned_set": (I, [P, I, P, I]),
         "kd_block_init": (I, [P, I, I, D, I]),
         "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
         "kd_block_set_initial": (I, [P, P]),
@@ -435,6 +437,29 @@ def kd_gemm_bf16_tn(A, Bt, C, engine=KD_GEMM_TCGEN05, stream=None):
     s = load().kd_gemm_bf16_tn(_ptr(A), _ptr(Bt), _ptr(C), int(M), int(N), int(K), int(C.stride(0)), int(engine), st)
     if s != KD_OK:
         raise KdError(s, "kd_gemm_bf16_tn failed")
+
+
+def kd_learned_get(ctx, phase, W):
+    """Copy W_phase into W (bfloat16 [2 nc][nc], host numpy uint16 / torch tensor or
+    device tensor); returns its usability flag."""
+    valid = ctypes.c_int()
+    _check(ctx, load().kd_learned_get(ctx, int(phase), _any_ptr_raw(W), ctypes.byref(valid)))
+    return bool(valid.value)
+
+
+def kd_learned_set(ctx, phase, W, valid):
+    return _check(ctx, load().kd_learned_set(ctx, int(phase), _any_ptr_raw(W), int(bool(valid))))
+
+
+def _any_ptr_raw(x):
+    """Address of a contiguous host numpy array or torch tensor (host or device), any dtype."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
 
 
 def kd_set_learned_gemm(ctx, engine):

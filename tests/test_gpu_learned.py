@@ -210,3 +210,39 @@ def test_parareal_gain_of_learned_coarse_propagator(kd):
     assert cl and not fl and sl[-1] <= 1e-8, sl
     assert kl < kc and (not cc or sl[-1] <= sc[-1]), (kl, kc, sc, sl)
     assert rel(ul[-1], uc[-1]) < 1e-5
+
+
+def test_operator_checkpoint_round_trip(kd):
+    """kd_learned_get / kd_learned_set: an operator copied out of one context and loaded
+    into another gives the same products bit for bit, with its usability flag; a loaded
+    zero operator gives zero."""
+    import torch
+    x = learned_inputs([6, 7, 8])
+    xt = torch.tensor(x.astype(np.complex64), device="cuda")
+    a, b = make_ctx(kd), make_ctx(kd)
+    try:
+        kd.kd_learned_init(a, N_PHASE, SLICE)
+        kd.kd_learned_init(b, N_PHASE, SLICE)
+        nc = 3 * M_SET * M_SET
+        W = np.zeros((2 * nc, nc), np.uint16)                     # BF16 bit patterns on the host
+        valid = kd.kd_learned_get(a, 5, W)
+        assert W.any()
+        Wz = torch.zeros((2 * nc, nc), dtype=torch.bfloat16, device="cuda")
+        kd.kd_learned_set(b, 2, Wz, False)
+        kd.kd_learned_set(b, 5, W, valid)
+        assert kd.kd_learned_get(b, 5, np.zeros_like(W)) == valid
+        ya, yb, y0 = (torch.zeros_like(xt) for _ in range(3))
+        kd.kd_learned_apply(a, xt, ya, 5, 3)
+        kd.kd_learned_apply(b, xt, yb, 5, 3)
+        kd.kd_learned_apply(b, xt, y0, 2, 3)
+        torch.cuda.synchronize()
+        assert torch.equal(ya, yb)
+        assert not y0.any()
+        W2 = np.zeros_like(W)
+        kd.kd_learned_get(b, 5, W2)
+        assert np.array_equal(W, W2)
+        with pytest.raises(kd.KdError):
+            kd.kd_learned_get(a, N_PHASE, W)
+    finally:
+        kd.kd_destroy(a)
+        kd.kd_destroy(b)
