@@ -359,6 +359,13 @@ kd_status kd_gemm_bf16_tn(const void* A, const void* Bt, float* C, int M, int N,
 /* Engine of the GEMMs in kd_learned_train / kd_learned_loss_grad (default KD_GEMM_TCGEN05). */
 kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine);
 
+/* Self-test of the bounded device-side waits (failure detection without a GPU fault):
+ * one CTA waits on an mbarrier phase with the same bounded-wait helper the kernels use;
+ * arrive = 1 gives it its arrival (KD_OK), arrive = 0 gives it none, and the wait gives up
+ * after max_ms milliseconds (0 < max_ms <= 1000) with KD_ETIMEOUT, the device still
+ * usable.  Synchronous on cuda_stream. */
+kd_status kd_selftest_wait(int arrive, double max_ms, void* cuda_stream);
+
 /* The host routine that kd_growth_arnoldi uses for its small dense eigenproblem, exposed
  * for checking: eigenvalues of an m x m complex upper Hessenberg matrix h (row-major,
  * interleaved re / im; entries below the subdiagonal must be zero) by the shifted QR

@@ -826,6 +826,7 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
 kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_max, double tol, double* u_slices,
                           kd_parareal_stats* stats) {
   if (!ctx) return KD_EINVAL;
+  NvtxRange range("kd_parareal_run");
   if (!b0) return fail(ctx, KD_EINVAL, "kd_parareal_run: b0 is NULL");
   if (N < 1 || N > KD_MAX_SLICES) return fail(ctx, KD_EINVAL, "kd_parareal_run: n_slices out of range");
   if (k_max < 0 || k_max > KD_MAX_ITERS) return fail(ctx, KD_EINVAL, "kd_parareal_run: k_max out of range");
@@ -874,10 +875,13 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
   } else {
   // iterate 0: serial coarse sweep
   KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
-  for (int i = 0; i < N; ++i)
-    if ((s = use_learned(ctx, i) ? learned_step(ctx, i, true, false) : coarse_step(ctx, i, Sc, dtc, true, false)) !=
-        KD_OK)
-      return s;
+  {
+    NvtxRange r0("serial sweep 0");
+    for (int i = 0; i < N; ++i)
+      if ((s = use_learned(ctx, i) ? learned_step(ctx, i, true, false) : coarse_step(ctx, i, Sc, dtc, true, false)) !=
+          KD_OK)
+        return s;
+  }
   KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
   KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");
   {
@@ -890,8 +894,12 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     // (the last slice is always swept so that sigma is measured)
     const int first = k - 1 < N - 1 ? k - 1 : N - 1;
     KD_CUDA(cudaEventRecord(ctx->ev[1], ctx->st), "event");
-    if ((s = fine_sweep(ctx, first, N, S, dt, k)) != KD_OK) return s;
+    {
+      NvtxRange rf("fine sweep");
+      if ((s = fine_sweep(ctx, first, N, S, dt, k)) != KD_OK) return s;
+    }
     KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
+    NvtxRange rs("serial sweep");
     // serial step; slice `first` has U_first unchanged, so G(U_first) is the stored
     // coarse value bit for bit and the coarse terms cancel without a coarse solve
     {

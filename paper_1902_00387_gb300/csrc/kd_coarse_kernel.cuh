@@ -8,6 +8,7 @@
 
 #include "kd_coarse.h"
 #include "kd_stage.cuh"
+#include "kd_wait.cuh"
 
 namespace cgrp = cooperative_groups;
 
@@ -79,24 +80,9 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 // bounded wait for the phase of the given parity; false after kHaloWaitCycles
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity))
-    if (clock64() - t0 > kHaloWaitCycles) return false;
-  return true;
+  return mbar_wait_bounded<true>(bar, parity, kHaloWaitCycles);
 }
 
 __device__ __forceinline__ void push(uint32_t dst, cx<float> v, uint32_t bar) {

@@ -1,6 +1,7 @@
 // Library-internal view of the context of include/kd.h and the helpers shared by the
 // C-ABI translation units (kd_abi.cu, kd_tune.cu, kd_sweep.cu).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 
 #include <string>
@@ -121,6 +122,15 @@ kd_status cuda_fail(kd_ctx* c, cudaError_t e, const char* where);
   } while (0)
 
 bool valid_n(int n);
+// NVTX range for the duration of a scope: the phases of a solve show up by name in a
+// profiler timeline (no cost when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 inline int kept(int n) { return 2 * (n / 3) + 1; }
 inline long compact_len(int n) { return 3L * kept(n) * kept(n); }  // complex entries per field
 int steps_for(double dT, double dt);

@@ -33,6 +33,7 @@
 
 #include "../../include/kd.h"
 #include "kd_learned.h"
+#include "kd_wait.cuh"
 
 namespace kd {
 
@@ -56,17 +57,7 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok = 0;
-  const long long t0 = clock64();
-  while (true) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
+  return mbar_wait_bounded<false>(bar, parity, kWaitCycles);
 }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
@@ -408,7 +399,40 @@ int gemm_bf16_tn_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, i
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// one CTA waits on an mbarrier that receives its only arrival (arrive = 1) or none
+__global__ void k_wait_selftest(int arrive, long long max_cycles, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(saddr(&bar));
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bar)) : "memory");
+  const bool ok = mbar_wait_bounded<false>(saddr(&bar), 0u, max_cycles);
+  __syncthreads();
+  if (threadIdx.x == 0) *status = ok ? 0 : 1;
+}
+
 }  // namespace kd
+
+extern "C" kd_status kd_selftest_wait(int arrive, double max_ms, void* cuda_stream) {
+  using namespace kd;
+  if (!(max_ms > 0) || max_ms > 1000.0) return KD_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* status = nullptr;
+  if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return KD_ENOMEM;
+  int clock_khz = 0, dev = 0, h = -1;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev) != cudaSuccess || clock_khz <= 0)
+    clock_khz = 2070000;
+  const long long cycles = (long long)(max_ms * clock_khz);
+  k_wait_selftest<<<1, 32, 0, st>>>(arrive ? 1 : 0, cycles, status);
+  kd_status s = KD_OK;
+  if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    s = KD_ECUDA;
+  else
+    s = h == 0 ? KD_OK : KD_ETIMEOUT;
+  cudaFree(status);
+  return s;
+}
 
 extern "C" kd_status kd_gemm_bf16_tn(const void* A, const void* Bt, float* C, int M, int N, int K, int ldc, int engine,
                                      void* cuda_stream) {

@@ -78,3 +78,17 @@ def test_gemm_argument_errors(kd):
     C = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(kd.KdError):
         kd.kd_gemm_bf16_tn(A, A, C)
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(kd):
+    """Failure detection without a fault: a wait whose producer never arrives returns
+    KD_ETIMEOUT after its limit, and the next kernels run normally."""
+    import torch
+    assert kd.kd_selftest_wait(True, 5.0) == kd.KD_OK
+    assert kd.kd_selftest_wait(False, 2.0) == kd.KD_ETIMEOUT
+    A, Bt = operands(256, 256, 128, 3)
+    C = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+    kd.kd_gemm_bf16_tn(A.cuda(), Bt.cuda(), C)
+    ref = A.double() @ Bt.double().T
+    bound = A.double().abs() @ Bt.double().abs().T
+    assert torch.all((C.cpu().double() - ref).abs() <= 2e-6 * bound + 1e-6)
