@@ -153,6 +153,18 @@ typedef struct {
 kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices, int k_max,
                           double tol, double* u_slices, kd_parareal_stats* stats);
 
+/* Checkpoint / resume of kd_parareal_run: continue Parareal from the iterate U^{k_done}
+ * of an earlier run (u_init, complex128 [n_slices+1][3][n][n], host or device, e.g. the
+ * u_slices that run returned after k_done iterations; slices 0..k_done of it are the
+ * exact fine solution, u_init[0] is b0).  Iterations k_done + 1 .. k_max follow, the
+ * first fine sweep in direct form, and give the values the uninterrupted run gives to
+ * FP32 round-off.  k_done = 0 starts Parareal from an arbitrary initial iterate instead of
+ * the coarse sweep.  stats->sigma[k - 1] holds the defects of the resumed iterations
+ * (0 for k <= k_done).  fine_form must be KD_FINE_INCREMENT (else KD_EUNSUPPORTED);
+ * otherwise as kd_parareal_run. */
+kd_status kd_parareal_resume(kd_ctx* ctx, const double* u_init, int k_done, double T, int n_slices, int k_max,
+                             double tol, double* u_slices, kd_parareal_stats* stats);
+
 /* Thread blocks per cluster of the persistent coarse solver (coarse sets up to 88 modes
  * a side): 0 = the default (a batch of fields that fits the GPU in clusters of 16: ~3 rows
  * per block, up to 16 blocks; larger batches: ~6 rows per block, at most 8), else 1..8 (1..16 where the

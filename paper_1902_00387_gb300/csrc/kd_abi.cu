@@ -823,13 +823,20 @@ kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double
   return KD_OK;
 }
 
-kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_max, double tol, double* u_slices,
-                          kd_parareal_stats* stats) {
+// Parareal from b0 (u_init NULL: iterate 0 is the serial coarse sweep), or resumed from
+// the iterate u_init = U^{k0} of an earlier run (slices 0..k0 exact): the iterations
+// k0 + 1, ... continue from it, the first fine sweep in direct form.
+static kd_status parareal_core(kd_ctx* ctx, const double* b0, const double* u_init, int k0, double T, int N,
+                               int k_max, double tol, double* u_slices, kd_parareal_stats* stats) {
   if (!ctx) return KD_EINVAL;
-  NvtxRange range("kd_parareal_run");
-  if (!b0) return fail(ctx, KD_EINVAL, "kd_parareal_run: b0 is NULL");
+  NvtxRange range(u_init ? "kd_parareal_resume" : "kd_parareal_run");
+  if (!b0 && !u_init) return fail(ctx, KD_EINVAL, "kd_parareal_run: b0 is NULL");
   if (N < 1 || N > KD_MAX_SLICES) return fail(ctx, KD_EINVAL, "kd_parareal_run: n_slices out of range");
   if (k_max < 0 || k_max > KD_MAX_ITERS) return fail(ctx, KD_EINVAL, "kd_parareal_run: k_max out of range");
+  if (u_init && (k0 < 0 || k0 > k_max))
+    return fail(ctx, KD_EINVAL, "kd_parareal_resume: need 0 <= k_done <= k_max");
+  if (u_init && ctx->p.fine_form != KD_FINE_INCREMENT)
+    return fail(ctx, KD_EUNSUPPORTED, "kd_parareal_resume: needs fine_form KD_FINE_INCREMENT");
   if (!(T > 0) || !isfinite(T)) return fail(ctx, KD_EINVAL, "kd_parareal_run: T must be > 0");
   const int n = ctx->p.n, nc = ctx->p.n_coarse;
   const double dT = T / N;
@@ -852,12 +859,19 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
   KD_LAUNCH(fill_slice_times(ctx->t0c, N + 1, 0, dT, ctx->st), "times");
 
   KD_CUDA(cudaEventRecord(ctx->ev[0], ctx->st), "event");
-  if ((s = copy_in_b0(ctx, b0)) != KD_OK) return s;
+  if (u_init) {
+    const size_t fb = 3UL * n * n * 16;
+    if ((s = ensure_full_tmp(ctx, fb * (N + 1))) != KD_OK) return s;
+    KD_CUDA(cudaMemcpyAsync(ctx->full_tmp, u_init, fb * (N + 1), cudaMemcpyDefault, ctx->st), "copy iterate");
+    KD_LAUNCH(full_to_compact(KD_C128, ctx->full_tmp, KD_C128, ctx->U, N + 1, n, ctx->st), "iterate to compact");
+  } else if ((s = copy_in_b0(ctx, b0)) != KD_OK) {
+    return s;
+  }
   if ((s = coarse_phases(ctx, N, Sc, dtc)) != KD_OK) return s;
   float ms_fine = 0.f, ms_coarse = 0.f;
-  int k_done = 0, conv = 0;
-  std::vector<double> sig;
-  if (ctx->overlap > 0 && N >= 2) {
+  int k_done = u_init ? k0 : 0, conv = 0;
+  std::vector<double> sig(u_init ? k0 : 0, 0.0);
+  if (ctx->overlap > 0 && N >= 2 && !u_init) {
     // the sweeps run on the high-priority stream, ordered after the caller's stream
     cudaStream_t user = ctx->st;
     KD_CUDA(cudaEventRecord(ctx->ev[1], user), "event");
@@ -873,9 +887,9 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
       return s;
     }
   } else {
-  // iterate 0: serial coarse sweep
+  // iterate 0: serial coarse sweep (none when resuming)
   KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
-  {
+  if (!u_init) {
     NvtxRange r0("serial sweep 0");
     for (int i = 0; i < N; ++i)
       if ((s = use_learned(ctx, i) ? learned_step(ctx, i, true, false) : coarse_step(ctx, i, Sc, dtc, true, false)) !=
@@ -889,14 +903,15 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     cudaEventElapsedTime(&m, ctx->ev[2], ctx->ev[3]);
     ms_coarse += m;
   }
-  for (int k = 1; k <= k_max; ++k) {
+  for (int k = k_done + 1; k <= k_max; ++k) {
     // parallel step over the slices that can still change: n >= k - 1
     // (the last slice is always swept so that sigma is measured)
     const int first = k - 1 < N - 1 ? k - 1 : N - 1;
     KD_CUDA(cudaEventRecord(ctx->ev[1], ctx->st), "event");
     {
       NvtxRange rf("fine sweep");
-      if ((s = fine_sweep(ctx, first, N, S, dt, k)) != KD_OK) return s;
+      // the first iteration of a run, or of a resumed run, is in direct form
+      if ((s = fine_sweep(ctx, first, N, S, dt, (u_init && k == k0 + 1) ? 1 : k)) != KD_OK) return s;
     }
     KD_CUDA(cudaEventRecord(ctx->ev[2], ctx->st), "event");
     NvtxRange rs("serial sweep");
@@ -939,7 +954,7 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     // iteration budget is spent (the increment form needs no stored coarse values, so
     // the switch keeps the iteration consistent)
     if (ctx->p.coarse_kind == KD_COARSE_LEARNED && !ctx->fallback &&
-        ((k >= 2 && sigma > sig[k - 2]) || (k_max > 1 && k >= k_max / 2)))
+        ((k >= k0 + 2 && sigma > sig[k - 2]) || (k_max > 1 && k >= k_max / 2)))
       ctx->fallback = 1;
   }
   }
@@ -970,8 +985,20 @@ kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_
     stats->n_launches = ctx->launches - launches0;
     stats->fallback_used = ctx->fallback;
   }
-  if (!conv && k_max > 0) return fail(ctx, KD_ENOTCONV, "kd_parareal_run: tol not reached within k_max");
+  if (!conv && k_max > k0) return fail(ctx, KD_ENOTCONV, "kd_parareal_run: tol not reached within k_max");
   return KD_OK;
+}
+
+kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int N, int k_max, double tol, double* u_slices,
+                          kd_parareal_stats* stats) {
+  return parareal_core(ctx, b0, nullptr, 0, T, N, k_max, tol, u_slices, stats);
+}
+
+kd_status kd_parareal_resume(kd_ctx* ctx, const double* u_init, int k_done, double T, int N, int k_max, double tol,
+                             double* u_slices, kd_parareal_stats* stats) {
+  if (!ctx) return KD_EINVAL;
+  if (!u_init) return fail(ctx, KD_EINVAL, "kd_parareal_resume: u_init is NULL");
+  return parareal_core(ctx, nullptr, u_init, k_done, T, N, k_max, tol, u_slices, stats);
 }
 
 kd_status kd_fine_serial(kd_ctx* ctx, const double* b0, double T, int N, double* u_slices) {

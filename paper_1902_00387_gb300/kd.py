@@ -81,7 +81,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
            "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
-           "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_parareal_resume", "kd_set_overlap", "kd_set_coarse_cluster",
            "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
@@ -130,6 +130,7 @@ def load():
         "kd_learned_get": (I, [P, I, P, ctypes.POINTER(I)]),
         "kd_learned_set": (I, [P, I, P, I]),
         "kd_selftest_wait": (I, [I, D, P]),
+        "kd_parareal_resume": (I, [P, P, I, D, I, I, D, P, ctypes.POINTER(kd_parareal_stats)]),
         "kd_block_init": (I, [P, I, I, D, I]),
         "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
         "kd_block_set_initial": (I, [P, P]),
@@ -264,6 +265,16 @@ def kd_parareal_run(ctx, b0, T, n_slices, k_max, tol, u_slices=None):
     st = kd_parareal_stats()
     s = load().kd_parareal_run(ctx, _any_ptr(b0, "complex128"), float(T), int(n_slices), int(k_max), float(tol),
                                _any_ptr(u_slices, "complex128"), ctypes.byref(st))
+    _check(ctx, s, allow=(KD_ENOTCONV,))
+    return s, st
+
+
+def kd_parareal_resume(ctx, u_init, k_done, T, n_slices, k_max, tol, u_slices=None):
+    """Continue Parareal from the iterate u_init (complex128 [n_slices+1][3][n][n]) of an
+    earlier run after k_done iterations.  Returns (status, stats)."""
+    st = kd_parareal_stats()
+    s = load().kd_parareal_resume(ctx, _any_ptr(u_init, "complex128"), int(k_done), float(T), int(n_slices),
+                                  int(k_max), float(tol), _any_ptr(u_slices, "complex128"), ctypes.byref(st))
     _check(ctx, s, allow=(KD_ENOTCONV,))
     return s, st
 

@@ -266,3 +266,58 @@ def test_pipelined_iterations_equal_unpipelined(kd, form, chunks):
     assert res[0][2] == res[1][2] == 5
     assert res[0][1] == res[1][1]
     assert np.array_equal(res[0][0], res[1][0])
+
+
+def c1_increment_ctx(kd):
+    p = kd.make_params(C1["flow"], C1["n"], C1["kz"], C1["Rm"], C1["dt"], kd.KD_C128, n_coarse=C1["nc"],
+                       dt_coarse=C1["dtc"], prec_coarse=kd.KD_C128, fine_form=kd.KD_FINE_INCREMENT)
+    return kd.kd_create(p)
+
+
+def test_resume_from_a_checkpointed_iterate(kd):
+    """kd_parareal_resume continues from the iterate an earlier run returned: iterations 3
+    and 4 resumed from U^2 equal those of the uninterrupted run (FP64; the first resumed
+    fine sweep is direct instead of incremental, so equal to round-off)."""
+    b0 = I.initial_field(C1["n"], C1["kz"], 2)
+    N, T = C1["N"], C1["T"]
+    ctx = c1_increment_ctx(kd)
+    try:
+        u2 = np.zeros((N + 1, 3, C1["n"], C1["n"]), np.complex128)
+        s, st2 = kd.kd_parareal_run(ctx, b0, T, N, 2, 0.0, u2)
+        u4 = np.zeros_like(u2)
+        s, st4 = kd.kd_parareal_run(ctx, b0, T, N, 4, 0.0, u4)
+        ur = np.zeros_like(u2)
+        s, str_ = kd.kd_parareal_resume(ctx, u2, 2, T, N, 4, 0.0, ur)
+    finally:
+        kd.kd_destroy(ctx)
+    assert str_.k_con == 4 and list(str_.sigma[:2]) == [0.0, 0.0]
+    for k in (2, 3):
+        assert abs(str_.sigma[k] - st4.sigma[k]) <= 1e-8 * st4.sigma[k], k
+    for i in range(N + 1):
+        assert rel(ur[i], u4[i]) < 1e-12, i
+
+
+def test_resume_from_the_fine_solution_is_converged(kd):
+    """An initial iterate that is already the serial fine solution is a fixed point: the
+    first defect is round-off."""
+    b0 = I.initial_field(C1["n"], C1["kz"], 3)
+    N, T = C1["N"], C1["T"]
+    ctx = c1_increment_ctx(kd)
+    try:
+        ser = np.zeros((N + 1, 3, C1["n"], C1["n"]), np.complex128)
+        kd.kd_fine_serial(ctx, b0, T, N, ser)
+        s, st = kd.kd_parareal_resume(ctx, ser, 0, T, N, 3, 1e-12)
+    finally:
+        kd.kd_destroy(ctx)
+    assert s == kd.KD_OK and st.k_con == 1 and st.sigma[0] < 1e-12
+
+
+def test_resume_needs_the_increment_form(kd):
+    ctx = c1_ctx(kd)                                 # KD_FINE_DIRECT
+    try:
+        u = np.zeros((C1["N"] + 1, 3, C1["n"], C1["n"]), np.complex128)
+        u[0] = I.initial_field(C1["n"], C1["kz"], 0)
+        with pytest.raises(kd.KdError):
+            kd.kd_parareal_resume(ctx, u, 0, C1["T"], C1["N"], 2, 0.0)
+    finally:
+        kd.kd_destroy(ctx)
