@@ -20,6 +20,7 @@
 #include "kd_fine2c.cuh"
 #include "kd_fine3.cuh"
 #include "kd_fine3c.cuh"
+#include "kd_fine2f.cuh"
 
 namespace kd {
 
@@ -127,7 +128,11 @@ struct Fine2Set {
   using ShC = ShapesC<N>;
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && (N == 128 || N == 256);
-  static int ncol() { return WIDE ? (R8 ? 4 : 3) : 1; }
+  // FP32 n = 128: column variant 4 is the persistent 2-block fused step (the row
+  // variant does not apply)
+  static constexpr bool FUSED = WIDE && N == 128;
+  static constexpr int kFusedCol = 4;
+  static int ncol() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
   static int nrow() { return WIDE ? (R8 ? 8 : 6) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
@@ -150,6 +155,11 @@ struct Fine2Set {
         return e;
       if ((e = cudaFuncSetAttribute(row2c_kernel<T, N, ShC::RT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Row2C<T, N, ShC::RT1>::smem)) != cudaSuccess)
+        return e;
+    }
+    if constexpr (FUSED) {
+      if ((e = cudaFuncSetAttribute(fused128_kernel<>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Fused128::smem)) != cudaSuccess)
         return e;
     }
     if constexpr (R8) {
@@ -213,6 +223,8 @@ struct Fine3Set {
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
+  static constexpr bool FUSED = false;   // no persistent fused step at these sizes
+  static constexpr int kFusedCol = -1;
   static int ncol() { return WIDE ? (R8 ? 5 : 4) : 1; }
   static int nrow() { return WIDE ? (R8 ? 9 : 7) : 1; }
   static cudaError_t prepare() {
@@ -300,9 +312,22 @@ struct Fine3Set {
 template <class Set>
 static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
   const FinePlan pl = cfg.plan;
-  const int cv = pl.col >= 0 && pl.col < Set::ncol() ? pl.col : 0;
+  int cv = pl.col >= 0 && pl.col < Set::ncol() ? pl.col : 0;
+  if constexpr (Set::FUSED) {
+    if (cv == Set::kFusedCol) cv = 0;   // (only for the calls the fused step does not cover)
+  }
   const int rv = pl.row >= 0 && pl.row < Set::nrow() ? pl.row : 0;
   int launches = 0;
+  if constexpr (Set::FUSED) {
+    // the persistent fused step: every step of every field in one launch (RK443, from X,
+    // no mixed field kept at the end, all fields for all steps)
+    if (pl.col == Set::kFusedCol && cfg.prologue && !cfg.store_last && !cfg.active &&
+        a0.scheme == SCHEME_RK443 && cfg.nsteps > 0) {
+      launch_k(fused128_kernel<>, (unsigned)(2 * a0.batch), Fused128::THREADS, Fused128::smem, cfg.st, cfg.pdl, a0,
+               cfg.nsteps);
+      return 1;
+    }
+  }
   if (cfg.prologue) {
     Set::row(rv, a0, 4, 1, cfg.st, cfg.pdl);
     ++launches;
