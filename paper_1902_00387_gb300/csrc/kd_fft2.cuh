@@ -143,7 +143,9 @@ __device__ __forceinline__ void fft2_3(cx<T> (&v)[3][Split<N>::R1], int a, const
 
 // One-component transform (the component-split kernels): the same passes as fft2_3 with
 // S(q, a2) the slot of matrix element (q, a2) of this thread's transform.
-template <typename T, int N, int DIR, class Slot>
+// WARP: the R2 lanes of every transform are consecutive threads of one warp and the
+// slots are the transform's own, so a warp barrier orders the exchange (no block barrier).
+template <typename T, int N, int DIR, class Slot, bool WARP = false>
 __device__ __forceinline__ void fft2_1(cx<T> (&v)[Split<N>::R1], int a, const cx<T>* tw, Slot S) {
   constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2, J = R1 / R2;
   dft_dif<T, R1, DIR>(v);
@@ -156,7 +158,10 @@ __device__ __forceinline__ void fft2_1(cx<T> (&v)[Split<N>::R1], int a, const cx
     }
     *S(q, a) = y;
   }
-  __syncthreads();
+  if (WARP)
+    __syncwarp();
+  else
+    __syncthreads();
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int q = a + R2 * j;

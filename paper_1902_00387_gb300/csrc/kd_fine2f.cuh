@@ -19,8 +19,10 @@
 // Before the first step the row pass transforms X (the prologue of the two-kernel path).
 // Rows of different blocks are disjoint, and columns within a block are disjoint, so
 // the passes need no barrier between their reads and writes of B.  The transforms are
-// the one-component register FFT of kd_fft2.cuh, one component at a time.  Their shared
-// exchange slots are one scratch area that the row and column passes reuse.
+// the one-component register FFT of kd_fft2.cuh, one component at a time.  Each transform
+// has its own shared exchange slots (the row and column passes reuse them), and its 8
+// lanes are one warp's consecutive threads, so its exchange needs only warp barriers: the
+// only block-wide barriers of a stage are the two cluster barriers.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -88,13 +90,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Fused128::THREADS, 1
   };
   cx<T> v[3][R1];
 
-  // one-component transforms of v[0..2] through this thread's exchange slots
+  // one-component transforms of v[0..2] through this transform's own exchange slots: its 8
+  // lanes are consecutive threads of one warp, so warp barriers order the exchange
   auto transform3 = [&](auto dir) {
     constexpr int DIR = decltype(dir)::value;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      fft2_1<T, N, DIR>(v[c], lane, s_tw, S);
-      __syncthreads();   // the slots are written again by the next component
+      fft2_1<T, N, DIR, decltype(S), true>(v[c], lane, s_tw, S);
+      __syncwarp();   // the slots are written again by the next component
     }
   };
   // inverse x transform of v (kept kx in input order) and its store into both halves
