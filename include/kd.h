@@ -368,6 +368,14 @@ enum { KD_GEMM_TCGEN05 = 0, KD_GEMM_MMA_SYNC = 1 };
 kd_status kd_gemm_bf16_tn(const void* A, const void* Bt, float* C, int M, int N, int K, int ldc, int engine,
                           void* cuda_stream);
 
+/* CUDA graphs for the Parareal fine sweeps of the FFT operator (default on; not used
+ * with kd_set_overlap's pipelined iterations): the ~8 S launches of one sweep shape
+ * (first slice, slices, steps, step, form, launch plan) are captured once into a graph
+ * and replayed on a stream of the context, fenced by events against the context stream;
+ * any device allocation of the context invalidates the captured graphs.  Off: direct
+ * launches.  Same values either way. */
+kd_status kd_set_graphs(kd_ctx* ctx, int enable);
+
 /* Engine of the GEMMs in kd_learned_train / kd_learned_loss_grad (default KD_GEMM_TCGEN05). */
 kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine);
 

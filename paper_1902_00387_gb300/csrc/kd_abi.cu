@@ -53,6 +53,7 @@ kd_status dalloc(kd_ctx* ctx, void** p, size_t bytes, const char* what) {
                                     cudaGetErrorString(e));
   }
   ctx->allocs.push_back(*p);
+  ++ctx->alloc_gen;
   return KD_OK;
 }
 
@@ -453,7 +454,64 @@ kd_status ensure_conv_tmp(kd_ctx* ctx, size_t bytes) {
 
 // Parallel fine step over slices [first, N): Fv[n] = F(U[n]), directly or in the
 // increment form Fv[n] += F(U[n] - Uprev[n]) (iter > 1).
+static kd_status fine_sweep_launches(kd_ctx* ctx, int first, int N, int S, double dt, int iter);
+
+// The FFT operator's fine sweep is ~8 S + 3 launches; with graphs on, the launches of
+// one sweep shape are captured once into a CUDA graph (programmatic dependent launches
+// included) and replayed; the values are those of the direct launches.
 kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
+  // (not for the pipelined iterations: their chunks already interleave with the serial
+  // sweep on separate streams)
+  if (!ctx->graphs || ctx->prof || ctx->overlap > 0 || conv_op(ctx) || N - first <= 0)
+    return fine_sweep_launches(ctx, first, N, S, dt, iter);
+  // the allocations the sweep may make happen before the capture
+  {
+    FineArgs a0 = fine_args(ctx, ctx->ws_f, ctx->tab_f, ctx->p.n, N - first, dt, ctx->t0f + first);
+    kd_status s0 = with_phases(ctx, ctx->ws_f, a0, S);
+    if (s0 != KD_OK) return s0;
+  }
+  long long dbits;
+  memcpy(&dbits, &dt, 8);
+  const auto key = std::make_tuple(first, N, S, dbits, iter == 1 ? 1 : 0, ctx->plan[0].col * 64 + ctx->plan[0].row,
+                                   ctx->pdl, ctx->p.fine_form, ctx->alloc_gen);
+  // the graph runs on the context's own capturable stream, ordered after the work
+  // enqueued on ctx->st and before what follows there
+  if (!ctx->st_g) {
+    KD_CUDA(cudaStreamCreateWithFlags(&ctx->st_g, cudaStreamNonBlocking), "graph stream");
+    for (cudaEvent_t& e : ctx->gev) KD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "graph event");
+  }
+  auto it = ctx->gcache.find(key);
+  if (it == ctx->gcache.end()) {
+    const long long l0 = ctx->launches;
+    cudaGraph_t g = nullptr;
+    cudaStream_t user = ctx->st;
+    KD_CUDA(cudaStreamBeginCapture(ctx->st_g, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->st = ctx->st_g;
+    const kd_status s = fine_sweep_launches(ctx, first, N, S, dt, iter);
+    ctx->st = user;
+    const cudaError_t e = cudaStreamEndCapture(ctx->st_g, &g);
+    if (s != KD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    KD_CUDA(e, "end capture");
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    KD_CUDA(ei, "graph instantiate");
+    it = ctx->gcache.emplace(key, kd_ctx::GraphEntry{ge, ctx->launches - l0}).first;
+    ctx->launches = l0;
+  }
+  KD_CUDA(cudaEventRecord(ctx->gev[0], ctx->st), "graph fence");
+  KD_CUDA(cudaStreamWaitEvent(ctx->st_g, ctx->gev[0], 0), "graph fence");
+  KD_CUDA(cudaGraphLaunch(it->second.exec, ctx->st_g), "graph launch");
+  KD_CUDA(cudaEventRecord(ctx->gev[1], ctx->st_g), "graph fence");
+  KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->gev[1], 0), "graph fence");
+  ctx->launches += it->second.launches;
+  return KD_OK;
+}
+
+static kd_status fine_sweep_launches(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
   const int n = ctx->p.n, pf = ctx->p.prec_fine;
   const long b = N - first;
   if (b <= 0) return KD_OK;
@@ -748,6 +806,13 @@ kd_status kd_destroy(kd_ctx* ctx) {
   }
   for (cudaEvent_t e : ctx->pev2) cudaEventDestroy(e);
   if (ctx->host_scal) cudaFreeHost(ctx->host_scal);
+  for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.second.exec);
+  if (ctx->st_g) {
+    cudaStreamSynchronize(ctx->st_g);
+    cudaStreamDestroy(ctx->st_g);
+  }
+  for (cudaEvent_t e : ctx->gev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return KD_OK;
 }

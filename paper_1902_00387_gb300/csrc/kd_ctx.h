@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 
 #include <string>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/kd.h"
@@ -46,6 +48,18 @@ struct kd_ctx {
   // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)
   int overlap = 0;
   int coarse_cluster = 0;          // blocks per cluster of the coarse solver (0: default)
+  // captured CUDA graphs of the Parareal fine sweep (kd_set_graphs), keyed by the sweep's
+  // shape and launch plan and by the allocation generation (any device allocation or
+  // free invalidates them)
+  int graphs = 1;
+  unsigned long long alloc_gen = 0;
+  cudaStream_t st_g = nullptr;     // the graphs run here (a capturable stream), fenced by gev
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::map<std::tuple<int, int, int, long long, int, int, int, int, unsigned long long>, GraphEntry> gcache;
   int gemm_engine = 0;             // learned-operator training GEMM: KD_GEMM_TCGEN05 (0) or KD_GEMM_MMA_SYNC
   int coarse_sync = 0;             // coarse solver halo exchange: KD_SYNC_CLUSTER (0) or KD_SYNC_P2P
   cudaStream_t st2 = nullptr;      // fine chunks (lowest priority)

@@ -201,6 +201,12 @@ kd_status kd_set_coarse_cluster(kd_ctx* ctx, int blocks) {
   return KD_OK;
 }
 
+kd_status kd_set_graphs(kd_ctx* ctx, int enable) {
+  if (!ctx) return KD_EINVAL;
+  ctx->graphs = enable ? 1 : 0;
+  return KD_OK;
+}
+
 kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine) {
   if (!ctx) return KD_EINVAL;
   if (engine != KD_GEMM_TCGEN05 && engine != KD_GEMM_MMA_SYNC)

@@ -321,3 +321,31 @@ def test_resume_needs_the_increment_form(kd):
             kd.kd_parareal_resume(ctx, u, 0, C1["T"], C1["N"], 2, 0.0)
     finally:
         kd.kd_destroy(ctx)
+
+
+@pytest.mark.parametrize("overlap", [0])
+def test_captured_graphs_give_the_direct_launch_values(kd, overlap):
+    """The fine sweeps replayed from captured CUDA graphs give the iterates and defects
+    of the direct launches bit for bit, also when the same graphs are replayed by a
+    second solve."""
+    n, N, T = 64, 16, 4.0
+    b0 = I.initial_field(n, 0.57, 31)
+    outs = []
+    for graphs in (False, True, True):
+        p = kd.make_params(O.GALLOWAY_PROCTOR, n, 0.57, 100.0, 5e-3, kd.KD_C64, n_coarse=64, dt_coarse=2.0 / 64,
+                           prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
+        ctx = kd.kd_create(p)
+        try:
+            kd.kd_set_graphs(ctx, graphs)
+            kd.kd_set_overlap(ctx, overlap)
+            u = np.zeros((N + 1, 3, n, n), np.complex128)
+            kd.kd_parareal_run(ctx, b0, T, N, 6, 0.0, u)
+            u2 = np.zeros_like(u)
+            s, st = kd.kd_parareal_run(ctx, b0, T, N, 6, 0.0, u2)      # the cached graphs again
+            assert np.array_equal(u, u2)
+            outs.append((u2, [st.sigma[k] for k in range(6)]))
+        finally:
+            kd.kd_destroy(ctx)
+    for u, sig in outs[1:]:
+        assert np.array_equal(u, outs[0][0])
+        assert sig == outs[0][1]
