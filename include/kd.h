@@ -228,7 +228,7 @@ kd_status kd_growth_rate(kd_ctx* ctx, const double* u_slices, int n_samples, dou
  * length slice_T starts at phase p when it starts at t = p slice_T).  Operators are
  * stored in BF16 as [Re W; Im W] ([2 nc][nc]) and applied with FP32 accumulation.
  * Vectors on the set ("learned vectors") are device complex FP32 [3][m][m] (ky-major),
- * interleaved (re, im).  The fine solution is the judge: pairs (x, F x) come from the
+ * interleaved (re, im).  The fine solution decides: pairs (x, F x) come from the
  * fine propagator, and kd_learned_eval compares W_p and the classical coarse
  * propagator against them; phases whose operator loses fall back to the classical one.
  * ------------------------------------------------------------------------------------ */

@@ -152,7 +152,7 @@ def test_training_reduces_error_below_classical(kd):
         kd.kd_learned_init(ctx, N_PHASE, SLICE)
         loss = _train(kd, ctx, 256, 10_000)
         assert np.all(loss[:, -1] < 0.1 * loss[:, 0])
-        # held-out pairs from the same distribution: the fine solution is the judge
+        # held-out pairs from the same distribution: the fine solution decides
         n = 8 * N_PHASE
         xv = learned_inputs(range(50_000, 50_000 + n)).astype(np.complex64)
         ph = np.arange(n) % N_PHASE
@@ -172,7 +172,7 @@ def test_parareal_gain_of_learned_coarse_propagator(kd):
     # with 5 RK443 steps of pi/40 per slice (cheap and crude), the learned one as a single
     # BF16 matrix fitted to fine-propagator pairs (1400 per phase, more than the 1323
     # unknowns per row) and started from that classical matrix.  The fine solution is
-    # the judge: the learned operator is more accurate on held-out pairs, Parareal needs
+    # the measure: the learned operator is more accurate on held-out pairs, Parareal needs
     # fewer iterations with it, and both reproduce the fine solution.
     import torch
     T, N, m21, dtc = 2 * np.pi, 16, 21, 0.08
