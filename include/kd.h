@@ -42,7 +42,7 @@ typedef enum {
   KD_ENOTCONV = 4,      /* Parareal reached k_max with sigma > tol (results still written) */
   KD_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
   KD_ENONFINITE = 6,    /* NaN or Inf met in a norm */
-  KD_EUNSUPPORTED = 7   /* valid request this build does not implement */
+  KD_EUNSUPPORTED = 7   /* valid request the library does not implement */
 } kd_status;
 
 enum { KD_FLOW_ROBERTS = 0, KD_FLOW_GALLOWAY_PROCTOR = 1, KD_FLOW_NONE = 2 };
