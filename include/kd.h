@@ -138,6 +138,8 @@ typedef struct {
   double ms_coarse;                    /* serial coarse sweeps incl. the initial one */
   int fallback_used;                   /* learned coarse propagator replaced by the classical one */
   long long n_launches;                /* kernels launched by this call */
+  double true_err[KD_MAX_ITERS];       /* with kd_set_reference: |U^k_N - b_ref| / |b_ref| after
+                                          iteration k (index k - 1); -1 otherwise */
 } kd_parareal_stats;
 
 /* Parareal (Sec. 3, Eq. 8; Algorithms of Sec. 4.1) over [0, T] with n_slices slices
@@ -152,6 +154,14 @@ typedef struct {
  * Synchronous.  Returns KD_ENOTCONV if tol was not reached (outputs still valid). */
 kd_status kd_parareal_run(kd_ctx* ctx, const double* b0, double T, int n_slices, int k_max,
                           double tol, double* u_slices, kd_parareal_stats* stats);
+
+/* Reference field for the relative error of every Parareal iterate (Sec. 5.1 measures
+ * solutions by their relative error against a reference solution; here next to the
+ * defect of Eq. 9): b_ref (complex128 [3][n][n], host or device), e.g. the serial fine
+ * solution at t = T from kd_fine_serial; kd_parareal_run then fills stats->true_err with
+ * |U^k_N - b_ref| / |b_ref| (last slice, FP64, fixed-order reduction).  Not computed by
+ * the pipelined iterations.  NULL removes the reference.  Synchronous. */
+kd_status kd_set_reference(kd_ctx* ctx, const double* b_ref);
 
 /* Checkpoint / resume of kd_parareal_run: continue Parareal from the iterate U^{k_done}
  * of an earlier run (u_init, complex128 [n_slices+1][3][n][n], host or device, e.g. the

@@ -774,13 +774,13 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   if ((s = make_tables(ctx, ctx->tab_f, params->n, params->prec_fine)) != KD_OK ||
       (s = make_tables(ctx, ctx->tab_c, params->n_coarse, params->prec_coarse)) != KD_OK ||
       (s = dalloc(ctx, (void**)&ctx->partials, 2 * 1024 * 8, "partials")) != KD_OK ||
-      (s = dalloc(ctx, (void**)&ctx->scal, 16 * 8, "scalars")) != KD_OK ||
+      (s = dalloc(ctx, (void**)&ctx->scal, 32 * 8, "scalars")) != KD_OK ||
       (s = dalloc(ctx, (void**)&ctx->Ebuf, (KD_MAX_SLICES + 1) * 8, "energies")) != KD_OK) {
     fprintf(stderr, "kd_create: %s\n", ctx->err.c_str());
     kd_destroy(ctx);
     return s;
   }
-  if (cudaMallocHost((void**)&ctx->host_scal, 16 * 8) != cudaSuccess) {
+  if (cudaMallocHost((void**)&ctx->host_scal, 32 * 8) != cudaSuccess) {
     kd_destroy(ctx);
     return KD_ENOMEM;
   }
@@ -935,7 +935,7 @@ static kd_status parareal_core(kd_ctx* ctx, const double* b0, const double* u_in
   if ((s = coarse_phases(ctx, N, Sc, dtc)) != KD_OK) return s;
   float ms_fine = 0.f, ms_coarse = 0.f;
   int k_done = u_init ? k0 : 0, conv = 0;
-  std::vector<double> sig(u_init ? k0 : 0, 0.0);
+  std::vector<double> sig(u_init ? k0 : 0, 0.0), terr(u_init ? k0 : 0, -1.0);
   if (ctx->overlap > 0 && N >= 2 && !u_init) {
     // the sweeps run on the high-priority stream, ordered after the caller's stream
     cudaStream_t user = ctx->st;
@@ -995,9 +995,17 @@ static kd_status parareal_core(kd_ctx* ctx, const double* b0, const double* u_in
       if ((s = use_learned(ctx, i) ? learned_step(ctx, i, false, i == N - 1)
                                    : coarse_step(ctx, i, Sc, dtc, false, i == N - 1)) != KD_OK)
         return s;
+    if (ctx->ref_T) {
+      // error of the last slice against the reference (scal[16])
+      const int nbr = rel_error_partials(ctx->U + 2 * (long)N * len, ctx->ref_T, len, ctx->partials, ctx->st);
+      if (nbr < 0) return fail(ctx, KD_ECUDA, "reference error launch failed");
+      KD_LAUNCH(finish_sigma(ctx->partials, nbr, ctx->scal + 16, ctx->st), "reference error");
+      KD_CUDA(cudaMemcpyAsync(ctx->host_scal + 16, ctx->scal + 16, 8, cudaMemcpyDeviceToHost, ctx->st), "error copy");
+    }
     KD_CUDA(cudaMemcpyAsync(ctx->host_scal, ctx->scal, 8, cudaMemcpyDeviceToHost, ctx->st), "sigma copy");
     KD_CUDA(cudaEventRecord(ctx->ev[3], ctx->st), "event");
     KD_CUDA(cudaEventSynchronize(ctx->ev[3]), "sync");
+    if (ctx->ref_T) terr.push_back(ctx->host_scal[16]);
     if (ctx->prof) prof_flush(ctx);
     float m1 = 0.f, m2 = 0.f;
     cudaEventElapsedTime(&m1, ctx->ev[1], ctx->ev[2]);
@@ -1038,6 +1046,7 @@ static kd_status parareal_core(kd_ctx* ctx, const double* b0, const double* u_in
     stats->dt_fine_used = dt;
     stats->dt_coarse_used = dtc;
     for (size_t i = 0; i < sig.size() && i < KD_MAX_ITERS; ++i) stats->sigma[i] = sig[i];
+    for (int i = 0; i < KD_MAX_ITERS; ++i) stats->true_err[i] = i < (int)terr.size() ? terr[i] : -1.0;
     KD_CUDA(cudaMemcpy(stats->energy, ctx->Ebuf, (N + 1) * 8, cudaMemcpyDeviceToHost), "energy copy");
     double fit[2];
     KD_CUDA(cudaMemcpy(fit, ctx->scal + 4, 16, cudaMemcpyDeviceToHost), "fit copy");
@@ -1051,6 +1060,24 @@ static kd_status parareal_core(kd_ctx* ctx, const double* b0, const double* u_in
     stats->fallback_used = ctx->fallback;
   }
   if (!conv && k_max > k0) return fail(ctx, KD_ENOTCONV, "kd_parareal_run: tol not reached within k_max");
+  return KD_OK;
+}
+
+kd_status kd_set_reference(kd_ctx* ctx, const double* b_ref) {
+  if (!ctx) return KD_EINVAL;
+  if (!b_ref) {
+    dfree(ctx, ctx->ref_T);
+    ctx->ref_T = nullptr;
+    return KD_OK;
+  }
+  const int n = ctx->p.n;
+  const size_t fb = 3UL * n * n * 16;
+  kd_status s;
+  if (!ctx->ref_T && (s = dalloc(ctx, (void**)&ctx->ref_T, (size_t)compact_len(n) * 16, "reference")) != KD_OK) return s;
+  if ((s = ensure_full_tmp(ctx, fb)) != KD_OK) return s;
+  KD_CUDA(cudaMemcpyAsync(ctx->full_tmp, b_ref, fb, cudaMemcpyDefault, ctx->st), "copy reference");
+  KD_LAUNCH(full_to_compact(KD_C128, ctx->full_tmp, KD_C128, ctx->ref_T, 1, n, ctx->st), "reference to compact");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   return KD_OK;
 }
 

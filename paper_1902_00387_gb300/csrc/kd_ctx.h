@@ -60,6 +60,7 @@ struct kd_ctx {
     long long launches;
   };
   std::map<std::tuple<int, int, int, long long, int, int, int, int, unsigned long long>, GraphEntry> gcache;
+  double* ref_T = nullptr;         // kd_set_reference: compact FP64 reference field at t = T
   int gemm_engine = 0;             // learned-operator training GEMM: KD_GEMM_TCGEN05 (0) or KD_GEMM_MMA_SYNC
   int coarse_sync = 0;             // coarse solver halo exchange: KD_SYNC_CLUSTER (0) or KD_SYNC_P2P
   cudaStream_t st2 = nullptr;      // fine chunks (lowest priority)

@@ -86,6 +86,9 @@ int parareal_update(const double* F, const void* g, int pg, double* Gold, double
                     int init, double* partials, cudaStream_t st);
 // sigma = sqrt(sum diff / sum norm) of `nblocks` partial pairs -> out[0]; also the two sums
 int finish_sigma(const double* partials, int nblocks, double* out, cudaStream_t st);
+// partials of |a - ref| / |ref| over len complex FP64 values for finish_sigma; returns the
+// block count (or -1)
+int rel_error_partials(const double* a, const double* ref, long len, double* partials, cudaStream_t st);
 // E[i] = sum |z|^2 over `len` complex128 entries of field i (stride len), i < count
 int energy_kernel(const double* fields, long len, int count, double* E, cudaStream_t st);
 // least-squares slope of 0.5 ln E_i against t_i = i * dt over t_i >= fit_from -> out[0];

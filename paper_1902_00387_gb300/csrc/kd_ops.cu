@@ -247,6 +247,40 @@ __global__ void k_finish_sigma(const double* partials, int nb, double* out) {
   }
 }
 
+// per block: partial sums of |a - r|^2 and |r|^2 (fixed order), for finish_sigma
+__global__ void k_rel_error(const cx<double>* a, const cx<double>* r, long len, double* partials) {
+  __shared__ double s_d[256], s_n[256];
+  double d = 0.0, nn = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < len; i += (long)gridDim.x * blockDim.x) {
+    const cx<double> x = a[i], y = r[i];
+    const double dx = x.x - y.x, dy = x.y - y.y;
+    d += dx * dx + dy * dy;
+    nn += y.x * y.x + y.y * y.y;
+  }
+  s_d[threadIdx.x] = d;
+  s_n[threadIdx.x] = nn;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s_d[threadIdx.x] += s_d[threadIdx.x + s];
+      s_n[threadIdx.x] += s_n[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s_d[0];
+    partials[2 * blockIdx.x + 1] = s_n[0];
+  }
+}
+
+int rel_error_partials(const double* a, const double* ref, long len, double* partials, cudaStream_t st) {
+  long nb = (len + 255) / 256;
+  if (nb > 256) nb = 256;
+  if (nb < 1) nb = 1;
+  k_rel_error<<<(unsigned)nb, 256, 0, st>>>((const cx<double>*)a, (const cx<double>*)ref, len, partials);
+  return cudaPeekAtLastError() == cudaSuccess ? (int)nb : -1;
+}
+
 int finish_sigma(const double* partials, int nblocks, double* out, cudaStream_t st) {
   k_finish_sigma<<<1, 256, 0, st>>>(partials, nblocks, out);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

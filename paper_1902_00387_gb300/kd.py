@@ -52,7 +52,8 @@ class kd_parareal_stats(ctypes.Structure):
                 ("dt_coarse_used", ctypes.c_double), ("sigma", ctypes.c_double * KD_MAX_ITERS),
                 ("energy", ctypes.c_double * (KD_MAX_SLICES + 1)), ("growth_rate", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_fine", ctypes.c_double), ("ms_coarse", ctypes.c_double),
-                ("fallback_used", ctypes.c_int), ("n_launches", ctypes.c_longlong)]
+                ("fallback_used", ctypes.c_int), ("n_launches", ctypes.c_longlong),
+                ("true_err", ctypes.c_double * KD_MAX_ITERS)]
 
 
 class kd_instance(ctypes.Structure):
@@ -81,7 +82,8 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_get_plan", "kd_autotune", "kd_sweep_run", "kd_set_dependent_launch", "kd_block_init",
            "kd_block_boundary_bytes", "kd_block_set_initial", "kd_block_set_boundary", "kd_block_get_boundary",
            "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
-           "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_parareal_resume", "kd_set_graphs", "kd_set_overlap", "kd_set_coarse_cluster",
+           "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_parareal_resume", "kd_set_graphs",
+           "kd_set_reference", "kd_set_overlap", "kd_set_coarse_cluster",
            "kd_set_coarse_sync"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
@@ -131,6 +133,7 @@ def load():
         "kd_learned_set": (I, [P, I, P, I]),
         "kd_selftest_wait": (I, [I, D, P]),
         "kd_set_graphs": (I, [P, I]),
+        "kd_set_reference": (I, [P, P]),
         "kd_parareal_resume": (I, [P, P, I, D, I, I, D, P, ctypes.POINTER(kd_parareal_stats)]),
         "kd_block_init": (I, [P, I, I, D, I]),
         "kd_block_boundary_bytes": (ctypes.c_size_t, [P]),
@@ -478,6 +481,12 @@ def _any_ptr_raw(x):
 def kd_selftest_wait(arrive, max_ms=1.0):
     """Bounded-wait self-test; returns the status (KD_OK or KD_ETIMEOUT)."""
     return load().kd_selftest_wait(int(bool(arrive)), float(max_ms), _current_stream())
+
+
+def kd_set_reference(ctx, b_ref):
+    """Reference field at t = T (complex128 [3][n][n], host or device; None removes it)
+    for stats.true_err of kd_parareal_run."""
+    return _check(ctx, load().kd_set_reference(ctx, _any_ptr(b_ref, "complex128") if b_ref is not None else None))
 
 
 def kd_set_graphs(ctx, enable):

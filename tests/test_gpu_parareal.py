@@ -349,3 +349,34 @@ def test_captured_graphs_give_the_direct_launch_values(kd, overlap):
     for u, sig in outs[1:]:
         assert np.array_equal(u, outs[0][0])
         assert sig == outs[0][1]
+
+
+def test_true_error_against_a_reference(kd):
+    """stats.true_err[k - 1] is the relative distance of the k-th iterate's last slice to
+    the reference set by kd_set_reference (here the serial fine solution): every entry
+    equals the distance of the final slice of a run stopped after k iterations, it is 0
+    at k = N (Parareal is then the serial fine run), and -1 without a reference."""
+    b0 = I.initial_field(C1["n"], C1["kz"], 4)
+    N = C1["N"]
+    ctx = c1_ctx(kd)
+    try:
+        ser = np.zeros((N + 1, 3, C1["n"], C1["n"]), np.complex128)
+        kd.kd_fine_serial(ctx, b0, C1["T"], N, ser)
+        kd.kd_set_reference(ctx, ser[-1])
+        dist = []
+        for k in (1, 2, 3):
+            par = np.zeros_like(ser)
+            kd.kd_parareal_run(ctx, b0, C1["T"], N, k, 0.0, par)
+            dist.append(rel(par[-1], ser[-1]))
+        _, st = kd.kd_parareal_run(ctx, b0, C1["T"], N, 3, 0.0)
+        te = [st.true_err[i] for i in range(kd.KD_MAX_ITERS)]
+        assert all(e == -1.0 for e in te[3:])
+        for k in range(3):
+            assert dist[k] > 0 and abs(te[k] - dist[k]) <= 1e-9 * dist[k], k
+        _, st = kd.kd_parareal_run(ctx, b0, C1["T"], N, N, 0.0)
+        assert st.true_err[N - 1] == 0.0
+        kd.kd_set_reference(ctx, None)
+        _, st = kd.kd_parareal_run(ctx, b0, C1["T"], N, 2, 0.0)
+        assert st.true_err[0] == -1.0 and st.true_err[1] == -1.0
+    finally:
+        kd.kd_destroy(ctx)
