@@ -846,6 +846,11 @@ def main():
     solve(b0_dev, u_dev)
     torch.cuda.synchronize()
     err = (torch.linalg.norm(u_dev[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
+    # error of every iterate against the serial fine solution (untimed solve)
+    kd.kd_set_reference(ctx, ser[-1])
+    st_ref = solve(b0_dev, u_dev)
+    kd.kd_set_reference(ctx, None)
+    true_err = [float(st_ref.true_err[i]) for i in range(st_ref.k_con)]
 
     # ---- roofline of the dominant fine kernel, from the live event timing
     hbm_peak, peak_kind = peaks()
@@ -879,8 +884,8 @@ def main():
                        fine_plan_ms_per_step=tune_ms),
         "time_to_solution_ms": ms_per_step, "serial_fine_ms": serial_ms,
         "speedup_vs_serial_fine": serial_ms / ms_per_step, "k_con": st.k_con,
-        "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "growth_rate": st.growth_rate,
-        "fine_mdof_steps_per_s": fine_rate,
+        "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "true_err_by_iteration": true_err,
+        "growth_rate": st.growth_rate, "fine_mdof_steps_per_s": fine_rate,
         "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
         "roofline": ({"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
                       "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
