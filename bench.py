@@ -81,6 +81,23 @@ def oracle_sample(nsteps):
     return 3 * n * n * nsteps / el / 1e6, el
 
 
+def oracle_extrapolated(n, kz, Rm, dt, S, N, nsteps):
+    """The oracle's fine propagator timed for `nsteps` steps of one GP slice of an n^2
+    workload whose full CPU run is out of reach, and the serial fine run of S steps x N
+    slices that this time per step implies (reported as extrapolated)."""
+    import kd_inputs
+    from oracle import kd_oracle as O
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    b = kd_inputs.initial_field(n, kz, 0)
+    O.propagate(b, prob, 0.0, dt, 1)
+    t = time.perf_counter()
+    O.propagate(b, prob, 0.0, dt, nsteps)
+    per = (time.perf_counter() - t) / nsteps
+    return {"value": 3 * n * n / per / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": "%d RK443 fine steps of one %d^2 GP slice, numpy FP64 oracle, %.3f s per step" % (nsteps, n, per),
+            "serial_fine_s_extrapolated": per * S * N}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -269,6 +286,8 @@ def run_learned(args):
                     "pairs_s": t_pairs, "train_s": t_train},
     })
     out["value"] = ms_l
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_extrapolated(n, W["kz"], W["Rm"], dt, W["fine_steps_per_slice"], N, 4)
     print(json.dumps(out), flush=True)
 
 
@@ -529,6 +548,8 @@ def run_large(args):
                      "peak": hbm_peak, "unit": "GB/s", "frac": k_ach / hbm_peak, "traffic": None,
                      "peak_kind": peak_kind, "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid])},
         "clocks": clk, "gpu_launches": int(st.n_launches),
+        "cpu_baseline": (None if args.no_cpu_baseline else
+                         oracle_extrapolated(n, W["kz"], W["Rm"], T / N / S, S, N, 2)),
     }
     print(json.dumps(out), flush=True)
     kd.kd_destroy(ctx)
