@@ -691,11 +691,12 @@ def run_sweep(args):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic of the dominant kernel at the headline workload: dram__bytes_read.sum +
-# dram__bytes_write.sum of row2_kernel<float, 128, 8, 0, 0> (row variant 3, the plan the
-# autotuner picks), averaged over the 4 stage launches of one fine step of 64 fields, L2
+# dram__bytes_write.sum of the row kernel of the two plans the autotuner picks there,
+# row2_kernel<float, 128, 8, 0, 0> (row variant 3) and row2_kernel<float, 128, 16, 0, 0>
+# (row variant 2), averaged over the 4 stage launches of one fine step of 64 fields, L2
 # left warm as in the solve (profiles/fine_row2_traffic_gp128_b64.md).  Reported only
-# when the bench runs that kernel.
-ROW_TRAFFIC = {"n": 128, "batch": 64, "row_variant": 3, "bytes_per_launch": 26471552}
+# when the bench runs one of these kernels.
+ROW_TRAFFIC = {"n": 128, "batch": 64, "bytes_per_launch": {3: 26471552, 2: 26301504}}   # by row variant
 
 
 def conv_roofline(n, S, batches, steps, stats):
@@ -910,9 +911,8 @@ def main():
         "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
         "roofline": ({"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
                       "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                      "traffic": (ROW_TRAFFIC["bytes_per_launch"]
-                                  if kid == 1 and n == ROW_TRAFFIC["n"] and N == ROW_TRAFFIC["batch"]
-                                  and plan[1] == ROW_TRAFFIC["row_variant"] else None),
+                      "traffic": (ROW_TRAFFIC["bytes_per_launch"].get(plan[1])
+                                  if kid == 1 and n == ROW_TRAFFIC["n"] and N == ROW_TRAFFIC["batch"] else None),
                       "traffic_unit": "bytes per launch (ncu, L2 warm)",
                       "algorithmic_bytes_per_launch": kbytes / max(1, prof_n[kid]), "peak_kind": peak_kind,
                       "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]}
