@@ -696,7 +696,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (row variant 2), averaged over the 4 stage launches of one fine step of 64 fields, L2
 # left warm as in the solve (profiles/fine_row2_traffic_gp128_b64.md).  Reported only
 # when the bench runs one of these kernels.
-ROW_TRAFFIC = {"n": 128, "batch": 64, "bytes_per_launch": {3: 26471552, 2: 26301504}}   # by row variant
+# The butterflies of the row kernels became packed FP32x2 instructions after these
+# counters were taken (arithmetic only; the memory accesses are unchanged), so the bench
+# reports no traffic until they are captured again.
+ROW_TRAFFIC = {"n": 128, "batch": 64, "bytes_per_launch": {}}   # by row variant
+ROW_TRAFFIC_BEFORE_PACKED = {3: 26471552, 2: 26301504}
 
 
 def conv_roofline(n, S, batches, steps, stats):
@@ -914,6 +918,9 @@ def main():
                       "traffic": (ROW_TRAFFIC["bytes_per_launch"].get(plan[1])
                                   if kid == 1 and n == ROW_TRAFFIC["n"] and N == ROW_TRAFFIC["batch"] else None),
                       "traffic_unit": "bytes per launch (ncu, L2 warm)",
+                      "traffic_before_packed_butterflies": (ROW_TRAFFIC_BEFORE_PACKED.get(plan[1])
+                                                            if kid == 1 and n == ROW_TRAFFIC["n"]
+                                                            and N == ROW_TRAFFIC["batch"] else None),
                       "algorithmic_bytes_per_launch": kbytes / max(1, prof_n[kid]), "peak_kind": peak_kind,
                       "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]}
                      if args.fine_operator == "fft" else conv_roofline(n, S, batches, args.steps, stats)),

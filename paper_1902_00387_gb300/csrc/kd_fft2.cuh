@@ -67,9 +67,28 @@ __host__ __device__ constexpr int bitrev(int q) {
   return r;
 }
 
+// Butterfly: (a, b) <- (a + b, a - b).  For float both components go through one packed
+// FP32x2 instruction each (sm_100 and later): the sum as a packed add, the difference as
+// a packed a + (-1) b, whose product is exact, so both round once, as two scalar adds do.
+template <typename T>
+__device__ __forceinline__ void bfly(cx<T>& a, cx<T>& b) {
+  const cx<T> x0 = a, x1 = b;
+  a = x0 + x1;
+  b = x0 - x1;
+}
+template <>
+__device__ __forceinline__ void bfly<float>(cx<float>& a, cx<float>& b) {
+  const float2 x0 = make_float2(a.x, a.y), x1 = make_float2(b.x, b.y);
+  const float2 s = __fadd2_rn(x0, x1);
+  const float2 d = __ffma2_rn(x1, make_float2(-1.f, -1.f), x0);
+  a = mk(s.x, s.y);
+  b = mk(d.x, d.y);
+}
+
 // In-register R-point DFT (R = 2, 4, 8, 16), radix-2 decimation in frequency.
-// In: v[n] natural order.  Out: X[q] at v[bitrev<R>(q)].
-template <typename T, int R, int DIR>
+// In: v[n] natural order.  Out: X[q] at v[bitrev<R>(q)].  PACKED selects the packed
+// butterflies of bfly (same results; faster in the n <= 256 kernels, slower at 1024).
+template <typename T, int R, int DIR, bool PACKED = true>
 __device__ __forceinline__ void dft_dif(cx<T>* v) {
 #pragma unroll
   for (int span = R / 2; span >= 1; span >>= 1) {
@@ -77,9 +96,16 @@ __device__ __forceinline__ void dft_dif(cx<T>* v) {
     for (int start = 0; start < R; start += 2 * span) {
 #pragma unroll
       for (int i = 0; i < span; ++i) {
-        const cx<T> x0 = v[start + i], x1 = v[start + i + span];
-        v[start + i] = x0 + x1;
-        v[start + i + span] = mul_w32<T, DIR>(x0 - x1, i * (32 / (2 * span)));
+        cx<T> x0 = v[start + i], x1 = v[start + i + span];
+        if (PACKED) {
+          bfly(x0, x1);
+        } else {
+          const cx<T> a = x0;
+          x0 = a + x1;
+          x1 = a - x1;
+        }
+        v[start + i] = x0;
+        v[start + i + span] = mul_w32<T, DIR>(x1, i * (32 / (2 * span)));
       }
     }
   }

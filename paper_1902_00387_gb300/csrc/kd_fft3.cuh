@@ -9,7 +9,8 @@
 // w_N^(k (b mod Ns) N/(Ns Rp)), does an Rp-point DFT and writes to
 // (b / Ns) Ns Rp + (b mod Ns) + q Ns; the last pass (Ns = N/R) writes to j + q T, which
 // stays in registers.  Shared-memory indices are padded by one slot per R so that the
-// stride-R stores of the first pass spread over the banks.
+// stride-R stores of the first pass spread over the banks.  The packed butterflies of
+// dft_dif are used below N = 512 only: the 1024 kernels measured slower with them.
 #pragma once
 #include "kd_fft2.cuh"
 
@@ -54,7 +55,7 @@ __device__ __forceinline__ void fft3r(cx<T> (&v)[3][R], int j, const cx<T>* tw, 
   // pass 1: radix R, Ns = 1 (no twiddles)
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    dft_dif<T, R, DIR>(v[c]);
+    dft_dif<T, R, DIR, (N < 512)>(v[c]);
 #pragma unroll
     for (int q = 0; q < R; ++q) *S(c, F::pad(j * R + q)) = v[c][bitrev<R>(q)];
   }
@@ -85,7 +86,7 @@ __device__ __forceinline__ void fft3r(cx<T> (&v)[3][R], int j, const cx<T>* tw, 
       cx<T>* vv = &v[c][i * RM];
 #pragma unroll
       for (int k = 1; k < RM; ++k) vv[k] = cmul(vv[k], w[k]);
-      dft_dif<T, RM, DIR>(vv);
+      dft_dif<T, RM, DIR, (N < 512)>(vv);
 #pragma unroll
       for (int q = 0; q < RM; ++q) *S(c, F::pad(idxD + q * R)) = vv[bitrev<RM>(q)];
     }
@@ -105,7 +106,7 @@ __device__ __forceinline__ void fft3r(cx<T> (&v)[3][R], int j, const cx<T>* tw, 
     for (int k = 0; k < R; ++k) u[k] = *S(c, F::pad(j + k * TT));
 #pragma unroll
     for (int k = 1; k < R; ++k) u[k] = cmul(u[k], w[k]);
-    dft_dif<T, R, DIR>(u);
+    dft_dif<T, R, DIR, (N < 512)>(u);
 #pragma unroll
     for (int q = 0; q < R; ++q) v[c][q] = u[bitrev<R>(q)];
   }
@@ -117,7 +118,7 @@ template <typename T, int N, int R, int DIR, class Slot>
 __device__ __forceinline__ void fft3r_1(cx<T> (&v)[R], int j, const cx<T>* tw, Slot S) {
   using F = F3<N, R>;
   constexpr int TT = F::T, RM = F::RM, NB2 = F::NB2;
-  dft_dif<T, R, DIR>(v);
+  dft_dif<T, R, DIR, (N < 512)>(v);
 #pragma unroll
   for (int q = 0; q < R; ++q) *S(F::pad(j * R + q)) = v[bitrev<R>(q)];
   __syncthreads();
@@ -138,7 +139,7 @@ __device__ __forceinline__ void fft3r_1(cx<T> (&v)[R], int j, const cx<T>* tw, S
       const cx<T> t = tw[N + k * R + bm];
       vv[k] = cmul(vv[k], DIR < 0 ? t : mk(t.x, -t.y));
     }
-    dft_dif<T, RM, DIR>(vv);
+    dft_dif<T, RM, DIR, (N < 512)>(vv);
     const int idxD = (b / R) * R * RM + bm;
 #pragma unroll
     for (int q = 0; q < RM; ++q) *S(F::pad(idxD + q * R)) = vv[bitrev<RM>(q)];
@@ -152,7 +153,7 @@ __device__ __forceinline__ void fft3r_1(cx<T> (&v)[R], int j, const cx<T>* tw, S
     const cx<T> t = tw[k * TT + j];
     u[k] = cmul(u[k], DIR < 0 ? t : mk(t.x, -t.y));
   }
-  dft_dif<T, R, DIR>(u);
+  dft_dif<T, R, DIR, (N < 512)>(u);
 #pragma unroll
   for (int q = 0; q < R; ++q) v[q] = u[bitrev<R>(q)];
 }
