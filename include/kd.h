@@ -28,6 +28,8 @@
 #ifndef KD_H_
 #define KD_H_
 
+#include <stddef.h> /* size_t */
+
 #ifdef __cplusplus
 extern "C" {
 #endif
