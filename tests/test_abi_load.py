@@ -79,3 +79,45 @@ def test_struct_layout_matches_header(lib, tmp_path):
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got == want, [(e, g, w) for e, g, w in zip(exprs, got, want) if g != w]
+
+
+def declarations():
+    """(return type, name, [parameter types]) of every function that include/kd.h declares."""
+    src = open(os.path.join(ROOT, "include", "kd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+    out = []
+    for ret, name, args in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(kd_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src):
+        params = [a.strip() for a in args.split(",")] if args.strip() not in ("", "void") else []
+        # drop the parameter name, keep the type
+        types = [re.sub(r"\b[A-Za-z_]\w*$", "", p).strip() if not p.endswith("*") else p for p in params]
+        out.append((" ".join(ret.split()), name, types))
+    return out
+
+
+def c_kind(t):
+    t = t.replace("const", "").strip()
+    if "*" in t:
+        return "ptr"
+    return {"int": "int", "double": "double", "float": "float", "long long": "i64", "size_t": "size",
+            "kd_status": "int"}[" ".join(t.split())]
+
+
+def ctypes_kind(ct):
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_float: "float", ctypes.c_longlong: "i64",
+            ctypes.c_size_t: "size"}[ct]
+
+
+def test_binding_signatures_match_header(lib):
+    """Every entry point's ctypes argument and return types agree with its C declaration
+    (count and kind), so the binding cannot pass an int where the ABI reads a double."""
+    decls = declarations()
+    assert len(decls) == len(declared_symbols())
+    for ret, name, types in decls:
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert [c_kind(t) for t in types] == [ctypes_kind(a) for a in fn.argtypes], name
+        want = "ptr" if "*" in ret else c_kind(ret)
+        assert want == ctypes_kind(fn.restype), (name, ret, fn.restype)
