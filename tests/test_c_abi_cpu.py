@@ -68,3 +68,33 @@ def test_c_program_calls_the_host_entry_points(tmp_path, lib_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.startswith("kd ")
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof and every field offset of the ABI structs, from the C compiler, equal those
+    of the ctypes structures of the binding."""
+    import paper_1902_00387_gb300.kd as K
+    structs = [K.kd_params, K.kd_parareal_stats, K.kd_instance, K.kd_instance_result, K.kd_sweep_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kd.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f in st._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == K.ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert got[(name, f[0])] == getattr(st, f[0]).offset, (name, f[0])
