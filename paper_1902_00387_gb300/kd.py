@@ -214,6 +214,38 @@ def kd_last_error(ctx):
     return load().kd_last_error(ctx).decode()
 
 
+# Grid side of every live context (by address), for the buffer-size checks below: the
+# library takes plain pointers and cannot tell how large a caller's buffer is.
+_CTX_N = {}
+
+
+def _addr(ctx):
+    return ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx
+
+
+def _numel(x):
+    return x.size if isinstance(x, np.ndarray) else x.numel()
+
+
+def _need(ctx, x, fields, what, n=None):
+    """Raise ValueError unless buffer x holds at least `fields` fields [3][n][n] of the
+    context's grid (x may be None where the ABI allows NULL)."""
+    if x is None:
+        return
+    n = n if n is not None else _CTX_N.get(_addr(ctx))
+    if n is None:
+        return
+    want = int(fields) * 3 * n * n
+    if _numel(x) < want:
+        raise ValueError("%s holds %d elements; %d fields of 3 x %d x %d need %d" % (what, _numel(x), fields, n, n,
+                                                                                  want))
+
+
+def _need_count(x, count, what):
+    if x is not None and _numel(x) < int(count):
+        raise ValueError("%s holds %d elements, needs %d" % (what, _numel(x), int(count)))
+
+
 def kd_create(params, stream=None):
     """Create a context; `stream` is a cudaStream_t address (default: torch's current stream)."""
     lib = load()
@@ -222,10 +254,12 @@ def kd_create(params, stream=None):
     s = lib.kd_create(ctypes.byref(params), st, ctypes.byref(out))
     if s != KD_OK:
         raise KdError(s, "kd_create failed")
+    _CTX_N[out.value] = int(params.n)
     return out
 
 
 def kd_destroy(ctx):
+    _CTX_N.pop(_addr(ctx), None)
     return _check(None, load().kd_destroy(ctx))
 
 
@@ -236,6 +270,9 @@ def _cdt(params_prec):
 def kd_fine_batched(ctx, b_in, b_out, t0, nsteps, batch, prec=KD_C64):
     """F: advance `batch` fields [batch][3][n][n] by `nsteps` fine steps (device tensors)."""
     dt = _cdt(prec)
+    _need(ctx, b_in, batch, "b_in")
+    _need(ctx, b_out, batch, "b_out")
+    _need_count(t0, batch, "t0")
     return _check(ctx, load().kd_fine_batched(ctx, _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
                                               int(nsteps), int(batch)))
 
@@ -243,6 +280,9 @@ def kd_fine_batched(ctx, b_in, b_out, t0, nsteps, batch, prec=KD_C64):
 def kd_fine_batched_static(params, b_in, b_out, t0, nsteps, batch, stream=None):
     """Allocation-free fine propagator (workspace in the library's static device array)."""
     dt = _cdt(params.prec_fine)
+    _need(None, b_in, batch, "b_in", n=params.n)
+    _need(None, b_out, batch, "b_out", n=params.n)
+    _need_count(t0, batch, "t0")
     st = _current_stream() if stream is None else stream
     s = load().kd_fine_batched_static(ctypes.byref(params), _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
                                       int(nsteps), int(batch), st)
@@ -253,6 +293,9 @@ def kd_fine_batched_static(params, b_in, b_out, t0, nsteps, batch, stream=None):
 
 def kd_coarse(ctx, b_in, b_out, t0, nsteps, batch):
     """G: restrict, coarse steps, prolong; complex128 device tensors [batch][3][n][n]."""
+    _need(ctx, b_in, batch, "b_in")
+    _need(ctx, b_out, batch, "b_out")
+    _need_count(t0, batch, "t0")
     return _check(ctx, load().kd_coarse(ctx, _ptr(b_in, "complex128"), _ptr(b_out, "complex128"),
                                         _ptr(t0, "float64"), int(nsteps), int(batch)))
 
@@ -266,6 +309,8 @@ def _any_ptr(x, dtype):
 def kd_parareal_run(ctx, b0, T, n_slices, k_max, tol, u_slices=None):
     """Parareal over [0, T]; b0 complex128 [3][n][n] and u_slices complex128
     [n_slices+1][3][n][n] may live on the host or the device.  Returns (status, stats)."""
+    _need(ctx, b0, 1, "b0")
+    _need(ctx, u_slices, n_slices + 1, "u_slices")
     st = kd_parareal_stats()
     s = load().kd_parareal_run(ctx, _any_ptr(b0, "complex128"), float(T), int(n_slices), int(k_max), float(tol),
                                _any_ptr(u_slices, "complex128"), ctypes.byref(st))
@@ -276,6 +321,8 @@ def kd_parareal_run(ctx, b0, T, n_slices, k_max, tol, u_slices=None):
 def kd_parareal_resume(ctx, u_init, k_done, T, n_slices, k_max, tol, u_slices=None):
     """Continue Parareal from the iterate u_init (complex128 [n_slices+1][3][n][n]) of an
     earlier run after k_done iterations.  Returns (status, stats)."""
+    _need(ctx, u_init, n_slices + 1, "u_init")
+    _need(ctx, u_slices, n_slices + 1, "u_slices")
     st = kd_parareal_stats()
     s = load().kd_parareal_resume(ctx, _any_ptr(u_init, "complex128"), int(k_done), float(T), int(n_slices),
                                   int(k_max), float(tol), _any_ptr(u_slices, "complex128"), ctypes.byref(st))
@@ -285,15 +332,20 @@ def kd_parareal_resume(ctx, u_init, k_done, T, n_slices, k_max, tol, u_slices=No
 
 def kd_fine_serial(ctx, b0, T, n_slices, u_slices):
     """Serial fine solution at the slice boundaries (same step rule as kd_parareal_run)."""
+    _need(ctx, b0, 1, "b0")
+    _need(ctx, u_slices, n_slices + 1, "u_slices")
     return _check(ctx, load().kd_fine_serial(ctx, _any_ptr(b0, "complex128"), float(T), int(n_slices),
                                              _any_ptr(u_slices, "complex128")))
 
 
 def kd_energy(ctx, fields, count, energy_out):
+    _need(ctx, fields, count, "fields")
+    _need_count(energy_out, count, "energy_out")
     return _check(ctx, load().kd_energy(ctx, _ptr(fields, "complex128"), int(count), _ptr(energy_out, "float64")))
 
 
 def kd_growth_rate(ctx, u_slices, n_samples, T, fit_from):
+    _need(ctx, u_slices, n_samples, "u_slices")
     rate = ctypes.c_double()
     _check(ctx, load().kd_growth_rate(ctx, _ptr(u_slices, "complex128"), int(n_samples), float(T),
                                       float(fit_from), ctypes.byref(rate)))
@@ -418,6 +470,8 @@ def kd_sweep_run(instances, b0, T, n_slices, k_max, tol, u_final=None, tune_cach
 
 def kd_growth_power(ctx, b0, t0, tau, max_iter, tol, b_out=None):
     """Power-iteration growth rate; returns (status, rate, iterations)."""
+    _need(ctx, b0, 1, "b0")
+    _need(ctx, b_out, 1, "b_out")
     rate, its = ctypes.c_double(), ctypes.c_int()
     s = load().kd_growth_power(ctx, _any_ptr(b0, "complex128"), float(t0), float(tau), int(max_iter), float(tol),
                                ctypes.byref(rate), ctypes.byref(its), _any_ptr(b_out, "complex128"))
@@ -429,6 +483,8 @@ def kd_growth_arnoldi(ctx, b0, t0, tau, m, nev, restarts, tol, b_out=None):
     """Restarted Arnoldi on the fine propagator over [t0, t0 + tau]; returns (status,
     multipliers (complex numpy array [nev], by decreasing modulus), rates ln|mu| / tau,
     restarts used)."""
+    _need(ctx, b0, 1, "b0")
+    _need(ctx, b_out, 1, "b_out")
     mu = np.zeros(2 * int(nev), np.float64)
     rate = np.zeros(int(nev), np.float64)
     its = ctypes.c_int()
@@ -486,6 +542,7 @@ def kd_selftest_wait(arrive, max_ms=1.0):
 def kd_set_reference(ctx, b_ref):
     """Reference field at t = T (complex128 [3][n][n], host or device; None removes it)
     for stats.true_err of kd_parareal_run."""
+    _need(ctx, b_ref, 1, "b_ref")
     return _check(ctx, load().kd_set_reference(ctx, _any_ptr(b_ref, "complex128") if b_ref is not None else None))
 
 

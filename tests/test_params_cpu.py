@@ -63,3 +63,43 @@ def test_null_arguments(kd):
     assert lib.kd_destroy(None) == kd.KD_OK
     assert kd.kd_last_error(None) == "NULL context"
     assert kd.kd_version().startswith("kd ")
+
+
+def test_binding_rejects_short_buffers_before_the_library(kd, monkeypatch):
+    """The binding knows each context's grid side and refuses buffers smaller than the
+    fields the call will touch (the library takes plain pointers); nothing reaches the
+    library here (a fake context address is registered, no CUDA call is made)."""
+    import ctypes
+    import numpy as np
+    n = 16
+    fake = ctypes.c_void_p(0x1000)
+    monkeypatch.setitem(kd.kd._CTX_N, fake.value, n)
+
+    class Trap:
+        def __getattr__(self, name):
+            raise AssertionError("library called: " + name)
+    monkeypatch.setattr(kd.kd, "load", lambda: Trap())
+    field = np.zeros((3, n, n), np.complex128)
+    short = np.zeros((3, n, n - 1), np.complex128)
+    slices = np.zeros((5, 3, n, n), np.complex128)
+    t0 = np.zeros(4)
+    cases = [
+        lambda: kd.kd_parareal_run(fake, short, 1.0, 4, 4, 0.0),
+        lambda: kd.kd_parareal_run(fake, field, 1.0, 5, 4, 0.0, slices),        # needs 6 slices
+        lambda: kd.kd_parareal_resume(fake, slices, 1, 1.0, 5, 4, 0.0),
+        lambda: kd.kd_fine_serial(fake, field, 1.0, 5, slices),
+        lambda: kd.kd_set_reference(fake, short),
+        lambda: kd.kd_energy(fake, slices, 6, np.zeros(6)),
+        lambda: kd.kd_energy(fake, slices, 5, np.zeros(4)),
+        lambda: kd.kd_growth_rate(fake, slices, 6, 1.0, 0.5),
+        lambda: kd.kd_growth_power(fake, short, 0.0, 1.0, 10, 1e-6),
+        lambda: kd.kd_growth_arnoldi(fake, field, 0.0, 1.0, 8, 2, 2, 1e-6, b_out=short),
+        lambda: kd.kd_coarse(fake, slices, slices, t0, 2, 6),
+        lambda: kd.kd_coarse(fake, slices, slices, t0, 2, 5),                   # t0 holds 4 times
+    ]
+    for i, call in enumerate(cases):
+        with pytest.raises(ValueError):
+            call()
+    # the right sizes pass the checks and reach the library
+    with pytest.raises(AssertionError, match="library called"):
+        kd.kd_parareal_run(fake, field, 1.0, 4, 4, 0.0, slices)
