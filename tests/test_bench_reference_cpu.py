@@ -27,6 +27,7 @@ def test_reference_arm_prints_one_line():
     assert d["config"]["workload"] == "gp_cp_128x128_parareal_64_slices"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cores"] == min(64, len(os.sched_getaffinity(0)))
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
