@@ -18,10 +18,12 @@ e2e    = the same with the initial field read from pinned host memory and all 65
 Also reported: serial fine time of the same problem with the same kernels, the
 speedup, k_con, the error against the serial fine solution, the roofline of the
 dominant kernel measured live with CUDA events, clocks during the timed region and
-the oracle timed on a bounded sample (cpu_baseline).
+the oracle timed on a bounded sample (cpu_baseline: one core; cpu_baseline_all_cores:
+one slice per host core).
 
 --impl reference times the CPU FP64 oracle (the slow reference program of this
-repository) on the host cores on a bounded sample of the same workload.
+repository) on the host cores, one slice per core, on a bounded sample of the same
+workload.
 """
 import argparse
 import json
