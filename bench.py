@@ -409,8 +409,9 @@ def run_steppers(args):
 def run_coarse_sweep(args):
     """The paper's coarse-resolution study (Sec. 5.2, fig. 6) on the config-2 problem:
     Parareal iterations and time to 1e-6 for N_C = 16, 32, 64, 128 (coarse step at the
-    stability limit of each coarse grid, min(20 dt, 2 / N_C), reading R15), against the
-    serial fine time with the same kernels."""
+    stability limit of each coarse grid, min(20 dt, 2 / N_C): explicit RK443 on an N_C grid
+    blows up above ~2.5 / N_C to 3 / N_C), against the serial fine time with the same
+    kernels."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -542,7 +543,7 @@ def run_large(args):
     torch.cuda.init()
     W = LARGE_WL
     n, N, T = W["n"], W["slices"], W["T"]
-    dtc = min(20 * W["dt_fine_max"], 2.0 / W["n_coarse"])     # coarse-grid stability (R15)
+    dtc = min(20 * W["dt_fine_max"], 2.0 / W["n_coarse"])     # explicit limit ~2.5 / N_C of the coarse grid
     p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], W["dt_fine_max"], kd.KD_C64,
                        n_coarse=W["n_coarse"], dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT)
     ctx = kd.kd_create(p)
