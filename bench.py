@@ -407,7 +407,7 @@ def run_steppers(args):
 
 # --------------------------------------------------------- coarse-grid sweep (Sec. 5.2)
 def run_coarse_sweep(args):
-    """The paper's coarse-resolution study (Sec. 5.2, fig. 6) on the config-2 problem:
+    """The paper's coarse-resolution study (Sec. 5.2, fig. 6) on the GP 128^2, 64-slice problem of the headline:
     Parareal iterations and time to 1e-6 for N_C = 16, 32, 64, 128 (coarse step at the
     stability limit of each coarse grid, min(20 dt, 2 / N_C): explicit RK443 on an N_C grid
     blows up above ~2.5 / N_C to 3 / N_C), against the serial fine time with the same
@@ -521,7 +521,7 @@ def run_roberts_coarse_sweep(args):
           flush=True)
 
 
-# ------------------------------------------------------------- large run (config 5)
+# ------------------------------------------------- large run (GP 1024^2, 256 slices)
 LARGE_WL = {
     "workload": "gp_cp_1024x1024_parareal_256_slices",
     "flow": "galloway-proctor", "n": 1024, "kz": 0.57, "Rm": 1e4, "dt_fine_max": 1e-3, "T": 2 * math.pi * 32,
@@ -531,7 +531,7 @@ LARGE_WL = {
 
 
 def run_large(args):
-    """Config 5: one Parareal solve of the GP 1024^2 problem with 256 slices resident on
+    """One Parareal solve of the GP 1024^2 problem with 256 slices resident on
     one GPU, against serial fine stepping with the same kernels; growth rate from the
     log-energy fit; fine-kernel roofline from a separately timed batched step."""
     import torch
@@ -643,7 +643,7 @@ def sweep_instances(kd, count, seed0):
 
 
 def run_sweep(args):
-    """Config 3: `--sweep-count` independent Parareal instances per rank in one
+    """The batched Rm / kz sweep: `--sweep-count` independent Parareal instances per rank in one
     kd_sweep_run call per step (ranks take disjoint seed ranges: weak scaling)."""
     import numpy as np
     import torch

@@ -146,7 +146,7 @@ def test_autotune_picks_a_plan_and_caches_it(kd, tmp_path):
         kd.kd_destroy(ctx)
 
 
-def test_roberts_slice_fp64_config1(kd):
+def test_roberts_slice_fp64_32(kd):
     # one Parareal slice of the Roberts 32^2 complex128 problem: 125 steps of 1e-2
     n, kz, Rm, dt = 32, 1.0, 8.0, 1e-2
     b = I.initial_batch(n, kz, [0])
@@ -155,7 +155,7 @@ def test_roberts_slice_fp64_config1(kd):
     assert rel(out[0], ref) < TOL64
 
 
-def test_gp_slice_fp32_config2(kd):
+def test_gp_slice_fp32_128(kd):
     # one Parareal slice of the GP 128^2 problem: dT = pi/4 in 158 steps, from t = 3 dT
     n, kz, Rm = 128, 0.57, 100.0
     dT = 2 * np.pi * 8 / 64

@@ -45,7 +45,7 @@ def c1_ctx(kd):
     return kd.kd_create(p)
 
 
-def test_parareal_config1_iterates_match_oracle(kd):
+def test_parareal_roberts32_iterates_match_oracle(kd):
     # Same number of iterations on both sides (tol = 0), FP64 everywhere.
     b0 = I.initial_field(C1["n"], C1["kz"], 0)
     kmax = 3
