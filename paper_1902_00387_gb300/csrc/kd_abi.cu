@@ -259,7 +259,7 @@ kd_status ensure_slices(kd_ctx* ctx, long N) {
   dfree(ctx, ctx->t0c);
   dfree(ctx, ctx->Uprev);
   ctx->cap_slices = 0;
-  const int n = ctx->p.n, nc = ctx->p.n_coarse;
+  const int n = ctx->p.n;
   kd_status s;
   if ((s = dalloc(ctx, (void**)&ctx->U, (N + 1) * compact_len(n) * 16, "U")) != KD_OK) return s;
   if ((s = dalloc(ctx, (void**)&ctx->Fv, N * compact_len(n) * 16, "F values")) != KD_OK) return s;
@@ -1592,7 +1592,6 @@ kd_status kd_growth_rate(kd_ctx* ctx, const double* u_slices, int n_samples, dou
   if (!u_slices || !rate_out || n_samples < 2 || !(T > 0))
     return fail(ctx, KD_EINVAL, "kd_growth_rate: bad argument");
   if (n_samples > KD_MAX_SLICES + 1) return fail(ctx, KD_EINVAL, "kd_growth_rate: too many samples");
-  kd_status s;
   const long len = 3L * ctx->p.n * ctx->p.n;
   KD_LAUNCH(energy_kernel(u_slices, len, n_samples, ctx->Ebuf, ctx->st), "energy");
   KD_LAUNCH(growth_fit(ctx->Ebuf, n_samples, T / (n_samples - 1), fit_from, ctx->scal + 4, ctx->st), "fit");
