@@ -11,8 +11,20 @@ The per-rank work is done by a block object (the library's kd_block_* calls in
 `LibBlock`); messages go through a communicator object (`TorchDistComm` for
 torch.distributed, one GPU per rank over NCCL or host tensors over gloo).  This module
 holds only the schedule: no arithmetic of the method.
+
+Failure detection (the paper assumes reliable MPI): with a `timeout`, a rank that waits
+longer than that for a boundary state, or whose send or defect broadcast fails (a peer
+that failed or left; the process group's own timeout bounds the broadcast), raises
+PipelineError naming the iteration and the peer instead of waiting forever.  A rank
+leaves only between its steps, so no device work of its own is in flight then.
 """
+import datetime
 import math
+
+
+class PipelineError(RuntimeError):
+    """A rank gave up on a peer: a boundary state that never arrived or could not be sent,
+    or a failed defect broadcast."""
 
 
 def block_of(rank, world, n_slices):
@@ -23,23 +35,40 @@ def block_of(rank, world, n_slices):
 
 
 class TorchDistComm:
-    """Point-to-point boundary messages and the defect broadcast over torch.distributed."""
+    """Point-to-point boundary messages and the defect broadcast over torch.distributed.
+    timeout (seconds, optional): how long a receive waits for its boundary state."""
 
-    def __init__(self, group=None):
+    def __init__(self, group=None, timeout=None):
         import torch.distributed as dist
         self.dist = dist
         self.group = group
+        self.timeout = timeout
 
     def send(self, buf, dst):
-        self.dist.send(buf, dst, group=self.group)
+        try:
+            self.dist.send(buf, dst, group=self.group)
+        except RuntimeError as e:
+            raise PipelineError("boundary state to rank %d failed: %s" % (dst, e)) from e
 
     def recv(self, buf, src):
-        self.dist.recv(buf, src, group=self.group)
+        if self.timeout is None:
+            self.dist.recv(buf, src, group=self.group)
+            return
+        req = self.dist.irecv(buf, src, group=self.group)
+        try:
+            done = req.wait(timeout=datetime.timedelta(seconds=self.timeout))
+        except RuntimeError as e:
+            raise PipelineError("no boundary state from rank %d within %.1f s" % (src, self.timeout)) from e
+        if done is False:
+            raise PipelineError("no boundary state from rank %d within %.1f s" % (src, self.timeout))
 
     def bcast_scalar(self, value, root, like):
         import torch
         t = torch.tensor([float(value)], dtype=torch.float64, device=like.device)
-        self.dist.broadcast(t, root, group=self.group)
+        try:
+            self.dist.broadcast(t, root, group=self.group)
+        except RuntimeError as e:
+            raise PipelineError("defect broadcast from rank %d failed: %s" % (root, e)) from e
         return float(t.item())
 
 
@@ -95,13 +124,19 @@ def parareal_pipeline(block, comm, rank, world, b0, T, n_slices, k_max, tol):
             comm.send(buf, rank + 1)
         return s
 
-    sweep(0)
+    def step(k, fn):
+        try:
+            return fn()
+        except PipelineError as e:
+            raise PipelineError("rank %d, iteration %d: %s" % (rank, k, e)) from e
+
+    step(0, lambda: sweep(0))
     sigmas = []
     k_con = k_max
     converged = False
     for k in range(1, k_max + 1):
         block.fine(k)
-        s = comm.bcast_scalar(sweep(k), last, buf)
+        s = step(k, lambda: comm.bcast_scalar(sweep(k), last, buf))
         sigmas.append(s)
         if not math.isfinite(s):
             raise FloatingPointError("non-finite Parareal defect at iteration %d" % k)

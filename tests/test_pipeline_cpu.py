@@ -135,3 +135,113 @@ def test_block_bounds_cover_the_slices():
             assert all(a[1] == b[0] for a, b in zip(blocks, blocks[1:]))
             sizes = [hi - lo for lo, hi in blocks]
             assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 1
+
+
+# ---- failure detection on the host: lost and late messages, a failing rank
+
+class FaultyComm:
+    """Wraps a communicator and injects faults on the host: `drop` = (rank, n) loses the
+    n-th boundary state that rank sends; `delay` = (rank, seconds) holds every send of
+    that rank back; `fail` = (rank, k) makes that rank's block raise in its fine step of
+    iteration k (a rank that fails between steps)."""
+
+    def __init__(self, inner, rank, drop=None, delay=None):
+        self.inner, self.rank, self.drop, self.delay = inner, rank, drop, delay
+        self.sent = 0
+
+    def send(self, buf, dst):
+        import time
+        self.sent += 1
+        if self.drop and self.drop == (self.rank, self.sent):
+            return
+        if self.delay and self.delay[0] == self.rank:
+            time.sleep(self.delay[1])
+        self.inner.send(buf, dst)
+
+    def recv(self, buf, src):
+        self.inner.recv(buf, src)
+
+    def bcast_scalar(self, value, root, like):
+        return self.inner.bcast_scalar(value, root, like)
+
+
+class FailingBlock(OracleBlock):
+    def __init__(self, *a, fail_at=None):
+        super().__init__(*a)
+        self.fail_at = fail_at
+
+    def fine(self, k):
+        if self.fail_at == k:
+            raise MemoryError("injected host failure in the fine step of iteration %d" % k)
+        super().fine(k)
+
+
+def _faulty_rank_main(rank, world, port, fault, outdir):
+    import datetime
+    import json
+    import torch.distributed as dist
+    from paper_1902_00387_gb300 import pipeline
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=6))
+    rec = {}
+    try:
+        prob = O.Problem(O.ROBERTS, N_GRID, 1.0, 8.0)
+        blk = FailingBlock(prob, 0.02, 0.1, 16, fail_at=fault.get("fail", {}).get(str(rank)))
+        comm = FaultyComm(pipeline.TorchDistComm(timeout=3.0), rank, drop=tuple(fault["drop"]) if "drop" in fault
+                          else None, delay=tuple(fault["delay"]) if "delay" in fault else None)
+        b0 = I.initial_field(N_GRID, 1.0, 5)
+        res = pipeline.parareal_pipeline(blk, comm, rank, world, b0, T, N_SLICES, 3, 0.0)
+        np.save(os.path.join(outdir, "U%d.npy" % rank), np.stack(blk.U))
+        rec = {"ok": True, "sigma": res["sigma"]}
+    except Exception as e:   # recorded for the test; the process then leaves cleanly
+        rec = {"ok": False, "type": type(e).__name__, "msg": str(e)[:300]}
+    finally:
+        with open(os.path.join(outdir, "rank%d.json" % rank), "w") as f:
+            json.dump(rec, f)
+        dist.destroy_process_group()
+
+
+def _run_faulty(fault, tmp_path, world=2, limit=60.0):
+    import json
+    import time
+    import torch.multiprocessing as mp
+    port = _free_port()
+    t = time.time()
+    ctx = mp.start_processes(_faulty_rank_main, args=(world, port, fault, str(tmp_path)), nprocs=world, join=False,
+                             start_method="spawn")
+    while not ctx.join(timeout=1.0):
+        if time.time() - t > limit:
+            for p in ctx.processes:     # the processes this test started, by handle
+                if p.is_alive():
+                    p.kill()
+            raise AssertionError("a rank did not finish within %.0f s" % limit)
+    out = [json.load(open(os.path.join(str(tmp_path), "rank%d.json" % r))) for r in range(world)]
+    return out, time.time() - t
+
+
+def test_late_boundary_state_changes_nothing(tmp_path):
+    out, _ = _run_faulty({"delay": [0, 0.4]}, tmp_path)
+    ref = _reference(3, 0.0)
+    assert all(o["ok"] for o in out)
+    for r in range(2):
+        lo, hi = r * N_SLICES // 2, (r + 1) * N_SLICES // 2
+        assert np.array_equal(np.load(os.path.join(str(tmp_path), "U%d.npy" % r)), np.stack(ref["U"][lo:hi + 1]))
+        assert out[r]["sigma"] == list(ref["sigma"])
+
+
+def test_lost_boundary_state_fails_every_rank_in_bounded_time(tmp_path):
+    # rank 0's second send is the boundary state of iteration 1's serial sweep
+    out, wall = _run_faulty({"drop": [0, 2]}, tmp_path)
+    assert not out[0]["ok"] and not out[1]["ok"]
+    assert out[1]["type"] == "PipelineError" and "iteration 1" in out[1]["msg"] and "rank 0" in out[1]["msg"]
+    assert out[0]["type"] == "PipelineError" and "iteration 1" in out[0]["msg"]
+    assert wall < 45
+
+
+def test_failed_rank_is_detected_by_its_peer(tmp_path):
+    out, wall = _run_faulty({"fail": {"1": 2}}, tmp_path)
+    assert out[1] == {"ok": False, "type": "MemoryError",
+                      "msg": "injected host failure in the fine step of iteration 2"}
+    assert not out[0]["ok"] and out[0]["type"] == "PipelineError" and "iteration 2" in out[0]["msg"]
+    assert wall < 45
