@@ -1,29 +1,33 @@
 #!/usr/bin/env python
-"""Benchmark: Parareal time-to-1e-6 against serial fine stepping on one GB300.
+"""Benchmark of the data-parallel fine propagator and of Parareal on one GB300.
 
-Workload (one "step" = one complete Parareal solve through the C ABI): the
-Galloway-Proctor circularly polarised flow on a 128 x 128 grid, kz = 0.57, Rm = 100,
-fine dt <= 5e-3 over T = 2 pi * 8 split into 64 slices (158 RK443 steps of pi/632
-per slice), complex64 fine propagator, classical coarse propagator on the same grid
-with a 3x larger step (51 steps per slice; the measured optimum of the coarse-grid sweep,
-`--config coarse-sweep`), FP64 update and convergence defect, the fine and
-coarse values evaluated on FP64 increments (F and G are linear in b), stopping at
-sigma <= 1e-6 (Eq. 9).
+Default workload (one "step" = one call of the C ABI's fine propagator):
+one IMEX RK443 fine step of all 256 time slices of the large Galloway-Proctor problem
+(1024 x 1024 grid, kz = 0.57, Rm = 1e4, T = 2 pi * 32 split into 256 slices of 786 steps,
+slice i starting at t = i T / 256), complex64 fields [256][3][1024][1024] resident in HBM,
+through kd_fine_batched: pack to the 2/3 set, the prologue, 4 x (column, row) kernels,
+unpack.
 
-value  = serial-fine-equivalent throughput of the solve: 3 n^2 x 64 x 158 degrees
-         of freedom x steps per solve / device time of the solve (Mdof.steps/s),
-         summed over ranks (each rank solves its own seeded instance: weak scaling).
-e2e    = the same with the initial field read from pinned host memory and all 65
-         slice states written back to pinned host memory inside the timed region.
-Also reported: serial fine time of the same problem with the same kernels, the
-speedup, k_con, the error against the serial fine solution, the roofline of the
-dominant kernel measured live with CUDA events, clocks during the timed region and
-the oracle timed on a bounded sample (cpu_baseline: one core; cpu_baseline_all_cores:
-one slice per host core).
+value  = 3 n^2 x 256 degrees of freedom x 1 step / device time of the call (Mdof.steps/s),
+         summed over ranks (each rank advances its own 256 slices: weak scaling).
+e2e    = the same with the fields read from pinned host memory and the result written
+         back to pinned host memory inside the timed region.
+roofline = the dominant fine kernel (column or row) of the call: its algorithmic bytes
+         per launch (two-pass model, complex64) over its average launch time, measured
+         with CUDA events on the context stream, against the measured HBM copy peak.
+Also reported beside the line: one Parareal solve of the 128^2 Galloway-Proctor problem
+(64 slices, time-to-1e-6 against serial fine stepping with the same kernels, k_con,
+errors against the complex64 and the complex128 serial fine solutions), clocks during the
+timed region, and the CPU FP64 oracle timed on a bounded sample (cpu_baseline).
+
+--config parareal prints the 128^2 Parareal solve as the line (the earlier headline);
+--config large runs one Parareal solve of the 1024^2 problem (minutes); --config sweep,
+learned, steppers, coarse-sweep, coarse-sweep-roberts run the studies of the other
+configurations; --config profile runs small repeatable cases for ncu.
 
 --impl reference times the CPU FP64 oracle (the slow reference program of this
-repository) on the host cores, one slice per core, on a bounded sample of the same
-workload.
+repository) on the host cores, one field per core, on a bounded sample of the same
+workload: one fine step of a 1024^2 field per core per step.
 """
 import argparse
 import json
@@ -49,6 +53,19 @@ WL = {
 METRIC = "Parareal time-to-1e-6 vs serial fine (1 GB300); fine Mdof·steps/s, HBM % peak"
 UNIT = "Mdof*steps/s"
 L2_FLUSH_BYTES = 512 << 20
+
+# The default line: one fine step of every slice of the large Galloway-Proctor problem.
+FINE_WL = {
+    "workload": "gp_cp_1024x1024_fine_step_256_slices",
+    "flow": "galloway-proctor", "n": 1024, "kz": 0.57, "Rm": 1e4, "T": 2 * math.pi * 32, "slices": 256,
+    "fine_steps_per_slice": 786, "steps_per_call": 1, "prec_fine": "complex64",
+    "inputs": "8 seeded |k|^-2 divergence-free fields (seeds 1000 + 8 rank ..) tiled over the 256 slices; "
+              "slice i starts at t = i T / 256",
+}
+
+
+def fine_wl_dt():
+    return FINE_WL["T"] / FINE_WL["slices"] / FINE_WL["fine_steps_per_slice"]
 
 
 def dist_env():
@@ -159,23 +176,53 @@ def oracle_extrapolated(n, kz, Rm, dt, S, N, nsteps):
             "serial_fine_s_extrapolated": per * S * N}
 
 
+def _oracle_field_step(task):
+    """Pool worker: one oracle fine step of the 1024^2 field of slice i of the default
+    workload, started together with the other workers; returns its compute time."""
+    i, nsteps = task
+    import kd_inputs
+    from oracle import kd_oracle as O
+    W = FINE_WL
+    prob = O.Problem(O.GALLOWAY_PROCTOR, W["n"], W["kz"], W["Rm"])
+    b = kd_inputs.initial_field(W["n"], W["kz"], 1000 + i % 8)
+    _BARRIER.wait(timeout=300)
+    t = time.perf_counter()
+    O.propagate(b, prob, i * W["T"] / W["slices"], fine_wl_dt(), nsteps)
+    return time.perf_counter() - t
+
+
 def run_reference(args):
+    """The CPU FP64 oracle on the default workload: every host core advances one 1024^2
+    slice by one fine step per reference step (spawned single-threaded workers started
+    together; the step time is the slowest worker's)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    per_step = 24   # fine steps of each core's slice per reference step
-    cores, worst = oracle_all_cores(per_step, args.warmup + args.steps)
-    secs = worst[args.warmup:]
-    value = args.steps * per_step * cores * 3 * WL["n"] ** 2 / sum(secs) / 1e6
+    import multiprocessing as mp
+    W = FINE_WL
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cores = max(1, min(cores, W["slices"]))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    pool = ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(barrier,))
+    try:
+        secs = [max(pool.map_async(_oracle_field_step, [(i, 1) for i in range(cores)], chunksize=1).get(900))
+                for _ in range(args.warmup + args.steps)][args.warmup:]
+    finally:
+        pool.terminate()
+        pool.join()
+    units = 3 * W["n"] ** 2 * cores
+    value = args.steps * units / sum(secs) / 1e6
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WL),
+        "config": dict(FINE_WL),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d RK443 fine steps of one 128^2 GP slice per core per step, %d cores "
-                                   "(one slice per core, as in the paper's layout), numpy FP64 oracle"
-                                   % (per_step, cores)},
+                         "sample": "one RK443 fine step of one 1024^2 GP slice per core per step, %d cores, "
+                                   "numpy FP64 oracle" % cores},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -749,19 +796,6 @@ def run_sweep(args):
 # (fused multiply-add) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM traffic of the dominant kernel at the headline workload: dram__bytes_read.sum +
-# dram__bytes_write.sum of the row kernel of the two plans the autotuner picks there,
-# row2_kernel<float, 128, 8, 0, 0> (row variant 3) and row2_kernel<float, 128, 16, 0, 0>
-# (row variant 2), averaged over the 4 stage launches of one fine step of 64 fields, L2
-# left warm as in the solve (profiles/fine_row2_traffic_gp128_b64.md).  Reported only
-# when the bench runs one of these kernels.
-# The butterflies of the row kernels became packed FP32x2 instructions after these
-# counters were taken (arithmetic only; the memory accesses are unchanged), so the bench
-# reports no traffic until they are captured again.
-ROW_TRAFFIC = {"n": 128, "batch": 64, "bytes_per_launch": {}}   # by row variant
-ROW_TRAFFIC_BEFORE_PACKED = {3: 26471552, 2: 26301504}
-
-
 def conv_roofline(n, S, batches, steps, stats):
     """ALU roofline of the convolution-form fine propagator: ~135 flops per kept mode and
     stage (the cross products with the 4 flow modes as 8 complex products and their sums,
@@ -784,68 +818,70 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# --------------------------------------------------------------------- main
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="parareal",
-                    choices=["parareal", "learned", "sweep", "large", "steppers", "coarse-sweep",
-                             "coarse-sweep-roberts"],
-                    help="parareal: the headline GP 128^2 workload; learned: learned vs classical coarse, GP 256^2; "
-                         "sweep: batched independent instances (Rm / kz sweep); large: GP 1024^2, 256 slices; "
-                         "steppers: RK111 / RK222 / RK443 accuracy per work; coarse-sweep: N_C study on the GP "
-                         "128^2 problem; coarse-sweep-roberts: N_C study at Rm 512, N_F 160")
-    ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
-    ap.add_argument("--fine-operator", default="fft", choices=["fft", "conv"],
-                    help="fft: the pseudo-spectral fine step (the workload's definition); conv: the same operator "
-                         "as the exact spectral convolution in one persistent launch")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.config == "learned":
-        run_learned(args)
-        return
-    if args.config == "sweep":
-        run_sweep(args)
-        return
-    if args.config == "large":
-        run_large(args)
-        return
-    if args.config == "steppers":
-        run_steppers(args)
-        return
-    if args.config == "coarse-sweep":
-        run_coarse_sweep(args)
-        return
-    if args.config == "coarse-sweep-roberts":
-        run_roberts_coarse_sweep(args)
-        return
+# ------------------------------------------------------------- shared set-up
+class Env:
+    """Rank, device, the library binding and the seeded input module of one bench process."""
 
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
+        self.rank, self.world, self.local = dist_env()
+        if self.world > 1:
+            dist.init_process_group("nccl")
+        torch.cuda.set_device(self.local)
+        import __graft_entry__
+        if self.rank == 0:
+            __graft_entry__.build()
+        if self.world > 1:
+            dist.barrier()
+        import kd_inputs
+        import paper_1902_00387_gb300 as kd
+        kd.load()
+        torch.cuda.init()
+        self.kd, self.I, self.torch, self.dist = kd, kd_inputs, torch, dist
+        self.stream = torch.cuda.current_stream()
 
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    import __graft_entry__
-    if rank == 0:
-        __graft_entry__.build()
-    if world > 1:
-        dist.barrier()
-    import kd_inputs
-    import paper_1902_00387_gb300 as kd
-    kd.load()
-    torch.cuda.init()
-    stream = torch.cuda.current_stream()
+    def max_over_ranks(self, v):
+        if self.world == 1:
+            return v
+        t = self.torch.tensor([v], dtype=self.torch.float64, device="cuda")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return t.item()
 
+    def timed(self, fn, steps, clocks=None, flush=None):
+        """Device time of `steps` calls of fn, each bracketed by CUDA events on the current
+        stream; barrier and synchronize on both sides of the region."""
+        torch = self.torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        res = []
+        if self.world > 1:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(float(i))          # evict L2 between steps (buffer > 129 MB L2)
+            ev[i][0].record(self.stream)
+            res.append(fn())
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        if self.world > 1:
+            self.dist.barrier()
+        return [x.elapsed_time(y) for x, y in ev], res, ck
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+# ------------------------------------------- Parareal, GP 128^2, 64 slices (the c2 solve)
+def parareal_c2(args, env, embedded):
+    """One Parareal solve of the 128^2 GP problem per step.  Returns the record of the
+    line (`embedded`: the keys reported beside the default line, no e2e or CPU baseline)."""
+    kd, torch = env.kd, env.torch
+    stream = env.stream
     n, N, T = WL["n"], WL["slices"], WL["T"]
     fine_op = kd.KD_FINE_CONV if args.fine_operator == "conv" else kd.KD_FINE_FFT
     params = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C64,
@@ -854,7 +890,7 @@ def main():
     ctx = kd.kd_create(params, stream.cuda_stream)
     tune_ms = kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 3, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
     plan = kd.kd_get_plan(ctx, kd.KD_GRID_FINE)
-    b0_host = torch.tensor(kd_inputs.initial_field(n, WL["kz"], 1000 + rank)).pin_memory()
+    b0_host = torch.tensor(env.I.initial_field(n, WL["kz"], 1000 + env.rank)).pin_memory()
     b0_dev = b0_host.to("cuda")
     u_dev = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128, device="cuda")
     u_host = torch.zeros((N + 1, 3, n, n), dtype=torch.complex128).pin_memory()
@@ -866,32 +902,13 @@ def main():
             raise RuntimeError("Parareal did not converge: " + kd.kd_last_error(ctx))
         return st
 
+    steps = args.steps if not embedded else max(3, min(args.steps, 5))
     for _ in range(args.warmup):
         solve(b0_dev, u_dev)
-
-    def timed(fn, steps, clocks=None):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        res = []
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(steps):
-            flush.fill_(float(i))          # evict L2 between steps (buffer > 129 MB L2)
-            ev[i][0].record(stream)
-            res.append(fn())
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        ck = clocks.stop() if clocks else None
-        if world > 1:
-            dist.barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, res, ck
-
-    # ---- main timed region: device-resident inputs, no instrumentation
+    # ---- timed region: device-resident inputs, no instrumentation
     launches0 = kd.kd_launch_count(ctx)
-    ms, stats, clk = timed(lambda: solve(b0_dev, u_dev), args.steps, ClockSampler(local))
+    ms, stats, clk = env.timed(lambda: solve(b0_dev, u_dev), steps, None if embedded else ClockSampler(env.local),
+                               flush)
     launches = kd.kd_launch_count(ctx) - launches0
     # ---- kernel timing for the roofline: the same solve with every fine launch bracketed
     # by CUDA events on the context stream (separate from the timed region: the events
@@ -903,43 +920,49 @@ def main():
     torch.cuda.synchronize()
     prof_ms, prof_n = kd.kd_profile_read(ctx)
     kd.kd_profile(ctx, 0)
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    ms_per_step = total_ms / args.steps
+    total_ms = env.max_over_ranks(sum(ms))
+    ms_per_step = total_ms / steps
     units = units_per_solve()
-    value = units * world * args.steps / (total_ms / 1e3) / 1e6
+    value = units * env.world * steps / (total_ms / 1e3) / 1e6
     st = stats[-1]
 
-    # ---- end to end: host initial field in, all slice states back to host
-    ms_e2e, _, _ = timed(lambda: solve(b0_host, u_host), max(2, args.steps // 2))
-    e2e_total = sum(ms_e2e)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = t.item()
-    e2e_value = units * world * len(ms_e2e) / (e2e_total / 1e3) / 1e6
-    d2h = (N + 1) * 3 * n * n * 16 + 8 * st.k_con + 8 * (N + 1) + 16
+    e2e = None
+    if not embedded:
+        # end to end: host initial field in, all slice states back to host
+        ms_e2e, _, _ = env.timed(lambda: solve(b0_host, u_host), max(2, steps // 2), flush=flush)
+        e2e_total = env.max_over_ranks(sum(ms_e2e))
+        d2h = (N + 1) * 3 * n * n * 16 + 8 * st.k_con + 8 * (N + 1) + 16
+        e2e = {"value": units * env.world * len(ms_e2e) / (e2e_total / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * n * n * 16, "d2h_bytes_per_step": d2h}
 
-    # ---- serial fine stepping of the same problem with the same kernels
+    # ---- serial fine stepping of the same problem with the same kernels (complex64) and
+    # with the complex128 kernels, the latter as the reference that separates the
+    # Parareal error from FP32 round-off
     ser = torch.zeros_like(u_dev)
     kd.kd_fine_serial(ctx, b0_dev, T, N, ser)
-    ms_ser, _, _ = timed(lambda: kd.kd_fine_serial(ctx, b0_dev, T, N, ser), 2)
+    ms_ser, _, _ = env.timed(lambda: kd.kd_fine_serial(ctx, b0_dev, T, N, ser), 2)
     serial_ms = min(ms_ser)
+    p128 = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C128)
+    ctx128 = kd.kd_create(p128, stream.cuda_stream)
+    ser128 = torch.zeros_like(u_dev)
+    kd.kd_fine_serial(ctx128, b0_dev, T, N, ser128)
+    torch.cuda.synchronize()
+    kd.kd_destroy(ctx128)
+    rel = lambda a, b: (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
     solve(b0_dev, u_dev)
     torch.cuda.synchronize()
-    err = (torch.linalg.norm(u_dev[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
-    # error of every iterate against the serial fine solution (untimed solve)
+    err = rel(u_dev[-1], ser[-1])
+    # error of every iterate against the complex64 and complex128 serial solutions (untimed)
     kd.kd_set_reference(ctx, ser[-1])
     st_ref = solve(b0_dev, u_dev)
+    kd.kd_set_reference(ctx, ser128[-1])
+    st_ref128 = solve(b0_dev, u_dev)
     kd.kd_set_reference(ctx, None)
     true_err = [float(st_ref.true_err[i]) for i in range(st_ref.k_con)]
+    true_err128 = [float(st_ref128.true_err[i]) for i in range(st_ref128.k_con)]
 
     # ---- roofline of the dominant fine kernel, from the live event timing
     hbm_peak, peak_kind = peaks()
-    dT = T / N
     S = st.n_fine_steps
     # fine-sweep batches over one solve: slices k-1..N-1 in iteration k
     batches = [N - min(k - 1, N - 1) for k in range(1, st.k_con + 1)]
@@ -948,23 +971,19 @@ def main():
     kid = 0 if prof_ms[0] >= prof_ms[1] else 1
     kbytes = (col_b, row_b)[kid]
     achieved = kbytes / (prof_ms[kid] / 1e3) / 1e9 if prof_ms[kid] > 0 else 0.0
-    fine_units = 3 * n * n * S * sum(batches) * args.steps
+    fine_units = 3 * n * n * S * sum(batches) * steps
     fine_rate = fine_units / (sum(x.ms_fine for x in stats) / 1e3) / 1e6
-
-    cpu = cpu_all = None
-    if rank == 0 and not args.no_cpu_baseline:
-        nsteps = 3 * S
-        v, el = oracle_sample(nsteps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d RK443 fine steps (3 slices) of the 128^2 GP problem, serial, numpy FP64 oracle, %.1f s"
-                         % (nsteps, el)}
-        try:
-            cpu_all = oracle_sample_all_cores(S)
-        except Exception as e:   # the all-cores figure is context; its failure must not cost the line
-            cpu_all = {"error": "%s: %s" % (type(e).__name__, e)}
-
+    if args.fine_operator == "fft":
+        roof = {"bound": "latency (L2-resident)", "kernel": ("fine column kernel", "fine row kernel")[kid],
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "algorithmic_bytes_per_launch": kbytes / max(1, prof_n[kid]), "peak_kind": peak_kind,
+                "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid],
+                "note": "the fine sweep's ~80 MB working set stays in the 129 MB L2; the HBM peak is the "
+                        "reference the byte model is quoted against, not this kernel's bound"}
+    else:
+        roof = conv_roofline(n, S, batches, steps, stats)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": env.world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 fine / f64 update", "data": "synthetic",
         "config": dict(WL, fine_steps_per_slice=S, coarse_steps_per_slice=st.n_coarse_steps,
@@ -974,30 +993,307 @@ def main():
         "time_to_solution_ms": ms_per_step, "serial_fine_ms": serial_ms,
         "speedup_vs_serial_fine": serial_ms / ms_per_step, "k_con": st.k_con,
         "sigma": list(st.sigma[:st.k_con]), "err_vs_serial_fine": err, "true_err_by_iteration": true_err,
+        "err_vs_serial_fine_c128": {
+            "parareal_by_iteration": true_err128,
+            "serial_fine_c64": rel(ser[-1], ser128[-1]),
+            "note": "relative L2 error of the last slice state against the serial fine solution computed "
+                    "with the complex128 kernels"},
         "growth_rate": st.growth_rate, "fine_mdof_steps_per_s": fine_rate,
         "phase_ms": {"fine": st.ms_fine, "coarse_and_update": st.ms_coarse},
-        "roofline": ({"bound": "hbm", "kernel": ("fine column kernel", "fine row kernel")[kid],
-                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                      "traffic": (ROW_TRAFFIC["bytes_per_launch"].get(plan[1])
-                                  if kid == 1 and n == ROW_TRAFFIC["n"] and N == ROW_TRAFFIC["batch"] else None),
-                      "traffic_unit": "bytes per launch (ncu, L2 warm)",
-                      "traffic_before_packed_butterflies": (ROW_TRAFFIC_BEFORE_PACKED.get(plan[1])
-                                                            if kid == 1 and n == ROW_TRAFFIC["n"]
-                                                            and N == ROW_TRAFFIC["batch"] else None),
-                      "algorithmic_bytes_per_launch": kbytes / max(1, prof_n[kid]), "peak_kind": peak_kind,
-                      "avg_launch_us": 1e3 * prof_ms[kid] / max(1, prof_n[kid]), "launches": prof_n[kid]}
-                     if args.fine_operator == "fft" else conv_roofline(n, S, batches, args.steps, stats)),
-        "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 16, "d2h_bytes_per_step": d2h},
+        "roofline": roof,
         "gpu_launches": launches,
-        "cpu_baseline": cpu,
-        "cpu_baseline_all_cores": cpu_all,
     }
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    if not embedded:
+        out["clocks"] = clk
+        out["e2e"] = e2e
     kd.kd_destroy(ctx)
-    if world > 1:
-        dist.destroy_process_group()
+    return out
+
+
+def run_parareal(args):
+    env = Env()
+    out = parareal_c2(args, env, embedded=False)
+    if env.rank == 0 and not args.no_cpu_baseline:
+        nsteps = 3 * out["config"]["fine_steps_per_slice"]
+        v, el = oracle_sample(nsteps)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "%d RK443 fine steps (3 slices) of the 128^2 GP problem, serial, numpy "
+                                         "FP64 oracle, %.1f s" % (nsteps, el)}
+        try:
+            out["cpu_baseline_all_cores"] = oracle_sample_all_cores(out["config"]["fine_steps_per_slice"])
+        except Exception as e:   # the all-cores figure is context; its failure must not cost the line
+            out["cpu_baseline_all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if env.rank == 0:
+        print(json.dumps(out), flush=True)
+    env.close()
+
+
+# ------------------------------------------------- the default line: the fine step, c5
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the fine
+# kernels of the default plan, from one ncu capture at 1024^2 x 16 slices scaled by 16 to
+# a 256-slice launch (the traffic grows with the slices); keyed by the kernel's name as
+# the bench reports it.  None until a capture of the current kernels is recorded.
+FINE_TRAFFIC = {}
+
+
+def run_fine_step(args):
+    env = Env()
+    kd, torch = env.kd, env.torch
+    W = FINE_WL
+    n, B = W["n"], W["slices"]
+    dt = fine_wl_dt()
+    params = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], dt, kd.KD_C64)
+    ctx = kd.kd_create(params, env.stream.cuda_stream)
+    tune_ms = kd.kd_autotune(ctx, kd.KD_GRID_FINE, B, 2, os.path.join(tempfile.gettempdir(), "kd_tune_cache.json"))
+    plan = kd.kd_get_plan(ctx, kd.KD_GRID_FINE)
+    seeds = range(1000 + 8 * env.rank, 1008 + 8 * env.rank)
+    base = torch.tensor(env.I.initial_batch(n, W["kz"], seeds), dtype=torch.complex64)
+    x_dev = base.cuda().repeat(B // 8, 1, 1, 1)
+    y_dev = torch.empty_like(x_dev)
+    t0 = torch.arange(B, dtype=torch.float64, device="cuda") * (W["T"] / B)
+
+    def step():
+        kd.kd_fine_batched(ctx, x_dev, y_dev, t0, W["steps_per_call"], B)
+
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region: inputs resident in HBM (6.4 GB in, 6.4 GB out: larger than L2)
+    launches0 = kd.kd_launch_count(ctx)
+    ms, _, clk = env.timed(step, args.steps, ClockSampler(env.local))
+    launches = kd.kd_launch_count(ctx) - launches0
+    total_ms = env.max_over_ranks(sum(ms))
+    ms_per_step = total_ms / args.steps
+    units = 3 * n * n * B * W["steps_per_call"]
+    value = units * env.world * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- per-kernel timing for the roofline (a separate pass: the events serialise the
+    # dependent launches)
+    prof_calls = 2
+    kd.kd_profile(ctx, 1)
+    for _ in range(prof_calls):
+        step()
+    torch.cuda.synchronize()
+    prof_ms, prof_n = kd.kd_profile_read(ctx)
+    kd.kd_profile(ctx, 0)
+    cb, rb = col_row_bytes(n, B)
+    hbm_peak, peak_kind = peaks()
+    kid = 0 if prof_ms[0] >= prof_ms[1] else 1
+    kname = ("fine column kernel", "fine row kernel")[kid]
+    avg_us = 1e3 * prof_ms[kid] / max(1, prof_n[kid])
+    kbytes = (cb, rb)[kid]
+    achieved = kbytes / (avg_us / 1e6) / 1e9
+    stage_ms = (prof_ms[0] + prof_ms[1]) / prof_calls
+    stage_bytes = 4 * (cb + rb) * W["steps_per_call"]
+    traffic = FINE_TRAFFIC.get((kname, tuple(plan)))
+
+    # ---- a longer call: the same kernels over 8 steps (the conversions amortised)
+    x2 = x_dev.clone()
+    ms8, _, _ = env.timed(lambda: kd.kd_fine_batched(ctx, x2, x2, t0, 8, B), 2)
+    del x2
+
+    # ---- end to end: fields from pinned host memory in, results to pinned host memory out
+    x_host = x_dev.cpu().pin_memory()
+    y_host = torch.empty_like(x_host).pin_memory()
+
+    def e2e_step():
+        x_dev.copy_(x_host, non_blocking=True)
+        step()
+        y_host.copy_(y_dev, non_blocking=True)
+
+    e2e_step()
+    ms_e2e, _, _ = env.timed(e2e_step, max(2, args.steps // 4))
+    e2e_total = env.max_over_ranks(sum(ms_e2e))
+    e2e_value = units * env.world * len(ms_e2e) / (e2e_total / 1e3) / 1e6
+    nbytes = x_host.numel() * x_host.element_size()
+    del x_host, y_host
+    torch.cuda.synchronize()
+    kd.kd_destroy(ctx)
+    del x_dev, y_dev
+    torch.cuda.empty_cache()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": env.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": dict(W, dt_fine=dt, l2="inputs and outputs (6.4 GB each) larger than the 129 MB L2, no flush",
+                       parallelism="all slices in one launch per kernel; ranks advance independent slice sets",
+                       fine_plan=list(plan), fine_plan_ms_per_step=tune_ms),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": kbytes, "avg_launch_us": avg_us, "launches": prof_n[kid],
+                     "traffic_unit": "dram bytes per launch (ncu, 16-slice capture x 16)"},
+        "fine_step_kernels": {
+            "ms_per_step": stage_ms, "two_pass_bytes_per_step": stage_bytes,
+            "achieved_gbs": stage_bytes / (stage_ms / 1e3) / 1e9,
+            "frac": stage_bytes / (stage_ms / 1e3) / 1e9 / hbm_peak,
+            "column_us_per_launch": 1e3 * prof_ms[0] / max(1, prof_n[0]),
+            "row_us_per_launch": 1e3 * prof_ms[1] / max(1, prof_n[1]),
+            "note": "the 4 column and 4 row launches of a step (the prologue included in the row kernel's "
+                    "launches), event-timed"},
+        "call_of_8_steps": {"ms": min(ms8), "mdof_steps_per_s": 8 * units / (min(ms8) / 1e3) / 1e6},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+    }
+    if env.rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_extrapolated(n, W["kz"], W["Rm"], dt, W["fine_steps_per_slice"], B, 2)
+    if not args.no_parareal:
+        c2 = parareal_c2(args, env, embedded=True)
+        out["parareal_gp128"] = {k: c2[k] for k in (
+            "time_to_solution_ms", "serial_fine_ms", "speedup_vs_serial_fine", "k_con", "sigma",
+            "err_vs_serial_fine", "true_err_by_iteration", "err_vs_serial_fine_c128", "growth_rate",
+            "fine_mdof_steps_per_s", "phase_ms", "roofline", "value", "unit", "steps")}
+        out["parareal_gp128"]["config"] = c2["config"]
+    if env.rank == 0:
+        print(json.dumps(out), flush=True)
+    env.close()
+
+
+# ------------------------------------------------------------ small cases for ncu
+def run_profile(args):
+    """Small repeatable launches for profiling (ncu -k ... -s ... -c ...):
+    --case fine: `--batch` seeded GP fields of side `--n` advanced by `--nsteps` fine steps,
+        once to warm up and once more (the launches to capture), plan `--plan c,r`;
+    --case parareal: one Parareal solve of the 128^2, 64-slice problem;
+    --case coarse: the classical coarse propagator on one field (`--n-coarse`, `--nsteps`);
+    --case gemm: the BF16 training GEMM `--gemm M,N,K` (`--engine` 0 tcgen05, 1 mma.sync).
+    Prints the device time of the second call."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import kd_inputs
+    import paper_1902_00387_gb300 as kd
+    kd.load()
+    torch.cuda.init()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    if args.case == "parareal":
+        n, N, T = WL["n"], WL["slices"], WL["T"]
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, WL["kz"], WL["Rm"], WL["dt_fine_max"], kd.KD_C64,
+                           n_coarse=WL["n_coarse"], dt_coarse=WL["dt_coarse_max"], prec_coarse=kd.KD_C64,
+                           fine_form=kd.KD_FINE_INCREMENT)
+        ctx = kd.kd_create(p)
+        if args.plan:
+            kd.kd_set_plan(ctx, kd.KD_GRID_FINE, *(int(v) for v in args.plan.split(",")))
+        else:
+            kd.kd_autotune(ctx, kd.KD_GRID_FINE, N, 2)
+        b0 = torch.tensor(kd_inputs.initial_field(n, WL["kz"], 1000), device="cuda")
+        e0, e1 = ev(), ev()
+        e0.record()
+        s, st = kd.kd_parareal_run(ctx, b0, T, N, WL["k_max"], WL["tol"])
+        e1.record()
+        torch.cuda.synchronize()
+        print("parareal GP 128^2 x 64 slices: %.1f ms, k_con %d, plan %s" % (e0.elapsed_time(e1), st.k_con,
+                                                                            kd.kd_get_plan(ctx)))
+        kd.kd_destroy(ctx)
+        return
+    if args.case == "gemm":
+        M, Nn, K = (int(v) for v in args.gemm.split(","))
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        Bt = torch.randn(Nn, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, Nn, device="cuda")
+        kd.kd_gemm_bf16_tn(A, Bt, C, args.engine)
+        e0, e1 = ev(), ev()
+        e0.record()
+        kd.kd_gemm_bf16_tn(A, Bt, C, args.engine)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print("gemm %dx%dx%d engine %d: %.3f ms, %.1f TFLOP/s" % (M, Nn, K, args.engine, ms, 2.0 * M * Nn * K / ms / 1e9))
+        return
+    if args.case == "coarse":
+        p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64,
+                           n_coarse=args.n_coarse, dt_coarse=2.0 / args.n_coarse, prec_coarse=kd.KD_C64)
+        ctx = kd.kd_create(p)
+        if args.cluster:
+            kd.kd_set_coarse_cluster(ctx, args.cluster)
+        kd.kd_set_coarse_sync(ctx, args.sync)
+        x = torch.tensor(kd_inputs.initial_batch(args.n, args.kz, [7]), dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        t0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        kd.kd_coarse(ctx, x, y, t0, args.nsteps, 1)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        kd.kd_coarse(ctx, x, y, t0, args.nsteps, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        print("coarse N_C=%d steps=%d cluster=%d sync=%d: %.3f ms, %.3f us per stage" % (
+            args.n_coarse, args.nsteps, args.cluster, args.sync, e0.elapsed_time(e1),
+            e0.elapsed_time(e1) * 1000 / (4 * args.nsteps)))
+        kd.kd_destroy(ctx)
+        return
+    p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, args.n, args.kz, args.Rm, args.dt, kd.KD_C64)
+    ctx = kd.kd_create(p)
+    if args.plan:
+        c, r = (int(v) for v in args.plan.split(","))
+        kd.kd_set_plan(ctx, kd.KD_GRID_FINE, c, r)
+    # distinct seeds up to 64 fields; beyond, 8 seeded fields tiled
+    nseed = args.batch if args.batch <= 64 else 8
+    base = torch.tensor(kd_inputs.initial_batch(args.n, args.kz, range(nseed)), dtype=torch.complex64, device="cuda")
+    x = base.repeat((args.batch + nseed - 1) // nseed, 1, 1, 1)[:args.batch].contiguous()
+    t0 = torch.arange(args.batch, dtype=torch.float64, device="cuda") * 0.785
+    kd.kd_fine_batched(ctx, x, x, t0, args.nsteps, args.batch)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    kd.kd_fine_batched(ctx, x, x, t0, args.nsteps, args.batch)
+    e1.record()
+    torch.cuda.synchronize()
+    print("n=%d batch=%d steps=%d plan %s: %.3f ms" % (args.n, args.batch, args.nsteps, kd.kd_get_plan(ctx),
+                                                       e0.elapsed_time(e1)))
+    kd.kd_destroy(ctx)
+
+
+# --------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parareal", action="store_true",
+                    help="default line: leave out the GP 128^2 Parareal solve reported beside it")
+    ap.add_argument("--config", default="fine-step",
+                    choices=["fine-step", "parareal", "learned", "sweep", "large", "steppers", "coarse-sweep",
+                             "coarse-sweep-roberts", "profile"],
+                    help="fine-step: one fine step of the 256 slices of the GP 1024^2 problem (default); "
+                         "parareal: Parareal on the GP 128^2 problem; learned: learned vs classical coarse, GP 256^2; "
+                         "sweep: batched independent instances (Rm / kz sweep); large: Parareal on GP 1024^2, "
+                         "256 slices; steppers: RK111 / RK222 / RK443 accuracy per work; coarse-sweep: N_C study on "
+                         "the GP 128^2 problem; coarse-sweep-roberts: N_C study at Rm 512, N_F 160; profile: small "
+                         "cases for ncu (--case)")
+    ap.add_argument("--sweep-count", type=int, default=32, help="instances per rank of --config sweep")
+    ap.add_argument("--fine-operator", default="fft", choices=["fft", "conv"],
+                    help="fft: the pseudo-spectral fine step (the workload's definition); conv: the same operator "
+                         "as the exact spectral convolution in one persistent launch")
+    # --config profile
+    ap.add_argument("--case", default="fine", choices=["fine", "parareal", "coarse", "gemm"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--nsteps", type=int, default=1)
+    ap.add_argument("--kz", type=float, default=0.57)
+    ap.add_argument("--Rm", type=float, default=1e4)
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--plan", default=None, help="column,row variant of the fine kernels")
+    ap.add_argument("--n-coarse", type=int, default=128)
+    ap.add_argument("--cluster", type=int, default=0, help="blocks per cluster of the coarse solver (0: default)")
+    ap.add_argument("--sync", type=int, default=0, help="coarse halo exchange: 0 cluster barrier, 1 point-to-point")
+    ap.add_argument("--gemm", default="4096,4096,4096", help="M,N,K of a BF16 GEMM to run")
+    ap.add_argument("--engine", type=int, default=0, help="GEMM engine: 0 tcgen05, 1 mma.sync")
+    args = ap.parse_args()
+    if args.config == "profile":
+        run_profile(args)
+        return
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    runs = {"fine-step": run_fine_step, "parareal": run_parareal, "learned": run_learned, "sweep": run_sweep,
+            "large": run_large, "steppers": run_steppers, "coarse-sweep": run_coarse_sweep,
+            "coarse-sweep-roberts": run_roberts_coarse_sweep}
+    runs[args.config](args)
 
 
 if __name__ == "__main__":

@@ -16,11 +16,14 @@
 //                     4 = persistent prefetching kernel (in registers);
 //                     5, 6 = component-split kernels with RT0 | RT0/2 rows per block;
 //                     7, 8 = 8 values per thread, staged | registers (n = 512)
+//   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), 4 columns per block
+//             row:    7 = warp-owned transforms, one row per block
 #pragma once
 #include "kd_fine2c.cuh"
 #include "kd_fine3.cuh"
 #include "kd_fine3c.cuh"
 #include "kd_fine2f.cuh"
+#include "kd_fine4.cuh"
 
 namespace kd {
 
@@ -217,18 +220,53 @@ static void launch_row3c(const FineArgs& a, int mode, int store, cudaStream_t st
   launch_k(row3c_kernel<T, N, RT>, gr, R::BLOCK, R::smem, st, pdl, a, mode, store);
 }
 
+// Warp-transform kernels (kd_fine4.cuh) of the n = 1024 complex64 grid: the row kernel
+// runs one row per block, 5 blocks per SM.
+#ifndef KD_COL4_COPY
+#define KD_COL4_COPY 16
+#endif
+constexpr int kRow4Rows = 1, kCol4Copy = KD_COL4_COPY;
+
+template <int N, int MODE>
+static void launch_row4(const FineArgs& a, int store, cudaStream_t st, bool pdl) {
+  using G = Row4<N, kRow4Rows, MODE>;
+  const long blocks = ((long)a.batch * a.P + kRow4Rows - 1) / kRow4Rows;
+  const long cap = (long)persistent_grid(1L << 30) * G::MINB;
+  launch_k(row4_kernel<N, kRow4Rows, MODE>, (unsigned)(blocks < cap ? blocks : cap), G::BLOCK, G::smem, st, pdl, a,
+           store);
+}
+
+template <int N, int MODE>
+static cudaError_t prepare_row4() {
+  using G = Row4<N, kRow4Rows, MODE>;
+  return cudaFuncSetAttribute(row4_kernel<N, kRow4Rows, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)G::smem);
+}
+
 template <typename T, int N>
 struct Fine3Set {
   using Sh = Shapes3<T, N>;
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
+  static constexpr bool W4 = WIDE && N == 1024;
+  static constexpr int kW4Col = 4, kW4Row = 7;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
-  static int ncol() { return WIDE ? (R8 ? 5 : 4) : 1; }
-  static int nrow() { return WIDE ? (R8 ? 9 : 7) : 1; }
+  static int ncol() { return WIDE ? (R8 || W4 ? 5 : 4) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 9 : (W4 ? 8 : 7)) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
+    if constexpr (W4) {
+      if ((e = cudaFuncSetAttribute(col4_kernel<N, kCol4Copy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col4<N, kCol4Copy>::smem)) != cudaSuccess)
+        return e;
+      if ((e = prepare_row4<N, 0>()) != cudaSuccess) return e;
+      if ((e = prepare_row4<N, 1>()) != cudaSuccess) return e;
+      if ((e = prepare_row4<N, 2>()) != cudaSuccess) return e;
+      if ((e = prepare_row4<N, 3>()) != cudaSuccess) return e;
+      if ((e = prepare_row4<N, 4>()) != cudaSuccess) return e;
+    }
     if ((e = prepare_col3<T, N, Sh::xt(0), 16>()) != cudaSuccess) return e;
     if ((e = prepare_row3<T, N, Sh::rt(0), true, 16>()) != cudaSuccess) return e;
     if ((e = prepare_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK222>()) != cudaSuccess) return e;
@@ -264,6 +302,14 @@ struct Fine3Set {
     return cudaSuccess;
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (W4) {
+      if (v == kW4Col) {
+        using C4 = Col4<N, kCol4Copy>;
+        launch_k(col4_kernel<N, kCol4Copy>, persistent_grid((long)a.batch * (N / C4::XG)), C4::BLOCK, C4::smem, st,
+                 pdl, a, s, j);
+        return;
+      }
+    }
     if constexpr (WIDE) {
       if (v == 3) return launch_col3c<T, N, XTC>(a, s, j, st, pdl);
     }
@@ -284,6 +330,17 @@ struct Fine3Set {
     if (!WIDE) v = 0;
     if (a.scheme == SCHEME_RK222) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK222>(a, mode, store, st, pdl);
     if (a.scheme == SCHEME_RK111) return launch_row3<T, N, Sh::rt(0), true, 16, SCHEME_RK111>(a, mode, store, st, pdl);
+    if constexpr (W4) {
+      if (v == kW4Row) {
+        switch (mode) {
+          case 0: return launch_row4<N, 0>(a, store, st, pdl);
+          case 1: return launch_row4<N, 1>(a, store, st, pdl);
+          case 2: return launch_row4<N, 2>(a, store, st, pdl);
+          case 3: return launch_row4<N, 3>(a, store, st, pdl);
+          default: return launch_row4<N, 4>(a, store, st, pdl);
+        }
+      }
+    }
     if constexpr (WIDE) {
       if (v == 5) return launch_row3c<T, N, RTC0>(a, mode, store, st, pdl);
       if (v == 6) return launch_row3c<T, N, RTC1>(a, mode, store, st, pdl);

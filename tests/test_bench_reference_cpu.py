@@ -1,6 +1,6 @@
 """The benchmark's reference arm (`bench.py --impl reference`: the CPU oracle on a bounded
-sample of the headline workload) prints one JSON line in the benchmark's format, and
-only on rank 0."""
+sample of the default workload, one fine step of a 1024^2 slice per core) prints one JSON
+line in the benchmark's format, and only on rank 0."""
 import json
 import os
 import subprocess
@@ -24,10 +24,10 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference"
     assert d["value"] > 0 and d["unit"] == "Mdof*steps/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] >= 3
-    assert d["config"]["workload"] == "gp_cp_128x128_parareal_64_slices"
+    assert d["config"]["workload"] == "gp_cp_1024x1024_fine_step_256_slices"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
-    assert cb["cores"] == min(64, len(os.sched_getaffinity(0)))
+    assert cb["cores"] == min(256, len(os.sched_getaffinity(0)))
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
