@@ -43,6 +43,9 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 
 __device__ __forceinline__ cx<float> conjf2(cx<float> w) { return mk(w.x, -w.y); }
 
+// Wait until at most one committed cp.async group of this thread is still in flight.
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // A warp's transpose buffer: 32 rows of 34 complex (the pad keeps 16-byte row starts and
 // spreads the 16-byte stores of a quarter warp over all banks).
 constexpr int kWPitch = 34;
@@ -226,6 +229,163 @@ __global__ void __launch_bounds__(Col4<N, CB>::BLOCK, 1) col4_kernel(FineArgs a,
         *(float4*)(dst + (long)row * N + h) = make_float4(e0.x, e0.y, e1.x, e1.y);
       }
     }
+  }
+  cp_async_wait_all();
+}
+
+// ------------------------------------------ column kernel, one warp per column
+// Col5: a warp owns one grid column and all three of its components (96 complex values a
+// lane), so u x b is formed in registers: no exchange between warps and the flow is
+// evaluated once per point.  A block of XG warps owns XG adjacent columns (XG = 8: 64-byte
+// runs of a row, one block per SM, the kernel the launch plans use; XG = 4: 32-byte runs,
+// two blocks per SM with independent barriers, measured slower at 1024^2 x 256: 3.88 against
+// 3.32 ms per launch, with 292 bytes of spills and the tables read from L1).  The input rows arrive one component at a time through two staging
+// buffers, loaded two components ahead with 16-byte cp.async; a row of a buffer is XG / 2
+// chunks of 16 bytes (columns 2h, 2h + 1), chunk h stored at h ^ (row bits), which keeps
+// the column reads of a half warp to two rows per bank.  The output of each component
+// goes through a padded staging area (odd pitch: conflict-free column writes) and leaves
+// as 16-byte stores.  With XG = 4 the twiddle and cos / sin tables are read from global
+// memory (L1) instead of shared memory, so that two blocks fit an SM.
+template <int N, int XG_>
+struct Col5 {
+  static_assert(N == 1024, "warp-owned transforms of 1024 points");
+  static_assert(XG_ == 4 || XG_ == 8, "4 or 8 columns per block");
+  static constexpr int XG = XG_;                // columns per group = warps per block
+  static constexpr int BLOCK = 32 * XG;
+  static constexpr int K = N / 3, P = 2 * K + 1;
+  static constexpr int OP = XG + 1;             // output staging pitch (complex)
+  static constexpr bool STAB = XG == 8;         // tables in shared memory
+  static constexpr int MINB = 8 / XG;
+  static constexpr size_t smem = ((size_t)XG * kWBuf + 2 * (size_t)P * XG + (size_t)P * OP + (STAB ? N : 0)) *
+                                     sizeof(cx<float>) + (STAB ? (size_t)N * sizeof(float2) : 0);
+  static_assert(MINB * (smem + 1024) <= 233472, "blocks fit the shared memory of an SM");
+  // complex index of column xi of staged row iy in an input buffer
+  __device__ __forceinline__ static int in_at(int iy, int xi) {
+    constexpr int H = XG / 2;                   // 16-byte chunks per row
+    const int swz = XG == 8 ? (iy >> 1) : (iy >> 2);
+    return iy * XG + ((((xi >> 1) ^ swz) & (H - 1)) << 1) + (xi & 1);
+  }
+};
+
+template <int N, int XG>
+__global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_kernel(FineArgs a, int step, int stage) {
+  using G = Col5<N, XG>;
+  constexpr int K = G::K, P = G::P, OP = G::OP, GPF = N / XG, H = XG / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* Tb = (cx<float>*)smem_raw;             // [XG][kWBuf] transpose buffers
+  cx<float>* In = Tb + XG * kWBuf;                  // [2][P][XG] staged input rows (swizzled chunks)
+  cx<float>* Out = In + 2 * P * XG;                 // [P][OP] output staging
+  cx<float>* s_tw = Out + P * OP;                   // [32][32] twiddles (STAB)
+  float2* s_cs = (float2*)(s_tw + N);               // (cos, sin)(2 pi j / N) (STAB)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cx<float>* S = Tb + warp * kWBuf;
+  const cx<float>* g_tw = (const cx<float>*)a.tw;
+  const float* g_cos = (const float*)a.cosg;
+  const float* g_sin = (const float*)a.sing;
+  if constexpr (G::STAB) {
+    wfft_table(s_tw, g_tw);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s_cs[i] = make_float2(g_cos[i], g_sin[i]);
+  }
+  auto twf = [&](int q) {
+    if constexpr (G::STAB) {
+      return s_tw[q * 32 + lane];
+    } else {
+      const float2 w = __ldg((const float2*)&g_tw[(lane * q) & (N - 1)]);
+      return mk(w.x, w.y);
+    }
+  };
+  auto csf = [&](int j) { return G::STAB ? s_cs[j] : make_float2(__ldg(&g_cos[j]), __ldg(&g_sin[j])); };
+  const long groups = (long)a.batch * GPF;
+  const long mine = groups > (long)blockIdx.x ? (groups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const cx<float>* M = (const cx<float>*)a.M;
+  cx<float>* W = (cx<float>*)a.W;
+  // load k of this block: component k % 3 of its group k / 3 into buffer k % 2
+  auto load = [&](long k) {
+    if (k < 3 * mine) {
+      const long g = blockIdx.x + (k / 3) * (long)gridDim.x;
+      const int c = (int)(k % 3);
+      const long b = g / GPF;
+      const int x0 = (int)(g - b * GPF) * XG;
+      const cx<float>* src = M + ((b * 3 + c) * (long)P) * N + x0;
+      cx<float>* dst = In + (k & 1) * P * XG;
+      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+        const int h = i & (H - 1), iy = i / H;
+        cp_async16(dst + G::in_at(iy, 2 * h), src + (long)iy * N + 2 * h, true);
+      }
+    }
+    cp_async_commit();   // possibly empty: keeps one group per load for the waits
+  };
+  griddep_wait();    // M is the predecessor's output
+  load(0);
+  load(1);
+  for (long j = 0; j < mine; ++j) {
+    const long g = blockIdx.x + j * (long)gridDim.x;
+    const long b = g / GPF;
+    const int x0 = (int)(g - b * GPF) * XG;
+    const int x = x0 + warp;
+    const Phase<float> ph = load_phase<float>(a, b, step, stage);
+    const float A = flow_amp<float>(a, b);
+    cx<float> v0[32], v1[32], v2[32];
+    // component c: staged ky rows -> registers -> inverse FFT in y
+    auto fetch = [&](cx<float>(&v)[32], int c) {
+      const long k = 3 * j + c;
+      cp_async_wait_group1();
+      __syncthreads();   // load k visible to the block (and, first time, the tables)
+      const cx<float>* buf = In + (k & 1) * P * XG;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int yy = lane + 32 * q;
+        const int ky = yy < N / 2 ? yy : yy - N;
+        if (wfft_never_kept<N>(q))
+          v[q] = mk(0.f, 0.f);
+        else
+          v[q] = (ky >= -K && ky <= K) ? buf[G::in_at(ky + K, warp)] : mk(0.f, 0.f);
+      }
+      __syncthreads();   // the buffer is read: it takes load k + 2
+      load(k + 2);
+      wfft1024<+1>(v, lane, S, twf);               // ky -> y: v[p] = b_c(x, y = lane + 32 p)
+    };
+    fetch(v0, 0);
+    fetch(v1, 1);
+    fetch(v2, 2);
+    // w = u x b at (x, y = lane + 32 p)
+    {
+      const float2 csx = csf(x);
+      const float uy = A * (csx.y * ph.cpx + csx.x * ph.spx);
+      const float uzx = csx.x * ph.cpx - csx.y * ph.spx;
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        const float2 csy = csf(lane + 32 * p);
+        const float ux = A * (csy.x * ph.cpy - csy.y * ph.spy);
+        const float uz = A * (uzx + (csy.y * ph.cpy + csy.x * ph.spy));
+        const cx<float> bx = v0[p], by = v1[p], bz = v2[p];
+        v0[p] = bz * uy - by * uz;
+        v1[p] = bx * uz - bz * ux;
+        v2[p] = by * ux - bx * uy;
+      }
+    }
+    // component c: forward FFT in y -> kept ky rows -> staging -> W
+    auto emit = [&](cx<float>(&v)[32], int c) {
+      wfft1024<-1>(v, lane, S, twf);               // y -> ky: v[p] = w_c(x, yy = lane + 32 p)
+      __syncthreads();   // the staging area is free (previous component stored)
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        if (wfft_never_kept<N>(p)) continue;
+        const int yy = lane + 32 * p;
+        const int ky = yy < N / 2 ? yy : yy - N;
+        if (ky >= -K && ky <= K) Out[(ky + K) * OP + warp] = v[p];
+      }
+      __syncthreads();
+      cx<float>* dst = W + ((b * 3 + c) * (long)P) * N + x0;
+      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+        const int h = i & (H - 1), row = i / H;
+        const cx<float> e0 = Out[row * OP + 2 * h], e1 = Out[row * OP + 2 * h + 1];
+        *(float4*)(dst + (long)row * N + 2 * h) = make_float4(e0.x, e0.y, e1.x, e1.y);
+      }
+    };
+    emit(v0, 0);
+    emit(v1, 1);
+    emit(v2, 2);
   }
   cp_async_wait_all();
 }

@@ -16,7 +16,9 @@
 //                     4 = persistent prefetching kernel (in registers);
 //                     5, 6 = component-split kernels with RT0 | RT0/2 rows per block;
 //                     7, 8 = 8 values per thread, staged | registers (n = 512)
-//   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), 4 columns per block
+//   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), one warp per component,
+//                     4 columns per block; 5 = warp-owned transforms, one warp per column,
+//                     8 columns per block
 //             row:    7 = warp-owned transforms, one row per block
 #pragma once
 #include "kd_fine2c.cuh"
@@ -249,17 +251,20 @@ struct Fine3Set {
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr bool W4 = WIDE && N == 1024;
-  static constexpr int kW4Col = 4, kW4Row = 7;
+  static constexpr int kW4Col = 4, kW5Col = 5, kW4Row = 7;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
-  static int ncol() { return WIDE ? (R8 || W4 ? 5 : 4) : 1; }
+  static int ncol() { return WIDE ? (R8 ? 5 : (W4 ? 6 : 4)) : 1; }
   static int nrow() { return WIDE ? (R8 ? 9 : (W4 ? 8 : 7)) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
     if constexpr (W4) {
       if ((e = cudaFuncSetAttribute(col4_kernel<N, kCol4Copy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Col4<N, kCol4Copy>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(col5_kernel<N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col5<N, 8>::smem)) != cudaSuccess)
         return e;
       if ((e = prepare_row4<N, 0>()) != cudaSuccess) return e;
       if ((e = prepare_row4<N, 1>()) != cudaSuccess) return e;
@@ -303,6 +308,12 @@ struct Fine3Set {
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
     if constexpr (W4) {
+      if (v == kW5Col) {
+        using C5 = Col5<N, 8>;
+        launch_k(col5_kernel<N, 8>, persistent_grid((long)a.batch * (N / C5::XG)), C5::BLOCK, C5::smem, st, pdl, a,
+                 s, j);
+        return;
+      }
       if (v == kW4Col) {
         using C4 = Col4<N, kCol4Copy>;
         launch_k(col4_kernel<N, kCol4Copy>, persistent_grid((long)a.batch * (N / C4::XG)), C4::BLOCK, C4::smem, st,
