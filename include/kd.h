@@ -315,13 +315,16 @@ kd_status kd_learned_apply(kd_ctx* ctx, const float* x, float* y, int phase, int
  *
  * The workspace lives in one file-scope device array of KD_STATIC_SCRATCH_BYTES that
  * every GPU loading the library keeps until the process exits.  A request needs
- *   256-byte-aligned sums of: 3 n complex-or-real table entries, 4 x batch x 3 x P^2
- *   and 2 x batch x 3 x P x n complex values (P = 2 (n/3) + 1), plus for the
- *   Galloway-Proctor flow batch x nsteps x 16 reals of flow phases,
- * in the bytes of prec_fine; larger requests return KD_EINVAL with a message on
- * stderr and enqueue nothing.  The first call on a device also looks up the array's
- * device address (cudaGetSymbolAddress) and sets the kernels' shared-memory limits,
- * with that device current; make that first call before any stream capture.  All
+ *   256-byte-aligned sums of: 3 n complex-or-real table entries, A x batch x 3 x P^2
+ *   and 2 x batch x 3 x P x n complex values (P = 2 (n/3) + 1; A = 5 for complex64:
+ *   state, its low part and three stage accumulators; A = 4 for complex128), plus for
+ *   the Galloway-Proctor flow batch x nsteps x 16 reals of flow phases,
+ * in the bytes of prec_fine (e.g. about 1.38 MB per complex64 field at n = 128, so at
+ * most 24 fields of the Roberts flow fit); larger requests return KD_EINVAL with a message on
+ * stderr and enqueue nothing.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device; the first call on a device, and the
+ * first call after cudaDeviceReset gave it a new context, also set the kernels'
+ * shared-memory limits; make such a call before any stream capture.  All
  * calls share the one array: calls that can overlap on the GPU (different streams
  * without ordering, several host threads) race and corrupt each other's results.
  * Every part of the array a call reads is written earlier in the same call, so the
@@ -440,7 +443,8 @@ kd_status kd_block_get_state(kd_ctx* ctx, int local_index, double* u);
  * The fine step's column and row kernels exist in several variants per grid and
  * precision (columns or rows per thread block; the row kernel's stage update run from
  * shared memory or from registers).  A plan is the pair (col, row) of variant indices;
- * {0, 0} is the default.  grid: 0 = the fine grid n, 1 = the coarse grid n_coarse. */
+ * {0, 0} is the default, except on the complex64 grid n = 1024, whose default is the
+ * warp-transform pair {5, 7}.  grid: 0 = the fine grid n, 1 = the coarse grid n_coarse. */
 enum { KD_GRID_FINE = 0, KD_GRID_COARSE = 1 };
 
 /* Number of column / row variants of the context's grid.  KD_EINVAL for a bad grid. */

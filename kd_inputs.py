@@ -26,6 +26,17 @@ def fft_wavenumbers(n):
 
 def initial_field(n, kz, seed):
     """Seeded solenoidal unit-norm field on the n x n grid (complex128 [3][n][n])."""
+    return _solenoidal(n, kz, seed, decay=True)
+
+
+def flat_field(n, kz, seed):
+    """Seeded solenoidal unit-norm field whose kept modes all have the same expected
+    amplitude (no |k3|^-2 decay): a test input that weighs the highest kept wavenumbers
+    as much as the lowest (complex128 [3][n][n])."""
+    return _solenoidal(n, kz, seed, decay=False)
+
+
+def _solenoidal(n, kz, seed, decay):
     rng = np.random.default_rng(seed)
     g = rng.standard_normal((2, 3, n, n))
     k = fft_wavenumbers(n)
@@ -34,7 +45,9 @@ def initial_field(n, kz, seed):
     K = n // 3
     keep = (np.abs(kx) <= K) & (np.abs(ky) <= K)
     k2 = kx * kx + ky * ky + kz * kz
-    b = (g[0] + 1j * g[1]) / np.sqrt(2.0) / k2
+    b = (g[0] + 1j * g[1]) / np.sqrt(2.0)
+    if decay:
+        b = b / k2
     b = np.where(keep, b, 0.0)
     kvec = (np.broadcast_to(kx, (n, n)), np.broadcast_to(ky, (n, n)),
             np.full((n, n), float(kz)))

@@ -116,6 +116,7 @@ kd_status ensure_ws(kd_ctx* ctx, FineWs& w, int n, int prec, long batch) {
   dfree(ctx, w.R2);
   dfree(ctx, w.R3);
   dfree(ctx, w.R4);
+  dfree(ctx, w.Xlo);
   dfree(ctx, w.M);
   dfree(ctx, w.W);
   dfree(ctx, w.ph);
@@ -128,6 +129,8 @@ kd_status ensure_ws(kd_ctx* ctx, FineWs& w, int n, int prec, long batch) {
   if ((s = dalloc(ctx, &w.R2, spec, "R2")) != KD_OK) return s;
   if ((s = dalloc(ctx, &w.R3, spec, "R3")) != KD_OK) return s;
   if ((s = dalloc(ctx, &w.R4, spec, "R4")) != KD_OK) return s;
+  // complex64 state: its low part within a propagation call (kd_stage.cuh)
+  if (prec == KD_C64 && (s = dalloc(ctx, &w.Xlo, spec, "state low part")) != KD_OK) return s;
   if ((s = dalloc(ctx, &w.M, mixed, "mixed M")) != KD_OK) return s;
   if ((s = dalloc(ctx, &w.W, mixed, "mixed W")) != KD_OK) return s;
   w.cap = batch;
@@ -153,6 +156,8 @@ FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int n, l
   a.R2 = w.R2;
   a.R3 = w.R3;
   a.R4 = w.R4;
+  a.Xlo = w.Xlo;
+  a.lo_valid = 0;
   a.M = w.M;
   a.W = w.W;
   a.tw = t.tw;
@@ -730,6 +735,8 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
   }
   kd_ctx* ctx = new kd_ctx();
   ctx->p = *params;
+  ctx->plan[0] = fine_default_plan(params->n, params->prec_fine);
+  ctx->plan[1] = fine_default_plan(params->n_coarse, params->prec_coarse);
   if (params->learned_modes > 0) {
     ctx->cK = params->learned_modes / 2;
     ctx->cP = params->learned_modes;

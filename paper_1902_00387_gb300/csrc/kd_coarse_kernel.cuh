@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
 
   const int M = hr * P;
   cx<T> x0[MPT][3], r2[MPT][3], r3[MPT][3], r4[MPT][3];
-  T lam_dt[MPT], inv_d[MPT], fkx[MPT], fky[MPT];
+  T lam_dt[MPT], gain[MPT], fkx[MPT], fky[MPT];
   const T kz = a.sp ? (T)a.sp[b].kz : (T)a.kz, dt = a.sp ? (T)a.sp[b].dt : (T)a.dt;
   const T inv_rm = T(1) / (a.sp ? (T)a.sp[b].Rm : (T)a.Rm);
 #pragma unroll
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
     fky[i] = (T)(iy - K);
     const T lam = (fkx[i] * fkx[i] + fky[i] * fky[i] + kz * kz) * inv_rm;
     lam_dt[i] = dt * lam;
-    inv_d[i] = T(1) / (T(1) + dt * T(0.5) * lam);
+    gain[i] = implicit_gain(dt * T(0.5) * lam);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       cx<T> v = mk(T(0), T(0));
@@ -316,28 +316,28 @@ __global__ void __launch_bounds__(NT) coarse_cluster_kernel(CoarseArgs a, int CS
           F[0] = mul_i(w[2] * fky[i] - w[1] * kz);
           F[1] = mul_i(w[0] * kz - w[2] * fkx[i]);
           F[2] = mul_i(w[1] * fkx[i] - w[0] * fky[i]);
-          const T dl = lam_dt[i], id = inv_d[i];
+          const T dl = lam_dt[i], gi = gain[i];
           cx<T> xn[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const cx<T> f = F[c];
             if (j == 0) {
-              const cx<T> x1 = (x0[i][c] + f * (dt * T(0.5))) * id;
+              const cx<T> x1 = implicit_solve(x0[i][c] + f * (dt * T(0.5)), gi);
               r2[i][c] = x0[i][c] + f * (dt * T(11.0 / 18.0)) - x1 * (dl * T(1.0 / 6.0));
               r3[i][c] = x0[i][c] + f * (dt * T(5.0 / 6.0)) + x1 * (dl * T(0.5));
               r4[i][c] = x0[i][c] + f * (dt * T(0.25)) - x1 * (dl * T(1.5));
               xn[c] = x1;
             } else if (j == 1) {
-              const cx<T> x2 = (r2[i][c] + f * (dt * T(1.0 / 18.0))) * id;
+              const cx<T> x2 = implicit_solve(r2[i][c] + f * (dt * T(1.0 / 18.0)), gi);
               r3[i][c] = r3[i][c] - f * (dt * T(5.0 / 6.0)) - x2 * (dl * T(0.5));
               r4[i][c] = r4[i][c] + f * (dt * T(1.75)) + x2 * (dl * T(1.5));
               xn[c] = x2;
             } else if (j == 2) {
-              const cx<T> x3 = (r3[i][c] + f * (dt * T(0.5))) * id;
+              const cx<T> x3 = implicit_solve(r3[i][c] + f * (dt * T(0.5)), gi);
               r4[i][c] = r4[i][c] + f * (dt * T(0.75)) - x3 * (dl * T(0.5));
               xn[c] = x3;
             } else {
-              const cx<T> x4 = (r4[i][c] - f * (dt * T(1.75))) * id;
+              const cx<T> x4 = implicit_solve(r4[i][c] - f * (dt * T(1.75)), gi);
               x0[i][c] = x4;
               xn[c] = x4;
             }

@@ -78,7 +78,9 @@ struct FineArgs {
   void* X;           // compact state              [batch][3][P][P]
   void* R2;          // stage accumulators          [batch][3][P][P]
   void* R3;
-  void* R4;
+  void* R4;          // holds R4 - X0 (the increment of the last stage over the state)
+  void* Xlo;         // complex64 only (else NULL): low part of the state, X + Xlo (see kd_stage.cuh)
+  int lo_valid;      // Xlo holds the low part of X (false before the first step of a call)
   void* M;           // mixed (inverse-x) field     [batch][3][P][n]
   void* W;           // mixed (forward-y) product   [batch][3][P][n]
   const void* tw;

@@ -28,6 +28,7 @@ struct FineWs {
   void* R2 = nullptr;
   void* R3 = nullptr;
   void* R4 = nullptr;
+  void* Xlo = nullptr;     // complex64: low part of the state within a propagation call
   void* M = nullptr;
   void* W = nullptr;
   void* ph = nullptr;      // flow-phase table

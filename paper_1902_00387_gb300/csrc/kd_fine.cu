@@ -108,6 +108,11 @@ static bool variants_T(int n, int* ncol, int* nrow) {
   return false;
 }
 
+FinePlan fine_default_plan(int n, int prec) {
+  if (n == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
+  return FinePlan();
+}
+
 bool fine_variants(int n, int prec, int* ncol, int* nrow) {
   return prec == 0 ? variants_T<float>(n, ncol, nrow) : variants_T<double>(n, ncol, nrow);
 }

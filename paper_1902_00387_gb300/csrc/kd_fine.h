@@ -14,7 +14,8 @@ struct LaunchProbe {
 
 // Launch plan of the fine kernels: index of the column-kernel and row-kernel variant
 // (tile shape, stage-update style) among those instantiated for the grid and precision;
-// {0, 0} is the default.  Chosen per (n, precision, batch) by the autotuner.
+// {0, 0} is the default ({5, 7} on the complex64 grid n = 1024, fine_default_plan).
+// Chosen per (n, precision, batch) by the autotuner.
 struct FinePlan {
   int col = 0;
   int row = 0;
@@ -43,6 +44,8 @@ size_t phase_table_bytes(int prec, long batch, int nsteps);
 int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
 // number of column / row variants instantiated for (n, prec); false if n is unsupported
 bool fine_variants(int n, int prec, int* ncol, int* nrow);
+// launch plan of a context before any autotuning or kd_set_plan
+FinePlan fine_default_plan(int n, int prec);
 // Enqueue cfg.nsteps RK443 steps on the compact state a.X after filling the phase table
 // a.phases (which must hold phase_table_bytes(prec, a.batch, nsteps)).  Returns the
 // number of kernels launched (negative on an unsupported grid size).
@@ -65,6 +68,8 @@ template <typename T, int N>
 cudaError_t fine3_prep();
 template <typename T, int N>
 void fine3_variants(int* ncol, int* nrow);
+template <typename T, int N>
+FinePlan fine3_default_plan();
 
 // ---- kd_ops.cu (layout conversions, Parareal update, norms)
 // full [batch][3][n][n] (precision pin) -> compact [batch][3][P][P] (precision pout)

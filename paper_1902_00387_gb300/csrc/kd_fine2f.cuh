@@ -78,7 +78,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Fused128::THREADS, 1
   const bool row_valid = slot < rows;
   const int iy = r * F::ROWS + (row_valid ? slot : 0);
   const T inv_n2 = T(1) / (T(N) * T(N));
-  const StageArrays<T> sa = stage_arrays<T>(a);
+  StageArrays<T> sa = stage_arrays<T>(a);
   const StageCoef<T> q = stage_coef<T>(a, b);
   const T A = flow_amp<T>(a, b);
   const long s0 = ((b * 3) * P + iy) * (long)P + K;            // compact index of (iy, kx = 0), component 0
@@ -132,6 +132,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Fused128::THREADS, 1
 
   const int stages = 4;
   for (int s = 0; s < nsteps; ++s) {
+    sa.lo_valid = s > 0 || a.lo_valid;   // the low part of the state exists from the second step
 #pragma unroll 1
     for (int j = 0; j < stages; ++j) {
       // ---- column pass: own columns, two rounds of 48

@@ -391,10 +391,10 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
 }
 
 // --------------------------------------------------------------------- row kernel
-// Compact stage arrays a row pass of stage MODE reads (X; R2, R3, R4; R3, R4; R4), in the
+// Compact arrays a row pass of stage MODE reads (X; R2, R3, R4; R3, R4; R4, X, Xlo), in the
 // order stage_update_1 takes them; the prologue (MODE 4) reads X before anything else and
 // stages nothing.
-__host__ __device__ constexpr int row4_reads(int mode) { return mode == 1 ? 3 : (mode == 2 ? 2 : (mode == 4 ? 0 : 1)); }
+__host__ __device__ constexpr int row4_reads(int mode) { return mode == 1 || mode == 3 ? 3 : (mode == 2 ? 2 : (mode == 4 ? 0 : 1)); }
 
 // Slots of a lane's kept kx registers: p <= 10 and p >= 21 (the others never hold a kept
 // wavenumber at n = 1024).
@@ -420,32 +420,40 @@ struct Row4 {
 
 // One component of one IMEX RK443 stage at compact index s (the expressions of
 // stage_update): f = F_c(X_j) (already scaled); r[0..] = the arrays the stage reads, in
-// the order X (stage 0), R2 R3 R4 (stage 1), R3 R4 (stage 2), R4 (stage 3).  Returns
-// X_{j+1}.
+// the order X (stage 0), R2 R3 R4 (stage 1), R3 R4 (stage 2), R4 X Xlo (stage 3; Xlo
+// zero before the first step).  R4 holds R4 - X0 and the state is the pair (X, Xlo) as
+// in state_add.  Returns X_{j+1}.
 template <int MODE>
 __device__ __forceinline__ cx<float> stage_update_1(const StageCoef<float>& q, const StageArrays<float>& sa, long s,
-                                                    float inv_d, float dl, const cx<float>* r, cx<float> f) {
+                                                    float g, float dl, const cx<float>* r, cx<float> f) {
   const float dt = q.dt;
   if (MODE == 0) {
     const cx<float> x0 = r[0];
-    const cx<float> x1 = (x0 + f * (dt * 0.5f)) * inv_d;
+    const cx<float> x1 = implicit_solve(x0 + f * (dt * 0.5f), g);
     sa.R2[s] = x0 + f * (dt * float(11.0 / 18.0)) - x1 * (dl * float(1.0 / 6.0));
     sa.R3[s] = x0 + f * (dt * float(5.0 / 6.0)) + x1 * (dl * 0.5f);
-    sa.R4[s] = x0 + f * (dt * 0.25f) - x1 * (dl * 1.5f);
+    sa.R4[s] = f * (dt * 0.25f) - x1 * (dl * 1.5f);
     return x1;
   } else if (MODE == 1) {
-    const cx<float> x2 = (r[0] + f * (dt * float(1.0 / 18.0))) * inv_d;
+    const cx<float> x2 = implicit_solve(r[0] + f * (dt * float(1.0 / 18.0)), g);
     sa.R3[s] = r[1] - f * (dt * float(5.0 / 6.0)) - x2 * (dl * 0.5f);
     sa.R4[s] = r[2] + f * (dt * 1.75f) + x2 * (dl * 1.5f);
     return x2;
   } else if (MODE == 2) {
-    const cx<float> x3 = (r[0] + f * (dt * 0.5f)) * inv_d;
+    const cx<float> x3 = implicit_solve(r[0] + f * (dt * 0.5f), g);
     sa.R4[s] = r[1] + f * (dt * 0.75f) - x3 * (dl * 0.5f);
     return x3;
   } else {
-    const cx<float> x4 = (r[0] - f * (dt * 1.75f)) * inv_d;
-    sa.X[s] = x4;
-    return x4;
+    const cx<float> x0 = r[1], lo = r[2];
+    const cx<float> e = final_increment(x0, r[0] - f * (dt * 1.75f), g);
+    float s0, e0, s1, e1, h0, l0, h1, l1;
+    two_sum(x0.x, e.x, s0, e0);
+    two_sum(x0.y, e.y, s1, e1);
+    two_sum(s0, lo.x + e0, h0, l0);
+    two_sum(s1, lo.y + e1, h1, l1);
+    sa.X[s] = mk(h0, h1);
+    sa.Xlo[s] = mk(l0, l1);
+    return mk(h0, h1);
   }
 }
 
@@ -471,7 +479,9 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
   auto twf = [&](int q) { return s_tw[q * 32 + lane]; };
   const StageArrays<float> sa = stage_arrays<float>(a);
   const cx<float>* src[3] = {MODE == 0 ? sa.X : (MODE == 1 ? sa.R2 : (MODE == 2 ? sa.R3 : sa.R4)),
-                             MODE == 1 ? sa.R3 : sa.R4, sa.R4};
+                             MODE == 1 ? sa.R3 : (MODE == 2 ? sa.R4 : sa.X), MODE == 1 ? sa.R4 : sa.Xlo};
+  // stage 3 before the first step of a call: the low part of the state is zero
+  const int npre = MODE == 3 && !sa.lo_valid ? 2 : NPRE;
   const long rows = (long)a.batch * P;
   griddep_wait();    // W (and the stage arrays) come from the predecessors
   for (long r0 = (long)blockIdx.x * ROWS; r0 < rows; r0 += (long)gridDim.x * ROWS) {
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
       for (int j = 0; j < NPRE; ++j)
 #pragma unroll
         for (int p = 0; p < 32; ++p) {
-          if (wfft_never_kept<N>(p)) continue;
+          if (wfft_never_kept<N>(p) || j >= npre) continue;
           const int xx = lane + 32 * p;
           const int kx = xx < N / 2 ? xx : xx - N;
           if (kx >= -K && kx <= K) cp_async8(Q + (j * kRow4Slots + row4_slot(p)) * 32 + lane, src[j] + sbase + kx);
@@ -536,11 +546,12 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
             const cx<float> w1 = h ? mk(e1.z, e1.w) : mk(e1.x, e1.y), w2 = h ? mk(e2.z, e2.w) : mk(e2.x, e2.y);
             const cx<float> f = mul_i(w2 * k1 - w1 * k2);
             const float lam = (fkx * fkx + lam_y) * sc.inv_rm;
-            const float inv_d = 1.f / (1.f + sc.dt * 0.5f * lam);
+            const float g = implicit_gain(sc.dt * 0.5f * lam);
             cx<float> r[3];
 #pragma unroll
-            for (int j = 0; j < NPRE; ++j) r[j] = Q[(j * kRow4Slots + row4_slot(pp)) * 32 + lane];
-            v[pp] = stage_update_1<MODE>(sc, sa, sbase + kx, inv_d, sc.dt * lam, r, f);
+            for (int j = 0; j < NPRE; ++j)
+              r[j] = j < npre ? Q[(j * kRow4Slots + row4_slot(pp)) * 32 + lane] : mk(0.f, 0.f);
+            v[pp] = stage_update_1<MODE>(sc, sa, sbase + kx, g, sc.dt * lam, r, f);
           }
         }
       }

@@ -256,6 +256,15 @@ struct Fine3Set {
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
   static int ncol() { return WIDE ? (R8 ? 5 : (W4 ? 6 : 4)) : 1; }
+  // plan of a context that is not autotuned: the warp-transform kernels where they exist
+  static FinePlan default_plan() {
+    FinePlan p;
+    if (W4) {
+      p.col = kW5Col;
+      p.row = kW4Row;
+    }
+    return p;
+  }
   static int nrow() { return WIDE ? (R8 ? 9 : (W4 ? 8 : 7)) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
@@ -391,7 +400,9 @@ static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
     // no mixed field kept at the end, all fields for all steps)
     if (pl.col == Set::kFusedCol && cfg.prologue && !cfg.store_last && !cfg.active &&
         a0.scheme == SCHEME_RK443 && cfg.nsteps > 0) {
-      launch_k(fused128_kernel<>, (unsigned)(2 * a0.batch), Fused128::THREADS, Fused128::smem, cfg.st, cfg.pdl, a0,
+      FineArgs af = a0;
+      af.lo_valid = 0;
+      launch_k(fused128_kernel<>, (unsigned)(2 * a0.batch), Fused128::THREADS, Fused128::smem, cfg.st, cfg.pdl, af,
                cfg.nsteps);
       return 1;
     }
@@ -403,6 +414,7 @@ static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
   FineArgs a = a0;
   const int stages = scheme_stages(a0.scheme);
   for (int s = 0; s < cfg.nsteps; ++s) {
+    a.lo_valid = s > 0;   // the low part of the state (kd_stage.cuh) exists from the second step
     if (cfg.active) {
       a.batch = cfg.active[s];
       if (a.batch <= 0) break;
@@ -453,6 +465,11 @@ void fine3_variants(int* ncol, int* nrow) {
   *nrow = Fine3Set<T, N>::nrow();
 }
 
+template <typename T, int N>
+FinePlan fine3_default_plan() {
+  return Fine3Set<T, N>::default_plan();
+}
+
 }  // namespace kd
 
 // Explicit instantiation of one (T, N) in the including translation unit.
@@ -463,4 +480,5 @@ void fine3_variants(int* ncol, int* nrow) {
 #define KD_FINE3_INSTANTIATE(T, N)                                        \
   template int kd::fine3_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
   template cudaError_t kd::fine3_prep<T, N>();                             \
-  template void kd::fine3_variants<T, N>(int*, int*);
+  template void kd::fine3_variants<T, N>(int*, int*);              \
+  template kd::FinePlan kd::fine3_default_plan<T, N>();

@@ -4,9 +4,11 @@
 // KD_STATIC_SCRATCH_BYTES; the call performs no cudaMalloc / cudaFree and no other
 // allocating call, and creates no context object.
 //
-// Host code cannot use the array's name as a device address, so the address is
-// obtained once per device with cudaGetSymbolAddress (with that device current) on
-// the first call on that device, together with the kernels' shared-memory opt-in.
+// Host code cannot use the array's name as a device address, so every call looks the
+// address up with cudaGetSymbolAddress (with the caller's device current; a host-side
+// lookup, no allocation).  The kernels' shared-memory opt-in is set on the first call on
+// a device and again whenever that address changes, i.e. after cudaDeviceReset gave the
+// device a new context, so that nothing cached from an earlier context is used.
 #include <math.h>
 #include <mutex>
 #include <stdio.h>
@@ -20,7 +22,7 @@ __device__ __align__(256) unsigned char g_static_scratch[KD_STATIC_SCRATCH_BYTES
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+void* g_scratch_addr[kMaxDevices] = {nullptr};   // address the kernels were set up for
 bool g_prepared[kMaxDevices][2] = {{false}};
 
 // Grid tables into the scratch: tw[e] = exp(-2 pi i e / n), cos / sin of 2 pi e / n,
@@ -71,7 +73,8 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   const size_t spec = align256((size_t)batch * 3 * P * P * cs);
   const size_t mixed = align256((size_t)batch * 3 * P * n * cs);
   const size_t phase = p->flow == KD_FLOW_GALLOWAY_PROCTOR ? align256(phase_table_bytes(prec, batch, nsteps)) : 0;
-  const size_t need = tab + 4 * spec + 2 * mixed + phase;
+  const int nspec = prec == KD_C64 ? 5 : 4;   // X, R2, R3, R4 (+ the state's low part, complex64)
+  const size_t need = tab + nspec * spec + 2 * mixed + phase;
   if (need > (size_t)KD_STATIC_SCRATCH_BYTES) {
     fprintf(stderr,
             "kd_fine_batched_static: this request needs %zu bytes of workspace, more than the %d bytes of the "
@@ -84,14 +87,15 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-      if (e != cudaSuccess || !ptr) {
-        fprintf(stderr, "kd_fine_batched_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-        return KD_ECUDA;
-      }
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      fprintf(stderr, "kd_fine_batched_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return KD_ECUDA;
+    }
+    if (ptr != g_scratch_addr[dev]) {   // first call on this device, or a new context
       g_scratch_addr[dev] = ptr;
+      g_prepared[dev][0] = g_prepared[dev][1] = false;
     }
     if (!g_prepared[dev][prec]) {
       cudaError_t e = fine_prepare(prec);
@@ -126,7 +130,9 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   a.R2 = q + spec;
   a.R3 = q + 2 * spec;
   a.R4 = q + 3 * spec;
-  q += 4 * spec;
+  a.Xlo = prec == KD_C64 ? q + 4 * spec : nullptr;
+  a.lo_valid = 0;
+  q += nspec * spec;
   a.M = q;
   a.W = q + mixed;
   q += 2 * mixed;
@@ -138,8 +144,9 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   a.cosg = cg;
   a.sing = sg;
   // Every scratch region is written before it is read in this call (tables, packed
-  // state, prologue mixed field, column output, stage-0 accumulators, phases), so no
-  // region has to be cleared.
+  // state, prologue mixed field, column output, stage-0 accumulators, phases, and the
+  // state's low part, written by the first step's last stage and read from the second
+  // step on), so no region has to be cleared.
   const unsigned tb = (unsigned)((n + 255) / 256);
   if (prec == KD_C64)
     k_static_tables<float><<<tb, 256, 0, st>>>(n, (float*)tw, (float*)cg, (float*)sg);

@@ -82,6 +82,50 @@ def test_large_grids_fp32(kd, n):
     assert rel(out[0], ref) < TOL32
 
 
+def test_full_slice_256_rm1000_matches_oracle(kd):
+    # one whole slice of the learned-coarse workload's fine propagator: GP 256^2,
+    # Rm = 1000, 800 steps of (2 pi / 16) / 800 from the start of slice 5
+    n, kz, Rm = 256, 0.57, 1000.0
+    dT = 2 * math.pi / 16
+    dt, S = dT / 800, 800
+    b = I.initial_batch(n, kz, [41])
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, [5 * dT], S)
+    ref = O.propagate(b[0], O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm), 5 * dT, dt, S)
+    assert rel(out[0], ref) < TOL32
+
+
+def test_large_workload_late_slices_match_oracle(kd):
+    # the 1024^2 workload's step (Rm = 1e4, dt = (2 pi 32 / 256) / 786) from the start
+    # times of its last and middle slices, 20 steps, in one batch, default launch plan
+    n, kz, Rm = 1024, 0.57, 1e4
+    dT = 2 * math.pi * 32 / 256
+    dt = dT / 786
+    b = I.initial_batch(n, kz, [51, 52])
+    t0 = [255 * dT, 128 * dT]
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, t0, 20)
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i in range(2):
+        assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 20)) < TOL32, i
+
+
+@pytest.mark.parametrize("n,nsteps", [(128, 20), (512, 6), (1024, 4)])
+def test_flat_spectrum_edge_ring(kd, n, nsteps):
+    """A flat-spectrum solenoidal input puts as much energy on the edge ring of the kept
+    square (|kx| = K or |ky| = K, the modes next to the 2/3 cut) as anywhere else; the
+    largest error there is bounded against the ring's largest oracle value."""
+    kz, Rm, dt = 0.57, 1e4, 1e-3
+    b = np.stack([I.flat_field(n, kz, 61)])
+    out = run_fine(kd, O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64, b, [3.1], nsteps)
+    ref = O.propagate(b[0], O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm), 3.1, dt, nsteps)
+    k = I.fft_wavenumbers(n)
+    K = n // 3
+    ax, ay = np.abs(k[None, :]), np.abs(k[:, None])
+    ring = (ax <= K) & (ay <= K) & ((ax == K) | (ay == K))
+    err = np.max(np.abs(out[0][:, ring] - ref[:, ring]))
+    assert err < 1e-5 * np.max(np.abs(ref[:, ring])), err / np.max(np.abs(ref[:, ring]))
+    assert rel(out[0], ref) < TOL32
+
+
 @pytest.mark.parametrize("n", [32, 128, 256, 512, 1024])
 def test_every_launch_plan_matches_oracle(kd, n):
     """Every instantiated (column, row) kernel variant: same oracle parity, and the same

@@ -380,3 +380,34 @@ def test_true_error_against_a_reference(kd):
         assert st.true_err[0] == -1.0 and st.true_err[1] == -1.0
     finally:
         kd.kd_destroy(ctx)
+
+
+def test_benched_gp128_solve_matches_oracle(kd):
+    """The 128^2 GP Parareal solve exactly as bench.py times it (64 slices, coarse step
+    2/128 on the fine grid, increment form, sigma <= 1e-6): sampled slices of the returned
+    iterate each propagated by the oracle over one slice, and the growth rate of the solve
+    against the oracle's serial FP64 run (Eq. 8, Eq. 9, Table 1 "Growth Rate")."""
+    import bench
+    W = bench.WL
+    n, N, T = W["n"], W["slices"], W["T"]
+    p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], W["dt_fine_max"], kd.KD_C64,
+                       n_coarse=W["n_coarse"], dt_coarse=W["dt_coarse_max"], prec_coarse=kd.KD_C64,
+                       fine_form=kd.KD_FINE_INCREMENT)
+    ctx = kd.kd_create(p)
+    b0 = I.initial_field(n, W["kz"], 1000)
+    out = np.zeros((N + 1, 3, n, n), np.complex128)
+    try:
+        status, st = kd.kd_parareal_run(ctx, b0, T, N, W["k_max"], W["tol"], out)
+    finally:
+        kd.kd_destroy(ctx)
+    assert status == kd.KD_OK and st.sigma[st.k_con - 1] <= W["tol"]
+    dT = T / N
+    S = st.n_fine_steps
+    assert S == bench.fine_steps_per_slice()
+    prob = O.Problem(O.GALLOWAY_PROCTOR, n, W["kz"], W["Rm"])
+    for i in (0, 21, 42, 63):
+        ref = O.propagate(out[i], prob, i * dT, dT / S, S)
+        assert rel(out[i + 1], ref) < 1e-5, i
+    U = O.serial_fine(b0, lambda u, i: O.propagate(u, prob, i * dT, dT / S, S), N)
+    g_ref = O.growth_rate(np.arange(N + 1) * dT, [O.energy(u) for u in U], 0.5 * T)
+    assert abs(st.growth_rate - g_ref) < 1e-4 * abs(g_ref), (st.growth_rate, g_ref)

@@ -51,6 +51,25 @@ def test_initial_spectrum_falls_as_k_to_the_minus_four():
     assert abs(slope) < 0.15, slope
 
 
+def test_flat_field_is_solenoidal_unit_norm_and_flat():
+    # same constraints as initial_field; E |b_hat(k)|^2 = 2 before normalisation for
+    # every kept k, so the edge ring of the kept square carries its share of the energy
+    n, kz = 96, 0.57
+    b = I.flat_field(n, kz, 5)
+    assert b.shape == (3, n, n) and abs(np.linalg.norm(b.ravel()) - 1.0) < 1e-14
+    k = I.fft_wavenumbers(n)
+    kx, ky = k[None, :], k[:, None]
+    assert np.max(np.abs(kx * b[0] + ky * b[1] + kz * b[2])) < 1e-14
+    K = n // 3
+    keep = (np.abs(kx) <= K) & (np.abs(ky) <= K)
+    assert np.all(b[:, ~keep] == 0)
+    e = sum(np.abs(I.flat_field(n, kz, s)) ** 2 for s in range(8)).sum(axis=0)
+    ring = keep & ((np.abs(kx) == K) | (np.abs(ky) == K))
+    inner = keep & (np.abs(kx) <= K // 2) & (np.abs(ky) <= K // 2)
+    assert abs(np.mean(e[ring]) / np.mean(e[inner]) - 1.0) < 0.1
+    assert not np.allclose(b, I.flat_field(n, kz, 6))
+
+
 def test_sweep_instances_follow_the_recipe():
     counts = {64: 0, 128: 0, 256: 0, 512: 0}
     seeds = range(1000, 1600)

@@ -315,6 +315,38 @@ def test_speedup_model_and_bounds():
     assert abs(O.speedup_model(3, 10, 0.0) - 10 / 3) < 1e-12
 
 
+def test_speedup_model_hand_values():
+    # Eq. 10 evaluated by hand in fractions, with a coarse/fine cost ratio that is not 0:
+    #   k = 3, N_p = 16, R_c/R_f = 1/16: (1 + 3/16)(1/16) + 3/16 = 19/256 + 48/256 = 67/256
+    #   k = 2, N_p = 64, R_c/R_f = 1/4:  (1 + 2/64)(1/4) + 2/64 = 33/128 + 4/128 = 37/128
+    # (dropping the (1 + k/N_p) factor would give 4 and 128/36 instead)
+    assert abs(O.speedup_model(3, 16, 1.0 / 16) - 256.0 / 67.0) < 1e-14
+    assert abs(O.speedup_model(2, 64, 0.25) - 128.0 / 37.0) < 1e-14
+
+
+@pytest.mark.parametrize("flow", [O.GALLOWAY_PROCTOR, O.ROBERTS])
+def test_coarse_propagator_is_the_fine_one_on_the_coarse_mode_set(flow):
+    # G of Sec. 3.2 restricts to the N_C grid and steps the same equations there.  On the
+    # same grid and step it is F itself; on a smaller grid it equals F on the fine grid
+    # with the state and the explicit term kept on the coarse square (no aliasing: the
+    # flow has |q| = 1 modes only).  The slice start time t0 != 0 enters both through the
+    # time-dependent GP flow.
+    n, n_c, kz, Rm = 48, 24, 0.57, 30.0
+    prob = O.Problem(flow, n, kz, Rm)
+    b = I.initial_field(n, kz, 4)
+    t0, dt, S = 1.3, 0.02, 12
+    assert np.array_equal(O.coarse_propagate(b, prob, n, t0, dt, S), O.propagate(b, prob, t0, dt, S))
+    k = I.fft_wavenumbers(n)
+    Kc = n_c // 3
+    mask = (np.abs(k[None, :]) <= Kc) & (np.abs(k[:, None]) <= Kc)
+    ref = O.propagate(b, prob, t0, dt, S, mask=mask)
+    got = O.coarse_propagate(b, prob, n_c, t0, dt, S)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+    if flow == O.GALLOWAY_PROCTOR:
+        later = O.coarse_propagate(b, prob, n_c, t0 + 0.5, dt, S)
+        assert np.linalg.norm(later - got) > 1e-4 * np.linalg.norm(got)
+
+
 # ------------------------------------------------------------------ growth rates
 def test_growth_fit_exact_exponential():
     t = np.linspace(0, 10, 21)

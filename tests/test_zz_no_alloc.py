@@ -2,9 +2,11 @@
 kd_fine_batched through the C ABI.  The static variant serves callers that cannot
 allocate device memory (a host application's pool owns the GPU memory, or a loop
 that cannot pay for cudaMalloc's device synchronisation); its workspace is a fixed
-device array inside the library.  This file is collected last on purpose."""
-import ctypes
+device array inside the library.
 
+The file name puts it last in collection order, so that a run stopping at its first
+failure has already run every other GPU test; it passes alone in a fresh process as
+well as after the others (every call writes the parts of the array it reads)."""
 import numpy as np
 import pytest
 
@@ -44,11 +46,7 @@ def run_both(kd, params, b, t0, nsteps):
     finally:
         kd.kd_destroy(ctx)
     out = torch.full_like(x, float("nan"))
-    lib = kd.load()
-    s = lib.kd_fine_batched_static(ctypes.byref(params), ctypes.c_void_p(x.data_ptr()),
-                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(tt.data_ptr()),
-                                   nsteps, b.shape[0], ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert s == kd.KD_OK
+    assert kd.kd_fine_batched_static(params, x, out, tt, nsteps, b.shape[0]) == kd.KD_OK
     torch.cuda.synchronize()
     return out.cpu().numpy(), ref.cpu().numpy()
 
@@ -68,13 +66,30 @@ def test_static_matches_fine_batched_on_two_calls_in_a_row(kd):
         assert rel(o2[i], r2[i]) < TOL64
 
 
+def test_static_call_allocates_no_device_memory(kd):
+    # the property the entry point exists for: once a first call has set the kernels up
+    # on this device, calls leave the device's free memory exactly as it was
+    import torch
+    p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, 64, 0.57, 100.0, 5e-3, kd.KD_C64)
+    x = torch.tensor(I.initial_batch(64, 0.57, [7, 8]), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    tt = torch.tensor([0.0, 0.6], dtype=torch.float64, device="cuda")
+    assert kd.kd_fine_batched_static(p, x, y, tt, 4, 2) == kd.KD_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert kd.kd_fine_batched_static(p, x, y, tt, 4, 2) == kd.KD_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_static_rejects_requests_beyond_the_scratch(kd):
     import torch
     p = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, 1024, 0.57, 1e4, 1e-3, kd.KD_C64)
     x = torch.zeros((8, 3, 1024, 1024), dtype=torch.complex64, device="cuda")
     t0 = torch.zeros(8, dtype=torch.float64, device="cuda")
-    lib = kd.load()
-    s = lib.kd_fine_batched_static(ctypes.byref(p), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                   ctypes.c_void_p(t0.data_ptr()), 2, 8, None)
-    assert s == kd.KD_EINVAL
+    with pytest.raises(kd.KdError) as err:
+        kd.kd_fine_batched_static(p, x, x, t0, 2, 8)
+    assert err.value.status == kd.KD_EINVAL
     assert not torch.isnan(x).any()
