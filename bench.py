@@ -1030,10 +1030,15 @@ def run_parareal(args):
 
 # ------------------------------------------------- the default line: the fine step, c5
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the fine
-# kernels of the default plan, from one ncu capture at 1024^2 x 16 slices scaled by 16 to
-# a 256-slice launch (the traffic grows with the slices); keyed by the kernel's name as
-# the bench reports it.  None until a capture of the current kernels is recorded.
-FINE_TRAFFIC = {}
+# kernels, from one ncu capture of the warp-transform plan (5, 7) at 1024^2 x 16 slices
+# (one fine step: the 4 stage launches of each kernel), averaged over the stages and
+# scaled by 16 to a 256-slice launch (the traffic grows with the slices); keyed by the
+# kernel's name as the bench reports it and the plan.  A plan without a capture of its
+# current kernels reports null.
+FINE_TRAFFIC = {
+    ("fine row kernel", (5, 7)): 16 * (1191.35 + 1374.87 + 1022.13 + 939.71) / 4 * 1e6,
+    ("fine column kernel", (5, 7)): 16 * (487.35 + 484.44 + 484.49 + 484.41) / 4 * 1e6,
+}
 
 
 def run_fine_step(args):
@@ -1128,8 +1133,8 @@ def run_fine_step(args):
             "frac": stage_bytes / (stage_ms / 1e3) / 1e9 / hbm_peak,
             "column_us_per_launch": 1e3 * prof_ms[0] / max(1, prof_n[0]),
             "row_us_per_launch": 1e3 * prof_ms[1] / max(1, prof_n[1]),
-            "note": "the 4 column and 4 row launches of a step (the prologue included in the row kernel's "
-                    "launches), event-timed"},
+            "note": "the 4 column and 4 row stage launches of a step, event-timed (the prologue's inverse x "
+                    "transform and the pack / unpack kernels of the call are outside these)"},
         "call_of_8_steps": {"ms": min(ms8), "mdof_steps_per_s": 8 * units / (min(ms8) / 1e3) / 1e6},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
