@@ -99,12 +99,17 @@ typedef struct {
   int fine_scheme;     /* KD_RK443 (default), KD_RK222 or KD_RK111 */
 } kd_params;
 
-/* Create a context for one problem.  `cuda_stream` is a cudaStream_t (may be NULL).
- * Allocates the grid tables on the current device.  Returns KD_EINVAL for
- * unsupported sizes and KD_ECUDA / KD_ENOMEM on device failures. */
+/* Create a context for one problem: the initial-value problem of Sec. 3 (the induction
+ * equation of Sec. 2 Eq. 1 with the flow, kz and Rm of params) with its fine and coarse
+ * discretisations; the set-up step of the Parareal algorithms of Sec. 4.1 (the
+ * communicators and solvers each process creates there are this context's tables and
+ * workspace here).  `cuda_stream` is a cudaStream_t (may be NULL).  Allocates the grid
+ * tables on the current device.  Returns KD_EINVAL for unsupported sizes and KD_ECUDA /
+ * KD_ENOMEM on device failures. */
 kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out);
 
-/* Release every resource of the context (waits for its stream first).  NULL is a no-op. */
+/* Release every resource of the context (waits for its stream first).  NULL is a no-op.
+ * No counterpart in the paper (resource management of this library). */
 kd_status kd_destroy(kd_ctx* ctx);
 
 /* Fine propagator F (Sec. 3): advance `batch` independent fields by `nsteps` RK443
@@ -529,7 +534,8 @@ long long kd_launch_count(kd_ctx* ctx);
 kd_status kd_profile(kd_ctx* ctx, int enable);
 kd_status kd_profile_read(kd_ctx* ctx, double* ms, long long* launches);
 
-/* Message of the last error on this context ("" if none).  Valid until the next call. */
+/* Message of the last error on this context ("" if none).  Valid until the next call.
+ * No counterpart in the paper (diagnostics of this library). */
 const char* kd_last_error(kd_ctx* ctx);
 
 /* Library version string. */

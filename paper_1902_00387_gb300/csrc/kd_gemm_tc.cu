@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // loader
+    int issued = 0;
     for (int kt = 0; kt < ktiles; ++kt) {
       const int s = kt % kTmaStages;
       if (kt >= kTmaStages && !mbar_wait(saddr(&empty[s]), (uint32_t)((kt / kTmaStages - 1) & 1))) {
@@ -277,6 +278,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(saddr(&full[s]), G::kStage);
       tma_load(a_s, &ta, kt * kBK, m0, saddr(&full[s]));
       tma_load(a_s + G::kATile, &tb, kt * kBK, n0, saddr(&full[s]));
+      issued = kt + 1;
+    }
+    if (issued < ktiles) {
+      // gave up: the copies already issued still write this CTA's shared memory; wait
+      // (bounded) until the last ring's worth of them has landed before the CTA may exit
+      for (int kt = issued > kTmaStages ? issued - kTmaStages : 0; kt < issued; ++kt)
+        mbar_wait(saddr(&full[kt % kTmaStages]), (uint32_t)((kt / kTmaStages) & 1));
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer

@@ -17,6 +17,13 @@ longer than that for a boundary state, or whose send or defect broadcast fails (
 that failed or left; the process group's own timeout bounds the broadcast), raises
 PipelineError naming the iteration and the peer instead of waiting forever.  A rank
 leaves only between its steps, so no device work of its own is in flight then.
+
+The receive timeout applies to host-side groups (gloo).  On an NCCL group a receive that
+the host stops waiting for stays queued on the GPU, waiting for a peer that never sends,
+so `TorchDistComm` refuses a receive timeout there: the bound on NCCL is the process
+group's own timeout (init_process_group(timeout=...)), whose watchdog aborts the
+communicator and fails the pending operation on the device as well; a failed send
+surfaces through that watchdog too, not as an exception of the send call.
 """
 import datetime
 import math
@@ -36,13 +43,17 @@ def block_of(rank, world, n_slices):
 
 class TorchDistComm:
     """Point-to-point boundary messages and the defect broadcast over torch.distributed.
-    timeout (seconds, optional): how long a receive waits for its boundary state."""
+    timeout (seconds, optional): how long a receive waits for its boundary state; not on
+    an NCCL group, whose process-group timeout bounds every operation instead."""
 
     def __init__(self, group=None, timeout=None):
         import torch.distributed as dist
         self.dist = dist
         self.group = group
         self.timeout = timeout
+        if timeout is not None and str(dist.get_backend(group)).lower() == "nccl":
+            raise ValueError("a receive timeout would leave the NCCL receive queued on the GPU; bound NCCL "
+                             "operations with the process group's timeout (init_process_group(timeout=...))")
 
     def send(self, buf, dst):
         try:

@@ -245,3 +245,16 @@ def test_failed_rank_is_detected_by_its_peer(tmp_path):
                       "msg": "injected host failure in the fine step of iteration 2"}
     assert not out[0]["ok"] and out[0]["type"] == "PipelineError" and "iteration 2" in out[0]["msg"]
     assert wall < 45
+
+
+def test_receive_timeout_refused_on_nccl_groups(monkeypatch):
+    # a receive the host stops waiting for would stay queued on the GPU with NCCL, so the
+    # communicator refuses the timeout there (the process group's own timeout bounds NCCL)
+    import torch.distributed as dist
+    from paper_1902_00387_gb300 import pipeline
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "nccl")
+    with pytest.raises(ValueError):
+        pipeline.TorchDistComm(timeout=2.0)
+    pipeline.TorchDistComm()                # no timeout: accepted
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "gloo")
+    assert pipeline.TorchDistComm(timeout=2.0).timeout == 2.0
