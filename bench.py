@@ -718,9 +718,12 @@ def run_sweep(args):
     ins = [q for _, q, _ in insts]
     cache = os.path.join(tempfile.gettempdir(), "kd_tune_cache.json")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # one prepared sweep for every step: groups, contexts and buffers made once, the fine
+    # steps of recurring iterations replayed from captured CUDA graphs
+    sw = kd.kd_sweep_create(ins, T, N)
 
     def solve(b0, out):
-        s, res, st = kd.kd_sweep_run(ins, b0, T, N, W["k_max"], W["tol"], u_final=out, tune_cache=cache)
+        s, res, st = kd.kd_sweep_exec(sw, b0, W["k_max"], W["tol"], u_final=out, tune_cache=cache)
         return s, res, st
 
     for _ in range(args.warmup):
@@ -760,8 +763,10 @@ def run_sweep(args):
         fine_bytes += sum(N - min(k - 1, N - 1) for k in range(1, r.k_con + 1)) * r.n_fine_steps * per_slice_step
     hbm_peak, peak_kind = peaks()
     achieved = fine_bytes / (st.ms_fine / 1e3) / 1e9
-    el_e2e, _, _ = timed(b0_host, u_host, max(1, args.steps // 2))
-    e2e_value = units * world * max(1, args.steps // 2) / el_e2e / 1e6
+    e2e_value = None
+    if not args.no_e2e:
+        el_e2e, _, _ = timed(b0_host, u_host, max(1, args.steps // 2))
+        e2e_value = units * world * max(1, args.steps // 2) / el_e2e / 1e6
     nbytes = sum(b.numel() * 16 for b in b0_host)
     ks = [r.k_con for r in results]
     by_n = {}
@@ -772,7 +777,8 @@ def run_sweep(args):
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 fine / f64 update", "data": "synthetic",
         "config": dict(W, l2="flushed between steps (512 MB write)",
-                       parallelism="instances x slices in one batched launch per grid; ranks take disjoint seeds"),
+                       parallelism="instances x slices in one batched launch per grid; ranks take disjoint seeds",
+                       graphs="fine steps of each (iteration, active set) captured once, replayed in later steps"),
         "instances_by_n": {str(k): len(v) for k, v in sorted(by_n.items())},
         "k_con_by_n": {str(k): v for k, v in sorted(by_n.items())},
         "converged": sum(1 for r in results if r.status == kd.KD_OK), "k_con_max": max(ks),
@@ -782,10 +788,12 @@ def run_sweep(args):
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": None, "peak_kind": peak_kind},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+                if e2e_value is not None else None),
         "gpu_launches": int(st.n_launches) * args.steps,
         "cpu_baseline": None,
     }
+    kd.kd_sweep_destroy(sw)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -1260,6 +1268,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parareal", action="store_true",
                     help="default line: leave out the GP 128^2 Parareal solve reported beside it")
+    ap.add_argument("--no-e2e", action="store_true", help="--config sweep: skip the end-to-end (host buffer) solves")
     ap.add_argument("--config", default="fine-step",
                     choices=["fine-step", "parareal", "learned", "sweep", "large", "steppers", "coarse-sweep",
                              "coarse-sweep-roberts", "profile"],
@@ -1291,7 +1300,10 @@ def main():
     if args.config == "profile":
         run_profile(args)
         return
-    args.warmup = max(args.warmup, 3)
+    # the measured lines take at least 3 warm-up steps; the sweep study, whose 256-instance
+    # solves take minutes, may take fewer (it reports the number it used)
+    if args.config != "sweep":
+        args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
         return

@@ -522,6 +522,26 @@ kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const double* const*
                        int k_max, double tol, const char* tune_cache, double* const* u_final,
                        kd_instance_result* results, kd_sweep_stats* stats, void* cuda_stream, char* err);
 
+/* A prepared sweep of the same kind (kd_sweep_run is kd_sweep_create, one kd_sweep_exec and
+ * kd_sweep_destroy).  kd_sweep_create groups the instances by (n, n_coarse) and makes
+ * each group's context, device buffers and workspaces once (KD_EINVAL for invalid
+ * instances or sizes, KD_ENOMEM / KD_ECUDA on device failures; err as above); the object
+ * is owned by the library until kd_sweep_destroy (NULL is a no-op).  kd_sweep_exec runs
+ * the Parareal iterations of every instance from b0 (arguments and results as in
+ * kd_sweep_run; tune_cache is read on the first exec only) and may be called any number
+ * of times.  The parallel fine step of each (iteration, set of unconverged instances) is
+ * captured into a CUDA graph the first time it occurs and replayed when it recurs, e.g.
+ * in a repeated exec of the same initial fields; kd_sweep_set_graphs(sw, 0) launches it
+ * directly instead (same values).  Same numerics as Eq. 8 / Eq. 9 per instance, as in
+ * kd_sweep_run. */
+typedef struct kd_sweep kd_sweep;
+kd_status kd_sweep_create(const kd_instance* inst, int n_inst, double T, int n_slices, void* cuda_stream,
+                          kd_sweep** out, char* err);
+kd_status kd_sweep_exec(kd_sweep* sw, const double* const* b0, int k_max, double tol, const char* tune_cache,
+                        double* const* u_final, kd_instance_result* results, kd_sweep_stats* stats, char* err);
+kd_status kd_sweep_set_graphs(kd_sweep* sw, int enable);
+kd_status kd_sweep_destroy(kd_sweep* sw);
+
 /* Number of kernels this context has launched since kd_create (-1 for NULL). */
 long long kd_launch_count(kd_ctx* ctx);
 

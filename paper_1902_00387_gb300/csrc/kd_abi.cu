@@ -461,24 +461,7 @@ kd_status ensure_conv_tmp(kd_ctx* ctx, size_t bytes) {
 // increment form Fv[n] += F(U[n] - Uprev[n]) (iter > 1).
 static kd_status fine_sweep_launches(kd_ctx* ctx, int first, int N, int S, double dt, int iter);
 
-// The FFT operator's fine sweep is ~8 S + 3 launches; with graphs on, the launches of
-// one sweep shape are captured once into a CUDA graph (programmatic dependent launches
-// included) and replayed; the values are those of the direct launches.
-kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
-  // (not for the pipelined iterations: their chunks already interleave with the serial
-  // sweep on separate streams)
-  if (!ctx->graphs || ctx->prof || ctx->overlap > 0 || conv_op(ctx) || N - first <= 0)
-    return fine_sweep_launches(ctx, first, N, S, dt, iter);
-  // the allocations the sweep may make happen before the capture
-  {
-    FineArgs a0 = fine_args(ctx, ctx->ws_f, ctx->tab_f, ctx->p.n, N - first, dt, ctx->t0f + first);
-    kd_status s0 = with_phases(ctx, ctx->ws_f, a0, S);
-    if (s0 != KD_OK) return s0;
-  }
-  long long dbits;
-  memcpy(&dbits, &dt, 8);
-  const auto key = std::make_tuple(first, N, S, dbits, iter == 1 ? 1 : 0, ctx->plan[0].col * 64 + ctx->plan[0].row,
-                                   ctx->pdl, ctx->p.fine_form, ctx->alloc_gen);
+kd_status run_graph(kd_ctx* ctx, const std::string& key, const std::function<kd_status()>& launches) {
   // the graph runs on the context's own capturable stream, ordered after the work
   // enqueued on ctx->st and before what follows there
   if (!ctx->st_g) {
@@ -492,7 +475,7 @@ kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) 
     cudaStream_t user = ctx->st;
     KD_CUDA(cudaStreamBeginCapture(ctx->st_g, cudaStreamCaptureModeThreadLocal), "begin capture");
     ctx->st = ctx->st_g;
-    const kd_status s = fine_sweep_launches(ctx, first, N, S, dt, iter);
+    const kd_status s = launches();
     ctx->st = user;
     const cudaError_t e = cudaStreamEndCapture(ctx->st_g, &g);
     if (s != KD_OK) {
@@ -514,6 +497,28 @@ kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) 
   KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->gev[1], 0), "graph fence");
   ctx->launches += it->second.launches;
   return KD_OK;
+}
+
+// The FFT operator's fine sweep is ~8 S + 3 launches; with graphs on, the launches of
+// one sweep shape are captured once into a CUDA graph (programmatic dependent launches
+// included) and replayed; the values are those of the direct launches.
+kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {
+  // (not for the pipelined iterations: their chunks already interleave with the serial
+  // sweep on separate streams)
+  if (!ctx->graphs || ctx->prof || ctx->overlap > 0 || conv_op(ctx) || N - first <= 0)
+    return fine_sweep_launches(ctx, first, N, S, dt, iter);
+  // the allocations the sweep may make happen before the capture
+  {
+    FineArgs a0 = fine_args(ctx, ctx->ws_f, ctx->tab_f, ctx->p.n, N - first, dt, ctx->t0f + first);
+    kd_status s0 = with_phases(ctx, ctx->ws_f, a0, S);
+    if (s0 != KD_OK) return s0;
+  }
+  long long dbits;
+  memcpy(&dbits, &dt, 8);
+  char key[192];
+  snprintf(key, sizeof(key), "parareal %d %d %d %lld %d %d %d %d %d %llu", first, N, S, dbits, iter == 1 ? 1 : 0,
+           ctx->plan[0].col, ctx->plan[0].row, ctx->pdl, ctx->p.fine_form, ctx->alloc_gen);
+  return run_graph(ctx, key, [&] { return fine_sweep_launches(ctx, first, N, S, dt, iter); });
 }
 
 static kd_status fine_sweep_launches(kd_ctx* ctx, int first, int N, int S, double dt, int iter) {

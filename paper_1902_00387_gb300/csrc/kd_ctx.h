@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <string>
+#include <functional>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -49,9 +50,9 @@ struct kd_ctx {
   // st2 while the serial sweep of iteration k runs on st (0: one batched sweep, no overlap)
   int overlap = 0;
   int coarse_cluster = 0;          // blocks per cluster of the coarse solver (0: default)
-  // captured CUDA graphs of the Parareal fine sweep (kd_set_graphs), keyed by the sweep's
-  // shape and launch plan and by the allocation generation (any device allocation or
-  // free invalidates them)
+  // captured CUDA graphs of fine sweeps (kd_set_graphs; run_graph), keyed by a signature
+  // of the sweep's shape and launch plan that includes the allocation generation (any
+  // device allocation or free invalidates them)
   int graphs = 1;
   unsigned long long alloc_gen = 0;
   cudaStream_t st_g = nullptr;     // the graphs run here (a capturable stream), fenced by gev
@@ -60,7 +61,7 @@ struct kd_ctx {
     cudaGraphExec_t exec;
     long long launches;
   };
-  std::map<std::tuple<int, int, int, long long, int, int, int, int, unsigned long long>, GraphEntry> gcache;
+  std::map<std::string, GraphEntry> gcache;
   double* ref_T = nullptr;         // kd_set_reference: compact FP64 reference field at t = T
   int gemm_engine = 0;             // learned-operator training GEMM: KD_GEMM_TCGEN05 (0) or KD_GEMM_MMA_SYNC
   int coarse_sync = 0;             // coarse solver halo exchange: KD_SYNC_CLUSTER (0) or KD_SYNC_P2P
@@ -166,6 +167,11 @@ kd_status coarse_step(kd_ctx* ctx, int i, int Sc, double dtc, bool init, bool la
 kd_status learned_step(kd_ctx* ctx, int i, bool init, bool last);
 bool use_learned(const kd_ctx* ctx, int i);
 kd_status fine_sweep(kd_ctx* ctx, int first, int N, int S, double dt, int iter);
+// Enqueue `launches` (work on ctx->st) through a CUDA graph captured once per `key` and
+// replayed on the context's graph stream, fenced against ctx->st; the values are those of
+// the direct launches.  The caller makes every allocation the launches need beforehand
+// and puts into `key` everything the launches depend on besides device data.
+kd_status run_graph(kd_ctx* ctx, const std::string& key, const std::function<kd_status()>& launches);
 kd_status copy_in_b0(kd_ctx* ctx, const double* b0);
 kd_status ensure_full_tmp(kd_ctx* ctx, size_t bytes);
 // the convolution-form fine operator (fine_operator KD_FINE_CONV) on FP64 compact fields

@@ -196,15 +196,13 @@ struct GroupBufs {
   size_t phc_bytes = 0;
 };
 
-kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int k_max, double tol,
-                    const char* tune_cache, const double* const* b0, double* const* u_final, GroupTimes& gt) {
+// Device buffers of a group and the workspaces its launches use (made once per sweep
+// object, before any launch is captured).
+kd_status alloc_group(kd_ctx* ctx, const std::vector<Member>& mem, int N, GroupBufs& g) {
   const int m = (int)mem.size();
   const int n = mem[0].in.n, nc = mem[0].in.n_coarse;
-  const int Kf = n / 3, Pf = kept(n), Kc = nc / 3, Pc = kept(nc);
-  const long len = compact_len(n), lenc = compact_len(nc);
-  const double dT = T / N;
+  const long len = compact_len(n);
   const long slots = (long)m * (N + 1);
-  GroupBufs g;
   kd_status s;
   if ((s = dalloc(ctx, (void**)&g.U, slots * len * 16, "sweep U")) != KD_OK ||
       (s = dalloc(ctx, (void**)&g.Fv, slots * len * 16, "sweep F values")) != KD_OK ||
@@ -224,19 +222,39 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
     return s;
   if ((s = ensure_ws(ctx, ctx->ws_f, n, KD_C64, (long)m * N)) != KD_OK) return s;
   if ((s = ensure_ws(ctx, ctx->ws_c, nc, KD_C64, m)) != KD_OK) return s;
-  if (tune_cache && (s = kd_autotune(ctx, KD_GRID_FINE, m * N, 2, tune_cache, nullptr)) != KD_OK) return s;
-  // initial fields -> U[member][0]
   const size_t fb = 3UL * n * n * 16;
-  {
-    const size_t need = fb > (size_t)len * 16 ? fb : (size_t)len * 16;
-    if (ctx->full_tmp_bytes < need) {
-      dfree(ctx, ctx->full_tmp);
-      ctx->full_tmp = nullptr;
-      ctx->full_tmp_bytes = 0;
-      if ((s = dalloc(ctx, &ctx->full_tmp, need, "staging")) != KD_OK) return s;
-      ctx->full_tmp_bytes = need;
-    }
+  const size_t need = fb > (size_t)len * 16 ? fb : (size_t)len * 16;
+  if (ctx->full_tmp_bytes < need) {
+    dfree(ctx, ctx->full_tmp);
+    ctx->full_tmp = nullptr;
+    ctx->full_tmp_bytes = 0;
+    if ((s = dalloc(ctx, &ctx->full_tmp, need, "staging")) != KD_OK) return s;
+    ctx->full_tmp_bytes = need;
   }
+  return KD_OK;
+}
+
+// One solve of every member of a group from its initial field (the Parareal iterations of
+// Eq. 8 with the defect of Eq. 9 per member).
+kd_status exec_group(kd_ctx* ctx, std::vector<Member>& mem, GroupBufs& g, double T, int N, int k_max, double tol,
+                     const double* const* b0, double* const* u_final, GroupTimes& gt) {
+  const int m = (int)mem.size();
+  const int n = mem[0].in.n, nc = mem[0].in.n_coarse;
+  const int Kf = n / 3, Pf = kept(n), Kc = nc / 3, Pc = kept(nc);
+  const long len = compact_len(n), lenc = compact_len(nc);
+  const double dT = T / N;
+  const long slots = (long)m * (N + 1);
+  const size_t fb = 3UL * n * n * 16;
+  kd_status s;
+  const long long launches0 = ctx->launches;
+  for (Member& mb : mem) {
+    mb.active = true;
+    mb.status = KD_OK;
+    mb.k = 0;
+    mb.sigma.clear();
+    mb.growth = 0.0;
+  }
+  // initial fields -> U[member][0]
   for (int r = 0; r < m; ++r) {
     KD_CUDA(cudaMemcpyAsync(ctx->full_tmp, b0[mem[r].idx], fb, cudaMemcpyDefault, ctx->st), "copy b0");
     KD_LAUNCH(full_to_compact(KD_C128, ctx->full_tmp, KD_C128, g.U + 2 * (long)r * (N + 1) * len, 1, n, ctx->st),
@@ -285,17 +303,32 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
       KD_CUDA(cudaMemcpyAsync(g.spf, spf.data(), nE * sizeof(SliceParams), cudaMemcpyHostToDevice, ctx->st),
               "slice params");
       KD_CUDA(cudaMemcpyAsync(g.t0f, t0f.data(), nE * 8, cudaMemcpyHostToDevice, ctx->st), "slice times");
-      k_delta_in_map<float><<<grid1(nE * len), 256, 0, ctx->st>>>((const cx<double>*)g.U, (cx<double>*)g.Up,
-                                                                    (cx<float>*)ctx->ws_f.X, g.emap, len, nE, k == 1);
-      KD_LAUNCH(0, "increment to fine");
       FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, nE, mem[Af[0]].dt, g.t0f);
       a.flow = KD_FLOW_GALLOWAY_PROCTOR;   // the phase table holds every field's flow
       a.sp = g.spf;
       if ((s = with_phases(ctx, ctx->ws_f, a, Smax)) != KD_OK) return s;
-      KD_LAUNCH(run_fine(ctx, 0, KD_C64, a, Smax, true, false, nullptr, act_f.data()), "fine steps");
-      k_accum_out_map<float><<<grid1(nE * len), 256, 0, ctx->st>>>((const cx<float>*)ctx->ws_f.X, (cx<double>*)g.Fv,
-                                                                     g.emap, len, nE, k == 1);
-      KD_LAUNCH(0, "accumulate fine");
+      auto launches = [&]() -> kd_status {
+        k_delta_in_map<float><<<grid1(nE * len), 256, 0, ctx->st>>>((const cx<double>*)g.U, (cx<double>*)g.Up,
+                                                                      (cx<float>*)ctx->ws_f.X, g.emap, len, nE, k == 1);
+        KD_LAUNCH(0, "increment to fine");
+        KD_LAUNCH(run_fine(ctx, 0, KD_C64, a, Smax, true, false, nullptr, act_f.data()), "fine steps");
+        k_accum_out_map<float><<<grid1(nE * len), 256, 0, ctx->st>>>((const cx<float>*)ctx->ws_f.X,
+                                                                       (cx<double>*)g.Fv, g.emap, len, nE, k == 1);
+        KD_LAUNCH(0, "accumulate fine");
+        return KD_OK;
+      };
+      if (ctx->graphs && !ctx->prof) {
+        // replayed when the same (iteration, active members, plan) recurs, e.g. in a
+        // repeated kd_sweep_exec of the same instances
+        std::string key = "sweep " + std::to_string(k == 1) + " " + std::to_string(first) + " " +
+                          std::to_string(nE) + " " + std::to_string(Smax) + " " + std::to_string(ctx->plan[0].col) +
+                          "," + std::to_string(ctx->plan[0].row) + " " + std::to_string(ctx->pdl) + " " +
+                          std::to_string(ctx->alloc_gen) + " :";
+        for (int r : Af) key += " " + std::to_string(r);
+        if ((s = run_graph(ctx, key, launches)) != KD_OK) return s;
+      } else if ((s = launches()) != KD_OK) {
+        return s;
+      }
     }
     KD_CUDA(cudaEventRecord(e1, ctx->st), "event");
     // ---- serial sweep
@@ -447,7 +480,7 @@ kd_status run_group(kd_ctx* ctx, std::vector<Member>& mem, double T, int N, int 
   }
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   for (int r = 0; r < m; ++r) mem[r].growth = fit[2 * r];
-  gt.launches = ctx->launches;
+  gt.launches = ctx->launches - launches0;
   return KD_OK;
 }
 
@@ -467,22 +500,44 @@ void set_err(char* err, const std::string& m) {
 
 }  // namespace
 
-extern "C" kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const double* const* b0, double T,
-                                  int n_slices, int k_max, double tol, const char* tune_cache, double* const* u_final,
-                                  kd_instance_result* results, kd_sweep_stats* stats, void* cuda_stream, char* err) {
-  const auto t_start = std::chrono::steady_clock::now();
+// A prepared sweep: the instances grouped by (n, n_coarse), each group with its context,
+// device buffers and workspaces, kept across kd_sweep_exec calls.
+struct kd_sweep {
+  double T = 0.0;
+  int N = 0;
+  int n_inst = 0;
+  struct Group {
+    kd_ctx* ctx = nullptr;
+    std::vector<Member> mem;
+    GroupBufs g;
+    bool tuned = false;
+  };
+  std::vector<Group> groups;
+};
+
+extern "C" kd_status kd_sweep_destroy(kd_sweep* sw) {
+  if (!sw) return KD_OK;
+  for (auto& gr : sw->groups)
+    if (gr.ctx) kd_destroy(gr.ctx);   // frees the group's buffers with the context's allocations
+  delete sw;
+  return KD_OK;
+}
+
+extern "C" kd_status kd_sweep_create(const kd_instance* inst, int n_inst, double T, int n_slices, void* cuda_stream,
+                                     kd_sweep** out, char* err) {
   set_err(err, "");
-  if (!inst || !b0 || n_inst < 1) return set_err(err, "kd_sweep_run: no instances"), KD_EINVAL;
-  if (n_slices < 1 || n_slices > KD_MAX_SLICES) return set_err(err, "kd_sweep_run: n_slices out of range"), KD_EINVAL;
-  if (k_max < 0 || k_max > KD_MAX_ITERS) return set_err(err, "kd_sweep_run: k_max out of range"), KD_EINVAL;
-  if (!(T > 0) || !isfinite(T)) return set_err(err, "kd_sweep_run: T must be > 0"), KD_EINVAL;
+  if (!out) return set_err(err, "kd_sweep_create: out is NULL"), KD_EINVAL;
+  *out = nullptr;
+  if (!inst || n_inst < 1) return set_err(err, "kd_sweep_create: no instances"), KD_EINVAL;
+  if (n_slices < 1 || n_slices > KD_MAX_SLICES) return set_err(err, "kd_sweep_create: n_slices out of range"), KD_EINVAL;
+  if (!(T > 0) || !isfinite(T)) return set_err(err, "kd_sweep_create: T must be > 0"), KD_EINVAL;
   for (int i = 0; i < n_inst; ++i) {
     std::string why;
-    if (!b0[i]) return set_err(err, "kd_sweep_run: b0[" + std::to_string(i) + "] is NULL"), KD_EINVAL;
-    if (!check_instance(inst[i], why)) return set_err(err, "kd_sweep_run: instance " + std::to_string(i) + ": " + why), KD_EINVAL;
+    if (!check_instance(inst[i], why))
+      return set_err(err, "kd_sweep_create: instance " + std::to_string(i) + ": " + why), KD_EINVAL;
   }
   const double dT = T / n_slices;
-  std::map<std::pair<int, int>, std::vector<Member>> groups;
+  std::map<std::pair<int, int>, std::vector<Member>> by_grid;
   for (int i = 0; i < n_inst; ++i) {
     Member mb;
     mb.idx = i;
@@ -491,42 +546,77 @@ extern "C" kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const dou
     mb.Sc = steps_for(dT, inst[i].dt_coarse);
     mb.dt = dT / mb.S;
     mb.dtc = dT / mb.Sc;
-    groups[{inst[i].n, inst[i].n_coarse}].push_back(mb);
+    by_grid[{inst[i].n, inst[i].n_coarse}].push_back(mb);
   }
-  kd_status worst = KD_OK;
-  GroupTimes total;
-  long long launches = 0;
-  for (auto& kv : groups) {
-    std::vector<Member>& mem = kv.second;
+  kd_sweep* sw = new kd_sweep();
+  sw->T = T;
+  sw->N = n_slices;
+  sw->n_inst = n_inst;
+  for (auto& kv : by_grid) {
+    kd_sweep::Group gr;
+    gr.mem = kv.second;
+    const Member& m0 = gr.mem[0];
     kd_params p;
     memset(&p, 0, sizeof(p));
-    p.flow = mem[0].in.flow;
-    p.n = mem[0].in.n;
-    p.kz = mem[0].in.kz;
-    p.Rm = mem[0].in.Rm;
-    p.dt_fine = mem[0].in.dt_fine;
+    p.flow = m0.in.flow;
+    p.n = m0.in.n;
+    p.kz = m0.in.kz;
+    p.Rm = m0.in.Rm;
+    p.dt_fine = m0.in.dt_fine;
     p.prec_fine = KD_C64;
-    p.n_coarse = mem[0].in.n_coarse;
-    p.dt_coarse = mem[0].in.dt_coarse;
+    p.n_coarse = m0.in.n_coarse;
+    p.dt_coarse = m0.in.dt_coarse;
     p.prec_coarse = KD_C64;
     p.coarse_kind = KD_COARSE_CLASSICAL;
     p.learned_modes = 0;
     p.fine_form = KD_FINE_INCREMENT;
-    kd_ctx* ctx = nullptr;
-    kd_status s = kd_create(&p, cuda_stream, &ctx);
-    if (s != KD_OK) return set_err(err, "kd_sweep_run: context creation failed"), s;
-    GroupTimes gt;
-    s = run_group(ctx, mem, T, n_slices, k_max, tol, tune_cache, b0, u_final, gt);
+    kd_status s = kd_create(&p, cuda_stream, &gr.ctx);
+    if (s == KD_OK) s = alloc_group(gr.ctx, gr.mem, n_slices, gr.g);
     if (s != KD_OK) {
-      set_err(err, "kd_sweep_run: " + ctx->err);
-      kd_destroy(ctx);
+      set_err(err, std::string("kd_sweep_create: ") + (gr.ctx ? gr.ctx->err : std::string("context creation failed")));
+      if (gr.ctx) kd_destroy(gr.ctx);
+      kd_sweep_destroy(sw);
       return s;
     }
+    sw->groups.push_back(std::move(gr));
+  }
+  *out = sw;
+  return KD_OK;
+}
+
+extern "C" kd_status kd_sweep_set_graphs(kd_sweep* sw, int enable) {
+  if (!sw) return KD_EINVAL;
+  for (auto& gr : sw->groups) kd_set_graphs(gr.ctx, enable);
+  return KD_OK;
+}
+
+extern "C" kd_status kd_sweep_exec(kd_sweep* sw, const double* const* b0, int k_max, double tol,
+                                   const char* tune_cache, double* const* u_final, kd_instance_result* results,
+                                   kd_sweep_stats* stats, char* err) {
+  const auto t_start = std::chrono::steady_clock::now();
+  set_err(err, "");
+  if (!sw || !b0) return set_err(err, "kd_sweep_exec: NULL sweep or b0"), KD_EINVAL;
+  if (k_max < 0 || k_max > KD_MAX_ITERS) return set_err(err, "kd_sweep_exec: k_max out of range"), KD_EINVAL;
+  for (int i = 0; i < sw->n_inst; ++i)
+    if (!b0[i]) return set_err(err, "kd_sweep_exec: b0[" + std::to_string(i) + "] is NULL"), KD_EINVAL;
+  kd_status worst = KD_OK;
+  GroupTimes total;
+  long long launches = 0;
+  for (auto& gr : sw->groups) {
+    std::vector<Member>& mem = gr.mem;
+    kd_ctx* ctx = gr.ctx;
+    kd_status s = KD_OK;
+    if (tune_cache && !gr.tuned) {
+      s = kd_autotune(ctx, KD_GRID_FINE, (int)mem.size() * sw->N, 2, tune_cache, nullptr);
+      gr.tuned = s == KD_OK;
+    }
+    GroupTimes gt;
+    if (s == KD_OK) s = exec_group(ctx, mem, gr.g, sw->T, sw->N, k_max, tol, b0, u_final, gt);
+    if (s != KD_OK) return set_err(err, "kd_sweep_exec: " + ctx->err), s;
     launches += gt.launches;
     total.fine += gt.fine;
     total.coarse += gt.coarse;
     total.dof += gt.dof;
-    kd_destroy(ctx);
     for (const Member& mb : mem) {
       if (mb.status == KD_ENONFINITE) worst = KD_ENONFINITE;
       else if (mb.status == KD_ENOTCONV && worst == KD_OK) worst = KD_ENOTCONV;
@@ -545,14 +635,31 @@ extern "C" kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const dou
   }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    stats->n_groups = (int)groups.size();
+    stats->n_groups = (int)sw->groups.size();
     stats->ms_fine = total.fine;
     stats->ms_coarse = total.coarse;
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     stats->n_launches = launches;
     stats->fine_dof_steps = total.dof;
   }
-  if (worst == KD_ENONFINITE) set_err(err, "kd_sweep_run: an instance's defect was not finite");
-  if (worst == KD_ENOTCONV) set_err(err, "kd_sweep_run: some instances did not reach tol within k_max");
+  if (worst == KD_ENONFINITE) set_err(err, "kd_sweep_exec: an instance's defect was not finite");
+  if (worst == KD_ENOTCONV) set_err(err, "kd_sweep_exec: some instances did not reach tol within k_max");
   return worst;
+}
+
+extern "C" kd_status kd_sweep_run(const kd_instance* inst, int n_inst, const double* const* b0, double T,
+                                  int n_slices, int k_max, double tol, const char* tune_cache, double* const* u_final,
+                                  kd_instance_result* results, kd_sweep_stats* stats, void* cuda_stream, char* err) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!b0 && inst && n_inst >= 1) return set_err(err, "kd_sweep_run: no instances"), KD_EINVAL;
+  if (k_max < 0 || k_max > KD_MAX_ITERS) return set_err(err, "kd_sweep_run: k_max out of range"), KD_EINVAL;
+  for (int i = 0; b0 && inst && i < n_inst; ++i)
+    if (!b0[i]) return set_err(err, "kd_sweep_run: b0[" + std::to_string(i) + "] is NULL"), KD_EINVAL;
+  kd_sweep* sw = nullptr;
+  kd_status s = kd_sweep_create(inst, n_inst, T, n_slices, cuda_stream, &sw, err);
+  if (s != KD_OK) return s;
+  s = kd_sweep_exec(sw, b0, k_max, tol, tune_cache, u_final, results, stats, err);
+  kd_sweep_destroy(sw);
+  if (stats) stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return s;
 }

@@ -84,7 +84,7 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parare
            "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
            "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_parareal_resume", "kd_set_graphs",
            "kd_set_reference", "kd_set_overlap", "kd_set_coarse_cluster",
-           "kd_set_coarse_sync"]
+           "kd_set_coarse_sync", "kd_sweep_create", "kd_sweep_exec", "kd_sweep_set_graphs", "kd_sweep_destroy"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -124,6 +124,11 @@ def load():
         "kd_sweep_run": (I, [ctypes.POINTER(kd_instance), I, ctypes.POINTER(P), D, I, I, D, ctypes.c_char_p,
                              ctypes.POINTER(P), ctypes.POINTER(kd_instance_result), ctypes.POINTER(kd_sweep_stats),
                              P, ctypes.c_char_p]),
+        "kd_sweep_create": (I, [ctypes.POINTER(kd_instance), I, D, I, P, ctypes.POINTER(P), ctypes.c_char_p]),
+        "kd_sweep_exec": (I, [P, ctypes.POINTER(P), I, D, ctypes.c_char_p, ctypes.POINTER(P),
+                              ctypes.POINTER(kd_instance_result), ctypes.POINTER(kd_sweep_stats), ctypes.c_char_p]),
+        "kd_sweep_set_graphs": (I, [P, I]),
+        "kd_sweep_destroy": (I, [P]),
         "kd_growth_power": (I, [P, P, D, D, I, D, ctypes.POINTER(D), ctypes.POINTER(I), P]),
         "kd_growth_arnoldi": (I, [P, P, D, D, I, I, I, D, P, P, ctypes.POINTER(I), P]),
         "kd_hessenberg_eig": (I, [I, P, P, P]),
@@ -466,6 +471,80 @@ def kd_sweep_run(instances, b0, T, n_slices, k_max, tol, u_final=None, tune_cach
     if s not in (KD_OK, KD_ENOTCONV):
         raise KdError(s, err.value.decode())
     return s, list(res), st
+
+
+class Sweep:
+    """A prepared batched sweep (kd_sweep_create): groups, contexts and device buffers made
+    once; exec() runs the Parareal iterations of every instance and may be repeated (the
+    fine steps of recurring (iteration, active set) shapes replay captured CUDA graphs)."""
+
+    def __init__(self, instances, T, n_slices, stream=None):
+        lib = load()
+        self.m = len(instances)
+        self.instances = list(instances)
+        arr = (kd_instance * self.m)(*instances)
+        err = ctypes.create_string_buffer(256)
+        h = ctypes.c_void_p()
+        strm = _current_stream() if stream is None else stream
+        s = lib.kd_sweep_create(arr, self.m, float(T), int(n_slices), strm, ctypes.byref(h), err)
+        if s != KD_OK:
+            raise KdError(s, err.value.decode())
+        self.h = h
+
+    def set_graphs(self, enable):
+        load().kd_sweep_set_graphs(self.h, int(bool(enable)))
+
+    def exec(self, b0, k_max, tol, u_final=None, tune_cache=None):
+        """Returns (status, results list, stats), as kd_sweep_run."""
+        lib = load()
+        m = self.m
+        if len(b0) != m or (u_final is not None and len(u_final) != m):
+            raise ValueError("one initial field (and one output, if given) per instance")
+        for i, (q, b) in enumerate(zip(self.instances, b0)):
+            _need(None, b, 1, "b0[%d]" % i, n=q.n)
+        keep = list(b0) + [u for u in (u_final or []) if u is not None]
+        b_ptrs = (ctypes.c_void_p * m)(*[_any_ptr(b, "complex128") for b in b0])
+        u_ptrs = None
+        if u_final is not None:
+            u_ptrs = (ctypes.c_void_p * m)(*[_any_ptr(u, "complex128") if u is not None else None for u in u_final])
+        res = (kd_instance_result * m)()
+        st = kd_sweep_stats()
+        err = ctypes.create_string_buffer(256)
+        s = lib.kd_sweep_exec(self.h, b_ptrs, int(k_max), float(tol), tune_cache.encode() if tune_cache else None,
+                              u_ptrs, res, ctypes.byref(st), err)
+        del keep
+        if s not in (KD_OK, KD_ENOTCONV):
+            raise KdError(s, err.value.decode())
+        return s, list(res), st
+
+    def close(self):
+        if self.h:
+            load().kd_sweep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kd_sweep_create(instances, T, n_slices, stream=None):
+    """kd_sweep_create: a prepared sweep (a Sweep object)."""
+    return Sweep(instances, T, n_slices, stream)
+
+
+def kd_sweep_exec(sw, b0, k_max, tol, u_final=None, tune_cache=None):
+    """kd_sweep_exec: returns (status, results list, stats)."""
+    return sw.exec(b0, k_max, tol, u_final=u_final, tune_cache=tune_cache)
+
+
+def kd_sweep_set_graphs(sw, enable):
+    sw.set_graphs(enable)
+
+
+def kd_sweep_destroy(sw):
+    sw.close()
 
 
 def kd_growth_power(ctx, b0, t0, tau, max_iter, tol, b_out=None):

@@ -114,3 +114,54 @@ def test_sweep_argument_errors(kd):
     bad = [kd.make_instance(O.ROBERTS, 48, 1.0, 8.0, 0.01, 16, 0.1)]
     with pytest.raises(kd.KdError):
         kd.kd_sweep_run(bad, b0, T, N, 4, 1e-6)
+
+
+def test_sweep_object_repeats_and_graphs_change_no_value(kd):
+    """A prepared sweep executed twice (the second exec replays the captured fine steps)
+    and once without graphs gives kd_sweep_run's results bit for bit."""
+    seeds = [501, 502, 503, 504, 505]
+    ins = [kd.make_instance(*x) for x in INSTANCES]
+    b0 = [I.initial_field(x[1], x[2], s).astype(np.complex128) for x, s in zip(INSTANCES, seeds)]
+    ref = [np.zeros_like(b) for b in b0]
+    s_ref, r_ref, _ = kd.kd_sweep_run(ins, b0, T, N, N, 1e-9, u_final=ref)
+    sw = kd.Sweep(ins, T, N)
+    try:
+        runs = []
+        for graphs in (True, True, False):
+            sw.set_graphs(graphs)
+            out = [np.zeros_like(b) for b in b0]
+            s, res, st = sw.exec(b0, N, 1e-9, u_final=out)
+            assert s == s_ref
+            runs.append((out, res, st))
+    finally:
+        sw.close()
+    for out, res, st in runs:
+        for i in range(len(INSTANCES)):
+            assert np.array_equal(out[i], ref[i]), i
+            assert res[i].k_con == r_ref[i].k_con
+            assert list(res[i].sigma[:res[i].k_con]) == list(r_ref[i].sigma[:r_ref[i].k_con])
+    assert runs[0][2].n_launches == runs[1][2].n_launches == runs[2][2].n_launches
+
+
+@pytest.mark.parametrize("n,flow", [(64, O.ROBERTS), (128, O.GALLOWAY_PROCTOR), (256, O.ROBERTS),
+                                    (512, O.GALLOWAY_PROCTOR)])
+def test_sweep_recipe_grid_sides_against_oracle(kd, n, flow):
+    """One instance of each grid side of the Rm / kz sweep (Rm = 50 (n / 64)^2, the recipe's
+    steps: GP dt = 0.128 / n, Roberts dt = 1.6 / n, coarse grid n / 2 with
+    dt_c = min(20 dt (GP) or 10 dt (Roberts), 2 / n_c)), run to K = N on a short horizon:
+    the final state is the oracle's serial fine solution at FP32 accuracy."""
+    Rm, kz = 50.0 * (n / 64) ** 2, 0.8
+    dt = 0.128 / n if flow == O.GALLOWAY_PROCTOR else 1.6 / n
+    nc = n // 2
+    dtc = min((20 if flow == O.GALLOWAY_PROCTOR else 10) * dt, 2.0 / nc)
+    TT, NN = (0.02, 4) if flow == O.GALLOWAY_PROCTOR else (0.2, 4)
+    ins = [kd.make_instance(flow, n, kz, Rm, dt, nc, dtc)]
+    b0 = [I.initial_field(n, kz, 600 + n).astype(np.complex128)]
+    out = [np.zeros_like(b0[0])]
+    status, res, st = kd.kd_sweep_run(ins, b0, TT, NN, NN, 0.0, u_final=out)
+    assert res[0].k_con == NN
+    prob = O.Problem(flow, n, kz, Rm)
+    dT = TT / NN
+    S = res[0].n_fine_steps
+    ser = O.serial_fine(b0[0], lambda u, i: O.propagate(u, prob, i * dT, dT / S, S), NN)
+    assert rel(out[0], ser[-1]) < 2e-5, rel(out[0], ser[-1])
