@@ -510,7 +510,7 @@ ROBERTS_SWEEP_WL = {
     "flow": "roberts", "n": 160, "kz": 2.87, "Rm": 512.0, "dt_fine": 1e-2, "T": 50.0, "slices": 10,
     "n_coarse": [20, 40, 60, 80, 100, 120, 160], "dt_coarse": "dt_fine * N_F / N_C (the stability limit ~1.6 / N)",
     "tol": 1e-6, "k_max": 10, "prec_fine": "complex64", "prec_coarse": "complex64", "update": "float64",
-    "fine_form": "increment", "fine_operator": "conv (N_F = 160 is not a power of two)",
+    "fine_form": "increment",
 }
 
 
@@ -526,7 +526,9 @@ def run_roberts_coarse_sweep(args):
     import paper_1902_00387_gb300 as kd
     kd.load()
     torch.cuda.init()
-    W = ROBERTS_SWEEP_WL
+    W = dict(ROBERTS_SWEEP_WL, fine_operator=args.fine_operator + (" (mixed-radix 5 x 32 FFT)" if args.fine_operator
+                                                                    == "fft" else " (spectral convolution)"))
+    fine_op = kd.KD_FINE_CONV if args.fine_operator == "conv" else kd.KD_FINE_FFT
     n, N, T = W["n"], W["slices"], W["T"]
     b0 = torch.tensor(kd_inputs.initial_field(n, W["kz"], 1000), device="cuda")
 
@@ -547,7 +549,7 @@ def run_roberts_coarse_sweep(args):
         dtc = W["dt_fine"] * n / nc
         p = kd.make_params(kd.KD_FLOW_ROBERTS, n, W["kz"], W["Rm"], W["dt_fine"], kd.KD_C64, n_coarse=nc,
                            dt_coarse=dtc, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT,
-                           fine_operator=kd.KD_FINE_CONV)
+                           fine_operator=fine_op)
         ctx = kd.kd_create(p)
         try:
             if serial is None:

@@ -74,14 +74,21 @@ enum { KD_RK443 = 0, KD_RK222 = 1, KD_RK111 = 2 };
 /* Problem and discretisation parameters (Sec. 2, Sec. 4, Table 1). */
 typedef struct {
   int flow;            /* KD_FLOW_*; NONE (u = 0) leaves pure diffusion */
-  int n;               /* fine grid side: 16, 32, 64, 128, 256, 512 or 1024; with
-                          KD_FINE_CONV any even side in [16, 190] (Table 1's N_F = 160) */
+  int n;               /* fine grid side, even (kept set |kx|, |ky| <= n/3).  KD_FINE_FFT:
+                          n = 16, 32, ..., 1024 and 96, 160, 192 (32 R, R = 3, 5, 6: mixed
+                          radix; Table 1's N_F = 160) transform on n itself; any other even
+                          n <= 286 on the smallest mixed-radix side m >= 2 (n/3) + 2: the flow
+                          has only the wavenumbers +-1, so m points resolve u x b on the kept
+                          set without aliasing, exactly as n points do (n = 240, the 3/2-padded
+                          grid of 160 kept modes, runs on m = 192).  KD_FINE_CONV: even
+                          n <= 190 */
   double kz;           /* wavenumber along the invariant direction (the paper's kx for GP) */
   double Rm;           /* magnetic Reynolds number (Eq. 2), > 0 */
   double dt_fine;      /* fine step delta t (upper bound; see kd_parareal_run) */
   int prec_fine;       /* KD_C64 or KD_C128 arithmetic of the fine propagator */
-  int n_coarse;        /* coarse grid side N_C, 16 <= N_C <= n: a power of two, or an even
-                          side whose dealiased set the cluster solver holds (N_C <= 190) */
+  int n_coarse;        /* coarse grid side N_C, even, 16 <= N_C <= n: the cluster solver when
+                          its dealiased set fits (N_C <= 190), else the FFT fine kernels (a
+                          side they take, as for n) */
   double dt_coarse;    /* coarse step Delta t (upper bound) */
   int prec_coarse;     /* KD_C64 or KD_C128 arithmetic of the classical coarse propagator */
   int coarse_kind;     /* KD_COARSE_CLASSICAL or KD_COARSE_LEARNED (needs kd_learned_init and

@@ -123,7 +123,7 @@ kd_status ensure_ws(kd_ctx* ctx, FineWs& w, int n, int prec, long batch) {
   w = FineWs();
   const size_t es = csize(prec);
   const size_t spec = (size_t)batch * compact_len(n) * es;
-  const size_t mixed = (size_t)batch * 3 * kept(n) * n * es;
+  const size_t mixed = (size_t)batch * 3 * kept(n) * fine_fft_grid(n) * es;   // x on the transform's grid
   kd_status s;
   if ((s = dalloc(ctx, &w.X, spec, "state")) != KD_OK) return s;
   if ((s = dalloc(ctx, &w.R2, spec, "R2")) != KD_OK) return s;
@@ -142,7 +142,7 @@ kd_status ensure_ws(kd_ctx* ctx, FineWs& w, int n, int prec, long batch) {
 FineArgs fine_args(const kd_ctx* ctx, const FineWs& w, const Tables& t, int n, long batch, double dt,
                    const double* t0) {
   FineArgs a;
-  a.n = n;
+  a.n = fine_fft_grid(n);   // the transforms' side; the kept set is that of n
   a.K = n / 3;
   a.P = kept(n);
   a.batch = (int)batch;
@@ -287,12 +287,12 @@ int steps_for(double dT, double dt) {
 kd_status check_params(const kd_params* p, std::string& why) {
   if (!p) return why = "params is NULL", KD_EINVAL;
   if (p->flow < 0 || p->flow > 2) return why = "flow must be 0, 1 or 2", KD_EINVAL;
-  // grids that are not powers of two are checked in kd_create against the cluster solver
+  // the convolution operator's limit is checked in kd_create against the cluster solver
   if (p->n < 16 || p->n > 1024 || (p->n & 1)) return why = "n must be even and in [16, 1024]", KD_EINVAL;
   if (p->n_coarse < 16 || p->n_coarse > p->n || (p->n_coarse & 1))
     return why = "n_coarse must be even and in [16, n]", KD_EINVAL;
-  if (!valid_n(p->n) && p->fine_operator != KD_FINE_CONV)
-    return why = "n must be a power of two in [16, 1024] (other sides need fine_operator KD_FINE_CONV)", KD_EINVAL;
+  if (p->fine_operator == KD_FINE_FFT && fine_fft_grid(p->n) == 0)
+    return why = "n must be a power of two or an even side <= 286 (fine_operator KD_FINE_FFT)", KD_EINVAL;
   if (!(p->Rm > 0) || !isfinite(p->Rm)) return why = "Rm must be finite and > 0", KD_EINVAL;
   if (!isfinite(p->kz)) return why = "kz must be finite", KD_EINVAL;
   if (!(p->dt_fine > 0) || !(p->dt_coarse > 0)) return why = "time steps must be > 0", KD_EINVAL;
@@ -770,21 +770,22 @@ kd_status kd_create(const kd_params* params, void* cuda_stream, kd_ctx** out) {
     delete ctx;
     return KD_ECUDA;
   }
-  // grid sides the cluster solver must hold (known once its kernels are set up)
+  // the kept set the convolution operator's cluster solver must hold (known once its
+  // kernels are set up)
   {
     std::string bad;
     if (params->fine_operator == KD_FINE_CONV && !coarse_conv_supported(kept(params->n)))
       bad = "fine_operator KD_FINE_CONV: the kept set of n does not fit the cluster solver (n <= 192)";
-    else if (!valid_n(params->n_coarse) && !coarse_conv_supported(ctx->cP))
-      bad = "n_coarse that is not a power of two needs a coarse set that fits the cluster solver";
+    else if (fine_fft_grid(params->n_coarse) == 0 && !coarse_conv_supported(ctx->cP))
+      bad = "n_coarse: neither a power of two, nor <= 286, nor a coarse set the cluster solver holds";
     if (!bad.empty()) {
       fprintf(stderr, "kd_create: %s\n", bad.c_str());
       kd_destroy(ctx);
       return KD_EINVAL;
     }
   }
-  if ((s = make_tables(ctx, ctx->tab_f, params->n, params->prec_fine)) != KD_OK ||
-      (s = make_tables(ctx, ctx->tab_c, params->n_coarse, params->prec_coarse)) != KD_OK ||
+  if ((s = make_tables(ctx, ctx->tab_f, fine_fft_grid(params->n), params->prec_fine)) != KD_OK ||
+      (s = make_tables(ctx, ctx->tab_c, fine_fft_grid(params->n_coarse), params->prec_coarse)) != KD_OK ||
       (s = dalloc(ctx, (void**)&ctx->partials, 2 * 1024 * 8, "partials")) != KD_OK ||
       (s = dalloc(ctx, (void**)&ctx->scal, 32 * 8, "scalars")) != KD_OK ||
       (s = dalloc(ctx, (void**)&ctx->Ebuf, (KD_MAX_SLICES + 1) * 8, "energies")) != KD_OK) {

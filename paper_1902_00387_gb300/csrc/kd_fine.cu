@@ -2,8 +2,9 @@
 // Parareal, Sec. 3 Eq. 8 and Sec. 4), all slices of a batch advanced by every launch.
 //
 // This file holds the flow-phase table and the dispatch to the kernel families
-// (kd_fine2.cuh for n <= 256, kd_fine3.cuh for n = 512, 1024, instantiated per
-// precision and grid in kd_fine2_*.cu / kd_fine3_*.cu).  One right-hand-side
+// (kd_fine2.cuh for n <= 256, kd_fine3.cuh / kd_fine4.cuh for n = 512, 1024, instantiated
+// per precision and grid in kd_fine2_*.cu / kd_fine3_*.cu; the mixed-radix kernels of
+// kd_fine_mr.cuh for n = 96, 160, 192 in kd_fine_mr.cu).  One right-hand-side
 // evaluation nabla_k x (u x b) followed by one IMEX stage is two kernels:
 //   column kernel : mixed M (ky rows, x columns) -> inverse FFT in y -> u x b on the
 //                   grid (u analytic, Sec. 2.1 / 2.2) -> forward FFT in y -> keep
@@ -105,16 +106,21 @@ static bool variants_T(int n, int* ncol, int* nrow) {
     case 512: fine3_variants<T, 512>(ncol, nrow); return true;
     case 1024: fine3_variants<T, 1024>(ncol, nrow); return true;
   }
+  if (fine_mr_side(n)) {
+    *ncol = *nrow = 1;
+    return true;
+  }
   return false;
 }
 
 FinePlan fine_default_plan(int n, int prec) {
-  if (n == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
+  if (fine_fft_grid(n) == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
   return FinePlan();
 }
 
 bool fine_variants(int n, int prec, int* ncol, int* nrow) {
-  return prec == 0 ? variants_T<float>(n, ncol, nrow) : variants_T<double>(n, ncol, nrow);
+  const int m = fine_fft_grid(n);
+  return prec == 0 ? variants_T<float>(m, ncol, nrow) : variants_T<double>(m, ncol, nrow);
 }
 
 template <typename T>
@@ -128,7 +134,7 @@ static int run_T(const FineArgs& a, const StepCfg& cfg) {
     case 512: return fine3_run<T, 512>(a, cfg);
     case 1024: return fine3_run<T, 1024>(a, cfg);
   }
-  return -1;
+  return fine_mr_run(sizeof(T) == 4 ? 0 : 1, a, cfg);
 }
 
 int fine_run(int prec, const FineArgs& a, const StepCfg& cfg) {

@@ -42,7 +42,7 @@ size_t phase_table_bytes(int prec, long batch, int nsteps);
 // fill FineArgs::phases (Galloway-Proctor, or any batch with per-slice parameters);
 // returns kernels launched
 int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
-// number of column / row variants instantiated for (n, prec); false if n is unsupported
+// number of column / row variants instantiated for (fine_fft_grid(n), prec); false if none
 bool fine_variants(int n, int prec, int* ncol, int* nrow);
 // launch plan of a context before any autotuning or kd_set_plan
 FinePlan fine_default_plan(int n, int prec);
@@ -53,6 +53,28 @@ int fine_run(int prec, const FineArgs& a, const StepCfg& cfg);
 // the same with the default plan and every field taking every step
 int fine_launch_steps(int prec, const FineArgs& a, int nsteps, bool prologue, bool store_last,
                       cudaStream_t st, const LaunchProbe* probe = nullptr);
+
+// ---- kd_fine_mr.cu: grid sides 32 R that are not powers of two (96, 160, 192)
+bool fine_mr_side(int n);
+int fine_mr_run(int prec, const FineArgs& a, const StepCfg& cfg);   // -1 for other sides
+// FFT sides of the fine kernels: powers of two in [16, 1024] and fine_mr_side
+inline bool fine_fft_side(int n) {
+  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || fine_mr_side(n);
+}
+// FFT side the fine kernels use for the grid side n of a problem (kept set |k| <= K = n/3):
+// n itself where it is an FFT side, else the smallest mixed-radix side m >= 2K + 2 (0 if
+// none, i.e. n >= 288).  Both flows have only the wavenumbers +-1 in x and y, so u x b of
+// a field with |k| <= K has |k| <= K + 1; on m >= 2K + 2 points no mode of it aliases onto
+// the kept set, and the kept modes of the step are those of the n-point pseudo-spectral
+// step (exactly, up to rounding).  Only the mixed-radix kernels take a kept set narrower
+// or wider than m / 3 (the power-of-two kernels fix K = N / 3 at compile time).  This runs
+// e.g. n = 240, the 3/2-padded grid of 160 kept modes a side, on the 192-point transform.
+inline int fine_fft_grid(int n) {
+  if (fine_fft_side(n)) return n;
+  for (int m : {96, 160, 192})
+    if (m >= 2 * (n / 3) + 2) return m;
+  return 0;
+}
 
 // ---- kd_fine2_*.cu (register-FFT kernels, n <= 256) and kd_fine3_*.cu (n = 512, 1024):
 // explicit instantiations per (T, N)

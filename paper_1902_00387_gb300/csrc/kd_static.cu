@@ -59,8 +59,8 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
     return KD_EINVAL;
   }
   const int n = p->n, prec = p->prec_fine;
-  const bool n_ok = n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
-  if (!n_ok || p->flow < 0 || p->flow > 2 || (prec != KD_C64 && prec != KD_C128) || !(p->Rm > 0) ||
+  if (n < 16 || n > 1024 || (n & 1) || fine_fft_grid(n) == 0 || p->flow < 0 || p->flow > 2 ||
+      (prec != KD_C64 && prec != KD_C128) || !(p->Rm > 0) ||
       !(p->dt_fine > 0) || !isfinite(p->kz) || p->fine_scheme < KD_RK443 || p->fine_scheme > KD_RK111) {
     fprintf(stderr, "kd_fine_batched_static: invalid parameters\n");
     return KD_EINVAL;
@@ -69,9 +69,10 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   // workspace carve-out (all offsets 256-byte aligned)
   const size_t rs = prec == KD_C64 ? 4 : 8, cs = 2 * rs;
   const int K = n / 3, P = 2 * K + 1;
-  const size_t tab = align256(n * cs) + 2 * align256(n * rs);
+  const int m = fine_fft_grid(n);   // the transforms' side (n itself for the FFT sides)
+  const size_t tab = align256(m * cs) + 2 * align256(m * rs);
   const size_t spec = align256((size_t)batch * 3 * P * P * cs);
-  const size_t mixed = align256((size_t)batch * 3 * P * n * cs);
+  const size_t mixed = align256((size_t)batch * 3 * P * m * cs);
   const size_t phase = p->flow == KD_FLOW_GALLOWAY_PROCTOR ? align256(phase_table_bytes(prec, batch, nsteps)) : 0;
   const int nspec = prec == KD_C64 ? 5 : 4;   // X, R2, R3, R4 (+ the state's low part, complex64)
   const size_t need = tab + nspec * spec + 2 * mixed + phase;
@@ -110,13 +111,13 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   cudaStream_t st = (cudaStream_t)cuda_stream;
   unsigned char* q = base;
   void* tw = q;
-  q += align256(n * cs);
+  q += align256(m * cs);
   void* cg = q;
-  q += align256(n * rs);
+  q += align256(m * rs);
   void* sg = q;
-  q += align256(n * rs);
+  q += align256(m * rs);
   FineArgs a;
-  a.n = n;
+  a.n = m;
   a.K = K;
   a.P = P;
   a.batch = batch;
@@ -147,11 +148,11 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   // state, prologue mixed field, column output, stage-0 accumulators, phases, and the
   // state's low part, written by the first step's last stage and read from the second
   // step on), so no region has to be cleared.
-  const unsigned tb = (unsigned)((n + 255) / 256);
+  const unsigned tb = (unsigned)((m + 255) / 256);
   if (prec == KD_C64)
-    k_static_tables<float><<<tb, 256, 0, st>>>(n, (float*)tw, (float*)cg, (float*)sg);
+    k_static_tables<float><<<tb, 256, 0, st>>>(m, (float*)tw, (float*)cg, (float*)sg);
   else
-    k_static_tables<double><<<tb, 256, 0, st>>>(n, (double*)tw, (double*)cg, (double*)sg);
+    k_static_tables<double><<<tb, 256, 0, st>>>(m, (double*)tw, (double*)cg, (double*)sg);
   if (cudaGetLastError() != cudaSuccess) return KD_ECUDA;
   if (full_to_compact(prec, b_in, prec, a.X, batch, n, st) < 0) return KD_ECUDA;
   if (nsteps > 0 && fine_launch_steps(prec, a, nsteps, true, false, st) < 0) return KD_ECUDA;

@@ -44,7 +44,7 @@ def test_version_and_argument_validation_without_gpu(lib):
     import paper_1902_00387_gb300 as kd
     assert "sm_103a" in kd.kd_version()
     out = ctypes.c_void_p()
-    bad = kd.make_params(kd.KD_FLOW_ROBERTS, 48, 1.0, 8.0, 1e-2)        # n not a power of two
+    bad = kd.make_params(kd.KD_FLOW_ROBERTS, 49, 1.0, 8.0, 1e-2)        # odd n
     assert lib.kd_create(ctypes.byref(bad), None, ctypes.byref(out)) == kd.KD_EINVAL
     bad = kd.make_params(kd.KD_FLOW_ROBERTS, 32, 1.0, -8.0, 1e-2)       # Rm <= 0
     assert lib.kd_create(ctypes.byref(bad), None, ctypes.byref(out)) == kd.KD_EINVAL

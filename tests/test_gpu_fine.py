@@ -322,11 +322,11 @@ def test_convolution_fine_operator_matches_oracle(kd, n, prec):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 4)) < (TOL32 if P == kd.KD_C64 else 1e-12)
 
 
-@pytest.mark.parametrize("n,op", [(256, "conv"), (192, "conv"), (96, "fft"), (160, "fft"), (97, "conv"),
-                                  (14, "conv")])
+@pytest.mark.parametrize("n,op", [(256, "conv"), (192, "conv"), (97, "fft"), (288, "fft"), (1000, "fft"),
+                                  (97, "conv"), (14, "conv")])
 def test_unsupported_grid_sides_rejected(kd, n, op):
     """The convolution operator holds at most 127 kept modes a side (n <= 190); the FFT
-    operator needs a power of two; every side is even and >= 16."""
+    operator takes powers of two and even sides up to 286; every side is even and >= 16."""
     f = kd.KD_FINE_CONV if op == "conv" else kd.KD_FINE_FFT
     with pytest.raises(kd.KdError):
         kd.kd_create(kd.make_params(O.ROBERTS, n, 1.0, 8.0, 1e-2, kd.KD_C64, n_coarse=16, fine_operator=f))

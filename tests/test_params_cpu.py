@@ -19,8 +19,7 @@ BASE = dict(flow=1, n=64, kz=0.57, Rm=100.0, dt_fine=5e-3, prec_fine=0, n_coarse
 
 BAD = [
     ("flow", 3), ("flow", -1),
-    ("n", 8), ("n", 15), ("n", 2048),
-    ("n", 96),                                  # not a power of two with the FFT operator
+    ("n", 8), ("n", 15), ("n", 2048), ("n", 97), ("n", 1026), ("n", 288), ("n", 1000),
     ("n_coarse", 17), ("n_coarse", 128), ("n_coarse", 8),
     ("Rm", 0.0), ("Rm", -1.0), ("Rm", math.inf), ("Rm", math.nan), ("kz", math.nan),
     ("dt_fine", 0.0), ("dt_coarse", -0.1), ("dt_fine", math.nan),
