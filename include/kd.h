@@ -268,7 +268,7 @@ kd_status kd_learned_init(kd_ctx* ctx, int n_phase, double slice_T);
  *   x, y : device learned vectors [n]; phase : host int[n] in [0, n_phase).  Synchronous. */
 kd_status kd_learned_pairs(kd_ctx* ctx, const float* x, int n, const int* phase, float* y);
 
-enum { KD_TRAIN_ADAM = 0, KD_TRAIN_MOMENTUM = 1 };
+enum { KD_TRAIN_ADAM = 0, KD_TRAIN_MOMENTUM = 1, KD_TRAIN_MINNORM = 2 };
 
 /* Train every W_p on its pairs, starting from W_classical, on
  *   L = (1/m) sum_i |W x_i - y_i|^2 + weight_decay |W - W_classical|^2;
@@ -279,6 +279,15 @@ enum { KD_TRAIN_ADAM = 0, KD_TRAIN_MOMENTUM = 1 };
  *                      lambda = (2/m) sum |x_i|^2 (lr <= 1); its updates stay in the span
  *                      of the training inputs, which matters when pairs are fewer than
  *                      the 3 m^2 unknowns of a row (Adam's per-weight scaling does not).
+ *   KD_TRAIN_MINNORM   the minimiser in closed form (epochs and lr unused):
+ *                      W = W0 + (Y - W0 X)(X^H X + m weight_decay I)^-1 X^H, X, Y the pairs
+ *                      of a phase as columns (m <= 4096 of them); with weight_decay = 0 the
+ *                      smallest change of W0 that maps every training input onto its
+ *                      output (W0 X in FP64 from the classical propagator, X^H X summed in
+ *                      FP32 per 32 unknowns and in FP64 across, its Cholesky inverse in FP64
+ *                      on the host, the correction GEMM in BF16 on the tensor cores).
+ *                      KD_EINVAL when the inputs of a phase are linearly dependent and
+ *                      weight_decay is 0. loss_out is not written.
  *   loss_out : host double[n_phase * epochs] data loss per phase and epoch (may be NULL).
  * Synchronous. */
 kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,

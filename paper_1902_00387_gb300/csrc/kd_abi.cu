@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <complex>
 #include <string>
 #include <vector>
 
@@ -1335,14 +1336,105 @@ kd_status forward_backward(kd_ctx* ctx, TrainBufs& b, int mp, int nc, double* lo
   return KD_OK;
 }
 
+// The classical coarse propagator over one slice of phase p applied to the m learned
+// vectors xp (complex FP32 [m][nc]) in FP64: g64 [m][nc].  Scratch: d64 (m nc complex
+// FP64), t0 (m doubles), ph (the coarse phase table of m fields).
+kd_status classical_on_set(kd_ctx* ctx, const float* xp, int m, int p, double* d64, double* g64, double* t0,
+                           void* ph) {
+  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P, pc = ctx->p.prec_coarse;
+  const int Sc = steps_for(ctx->l_sliceT, ctx->p.dt_coarse);
+  const double dtc = ctx->l_sliceT / Sc;
+  KD_LAUNCH(learned_f32_to_f64(xp, d64, (long)m * nc, ctx->st), "to f64");
+  KD_LAUNCH(fill_times(t0, m, p * ctx->l_sliceT, 0.0, ctx->st), "times");
+  FineArgs fa = fine_args(ctx, ctx->ws_c, ctx->tab_c, ctx->p.n_coarse, m, dtc, t0);
+  fa.phases = ph;
+  KD_LAUNCH(launch_phases(pc, fa, Sc, ctx->st), "phases");
+  CoarseArgs c = coarse_args(ctx, Sc, dtc);
+  c.Kf = K;
+  c.Pf = P;
+  c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? ph : nullptr;
+  c.Un = d64;
+  c.mode = COARSE_OUT;
+  c.g64 = g64;
+  KD_LAUNCH(coarse_conv_launch(pc, c, m, ctx->st), "classical");
+  return KD_OK;
+}
+
+// In-place inverse of the Hermitian positive definite m x m matrix A (row-major) by its
+// Cholesky factor A = L L^H: A^-1 = L^-H L^-1.  False if A is not positive definite.
+bool herm_inverse(std::vector<std::complex<double>>& A, int m) {
+  using C = std::complex<double>;
+  auto a = [&](int i, int j) -> C& { return A[(size_t)i * m + j]; };
+  for (int j = 0; j < m; ++j) {            // L in the lower triangle
+    double d = a(j, j).real();
+    for (int k = 0; k < j; ++k) d -= std::norm(a(j, k));
+    if (!(d > 0.0)) return false;
+    const double l = sqrt(d);
+    a(j, j) = l;
+    for (int i = j + 1; i < m; ++i) {
+      C t = a(i, j);
+      for (int k = 0; k < j; ++k) t -= a(i, k) * std::conj(a(j, k));
+      a(i, j) = t / l;
+    }
+  }
+  std::vector<C> Li((size_t)m * m, C(0.0));   // L^-1, lower triangular
+  for (int j = 0; j < m; ++j) {
+    Li[(size_t)j * m + j] = 1.0 / a(j, j);
+    for (int i = j + 1; i < m; ++i) {
+      C t(0.0);
+      for (int k = j; k < i; ++k) t -= a(i, k) * Li[(size_t)k * m + j];
+      Li[(size_t)i * m + j] = t / a(i, i);
+    }
+  }
+  for (int i = 0; i < m; ++i)                // (L^-H L^-1)[i][j] = sum_k conj(Li[k][i]) Li[k][j]
+    for (int j = 0; j <= i; ++j) {
+      C t(0.0);
+      for (int k = i; k < m; ++k) t += std::conj(Li[(size_t)k * m + i]) * Li[(size_t)k * m + j];
+      a(i, j) = t;
+      a(j, i) = std::conj(t);
+    }
+  return true;
+}
+
+// KD_TRAIN_MINNORM for one phase whose m pairs are loaded in b: W = W0 + R (G + lambda I)^-1
+// X^H with R = Y - W0 X (W0 X by the classical propagator in FP64), G = X^H X, lambda = m wd
+// (the minimiser of the training objective, in the span of the inputs when wd = 0); the
+// correction R G^-1 X^H is the gradient GEMM with R G^-1 in place of the residual.
+kd_status minnorm_phase(kd_ctx* ctx, TrainBufs& b, int p, int m, int mp, int nc, float wd, const float* W0,
+                        double* d64, double* g64, double* t0, void* ph, float* Rf, double* G64, float* G32) {
+  const int ld = (nc + 7) & ~7;
+  kd_status s;
+  if ((s = classical_on_set(ctx, b.xp, m, p, d64, g64, t0, ph)) != KD_OK) return s;
+  KD_LAUNCH(learned_resid64(b.yp, g64, Rf, (long)m * nc, ctx->st), "residual");
+  KD_LAUNCH(learned_gram(b.xp, m, nc, G64, ctx->st), "gram");
+  std::vector<std::complex<double>> G((size_t)m * m);
+  KD_CUDA(cudaMemcpyAsync(G.data(), G64, G.size() * 16, cudaMemcpyDeviceToHost, ctx->st), "gram");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  for (int i = 0; i < m; ++i) G[(size_t)i * m + i] += (double)m * wd;
+  if (!herm_inverse(G, m))
+    return fail(ctx, KD_EINVAL, "kd_learned_train: the pairs' inputs of phase " + std::to_string(p) +
+                                    " are linearly dependent; use weight_decay > 0");
+  std::vector<float> g32(2 * G.size());
+  for (size_t i = 0; i < G.size(); ++i) {
+    g32[2 * i] = (float)G[i].real();
+    g32[2 * i + 1] = (float)G[i].imag();
+  }
+  KD_CUDA(cudaMemcpyAsync(G32, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, ctx->st), "inverse");
+  KD_LAUNCH(learned_minnorm_operand(Rf, G32, m, mp, nc, b.A2, ctx->st), "operand");
+  KD_LAUNCH(train_gemm(ctx, b, b.A2, b.XtT, b.C2, 2 * nc, nc, 2 * mp, ld), "correction gemm");
+  KD_LAUNCH(learned_add_bf16(W0, b.C2, ctx->l_W + (size_t)p * 2 * nc * ld, 2L * nc * ld, ctx->st), "store");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");   // g32 is host memory of this frame
+  return KD_OK;
+}
+
 }  // namespace
 
 kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const int* phase, int n, int epochs, float lr,
                            float weight_decay, int method, double* loss_out) {
   if (!ctx) return KD_EINVAL;
   if (ctx->l_nphase == 0) return fail(ctx, KD_EINVAL, "kd_learned_train: call kd_learned_init first");
-  if (!x || !y || !phase || n <= 0 || epochs < 0 || !(lr >= 0) ||
-      (method != KD_TRAIN_ADAM && method != KD_TRAIN_MOMENTUM))
+  if (!x || !y || !phase || n <= 0 || epochs < 0 || !(lr >= 0) || !(weight_decay >= 0) ||
+      (method != KD_TRAIN_ADAM && method != KD_TRAIN_MOMENTUM && method != KD_TRAIN_MINNORM))
     return fail(ctx, KD_EINVAL, "kd_learned_train: bad arguments");
   const int P = ctx->cP, nc = 3 * P * P, ld = (nc + 7) & ~7;
   const size_t wcount = (size_t)2 * nc * ld;
@@ -1356,6 +1448,33 @@ kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const in
   const int mp = (int)roundup4(mmax);
   kd_status s;
   TrainBufs b;
+  if (method == KD_TRAIN_MINNORM) {
+    if (mmax > 4096) return fail(ctx, KD_EINVAL, "kd_learned_train: KD_TRAIN_MINNORM takes at most 4096 pairs a phase");
+    double *d64 = nullptr, *g64 = nullptr, *t0 = nullptr, *G64 = nullptr;
+    float *Rf = nullptr, *G32 = nullptr;
+    void* ph = nullptr;
+    if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
+    const int Sc = steps_for(ctx->l_sliceT, ctx->p.dt_coarse);
+    if ((s = dalloc(ctx, (void**)&d64, (size_t)mp * nc * 16, "inputs")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&g64, (size_t)mp * nc * 16, "classical outputs")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&t0, (size_t)mp * 8, "times")) != KD_OK) return s;
+    if ((s = dalloc(ctx, &ph, phase_table_bytes(ctx->p.prec_coarse, mp, Sc), "phases")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&Rf, (size_t)mp * nc * 8, "residual")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&G64, (size_t)mp * mp * 16, "gram")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&G32, (size_t)mp * mp * 8, "gram inverse")) != KD_OK) return s;
+    for (int p = 0; p < ctx->l_nphase; ++p) {
+      const int m = (int)byp[p].size();
+      if (m == 0) continue;
+      if ((s = load_pairs(ctx, b, x, y, byp[p], mp, nc)) != KD_OK) return s;
+      if ((s = minnorm_phase(ctx, b, p, m, mp, nc, weight_decay, ctx->l_W0 + (size_t)p * wcount, d64, g64, t0, ph,
+                             Rf, G64, G32)) != KD_OK)
+        return s;
+    }
+    if ((s = check_gemm(ctx, b)) != KD_OK) return s;
+    free_train_bufs(ctx, b);
+    for (void* q : {(void*)d64, (void*)g64, (void*)t0, ph, (void*)Rf, (void*)G64, (void*)G32}) dfree(ctx, q);
+    return KD_OK;
+  }
   float *Wm = nullptr, *m1 = nullptr, *v = nullptr;
   double* lossd = nullptr;
   if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
@@ -1503,9 +1622,8 @@ kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int
   if (!ctx) return KD_EINVAL;
   if (ctx->l_nphase == 0 || !x || !y || !phase || n <= 0 || !err_learned || !err_classical)
     return fail(ctx, KD_EINVAL, "kd_learned_eval: bad arguments");
-  const int K = ctx->cK, P = ctx->cP, nc = 3 * P * P, pc = ctx->p.prec_coarse;
+  const int P = ctx->cP, nc = 3 * P * P, pc = ctx->p.prec_coarse;
   const int Sc = steps_for(ctx->l_sliceT, ctx->p.dt_coarse);
-  const double dtc = ctx->l_sliceT / Sc;
   std::vector<std::vector<int>> byp(ctx->l_nphase);
   for (int i = 0; i < n; ++i) {
     if (phase[i] < 0 || phase[i] >= ctx->l_nphase) return fail(ctx, KD_EINVAL, "kd_learned_eval: bad phase index");
@@ -1537,19 +1655,7 @@ kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int
     if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");
     KD_LAUNCH(sum_partials(ctx->partials, nb, ctx->scal + 8, ctx->st), "norm");
     // classical coarse propagator on the same set
-    KD_LAUNCH(learned_f32_to_f64(b.xp, d64, (long)m * nc, ctx->st), "to f64");
-    KD_LAUNCH(fill_times(t0, m, p * ctx->l_sliceT, 0.0, ctx->st), "times");
-    FineArgs fa = fine_args(ctx, ctx->ws_c, ctx->tab_c, ctx->p.n_coarse, m, dtc, t0);
-    fa.phases = ph;
-    KD_LAUNCH(launch_phases(pc, fa, Sc, ctx->st), "phases");
-    CoarseArgs c = coarse_args(ctx, Sc, dtc);
-    c.Kf = K;
-    c.Pf = P;
-    c.phases = ctx->p.flow == KD_FLOW_GALLOWAY_PROCTOR ? ph : nullptr;
-    c.Un = d64;
-    c.mode = COARSE_OUT;
-    c.g64 = g64;
-    KD_LAUNCH(coarse_conv_launch(pc, c, m, ctx->st), "classical");
+    if ((s = classical_on_set(ctx, b.xp, m, p, d64, g64, t0, ph)) != KD_OK) return s;
     KD_LAUNCH(learned_f64_to_f32(g64, pred, (long)m * nc, ctx->st), "to f32");
     nb = diff_norms(pred, b.yp, 2L * m * nc, ctx->partials, ctx->st);
     if (nb < 0) return fail(ctx, KD_ECUDA, "norm launch failed");

@@ -557,4 +557,122 @@ int diff_norms(const float* a, const float* b, long count, double* partials, cud
   return e != cudaSuccess ? -(int)e : (int)g;
 }
 
+// ------------------------------------------------------------ minimum-norm correction
+// Gram matrix G[i][j] = x_i^H x_j of m learned vectors (complex FP32 [m][nc]), as complex
+// FP64 [m][m].  A block computes a 16 x 16 tile; the products of a 32-wide chunk of the
+// unknowns are summed in FP32 and the chunk sums in FP64.
+constexpr int GT = 16, GK = 32;
+
+__global__ void __launch_bounds__(GT * GT) k_gram(const float2* x, int m, int nc, double2* G) {
+  __shared__ float2 xi[GT][GK + 1], xj[GT][GK + 1];
+  const int ti = threadIdx.x / GT, tj = threadIdx.x % GT;
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  double ar = 0.0, ai = 0.0;
+  for (int k0 = 0; k0 < nc; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += GT * GT) {
+      const int r = e / GK, k = k0 + e % GK;
+      const bool in = k < nc;
+      xi[r][e % GK] = in && i0 + r < m ? x[(long)(i0 + r) * nc + k] : make_float2(0.f, 0.f);
+      xj[r][e % GK] = in && j0 + r < m ? x[(long)(j0 + r) * nc + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float sr = 0.f, si = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      const float2 a = xi[ti][k], b = xj[tj][k];   // conj(a) b
+      sr = fmaf(a.x, b.x, fmaf(a.y, b.y, sr));
+      si = fmaf(a.x, b.y, fmaf(-a.y, b.x, si));
+    }
+    ar += sr;
+    ai += si;
+    __syncthreads();
+  }
+  if (i0 + ti < m && j0 + tj < m) G[(long)(i0 + ti) * m + j0 + tj] = make_double2(ar, ai);
+}
+
+int learned_gram(const float* x, int m, int nc, double* G, cudaStream_t st) {
+  const dim3 grid((m + GT - 1) / GT, (m + GT - 1) / GT);
+  k_gram<<<grid, GT * GT, 0, st>>>((const float2*)x, m, nc, (double2*)G);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// R[l] = y[l] - g[l], rounded to complex FP32 (g: FP64 classical outputs)
+__global__ void k_resid64(const float* y, const double* g, float* R, long total) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    R[i] = (float)((double)y[i] - g[i]);
+}
+
+int learned_resid64(const float* y, const double* g, float* R, long n_complex, cudaStream_t st) {
+  k_resid64<<<grid1(2 * n_complex), TB, 0, st>>>(y, g, R, 2 * n_complex);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// A_n = sum_{l < m} R_l Ginv[l][n] (complex FP32 sums) written as the gradient GEMM's left
+// operand A2[2 nc][2 mp]: row j (Re A_n[j], Im A_n[j]), row nc + j (Im A_n[j], -Re A_n[j]);
+// columns n in [m, mp) zero.  A block computes 16 n x 64 j; Ginv is FP32 complex [m][m].
+constexpr int CJ = 64, CN = 16, CL = 16;
+
+__global__ void __launch_bounds__(256) k_minnorm_operand(const float2* R, const float2* Gi, int m, int mp, int nc,
+                                                         __nv_bfloat16* A2) {
+  __shared__ float2 sR[CL][CJ], sG[CL][CN + 1];
+  const int j0 = blockIdx.x * CJ, n0 = blockIdx.y * CN;
+  const int tj = threadIdx.x % CJ, tn = threadIdx.x / CJ;   // 64 x 4 threads, 4 n each
+  float2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int l0 = 0; l0 < m; l0 += CL) {
+    for (int e = threadIdx.x; e < CL * CJ; e += 256) {
+      const int l = l0 + e / CJ, j = j0 + e % CJ;
+      sR[e / CJ][e % CJ] = l < m && j < nc ? R[(long)l * nc + j] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < CL * CN; e += 256) {
+      const int l = l0 + e / CN, n = n0 + e % CN;
+      sG[e / CN][e % CN] = l < m && n < m ? Gi[(long)l * m + n] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < CL; ++l) {
+      const float2 r = sR[l][tj];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 g = sG[l][tn * 4 + q];
+        acc[q].x = fmaf(r.x, g.x, fmaf(-r.y, g.y, acc[q].x));
+        acc[q].y = fmaf(r.x, g.y, fmaf(r.y, g.x, acc[q].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int j = j0 + tj;
+  if (j >= nc) return;
+  const long m2 = 2L * mp;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int n = n0 + tn * 4 + q;
+    if (n >= mp) continue;
+    const float2 a = n < m ? acc[q] : make_float2(0.f, 0.f);
+    A2[(long)j * m2 + n] = __float2bfloat16(a.x);
+    A2[(long)j * m2 + mp + n] = __float2bfloat16(a.y);
+    A2[(long)(nc + j) * m2 + n] = __float2bfloat16(a.y);
+    A2[(long)(nc + j) * m2 + mp + n] = __float2bfloat16(-a.x);
+  }
+}
+
+int learned_minnorm_operand(const float* R, const float* Ginv, int m, int mp, int nc, __nv_bfloat16* A2,
+                            cudaStream_t st) {
+  const dim3 grid((nc + CJ - 1) / CJ, (mp + CN - 1) / CN);
+  k_minnorm_operand<<<grid, 256, 0, st>>>((const float2*)R, (const float2*)Ginv, m, mp, nc, A2);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Wbf = bf16(W0 + D) (stacked operators)
+__global__ void k_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    Wbf[i] = __float2bfloat16(W0[i] + D[i]);
+}
+
+int learned_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count, cudaStream_t st) {
+  k_add_bf16<<<grid1(count), TB, 0, st>>>(W0, D, Wbf, count);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 }  // namespace kd

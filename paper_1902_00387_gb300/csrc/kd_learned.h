@@ -74,5 +74,16 @@ int f32_to_bf16(const float* x, __nv_bfloat16* y, long count, cudaStream_t st);
 int sum_partials(const double* p, int count, double* out, cudaStream_t st);
 // relative errors: out[0] = sum |a - b|^2, out[1] = sum |b|^2 over `count` floats
 int diff_norms(const float* a, const float* b, long count, double* partials, cudaStream_t st);
+// minimum-norm correction W = W0 + (Y - W0 X)(X^H X + lambda I)^-1 X^H (KD_TRAIN_MINNORM):
+// G = X^H X, complex FP64 [m][m], of the learned vectors x [m][nc]
+int learned_gram(const float* x, int m, int nc, double* G, cudaStream_t st);
+// R = y - g (g the classical outputs in FP64), complex FP32, n_complex values
+int learned_resid64(const float* y, const double* g, float* R, long n_complex, cudaStream_t st);
+// A = R Ginv (Ginv complex FP32 [m][m]) as the gradient GEMM's left operand A2 [2 nc][2 mp]
+// (the layout learned_residual writes), zero in the padding columns n >= m
+int learned_minnorm_operand(const float* R, const float* Ginv, int m, int mp, int nc, __nv_bfloat16* A2,
+                            cudaStream_t st);
+// Wbf = bf16(W0 + D)
+int learned_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count, cudaStream_t st);
 
 }  // namespace kd

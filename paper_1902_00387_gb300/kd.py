@@ -25,7 +25,7 @@ KD_FINE_FFT, KD_FINE_CONV = 0, 1
 KD_RK443, KD_RK222, KD_RK111 = 0, 1, 2
 KD_SYNC_CLUSTER, KD_SYNC_P2P, KD_SYNC_PULL = 0, 1, 2
 KD_GEMM_TCGEN05, KD_GEMM_MMA_SYNC = 0, 1
-KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM = 0, 1
+KD_TRAIN_ADAM, KD_TRAIN_MOMENTUM, KD_TRAIN_MINNORM = 0, 1, 2
 KD_GRID_FINE, KD_GRID_COARSE = 0, 1
 KD_MAX_SLICES = 1024
 KD_MAX_ITERS = 256

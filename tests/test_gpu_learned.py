@@ -246,3 +246,58 @@ def test_operator_checkpoint_round_trip(kd):
     finally:
         kd.kd_destroy(a)
         kd.kd_destroy(b)
+
+
+def _bf16_bits_to_complex(Wb):
+    """BF16 bit patterns of a stacked operator [2 nc][nc] -> complex [nc][nc]."""
+    f = (Wb.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    nc = Wb.shape[1]
+    return f[:nc] + 1j * f[nc:]
+
+
+@pytest.mark.parametrize("wd", [0.0, 1e-2])
+def test_minimum_norm_correction_matches_oracle_ridge(kd, wd):
+    """KD_TRAIN_MINNORM against the oracle's closed-form minimiser (learned_ridge): pairs
+    from the oracle's fine propagator, the centre W0 the oracle's coarse propagator on the
+    learned set (columns from unit vectors), 48 pairs for 192 unknowns a row.  With wd = 0
+    the operator maps every training input onto its output (to BF16 rounding) although the
+    classical one misses them by more."""
+    import torch
+    ph, m = 3, 48
+    X = learned_inputs(range(70_000, 70_000 + m)).reshape(m, NC)
+    prob = O.Problem(O.GALLOWAY_PROCTOR, N_FINE, KZ, RM)
+    S = math.ceil(SLICE / DT_F - 1e-9)
+    shape = (3, M_SET, M_SET)
+    Y = np.stack([O.learned_restrict(O.propagate(O.learned_prolong(x.reshape(shape), M_SET, N_FINE), prob, ph * SLICE,
+                                                 SLICE / S, S), M_SET).ravel() for x in X])
+    ng = 16                                          # grid with no aliasing for |k| <= 4
+    probc = O.Problem(O.GALLOWAY_PROCTOR, ng, KZ, RM)
+    Sc = math.ceil(SLICE / DT_C - 1e-9)
+    mask = O.learned_mask(ng, M_SET)
+    W0 = np.zeros((NC, NC), np.complex128)
+    for j in range(NC):
+        e = np.zeros(NC, np.complex128)
+        e[j] = 1.0
+        W0[:, j] = O.learned_restrict(O.propagate(O.learned_prolong(e.reshape(shape), M_SET, ng), probc, ph * SLICE,
+                                                  SLICE / Sc, Sc, mask=mask), M_SET).ravel()
+    ref = O.learned_ridge(X, Y, W0, wd)
+    ctx = make_ctx(kd)
+    try:
+        kd.kd_learned_init(ctx, N_PHASE, SLICE)
+        xt = torch.tensor(X.reshape(m, *shape).astype(np.complex64), device="cuda")
+        yt = torch.tensor(Y.reshape(m, *shape).astype(np.complex64), device="cuda")
+        kd.kd_learned_train(ctx, xt, yt, [ph] * m, m, 0, 0.0, wd, N_PHASE, kd.KD_TRAIN_MINNORM)
+        Wb = np.zeros((2 * NC, NC), np.uint16)
+        kd.kd_learned_get(ctx, ph, Wb)
+    finally:
+        kd.kd_destroy(ctx)
+    W = _bf16_bits_to_complex(Wb)
+    assert rel(W, ref) < 4e-3                                  # BF16 storage of the operator
+    dW, dref = W - W0, ref - W0
+    assert rel(dW, dref) < 0.1                                 # the correction itself
+    err = rel(X @ W.T, Y)
+    err0 = rel(X @ W0.T, Y)
+    if wd == 0.0:
+        assert err < 5e-3 and err0 > 5 * err, (err, err0)
+    else:
+        assert err < err0, (err, err0)
