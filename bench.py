@@ -296,7 +296,9 @@ LEARNED_WL = {
     "workload": "gp_cp_256x256_parareal_128_slices_learned_coarse",
     "flow": "galloway-proctor", "n": 256, "kz": 0.57, "Rm": 1000.0, "slices": 128, "slice": 2 * math.pi / 16,
     "fine_steps_per_slice": 800, "coarse_dt_over_fine_dt": 20, "learned_modes": 49, "phases": 16,
-    "pairs_per_phase": 256, "epochs": 300, "lr": 0.5, "optimizer": "momentum", "tol": 1e-6, "k_max": 32,
+    "pairs_per_phase": 256, "epochs": 300, "lr": 0.5, "optimizer": "minnorm (closed form) and momentum",
+    "tol": 1e-6, "k_max": 32,
+    "pair_count_study": {"phases": [0, 1], "pairs": [64, 256, 1024], "heldout_per_phase": 64},
 }
 
 
@@ -351,44 +353,144 @@ def run_learned(args):
     ms_s = e0.elapsed_time(e1)
     kd.kd_destroy(ctx)
 
+    # the classical propagator with the fine step on the same set (20x the work of the
+    # benched one): how much accuracy of G on the set alone buys in iterations
+    p1 = kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], dt, kd.KD_C64, n_coarse=64,
+                        dt_coarse=dt, prec_coarse=kd.KD_C64, fine_form=kd.KD_FINE_INCREMENT, learned_modes=m,
+                        coarse_kind=kd.KD_COARSE_CLASSICAL)
+    ctx = kd.kd_create(p1)
+    ms_a, st_a, u_a = solve(ctx)
+    acc = {"ms": ms_a, "k_con": st_a.k_con, "converged": bool(st_a.converged),
+           "sigma": list(st_a.sigma[:st_a.k_con])}
+    kd.kd_learned_init(ctx, W["phases"], W["slice"])
+    acc_ctx = ctx
+
     # learned: build from the classical propagator, pairs from the fine propagator, train
     ctx = ctx_for(kd.KD_COARSE_LEARNED)
     t = time.perf_counter()
     kd.kd_learned_init(ctx, W["phases"], W["slice"])
+    t_init = time.perf_counter() - t
+
+    def inputs(seed0, count):
+        # seeded |k|^-2 fields drawn on an 80^2 grid (|k| <= 26 covers the set)
+        x = np.stack([O.learned_restrict(kd_inputs.initial_field(80, W["kz"], seed0 + i), m) for i in range(count)])
+        return torch.tensor(x.astype(np.complex64), device="cuda")
+
+    def pairs(xt, ph):
+        yt = torch.zeros_like(xt)
+        kd.kd_learned_pairs(ctx, xt, len(ph), ph, yt)
+        return yt
+
     npair = W["pairs_per_phase"] * W["phases"]
-    # training inputs: seeded |k|^-2 fields drawn on an 80^2 grid (|k| <= 26 covers the set)
-    x = np.stack([O.learned_restrict(kd_inputs.initial_field(80, W["kz"], 10_000 + i), m) for i in range(npair)])
-    xt = torch.tensor(x.astype(np.complex64), device="cuda")
-    yt = torch.zeros_like(xt)
+    t = time.perf_counter()
+    xt = inputs(10_000, npair)
     ph = np.arange(npair) % W["phases"]
-    kd.kd_learned_pairs(ctx, xt, npair, ph, yt)
+    yt = pairs(xt, ph)
     t_pairs = time.perf_counter() - t
+    nv = 16 * W["phases"]
+    xvt = inputs(90_000, nv)
+    phv = np.arange(nv) % W["phases"]
+    yvt = pairs(xvt, phv)
+    # the classical operator as stored (BF16 matrix) before any training
+    e_bf16, ec = kd.kd_learned_eval(ctx, xvt, yvt, phv, nv, W["phases"])
+    _, e_acc = kd.kd_learned_eval(acc_ctx, xvt, yvt, phv, nv, W["phases"])
+    acc["heldout_err_median"] = float(np.median(e_acc))
+    kd.kd_destroy(acc_ctx)
+    # momentum descent from the classical matrix (the earlier training)
     t = time.perf_counter()
     loss = kd.kd_learned_train(ctx, xt, yt, ph, npair, W["epochs"], W["lr"], 0.0, W["phases"], kd.KD_TRAIN_MOMENTUM)
-    t_train = time.perf_counter() - t
-    nv = 16 * W["phases"]
-    xv = np.stack([O.learned_restrict(kd_inputs.initial_field(80, W["kz"], 90_000 + i), m) for i in range(nv)])
-    xvt = torch.tensor(xv.astype(np.complex64), device="cuda")
-    yvt = torch.zeros_like(xvt)
-    phv = np.arange(nv) % W["phases"]
-    kd.kd_learned_pairs(ctx, xvt, nv, phv, yvt)
+    t_mom = time.perf_counter() - t
+    e_mom, _ = kd.kd_learned_eval(ctx, xvt, yvt, phv, nv, W["phases"])
+    # The closed-form minimiser (KD_TRAIN_MINNORM; what momentum descent tends to) on the
+    # study phases: its ridge lambda = alpha mean |x|^2 chosen on held-out pairs, then the
+    # held-out error against the number of pairs.
+    PS = W["pair_count_study"]
+    mmax, nh = max(PS["pairs"]), PS["heldout_per_phase"]
+    phs = np.array(PS["phases"] * mmax)
+    xs = inputs(200_000, len(phs))
+    ys = pairs(xs, phs)
+    phh = np.array(PS["phases"] * nh)
+    xh = inputs(300_000, len(phh))
+    yh = pairs(xh, phh)
+    msq = float((torch.linalg.norm(xs.reshape(len(phs), -1), dim=1) ** 2).mean())
+
+    def minnorm(x_, y_, ph_, alpha, mm):
+        kd.kd_learned_train(ctx, x_, y_, ph_, len(ph_), 0, 0.0, alpha * msq / mm, W["phases"], kd.KD_TRAIN_MINNORM)
+
+    def study_err(mm, alpha):
+        k = mm * len(PS["phases"])
+        minnorm(xs[:k], ys[:k], phs[:k], alpha, mm)
+        a, c = kd.kd_learned_eval(ctx, xh, yh, phh, len(phh), W["phases"])
+        return [float(a[p]) for p in PS["phases"]], [float(c[p]) for p in PS["phases"]]
+
+    alphas = [0.0, 1e-4, 1e-3, 1e-2, 1e-1]
+    m0 = W["pairs_per_phase"]
+    by_alpha = []
+    for a_ in alphas:
+        e_, c_ = study_err(m0, a_)
+        by_alpha.append({"alpha": a_, "heldout_err": e_, "heldout_err_classical": c_})
+    best = min(by_alpha, key=lambda r: float(np.mean(r["heldout_err"])))["alpha"]
+    curve = []
+    for mm in PS["pairs"]:
+        for a_ in sorted({0.0, best}):
+            e_, c_ = study_err(mm, a_)
+            curve.append({"pairs_per_phase": mm, "alpha": a_, "heldout_err_minnorm": e_, "heldout_err_classical": c_})
+    # every phase with the chosen ridge, then the solve
+    t = time.perf_counter()
+    minnorm(xt, yt, ph, best, W["pairs_per_phase"])
+    torch.cuda.synchronize()
+    t_mn = time.perf_counter() - t
     el, ec = kd.kd_learned_eval(ctx, xvt, yvt, phv, nv, W["phases"])
     solve(ctx)
     ms_l, st_l, u_l = solve(ctx)
     kd.kd_destroy(ctx)
     err = lambda u: (torch.linalg.norm(u[-1] - ser[-1]) / torch.linalg.norm(ser[-1])).item()
+    # What no operator on the set can change: Parareal's update leaves the modes outside the
+    # set to the fine propagator alone (the coarse propagator is zero there), so their error
+    # after iteration k + 1 is P F applied to the error of iteration k.  Its outside-to-outside
+    # block P F P over one slice (from t = 0) is measured by power iteration; its norm bounds
+    # the per-iteration contraction of that part of the defect for any coarse operator.
+    fctx = kd.kd_create(kd.make_params(kd.KD_FLOW_GALLOWAY_PROCTOR, n, W["kz"], W["Rm"], dt, kd.KD_C128))
+    kk = torch.fft.fftfreq(n, 1.0 / n, device="cuda").round().long()
+    inside = ((kk[None, :] >= -(m // 2)) & (kk[None, :] < m - m // 2) &
+              (kk[:, None] >= -(m // 2)) & (kk[:, None] < m - m // 2))
+    v = torch.tensor(kd_inputs.initial_field(n, W["kz"], 4242), device="cuda")
+    v[:, inside] = 0
+    v /= torch.linalg.norm(v)
+    t00 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rho_hist = []
+    w = torch.empty_like(v)
+    for _ in range(30):
+        kd.kd_fine_batched(fctx, v[None], w[None], t00, W["fine_steps_per_slice"], 1, kd.KD_C128)
+        w[:, inside] = 0
+        r = torch.linalg.norm(w).item()
+        rho_hist.append(r)
+        v = w / r
+    kd.kd_destroy(fctx)
+    outside_frac = (torch.linalg.norm(ser[-1][:, ~inside]) / torch.linalg.norm(ser[-1])).item()
+    sc = list(st_c.sigma[:st_c.k_con])
     out.update({
         "serial_fine_ms": ms_s,
-        "classical": {"ms": ms_c, "k_con": st_c.k_con, "sigma": list(st_c.sigma[:st_c.k_con]),
+        "classical": {"ms": ms_c, "k_con": st_c.k_con, "sigma": sc, "converged": bool(st_c.converged),
                       "err_vs_serial_fine": err(u_c), "speedup_vs_serial_fine": ms_s / ms_c,
-                      "growth_rate": st_c.growth_rate},
+                      "growth_rate": st_c.growth_rate,
+                      "sigma_ratio_last8": [sc[i + 1] / sc[i] for i in range(max(0, len(sc) - 9), len(sc) - 1)]},
         "learned": {"ms": ms_l, "k_con": st_l.k_con, "sigma": list(st_l.sigma[:st_l.k_con]),
+                    "converged": bool(st_l.converged), "method": "minnorm", "ridge_alpha": best,
                     "fallback_used": bool(st_l.fallback_used), "err_vs_serial_fine": err(u_l),
                     "speedup_vs_serial_fine": ms_s / ms_l, "phases_kept": int(np.sum(el <= ec)),
-                    "heldout_err_learned_median": float(np.median(el)),
+                    "heldout_err_minnorm_median": float(np.median(el)),
+                    "heldout_err_momentum_median": float(np.median(e_mom)),
+                    "heldout_err_classical_bf16_median": float(np.median(e_bf16)),
                     "heldout_err_classical_median": float(np.median(ec)),
-                    "train_loss_first_last": [float(loss[:, 0].mean()), float(loss[:, -1].mean())],
-                    "pairs_s": t_pairs, "train_s": t_train},
+                    "train_loss_momentum_first_last": [float(loss[:, 0].mean()), float(loss[:, -1].mean())],
+                    "init_s": t_init, "pairs_s": t_pairs, "train_momentum_s": t_mom, "train_minnorm_s": t_mn},
+        "classical_fine_step_on_set": acc,
+        "ridge_study": by_alpha,
+        "pair_count_study": curve,
+        "outside_set": {"modes": "kx, ky outside [-%d, %d)" % (m // 2, m - m // 2),
+                        "norm_fraction_of_serial_fine_final_state": outside_frac,
+                        "rho_outside_block_one_slice": rho_hist[-1], "rho_history": rho_hist},
     })
     out["value"] = ms_l
     if not args.no_cpu_baseline:

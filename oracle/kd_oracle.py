@@ -467,6 +467,14 @@ def learned_ridge(X, Y, W0, wd):
     return np.linalg.solve(A.T, B.T).T
 
 
+def learned_minnorm(X, Y, W0):
+    """The smallest change of W0 (Frobenius norm) for which W x_i = y_i for every pair:
+        W = W0 + (Y^T - W0 X^T) pinv(X^T),
+    X, Y: [m, nc] (rows are pairs).  With fewer pairs than unknowns of a row it is the
+    limit of learned_ridge as wd -> 0 (learned_ridge itself needs wd > 0 there)."""
+    return W0 + (Y.T - W0 @ X.T) @ np.linalg.pinv(X.T)
+
+
 def learned_exact_map(prob, m, t0, dt, nsteps):
     """The fine propagator's map on the learned set, R F P, column by column (one fine
     propagation of every unit vector; tiny sets only)."""

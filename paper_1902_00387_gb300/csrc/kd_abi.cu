@@ -1400,8 +1400,18 @@ bool herm_inverse(std::vector<std::complex<double>>& A, int m) {
 // X^H with R = Y - W0 X (W0 X by the classical propagator in FP64), G = X^H X, lambda = m wd
 // (the minimiser of the training objective, in the span of the inputs when wd = 0); the
 // correction R G^-1 X^H is the gradient GEMM with R G^-1 in place of the residual.
-kd_status minnorm_phase(kd_ctx* ctx, TrainBufs& b, int p, int m, int mp, int nc, float wd, const float* W0,
-                        double* d64, double* g64, double* t0, void* ph, float* Rf, double* G64, float* G32) {
+struct MinnormBufs {
+  double *d64 = nullptr, *g64 = nullptr, *t0 = nullptr, *G64 = nullptr;
+  float *Rf = nullptr, *G32 = nullptr, *Cb = nullptr, *Cc = nullptr;
+  __nv_bfloat16 *A2lo = nullptr, *XtTlo = nullptr;
+  void* ph = nullptr;
+};
+
+kd_status minnorm_phase(kd_ctx* ctx, TrainBufs& b, MinnormBufs& q, int p, int m, int mp, int nc, float wd,
+                        const float* W0) {
+  double *d64 = q.d64, *g64 = q.g64, *t0 = q.t0, *G64 = q.G64;
+  float *Rf = q.Rf, *G32 = q.G32;
+  void* ph = q.ph;
   const int ld = (nc + 7) & ~7;
   kd_status s;
   if ((s = classical_on_set(ctx, b.xp, m, p, d64, g64, t0, ph)) != KD_OK) return s;
@@ -1420,9 +1430,14 @@ kd_status minnorm_phase(kd_ctx* ctx, TrainBufs& b, int p, int m, int mp, int nc,
     g32[2 * i + 1] = (float)G[i].imag();
   }
   KD_CUDA(cudaMemcpyAsync(G32, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, ctx->st), "inverse");
-  KD_LAUNCH(learned_minnorm_operand(Rf, G32, m, mp, nc, b.A2, ctx->st), "operand");
+  // A X^H = A_hi X_hi + A_lo X_hi + A_hi X_lo (A_lo X_lo dropped): three BF16 GEMMs
+  KD_LAUNCH(learned_minnorm_operand(Rf, G32, m, mp, nc, b.A2, q.A2lo, ctx->st), "operand");
+  KD_LAUNCH(learned_pack_x_lo(b.xp, mp, nc, q.XtTlo, ctx->st), "x low part");
   KD_LAUNCH(train_gemm(ctx, b, b.A2, b.XtT, b.C2, 2 * nc, nc, 2 * mp, ld), "correction gemm");
-  KD_LAUNCH(learned_add_bf16(W0, b.C2, ctx->l_W + (size_t)p * 2 * nc * ld, 2L * nc * ld, ctx->st), "store");
+  KD_LAUNCH(train_gemm(ctx, b, q.A2lo, b.XtT, q.Cb, 2 * nc, nc, 2 * mp, ld), "correction gemm");
+  KD_LAUNCH(train_gemm(ctx, b, b.A2, q.XtTlo, q.Cc, 2 * nc, nc, 2 * mp, ld), "correction gemm");
+  KD_LAUNCH(learned_add_bf16(W0, b.C2, q.Cb, q.Cc, ctx->l_W + (size_t)p * 2 * nc * ld, 2L * nc * ld, ctx->st),
+            "store");
   KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");   // g32 is host memory of this frame
   return KD_OK;
 }
@@ -1450,29 +1465,35 @@ kd_status kd_learned_train(kd_ctx* ctx, const float* x, const float* y, const in
   TrainBufs b;
   if (method == KD_TRAIN_MINNORM) {
     if (mmax > 4096) return fail(ctx, KD_EINVAL, "kd_learned_train: KD_TRAIN_MINNORM takes at most 4096 pairs a phase");
-    double *d64 = nullptr, *g64 = nullptr, *t0 = nullptr, *G64 = nullptr;
-    float *Rf = nullptr, *G32 = nullptr;
-    void* ph = nullptr;
+    MinnormBufs q;
     if ((s = train_bufs(ctx, b, mp, nc)) != KD_OK) return s;
     const int Sc = steps_for(ctx->l_sliceT, ctx->p.dt_coarse);
-    if ((s = dalloc(ctx, (void**)&d64, (size_t)mp * nc * 16, "inputs")) != KD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&g64, (size_t)mp * nc * 16, "classical outputs")) != KD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&t0, (size_t)mp * 8, "times")) != KD_OK) return s;
-    if ((s = dalloc(ctx, &ph, phase_table_bytes(ctx->p.prec_coarse, mp, Sc), "phases")) != KD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&Rf, (size_t)mp * nc * 8, "residual")) != KD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&G64, (size_t)mp * mp * 16, "gram")) != KD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&G32, (size_t)mp * mp * 8, "gram inverse")) != KD_OK) return s;
+    const size_t cbytes = 2 * (size_t)nc * ld * 4;
+    if ((s = dalloc(ctx, (void**)&q.d64, (size_t)mp * nc * 16, "inputs")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.g64, (size_t)mp * nc * 16, "classical outputs")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.t0, (size_t)mp * 8, "times")) != KD_OK) return s;
+    if ((s = dalloc(ctx, &q.ph, phase_table_bytes(ctx->p.prec_coarse, mp, Sc), "phases")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.Rf, (size_t)mp * nc * 8, "residual")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.G64, (size_t)mp * mp * 16, "gram")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.G32, (size_t)mp * mp * 8, "gram inverse")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.A2lo, 2 * (size_t)nc * 2 * mp * 2, "operand low part")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.XtTlo, (size_t)nc * 2 * mp * 2, "x low part")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.Cb, cbytes, "correction")) != KD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&q.Cc, cbytes, "correction")) != KD_OK) return s;
+    KD_CUDA(cudaMemsetAsync(q.Cb, 0, cbytes, ctx->st), "memset");   // padding columns stay 0
+    KD_CUDA(cudaMemsetAsync(q.Cc, 0, cbytes, ctx->st), "memset");
     for (int p = 0; p < ctx->l_nphase; ++p) {
       const int m = (int)byp[p].size();
       if (m == 0) continue;
       if ((s = load_pairs(ctx, b, x, y, byp[p], mp, nc)) != KD_OK) return s;
-      if ((s = minnorm_phase(ctx, b, p, m, mp, nc, weight_decay, ctx->l_W0 + (size_t)p * wcount, d64, g64, t0, ph,
-                             Rf, G64, G32)) != KD_OK)
+      if ((s = minnorm_phase(ctx, b, q, p, m, mp, nc, weight_decay, ctx->l_W0 + (size_t)p * wcount)) != KD_OK)
         return s;
     }
     if ((s = check_gemm(ctx, b)) != KD_OK) return s;
     free_train_bufs(ctx, b);
-    for (void* q : {(void*)d64, (void*)g64, (void*)t0, ph, (void*)Rf, (void*)G64, (void*)G32}) dfree(ctx, q);
+    for (void* v : {(void*)q.d64, (void*)q.g64, (void*)q.t0, q.ph, (void*)q.Rf, (void*)q.G64, (void*)q.G32,
+                    (void*)q.A2lo, (void*)q.XtTlo, (void*)q.Cb, (void*)q.Cc})
+      dfree(ctx, v);
     return KD_OK;
   }
   float *Wm = nullptr, *m1 = nullptr, *v = nullptr;

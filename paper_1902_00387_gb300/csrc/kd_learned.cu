@@ -612,8 +612,13 @@ int learned_resid64(const float* y, const double* g, float* R, long n_complex, c
 // columns n in [m, mp) zero.  A block computes 16 n x 64 j; Ginv is FP32 complex [m][m].
 constexpr int CJ = 64, CN = 16, CL = 16;
 
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16(v);
+  lo = __float2bfloat16(v - __bfloat162float(hi));
+}
+
 __global__ void __launch_bounds__(256) k_minnorm_operand(const float2* R, const float2* Gi, int m, int mp, int nc,
-                                                         __nv_bfloat16* A2) {
+                                                         __nv_bfloat16* A2, __nv_bfloat16* A2lo) {
   __shared__ float2 sR[CL][CJ], sG[CL][CN + 1];
   const int j0 = blockIdx.x * CJ, n0 = blockIdx.y * CN;
   const int tj = threadIdx.x % CJ, tn = threadIdx.x / CJ;   // 64 x 4 threads, 4 n each
@@ -650,28 +655,57 @@ __global__ void __launch_bounds__(256) k_minnorm_operand(const float2* R, const 
     const int n = n0 + tn * 4 + q;
     if (n >= mp) continue;
     const float2 a = n < m ? acc[q] : make_float2(0.f, 0.f);
-    A2[(long)j * m2 + n] = __float2bfloat16(a.x);
-    A2[(long)j * m2 + mp + n] = __float2bfloat16(a.y);
-    A2[(long)(nc + j) * m2 + n] = __float2bfloat16(a.y);
-    A2[(long)(nc + j) * m2 + mp + n] = __float2bfloat16(-a.x);
+    __nv_bfloat16 rh, rl, ih, il, mh, ml;
+    split_bf16(a.x, rh, rl);
+    split_bf16(a.y, ih, il);
+    split_bf16(-a.x, mh, ml);
+    A2[(long)j * m2 + n] = rh;
+    A2[(long)j * m2 + mp + n] = ih;
+    A2[(long)(nc + j) * m2 + n] = ih;
+    A2[(long)(nc + j) * m2 + mp + n] = mh;
+    A2lo[(long)j * m2 + n] = rl;
+    A2lo[(long)j * m2 + mp + n] = il;
+    A2lo[(long)(nc + j) * m2 + n] = il;
+    A2lo[(long)(nc + j) * m2 + mp + n] = ml;
   }
 }
 
 int learned_minnorm_operand(const float* R, const float* Ginv, int m, int mp, int nc, __nv_bfloat16* A2,
-                            cudaStream_t st) {
+                            __nv_bfloat16* A2lo, cudaStream_t st) {
   const dim3 grid((nc + CJ - 1) / CJ, (mp + CN - 1) / CN);
-  k_minnorm_operand<<<grid, 256, 0, st>>>((const float2*)R, (const float2*)Ginv, m, mp, nc, A2);
+  k_minnorm_operand<<<grid, 256, 0, st>>>((const float2*)R, (const float2*)Ginv, m, mp, nc, A2, A2lo);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-// Wbf = bf16(W0 + D) (stacked operators)
-__global__ void k_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
-    Wbf[i] = __float2bfloat16(W0[i] + D[i]);
+// XtTlo: x - bf16(x) in BF16, laid out as learned_pack_x's XtT ([nc][2 m])
+__global__ void k_pack_x_lo(const float* x, int m, int nc, __nv_bfloat16* XtTlo, long total) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long n = i / nc;
+    const int j = (int)(i - n * nc);
+    __nv_bfloat16 h, l;
+    split_bf16(x[2 * i], h, l);
+    XtTlo[(long)j * 2 * m + n] = l;
+    split_bf16(x[2 * i + 1], h, l);
+    XtTlo[(long)j * 2 * m + m + n] = l;
+  }
 }
 
-int learned_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count, cudaStream_t st) {
-  k_add_bf16<<<grid1(count), TB, 0, st>>>(W0, D, Wbf, count);
+int learned_pack_x_lo(const float* x, int m, int nc, __nv_bfloat16* XtTlo, cudaStream_t st) {
+  const long total = (long)m * nc;
+  k_pack_x_lo<<<grid1(total), TB, 0, st>>>(x, m, nc, XtTlo, total);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Wbf = bf16(W0 + D0 + D1 + D2) (stacked operators)
+__global__ void k_add_bf16(const float* W0, const float* D0, const float* D1, const float* D2, __nv_bfloat16* Wbf,
+                           long count) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    Wbf[i] = __float2bfloat16(W0[i] + (D0[i] + (D1[i] + D2[i])));
+}
+
+int learned_add_bf16(const float* W0, const float* D0, const float* D1, const float* D2, __nv_bfloat16* Wbf,
+                     long count, cudaStream_t st) {
+  k_add_bf16<<<grid1(count), TB, 0, st>>>(W0, D0, D1, D2, Wbf, count);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

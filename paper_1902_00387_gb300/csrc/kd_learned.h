@@ -80,10 +80,15 @@ int learned_gram(const float* x, int m, int nc, double* G, cudaStream_t st);
 // R = y - g (g the classical outputs in FP64), complex FP32, n_complex values
 int learned_resid64(const float* y, const double* g, float* R, long n_complex, cudaStream_t st);
 // A = R Ginv (Ginv complex FP32 [m][m]) as the gradient GEMM's left operand A2 [2 nc][2 mp]
-// (the layout learned_residual writes), zero in the padding columns n >= m
+// (the layout learned_residual writes), zero in the padding columns n >= m, split in two
+// BF16 terms A2 + A2lo (A2lo = the rounding error of A2), so that the correction GEMM
+// A X^H keeps ~16 bits where its terms cancel
 int learned_minnorm_operand(const float* R, const float* Ginv, int m, int mp, int nc, __nv_bfloat16* A2,
-                            cudaStream_t st);
-// Wbf = bf16(W0 + D)
-int learned_add_bf16(const float* W0, const float* D, __nv_bfloat16* Wbf, long count, cudaStream_t st);
+                            __nv_bfloat16* A2lo, cudaStream_t st);
+// the rounding error x - bf16(x) of learned_pack_x's XtT operand, same layout
+int learned_pack_x_lo(const float* x, int m, int nc, __nv_bfloat16* XtTlo, cudaStream_t st);
+// Wbf = bf16(W0 + D0 + D1 + D2)
+int learned_add_bf16(const float* W0, const float* D0, const float* D1, const float* D2, __nv_bfloat16* Wbf,
+                     long count, cudaStream_t st);
 
 }  // namespace kd

@@ -257,20 +257,17 @@ def _bf16_bits_to_complex(Wb):
 
 @pytest.mark.parametrize("wd", [0.0, 1e-2])
 def test_minimum_norm_correction_matches_oracle_ridge(kd, wd):
-    """KD_TRAIN_MINNORM against the oracle's closed-form minimiser (learned_ridge): pairs
-    from the oracle's fine propagator, the centre W0 the oracle's coarse propagator on the
-    learned set (columns from unit vectors), 48 pairs for 192 unknowns a row.  With wd = 0
-    the operator maps every training input onto its output (to BF16 rounding) although the
-    classical one misses them by more."""
+    """KD_TRAIN_MINNORM against the oracle's closed-form minimisers (learned_minnorm for
+    wd = 0, learned_ridge for wd > 0), with
+    the centre W0 the oracle's coarse propagator on the learned set (columns from unit
+    vectors) and 48 pairs for 192 unknowns a row.  The outputs are y = (W0 + D) x for a
+    fixed perturbation D of 20% of W0, so that the correction (D projected on the span of
+    the inputs) is far above the BF16 resolution of the stored operator.  With wd = 0 the
+    operator maps every training input onto its output."""
     import torch
     ph, m = 3, 48
-    X = learned_inputs(range(70_000, 70_000 + m)).reshape(m, NC)
-    prob = O.Problem(O.GALLOWAY_PROCTOR, N_FINE, KZ, RM)
-    S = math.ceil(SLICE / DT_F - 1e-9)
-    shape = (3, M_SET, M_SET)
-    Y = np.stack([O.learned_restrict(O.propagate(O.learned_prolong(x.reshape(shape), M_SET, N_FINE), prob, ph * SLICE,
-                                                 SLICE / S, S), M_SET).ravel() for x in X])
-    ng = 16                                          # grid with no aliasing for |k| <= 4
+    X = learned_inputs(range(70_000, 70_000 + m))               # learned vectors [m][NC]
+    ng = 16                                                     # grid with no aliasing for |k| <= 4
     probc = O.Problem(O.GALLOWAY_PROCTOR, ng, KZ, RM)
     Sc = math.ceil(SLICE / DT_C - 1e-9)
     mask = O.learned_mask(ng, M_SET)
@@ -278,14 +275,18 @@ def test_minimum_norm_correction_matches_oracle_ridge(kd, wd):
     for j in range(NC):
         e = np.zeros(NC, np.complex128)
         e[j] = 1.0
-        W0[:, j] = O.learned_restrict(O.propagate(O.learned_prolong(e.reshape(shape), M_SET, ng), probc, ph * SLICE,
-                                                  SLICE / Sc, Sc, mask=mask), M_SET).ravel()
-    ref = O.learned_ridge(X, Y, W0, wd)
+        W0[:, j] = O.learned_restrict(O.propagate(O.learned_prolong(e, M_SET, ng), probc, ph * SLICE, SLICE / Sc, Sc,
+                                                  mask=mask), M_SET)
+    rng = np.random.default_rng(5)
+    D = rng.standard_normal((NC, NC)) + 1j * rng.standard_normal((NC, NC))
+    D *= 0.2 * np.linalg.norm(W0) / np.linalg.norm(D)
+    Y = X @ (W0 + D).T
+    ref = O.learned_ridge(X, Y, W0, wd) if wd > 0 else O.learned_minnorm(X, Y, W0)
     ctx = make_ctx(kd)
     try:
         kd.kd_learned_init(ctx, N_PHASE, SLICE)
-        xt = torch.tensor(X.reshape(m, *shape).astype(np.complex64), device="cuda")
-        yt = torch.tensor(Y.reshape(m, *shape).astype(np.complex64), device="cuda")
+        xt = torch.tensor(X.astype(np.complex64), device="cuda")
+        yt = torch.tensor(Y.astype(np.complex64), device="cuda")
         kd.kd_learned_train(ctx, xt, yt, [ph] * m, m, 0, 0.0, wd, N_PHASE, kd.KD_TRAIN_MINNORM)
         Wb = np.zeros((2 * NC, NC), np.uint16)
         kd.kd_learned_get(ctx, ph, Wb)
@@ -293,11 +294,9 @@ def test_minimum_norm_correction_matches_oracle_ridge(kd, wd):
         kd.kd_destroy(ctx)
     W = _bf16_bits_to_complex(Wb)
     assert rel(W, ref) < 4e-3                                  # BF16 storage of the operator
-    dW, dref = W - W0, ref - W0
-    assert rel(dW, dref) < 0.1                                 # the correction itself
-    err = rel(X @ W.T, Y)
-    err0 = rel(X @ W0.T, Y)
+    assert rel(W - W0, ref - W0) < 0.05                        # the correction itself
+    err, err0 = rel(X @ W.T, Y), rel(X @ W0.T, Y)
     if wd == 0.0:
-        assert err < 5e-3 and err0 > 5 * err, (err, err0)
+        assert err < 0.02 * err0, (err, err0)                  # interpolation
     else:
         assert err < err0, (err, err0)

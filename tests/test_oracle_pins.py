@@ -452,6 +452,22 @@ def test_learned_ridge_solution_zeroes_gradient_and_recovers_exact_map():
     assert np.abs(Wr - Wstar).max() < 1e-10
 
 
+def test_learned_minnorm_interpolates_and_changes_nothing_off_the_inputs():
+    # the defining properties: W x_i = y_i, and (W - W0) v = 0 for every v orthogonal to
+    # the inputs (complex inner product); learned_ridge tends to it as wd -> 0
+    rng = np.random.default_rng(6)
+    nc, m = 7, 3
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    W0, X, Y = c(nc, nc), c(m, nc), c(m, nc)
+    W = O.learned_minnorm(X, Y, W0)
+    assert np.abs(X @ W.T - Y).max() < 1e-12
+    Q, _ = np.linalg.qr(X.T, mode="complete")                 # last nc - m columns: x_i^H v = 0
+    V = Q[:, m:]
+    assert np.abs(np.conj(X) @ V).max() < 1e-12
+    assert np.abs((W - W0) @ V).max() < 1e-12
+    assert np.abs(O.learned_ridge(X, Y, W0, 1e-7) - W).max() < 1e-5
+
+
 def test_learned_exact_map_reproduces_fine_pairs():
     # R F P is the fine propagator restricted to the set: zero loss on its own pairs
     prob = O.Problem(O.GALLOWAY_PROCTOR, 16, 0.57, 30.0)
