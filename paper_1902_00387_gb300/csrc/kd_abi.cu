@@ -847,13 +847,24 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
     KD_LAUNCH(compact_to_full(KD_C128, tmp, pf, b_out, batch, n, ctx->st), "unpack");
     return KD_OK;
   }
-  KD_LAUNCH(full_to_compact(pf, b_in, pf, ctx->ws_f.X, batch, n, ctx->st), "pack");
+  // kernels that take the state in the caller's layout skip the pack and unpack passes:
+  // the first step reads b_in, the last writes the kept entries of b_out, and the rest of
+  // b_out is zeroed (b_in == b_out is fine: a row is read before it is written)
+  const bool full_io = nsteps > 0 && fine_full_io(n, pf, ctx->plan[0], ctx->p.fine_scheme);
+  if (!full_io) KD_LAUNCH(full_to_compact(pf, b_in, pf, ctx->ws_f.X, batch, n, ctx->st), "pack");
   FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, ctx->p.dt_fine, t0);
+  if (full_io) {
+    a.x_in_full = b_in;
+    a.x_out_full = b_out;
+  }
   if ((s = with_phases(ctx, ctx->ws_f, a, nsteps)) != KD_OK) return s;
   LaunchProbe pr = probe_of(ctx);
   if (nsteps > 0)
     KD_LAUNCH(run_fine(ctx, 0, pf, a, nsteps, true, false, ctx->prof ? &pr : nullptr), "fine steps");
-  KD_LAUNCH(compact_to_full(pf, ctx->ws_f.X, pf, b_out, batch, n, ctx->st), "unpack");
+  if (full_io)
+    KD_LAUNCH(zero_outside_kept(pf, b_out, batch, n, ctx->st), "zero fill");
+  else
+    KD_LAUNCH(compact_to_full(pf, ctx->ws_f.X, pf, b_out, batch, n, ctx->st), "unpack");
   return KD_OK;
 }
 

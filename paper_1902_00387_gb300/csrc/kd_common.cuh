@@ -91,6 +91,12 @@ struct FineArgs {
   const SliceParams* sp;  // optional [batch] per-slice parameters (NULL: the scalars above);
                           // with sp the phase table is read for every field (flow = FLOW_GP)
   int scheme;             // IMEX scheme of the fine step: SCHEME_RK443 / RK222 / RK111
+  // The state in the caller's full layout [batch][3][n][n] (FFT order), for kernels that
+  // read or write it there directly (fine_full_io): x_in_full, if set, replaces X as the
+  // state read before the first step's update; x_out_full, if set, receives the state
+  // after the last step (its kept entries; X and Xlo are not written then).
+  const void* x_in_full = nullptr;
+  void* x_out_full = nullptr;
 };
 
 // IMEX Runge-Kutta schemes of the fine step (match include/kd.h KD_RK*) and their stage

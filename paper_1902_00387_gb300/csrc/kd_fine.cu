@@ -118,6 +118,10 @@ FinePlan fine_default_plan(int n, int prec) {
   return FinePlan();
 }
 
+bool fine_full_io(int n, int prec, const FinePlan& plan, int scheme) {
+  return n == 1024 && prec == 0 && plan.row == kRow4Variant && scheme == SCHEME_RK443;
+}
+
 bool fine_variants(int n, int prec, int* ncol, int* nrow) {
   const int m = fine_fft_grid(n);
   return prec == 0 ? variants_T<float>(m, ncol, nrow) : variants_T<double>(m, ncol, nrow);

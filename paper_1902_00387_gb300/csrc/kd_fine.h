@@ -46,6 +46,12 @@ int launch_phases(int prec, const FineArgs& a, int nsteps, cudaStream_t st);
 bool fine_variants(int n, int prec, int* ncol, int* nrow);
 // launch plan of a context before any autotuning or kd_set_plan
 FinePlan fine_default_plan(int n, int prec);
+// Row variant of the warp-transform row kernel of the complex64 n = 1024 grid
+constexpr int kRow4Variant = 7;
+// whether the plan's kernels read the first step's state from FineArgs::x_in_full and
+// write the last step's to x_out_full (the caller's layout, no pack / unpack pass):
+// RK443 steps of the row kernel kRow4Variant
+bool fine_full_io(int n, int prec, const FinePlan& plan, int scheme);
 // Enqueue cfg.nsteps RK443 steps on the compact state a.X after filling the phase table
 // a.phases (which must hold phase_table_bytes(prec, a.batch, nsteps)).  Returns the
 // number of kernels launched (negative on an unsupported grid size).
@@ -98,6 +104,8 @@ FinePlan fine3_default_plan();
 int full_to_compact(int pin, const void* full, int pout, void* comp, long batch, int n, cudaStream_t st);
 // compact -> full, zeros outside the kept square
 int compact_to_full(int pin, const void* comp, int pout, void* full, long batch, int n, cudaStream_t st);
+// zeros at the entries of the full layout outside the kept square (the rest untouched)
+int zero_outside_kept(int prec, void* full, long batch, int n, cudaStream_t st);
 // compact (n_src grid, precision pin) -> compact (n_dst grid, precision pout):
 // truncation when n_dst < n_src, zero padding when n_dst > n_src
 int compact_resample(int pin, const void* src, int n_src, int pout, void* dst, int n_dst, long batch,

@@ -422,10 +422,12 @@ struct Row4 {
 // stage_update): f = F_c(X_j) (already scaled); r[0..] = the arrays the stage reads, in
 // the order X (stage 0), R2 R3 R4 (stage 1), R3 R4 (stage 2), R4 X Xlo (stage 3; Xlo
 // zero before the first step).  R4 holds R4 - X0 and the state is the pair (X, Xlo) as
-// in state_add.  Returns X_{j+1}.
+// in state_add.  Returns X_{j+1}.  Stage 3 stores the state in X and Xlo, or, with xout
+// set (the last step of a call), its rounded value at *xout only.
 template <int MODE>
 __device__ __forceinline__ cx<float> stage_update_1(const StageCoef<float>& q, const StageArrays<float>& sa, long s,
-                                                    float g, float dl, const cx<float>* r, cx<float> f) {
+                                                    float g, float dl, const cx<float>* r, cx<float> f,
+                                                    cx<float>* xout) {
   const float dt = q.dt;
   if (MODE == 0) {
     const cx<float> x0 = r[0];
@@ -451,8 +453,12 @@ __device__ __forceinline__ cx<float> stage_update_1(const StageCoef<float>& q, c
     two_sum(x0.y, e.y, s1, e1);
     two_sum(s0, lo.x + e0, h0, l0);
     two_sum(s1, lo.y + e1, h1, l1);
-    sa.X[s] = mk(h0, h1);
-    sa.Xlo[s] = mk(l0, l1);
+    if (xout) {
+      *xout = mk(h0, h1);
+    } else {
+      sa.X[s] = mk(h0, h1);
+      sa.Xlo[s] = mk(l0, l1);
+    }
     return mk(h0, h1);
   }
 }
@@ -480,6 +486,11 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
   const StageArrays<float> sa = stage_arrays<float>(a);
   const cx<float>* src[3] = {MODE == 0 ? sa.X : (MODE == 1 ? sa.R2 : (MODE == 2 ? sa.R3 : sa.R4)),
                              MODE == 1 ? sa.R3 : (MODE == 2 ? sa.R4 : sa.X), MODE == 1 ? sa.R4 : sa.Xlo};
+  // the array holding the state X among src (stages 0 and 3), read from the caller's
+  // layout [batch][3][N][N] in the first step when x_in_full is set
+  constexpr int XSRC = MODE == 0 ? 0 : (MODE == 3 ? 1 : -1);
+  const cx<float>* xin = (const cx<float>*)a.x_in_full;
+  cx<float>* xout = MODE == 3 ? (cx<float>*)a.x_out_full : nullptr;
   // stage 3 before the first step of a call: the low part of the state is zero
   const int npre = MODE == 3 && !sa.lo_valid ? 2 : NPRE;
   const long rows = (long)a.batch * P;
@@ -490,6 +501,8 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
     const long b = row / P;
     const int iy = (int)(row - b * P);
     const long sbase = ((b * 3 + c) * P + iy) * (long)P + K;   // compact index of kx = 0
+    // the row (b, c, ky = iy - K) in the caller's layout: element kx at (kx mod N)
+    const long fbase = ((b * 3 + c) * N + (iy - K < 0 ? iy - K + N : iy - K)) * (long)N;
     cx<float> v[32];
     if (MODE == 4) {
 #pragma unroll
@@ -499,7 +512,7 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
         if (wfft_never_kept<N>(k))
           v[k] = mk(0.f, 0.f);
         else
-          v[k] = (kx >= -K && kx <= K) ? sa.X[sbase + kx] : mk(0.f, 0.f);
+          v[k] = (kx >= -K && kx <= K) ? (xin ? xin[fbase + xx] : sa.X[sbase + kx]) : mk(0.f, 0.f);
       }
     } else {
       // the stage arrays of this lane's kept kx -> Q (each lane later reads only its own copies)
@@ -510,7 +523,9 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
           if (wfft_never_kept<N>(p) || j >= npre) continue;
           const int xx = lane + 32 * p;
           const int kx = xx < N / 2 ? xx : xx - N;
-          if (kx >= -K && kx <= K) cp_async8(Q + (j * kRow4Slots + row4_slot(p)) * 32 + lane, src[j] + sbase + kx);
+          if (kx >= -K && kx <= K)
+            cp_async8(Q + (j * kRow4Slots + row4_slot(p)) * 32 + lane,
+                      j == XSRC && xin ? xin + fbase + xx : src[j] + sbase + kx);
         }
       cp_async_commit();
       const cx<float>* Wr = (const cx<float>*)a.W + ((b * 3 + c) * P + iy) * (long)N;
@@ -551,7 +566,8 @@ __global__ void __launch_bounds__(Row4<N, ROWS, MODE>::BLOCK, Row4<N, ROWS, MODE
 #pragma unroll
             for (int j = 0; j < NPRE; ++j)
               r[j] = j < npre ? Q[(j * kRow4Slots + row4_slot(pp)) * 32 + lane] : mk(0.f, 0.f);
-            v[pp] = stage_update_1<MODE>(sc, sa, sbase + kx, g, sc.dt * lam, r, f);
+            v[pp] = stage_update_1<MODE>(sc, sa, sbase + kx, g, sc.dt * lam, r, f,
+                                         xout ? xout + fbase + xx : nullptr);
           }
         }
       }

@@ -251,7 +251,7 @@ struct Fine3Set {
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr bool W4 = WIDE && N == 1024;
-  static constexpr int kW4Col = 4, kW5Col = 5, kW4Row = 7;
+  static constexpr int kW4Col = 4, kW5Col = 5, kW4Row = kRow4Variant;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
@@ -415,6 +415,9 @@ static int run_steps(const FineArgs& a0, const StepCfg& cfg) {
   const int stages = scheme_stages(a0.scheme);
   for (int s = 0; s < cfg.nsteps; ++s) {
     a.lo_valid = s > 0;   // the low part of the state (kd_stage.cuh) exists from the second step
+    // the caller's layout holds the state before the first step and receives it after the last
+    a.x_in_full = s == 0 ? a0.x_in_full : nullptr;
+    a.x_out_full = s == cfg.nsteps - 1 ? a0.x_out_full : nullptr;
     if (cfg.active) {
       a.batch = cfg.active[s];
       if (a.batch <= 0) break;

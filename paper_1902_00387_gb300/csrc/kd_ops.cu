@@ -98,6 +98,30 @@ int compact_to_full(int pin, const void* comp, int pout, void* full, long batch,
   if (pin == 0 && pout == 1) return c2f<float, double>(comp, full, batch, n, st);
   return c2f<float, float>(comp, full, batch, n, st);
 }
+// Zeros of the full layout outside the kept square: whole rows |ky| > K, and the columns
+// |kx| > K of the other rows (a row of the full layout in 16-byte pieces where aligned).
+template <typename T>
+__global__ void k_zero_unkept(cx<T>* full, long rows, int n, int K) {
+  const int w = n - (2 * K + 1);            // unkept columns K + 1 .. n - K - 1 of a kept row
+  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int y = (int)(r % n);
+    const bool kept = y <= K || y >= n - K;
+    cx<T>* row = full + r * (long)n;
+    const int c0 = kept ? K + 1 : 0, cnt = kept ? w : n;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) row[c0 + i] = mk(T(0), T(0));
+  }
+}
+
+int zero_outside_kept(int prec, void* full, long batch, int n, cudaStream_t st) {
+  const long rows = batch * 3L * n;
+  const unsigned g = rows < 65535L * 8 ? (unsigned)rows : 65535u * 8;
+  if (prec == 1)
+    k_zero_unkept<double><<<g, 256, 0, st>>>((cx<double>*)full, rows, n, n / 3);
+  else
+    k_zero_unkept<float><<<g, 256, 0, st>>>((cx<float>*)full, rows, n, n / 3);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int compact_resample(int pin, const void* src, int ns, int pout, void* dst, int nd, long batch, cudaStream_t st) {
   if (pin == 1 && pout == 1) return rs<double, double>(src, ns, dst, nd, batch, st);
   if (pin == 1 && pout == 0) return rs<double, float>(src, ns, dst, nd, batch, st);

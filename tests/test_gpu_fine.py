@@ -108,6 +108,39 @@ def test_large_workload_late_slices_match_oracle(kd):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 20)) < TOL32, i
 
 
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_state_in_the_callers_layout_at_1024(kd, nsteps):
+    """The default 1024^2 complex64 plan reads the first step's state from the input and
+    writes the last step's into the output (no pack / unpack pass): against the oracle,
+    every entry outside the kept square exactly zero in an output that held NaN before,
+    and the in-place call (input = output) equal to it bit for bit."""
+    import torch
+    n, kz, Rm, dt = 1024, 0.57, 1e4, 1e-3
+    b = I.initial_batch(n, kz, [71, 72])
+    t0 = [0.4, 77.0]
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64))
+    try:
+        assert tuple(kd.kd_get_plan(ctx, kd.KD_GRID_FINE)) == (5, 7)
+        x = torch.tensor(b, dtype=torch.complex64, device="cuda")
+        y = torch.full_like(x, float("nan"))
+        tt = torch.tensor(t0, dtype=torch.float64, device="cuda")
+        kd.kd_fine_batched(ctx, x, y, tt, nsteps, 2)
+        z = x.clone()
+        kd.kd_fine_batched(ctx, z, z, tt, nsteps, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(y, z)
+        assert torch.equal(x, torch.tensor(b, dtype=torch.complex64, device="cuda"))   # input untouched
+        out = y.cpu().numpy().astype(np.complex128)
+    finally:
+        kd.kd_destroy(ctx)
+    k = I.fft_wavenumbers(n)
+    kept = (np.abs(k)[None, :] <= n // 3) & (np.abs(k)[:, None] <= n // 3)
+    assert np.all(out[:, :, ~kept] == 0)
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i in range(2):
+        assert rel(out[i], O.propagate(b[i], p, t0[i], dt, nsteps)) < TOL32, i
+
+
 @pytest.mark.parametrize("n,nsteps", [(128, 20), (512, 6), (1024, 4)])
 def test_flat_spectrum_edge_ring(kd, n, nsteps):
     """A flat-spectrum solenoidal input puts as much energy on the edge ring of the kept
