@@ -1148,8 +1148,8 @@ def run_parareal(args):
 # kernel's name as the bench reports it and the plan.  A plan without a capture of its
 # current kernels reports null.
 FINE_TRAFFIC = {
-    ("fine row kernel", (5, 7)): 16 * (1191.35 + 1374.87 + 1022.13 + 939.71) / 4 * 1e6,
-    ("fine column kernel", (5, 7)): 16 * (487.35 + 484.44 + 484.49 + 484.41) / 4 * 1e6,
+    ("fine row kernel", (5, 7)): 16 * (1196.98 + 1375.10 + 1022.11 + 785.55) / 4 * 1e6,
+    ("fine column kernel", (5, 7)): 16 * (484.47 + 484.48 + 484.51 + 484.42) / 4 * 1e6,
 }
 
 
