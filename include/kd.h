@@ -128,6 +128,18 @@ kd_status kd_destroy(kd_ctx* ctx);
 kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const double* t0,
                           int nsteps, int batch);
 
+/* The fine propagator of kd_fine_batched on fields in HOST memory: the batch moves in
+ * chunks of `chunk` fields (0: all at once), the copy in of a chunk, its propagation and
+ * the copy out of the previous chunk overlapping on three streams (two device slots per
+ * direction, allocated on first use and kept).  Same values as kd_fine_batched, field by
+ * field.  No counterpart in the paper (host I/O of this library).
+ *   h_in, h_out : host, [batch][3][n][n] complex in params.prec_fine (page-locked memory
+ *                 lets the copies overlap; pageable memory works, slower); may alias.
+ *   t0          : host double[batch] start times.
+ * Synchronous: returns when h_out holds the result. */
+kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0,
+                               int nsteps, int batch, int chunk);
+
 /* Classical coarse propagator G (Sec. 3.2, Sec. 5.2): restrict each field to the
  * N_C grid (Fourier truncation), take `nsteps` RK443 steps of params.dt_coarse in
  * params.prec_coarse, prolong (zero-pad) back to n.

@@ -819,6 +819,13 @@ kd_status kd_destroy(kd_ctx* ctx) {
     cudaStreamDestroy(ctx->st_hi);
   }
   for (cudaEvent_t e : ctx->pev2) cudaEventDestroy(e);
+  for (cudaStream_t q : {ctx->st_h2d, ctx->st_d2h})
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
+  for (cudaEvent_t e : ctx->hev)
+    if (e) cudaEventDestroy(e);
   if (ctx->host_scal) cudaFreeHost(ctx->host_scal);
   for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.second.exec);
   if (ctx->st_g) {
@@ -865,6 +872,67 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
     KD_LAUNCH(zero_outside_kept(pf, b_out, batch, n, ctx->st), "zero fill");
   else
     KD_LAUNCH(compact_to_full(pf, ctx->ws_f.X, pf, b_out, batch, n, ctx->st), "unpack");
+  return KD_OK;
+}
+
+kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
+                               int chunk) {
+  if (!ctx) return KD_EINVAL;
+  if (!h_in || !h_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: NULL buffer");
+  if (batch < 0 || nsteps < 0 || chunk < 0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: negative argument");
+  if (batch == 0) return KD_OK;
+  if (chunk == 0 || chunk > batch) chunk = batch;
+  const int n = ctx->p.n;
+  const size_t fb = 3 * (size_t)n * n * csize(ctx->p.prec_fine);   // bytes of one field
+  const size_t slot = fb * chunk;
+  kd_status s;
+  if (ctx->hio_bytes < slot) {
+    for (void*& q : ctx->hio) {
+      dfree(ctx, q);
+      q = nullptr;
+    }
+    ctx->hio_bytes = 0;
+    for (void*& q : ctx->hio)
+      if ((s = dalloc(ctx, &q, slot, "host-call chunk")) != KD_OK) return s;
+    ctx->hio_bytes = slot;
+  }
+  if (ctx->hio_t0_cap < batch) {
+    dfree(ctx, ctx->hio_t0);
+    ctx->hio_t0 = nullptr;
+    ctx->hio_t0_cap = 0;
+    if ((s = dalloc(ctx, (void**)&ctx->hio_t0, (size_t)batch * 8, "host-call times")) != KD_OK) return s;
+    ctx->hio_t0_cap = batch;
+  }
+  if (!ctx->st_h2d) {
+    KD_CUDA(cudaStreamCreateWithFlags(&ctx->st_h2d, cudaStreamNonBlocking), "copy stream");
+    KD_CUDA(cudaStreamCreateWithFlags(&ctx->st_d2h, cudaStreamNonBlocking), "copy stream");
+    for (cudaEvent_t& e : ctx->hev) KD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+  }
+  // events per slot q: hev[q] input copied in, hev[2 + q] computed, hev[4 + q] output copied out
+  KD_CUDA(cudaMemcpyAsync(ctx->hio_t0, t0, (size_t)batch * 8, cudaMemcpyHostToDevice, ctx->st), "times");
+  KD_CUDA(cudaEventRecord(ctx->hev[2], ctx->st), "event");
+  KD_CUDA(cudaEventRecord(ctx->hev[3], ctx->st), "event");
+  KD_CUDA(cudaEventRecord(ctx->hev[4], ctx->st), "event");
+  KD_CUDA(cudaEventRecord(ctx->hev[5], ctx->st), "event");
+  const int nchunks = (batch + chunk - 1) / chunk;
+  for (int c = 0; c < nchunks; ++c) {
+    const int q = c & 1, f0 = c * chunk, nb = batch - f0 < chunk ? batch - f0 : chunk;
+    void *din = ctx->hio[q], *dout = ctx->hio[2 + q];
+    // input slot q is free once chunk c - 2 has been computed
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_h2d, ctx->hev[2 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync(din, (const char*)h_in + f0 * fb, nb * fb, cudaMemcpyHostToDevice, ctx->st_h2d), "copy in");
+    KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st_h2d), "event");
+    // compute after the copy in, into an output slot that chunk c - 2 has left
+    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[q], 0), "wait");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[4 + q], 0), "wait");
+    if ((s = kd_fine_batched(ctx, din, dout, ctx->hio_t0 + f0, nsteps, nb)) != KD_OK) return s;
+    KD_CUDA(cudaEventRecord(ctx->hev[2 + q], ctx->st), "event");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_d2h, ctx->hev[2 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync((char*)h_out + f0 * fb, dout, nb * fb, cudaMemcpyDeviceToHost, ctx->st_d2h), "copy out");
+    KD_CUDA(cudaEventRecord(ctx->hev[4 + q], ctx->st_d2h), "event");
+  }
+  KD_CUDA(cudaStreamSynchronize(ctx->st_d2h), "sync");
+  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
   return KD_OK;
 }
 

@@ -70,6 +70,14 @@ struct kd_ctx {
   std::vector<cudaEvent_t> pev2;   // chunk release / fine-done / timing events
   void* conv_tmp = nullptr;        // FP64 staging of the convolution fine operator
   size_t conv_tmp_bytes = 0;
+  // kd_fine_batched_host: device slots of the chunks in flight (in 0, in 1, out 0, out 1),
+  // the start times, the copy streams and their events
+  void* hio[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t hio_bytes = 0;
+  double* hio_t0 = nullptr;
+  int hio_t0_cap = 0;
+  cudaStream_t st_h2d = nullptr, st_d2h = nullptr;
+  cudaEvent_t hev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t st = nullptr;
   int device = 0;
   kdi::Tables tab_f, tab_c;

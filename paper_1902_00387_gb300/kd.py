@@ -75,7 +75,7 @@ class kd_sweep_stats(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
+EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_fine_batched_host", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
            "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
@@ -101,6 +101,7 @@ def load():
         "kd_create": (I, [ctypes.POINTER(kd_params), P, ctypes.POINTER(P)]),
         "kd_destroy": (I, [P]),
         "kd_fine_batched": (I, [P, P, P, P, I, I]),
+        "kd_fine_batched_host": (I, [P, P, P, P, I, I, I]),
         "kd_coarse": (I, [P, P, P, P, I, I]),
         "kd_parareal_run": (I, [P, P, D, I, I, D, P, ctypes.POINTER(kd_parareal_stats)]),
         "kd_fine_serial": (I, [P, P, D, I, P]),
@@ -280,6 +281,29 @@ def kd_fine_batched(ctx, b_in, b_out, t0, nsteps, batch, prec=KD_C64):
     _need_count(t0, batch, "t0")
     return _check(ctx, load().kd_fine_batched(ctx, _ptr(b_in, dt), _ptr(b_out, dt), _ptr(t0, "float64"),
                                               int(nsteps), int(batch)))
+
+
+def _host_ptr(x, dtype):
+    """Address of a contiguous HOST buffer (numpy array or CPU torch tensor)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            raise TypeError("a host (CPU) buffer is required here")
+    except ImportError:
+        pass
+    return _ptr(x, dtype, device=False)
+
+
+def kd_fine_batched_host(ctx, h_in, h_out, t0, nsteps, batch, chunk=0, prec=KD_C64):
+    """F on fields in host memory (numpy arrays or CPU tensors, page-locked for overlap):
+    the batch streams through the GPU in chunks of `chunk` fields (0: one chunk); t0 is a
+    host float64 array.  Returns when h_out holds the result."""
+    dt = _cdt(prec)
+    _need(ctx, h_in, batch, "h_in")
+    _need(ctx, h_out, batch, "h_out")
+    _need_count(t0, batch, "t0")
+    return _check(ctx, load().kd_fine_batched_host(ctx, _host_ptr(h_in, dt), _host_ptr(h_out, dt),
+                                                   _host_ptr(t0, "float64"), int(nsteps), int(batch), int(chunk)))
 
 
 def kd_fine_batched_static(params, b_in, b_out, t0, nsteps, batch, stream=None):

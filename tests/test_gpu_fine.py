@@ -141,6 +141,35 @@ def test_state_in_the_callers_layout_at_1024(kd, nsteps):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, nsteps)) < TOL32, i
 
 
+@pytest.mark.parametrize("n,chunk,pinned", [(128, 0, True), (128, 2, False), (1024, 2, True)])
+def test_host_buffer_call_equals_device_call(kd, n, chunk, pinned):
+    """kd_fine_batched_host (fields in host memory, streamed through the GPU in chunks,
+    the last one ragged) gives kd_fine_batched's values bit for bit, in place as well."""
+    import torch
+    kz, Rm, dt, S = 0.57, 1e4, 1e-3, 3
+    B = 5 if n == 128 else 3
+    b = I.initial_batch(n, kz, range(80, 80 + B))
+    t0 = np.arange(B, dtype=np.float64) * 0.37
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64))
+    try:
+        x = torch.tensor(b, dtype=torch.complex64)
+        y = torch.full_like(x, float("nan"))
+        if pinned:
+            x, y = x.pin_memory(), y.pin_memory()
+        kd.kd_fine_batched_host(ctx, x, y, t0, S, B, chunk)
+        xd = x.cuda()
+        yd = torch.empty_like(xd)
+        kd.kd_fine_batched(ctx, xd, yd, torch.tensor(t0, device="cuda"), S, B)
+        torch.cuda.synchronize()
+        assert torch.equal(y, yd.cpu())
+        kd.kd_fine_batched_host(ctx, x, x, t0, S, B, chunk)
+        assert torch.equal(x, y)
+        with pytest.raises(TypeError):
+            kd.kd_fine_batched_host(ctx, xd, y, t0, S, B, chunk)      # a device buffer is refused
+    finally:
+        kd.kd_destroy(ctx)
+
+
 @pytest.mark.parametrize("n,nsteps", [(128, 20), (512, 6), (1024, 4)])
 def test_flat_spectrum_edge_ring(kd, n, nsteps):
     """A flat-spectrum solenoidal input puts as much energy on the edge ring of the kept
