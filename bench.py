@@ -1153,7 +1153,7 @@ FINE_TRAFFIC = {
 }
 
 
-E2E_CHUNK = 32   # fields per chunk of the end-to-end host-buffer call
+E2E_CHUNK = 8    # fields per chunk of the end-to-end host-buffer call (32 chunks)
 
 
 def run_fine_step(args):
@@ -1254,7 +1254,8 @@ def run_fine_step(args):
         "call_of_8_steps": {"ms": min(ms8), "mdof_steps_per_s": 8 * units / (min(ms8) / 1e3) / 1e6},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                "call": "kd_fine_batched_host, pinned host buffers, chunks of %d fields" % E2E_CHUNK},
+                "call": "kd_fine_batched_host, pinned host buffers, chunks of %d fields" % E2E_CHUNK,
+                "ms_per_step": [round(v, 3) for v in ms_e2e]},
         "gpu_launches": launches,
     }
     if env.rank == 0 and not args.no_cpu_baseline:

@@ -129,7 +129,7 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
                           int nsteps, int batch);
 
 /* The fine propagator of kd_fine_batched on fields in HOST memory: the batch moves in
- * chunks of `chunk` fields (0: all at once), the copy in of a chunk, its propagation and
+ * chunks of `chunk` fields (0: batch / 32 rounded up), the copy in of a chunk, its propagation and
  * the copy out of the previous chunk overlapping on three streams (two device slots per
  * direction, allocated on first use and kept).  Same values as kd_fine_batched, field by
  * field.  No counterpart in the paper (host I/O of this library).

@@ -881,7 +881,8 @@ kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const
   if (!h_in || !h_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: NULL buffer");
   if (batch < 0 || nsteps < 0 || chunk < 0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: negative argument");
   if (batch == 0) return KD_OK;
-  if (chunk == 0 || chunk > batch) chunk = batch;
+  if (chunk == 0) chunk = (batch + 31) / 32;   // ~32 chunks: short pipeline fill and drain
+  if (chunk > batch) chunk = batch;
   const int n = ctx->p.n;
   const size_t fb = 3 * (size_t)n * n * csize(ctx->p.prec_fine);   // bytes of one field
   const size_t slot = fb * chunk;

@@ -296,7 +296,7 @@ def _host_ptr(x, dtype):
 
 def kd_fine_batched_host(ctx, h_in, h_out, t0, nsteps, batch, chunk=0, prec=KD_C64):
     """F on fields in host memory (numpy arrays or CPU tensors, page-locked for overlap):
-    the batch streams through the GPU in chunks of `chunk` fields (0: one chunk); t0 is a
+    the batch streams through the GPU in chunks of `chunk` fields (0: batch / 32); t0 is a
     host float64 array.  Returns when h_out holds the result."""
     dt = _cdt(prec)
     _need(ctx, h_in, batch, "h_in")

@@ -141,7 +141,7 @@ def test_state_in_the_callers_layout_at_1024(kd, nsteps):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, nsteps)) < TOL32, i
 
 
-@pytest.mark.parametrize("n,chunk,pinned", [(128, 0, True), (128, 2, False), (1024, 2, True)])
+@pytest.mark.parametrize("n,chunk,pinned", [(128, 0, True), (128, 2, False), (128, 5, True), (1024, 2, True)])
 def test_host_buffer_call_equals_device_call(kd, n, chunk, pinned):
     """kd_fine_batched_host (fields in host memory, streamed through the GPU in chunks,
     the last one ragged) gives kd_fine_batched's values bit for bit, in place as well."""
