@@ -875,6 +875,34 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
   return KD_OK;
 }
 
+// The chunk pipeline of kd_fine_batched_host (slots and streams set up by the caller);
+// enqueues everything and returns without waiting.
+static kd_status host_chunks(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
+                             int chunk, size_t fb) {
+  kd_status s;
+  // events per slot q: hev[q] input copied in, hev[2 + q] computed, hev[4 + q] output copied out
+  KD_CUDA(cudaMemcpyAsync(ctx->hio_t0, t0, (size_t)batch * 8, cudaMemcpyHostToDevice, ctx->st), "times");
+  for (int q = 2; q < 6; ++q) KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st), "event");
+  const int nchunks = (batch + chunk - 1) / chunk;
+  for (int c = 0; c < nchunks; ++c) {
+    const int q = c & 1, f0 = c * chunk, nb = batch - f0 < chunk ? batch - f0 : chunk;
+    void *din = ctx->hio[q], *dout = ctx->hio[2 + q];
+    // input slot q is free once chunk c - 2 has been computed
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_h2d, ctx->hev[2 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync(din, (const char*)h_in + f0 * fb, nb * fb, cudaMemcpyHostToDevice, ctx->st_h2d), "copy in");
+    KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st_h2d), "event");
+    // compute after the copy in, into an output slot that chunk c - 2 has left
+    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[q], 0), "wait");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[4 + q], 0), "wait");
+    if ((s = kd_fine_batched(ctx, din, dout, ctx->hio_t0 + f0, nsteps, nb)) != KD_OK) return s;
+    KD_CUDA(cudaEventRecord(ctx->hev[2 + q], ctx->st), "event");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_d2h, ctx->hev[2 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync((char*)h_out + f0 * fb, dout, nb * fb, cudaMemcpyDeviceToHost, ctx->st_d2h), "copy out");
+    KD_CUDA(cudaEventRecord(ctx->hev[4 + q], ctx->st_d2h), "event");
+  }
+  return KD_OK;
+}
+
 kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
                                int chunk) {
   if (!ctx) return KD_EINVAL;
@@ -909,31 +937,13 @@ kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const
     KD_CUDA(cudaStreamCreateWithFlags(&ctx->st_d2h, cudaStreamNonBlocking), "copy stream");
     for (cudaEvent_t& e : ctx->hev) KD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
   }
-  // events per slot q: hev[q] input copied in, hev[2 + q] computed, hev[4 + q] output copied out
-  KD_CUDA(cudaMemcpyAsync(ctx->hio_t0, t0, (size_t)batch * 8, cudaMemcpyHostToDevice, ctx->st), "times");
-  KD_CUDA(cudaEventRecord(ctx->hev[2], ctx->st), "event");
-  KD_CUDA(cudaEventRecord(ctx->hev[3], ctx->st), "event");
-  KD_CUDA(cudaEventRecord(ctx->hev[4], ctx->st), "event");
-  KD_CUDA(cudaEventRecord(ctx->hev[5], ctx->st), "event");
-  const int nchunks = (batch + chunk - 1) / chunk;
-  for (int c = 0; c < nchunks; ++c) {
-    const int q = c & 1, f0 = c * chunk, nb = batch - f0 < chunk ? batch - f0 : chunk;
-    void *din = ctx->hio[q], *dout = ctx->hio[2 + q];
-    // input slot q is free once chunk c - 2 has been computed
-    KD_CUDA(cudaStreamWaitEvent(ctx->st_h2d, ctx->hev[2 + q], 0), "wait");
-    KD_CUDA(cudaMemcpyAsync(din, (const char*)h_in + f0 * fb, nb * fb, cudaMemcpyHostToDevice, ctx->st_h2d), "copy in");
-    KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st_h2d), "event");
-    // compute after the copy in, into an output slot that chunk c - 2 has left
-    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[q], 0), "wait");
-    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[4 + q], 0), "wait");
-    if ((s = kd_fine_batched(ctx, din, dout, ctx->hio_t0 + f0, nsteps, nb)) != KD_OK) return s;
-    KD_CUDA(cudaEventRecord(ctx->hev[2 + q], ctx->st), "event");
-    KD_CUDA(cudaStreamWaitEvent(ctx->st_d2h, ctx->hev[2 + q], 0), "wait");
-    KD_CUDA(cudaMemcpyAsync((char*)h_out + f0 * fb, dout, nb * fb, cudaMemcpyDeviceToHost, ctx->st_d2h), "copy out");
-    KD_CUDA(cudaEventRecord(ctx->hev[4 + q], ctx->st_d2h), "event");
-  }
-  KD_CUDA(cudaStreamSynchronize(ctx->st_d2h), "sync");
-  KD_CUDA(cudaStreamSynchronize(ctx->st), "sync");
+  s = host_chunks(ctx, h_in, h_out, t0, nsteps, batch, chunk, fb);
+  // whatever happened, no copy of the caller's memory is left in flight on return
+  const cudaError_t e1 = cudaStreamSynchronize(ctx->st_h2d), e2 = cudaStreamSynchronize(ctx->st_d2h);
+  const cudaError_t e3 = cudaStreamSynchronize(ctx->st);
+  if (s != KD_OK) return s;
+  for (cudaError_t e : {e1, e2, e3})
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kd_fine_batched_host");
   return KD_OK;
 }
 
