@@ -1145,11 +1145,12 @@ def run_parareal(args):
 # kernels, from one ncu capture of the warp-transform plan (5, 7) at 1024^2 x 16 slices
 # (one fine step: the 4 stage launches of each kernel), averaged over the stages and
 # scaled by 16 to a 256-slice launch (the traffic grows with the slices); keyed by the
-# kernel's name as the bench reports it and the plan.  A plan without a capture of its
-# current kernels reports null.
+# kernel's name as the bench reports it and its variant (column variant for the column
+# kernel, row variant for the row kernel).  A variant without a capture of its current
+# code reports null.
 FINE_TRAFFIC = {
-    ("fine row kernel", (5, 7)): 16 * (1196.98 + 1375.10 + 1022.11 + 785.55) / 4 * 1e6,
-    ("fine column kernel", (5, 7)): 16 * (484.47 + 484.48 + 484.51 + 484.42) / 4 * 1e6,
+    ("fine row kernel", 7): 16 * (1196.98 + 1375.10 + 1022.11 + 785.55) / 4 * 1e6,
+    ("fine column kernel", 5): 16 * (484.47 + 484.48 + 484.51 + 484.42) / 4 * 1e6,
 }
 
 
@@ -1204,7 +1205,7 @@ def run_fine_step(args):
     achieved = kbytes / (avg_us / 1e6) / 1e9
     stage_ms = (prof_ms[0] + prof_ms[1]) / prof_calls
     stage_bytes = 4 * (cb + rb) * W["steps_per_call"]
-    traffic = FINE_TRAFFIC.get((kname, tuple(plan)))
+    traffic = FINE_TRAFFIC.get((kname, plan[kid]))
 
     # ---- a longer call: the same kernels over 8 steps (the conversions amortised)
     x2 = x_dev.clone()

@@ -236,28 +236,35 @@ __global__ void __launch_bounds__(Col4<N, CB>::BLOCK, 1) col4_kernel(FineArgs a,
 // ------------------------------------------ column kernel, one warp per column
 // Col5: a warp owns one grid column and all three of its components (96 complex values a
 // lane), so u x b is formed in registers: no exchange between warps and the flow is
-// evaluated once per point.  A block of XG warps owns XG adjacent columns (XG = 8: 64-byte
-// runs of a row, one block per SM, the kernel the launch plans use; XG = 4: 32-byte runs,
-// two blocks per SM with independent barriers, measured slower at 1024^2 x 256: 3.88 against
-// 3.32 ms per launch, with 292 bytes of spills and the tables read from L1).  The input rows arrive one component at a time through two staging
-// buffers, loaded two components ahead with 16-byte cp.async; a row of a buffer is XG / 2
-// chunks of 16 bytes (columns 2h, 2h + 1), chunk h stored at h ^ (row bits), which keeps
-// the column reads of a half warp to two rows per bank.  The output of each component
-// goes through a padded staging area (odd pitch: conflict-free column writes) and leaves
-// as 16-byte stores.  With XG = 4 the twiddle and cos / sin tables are read from global
-// memory (L1) instead of shared memory, so that two blocks fit an SM.
-template <int N, int XG_>
+// evaluated once per point.  A group of XG warps owns XG adjacent columns; a block holds GR
+// groups.  XG = 8, GR = 1: 64-byte runs of a row, one block per SM, block barriers.  XG = 4,
+// GR = 2: two groups of four warps in one block, each with its own staging buffers and
+// named barriers, so that one group copies while the other transforms; the tables stay in
+// shared memory.  XG = 4, GR = 1: two blocks per SM with the tables read from global memory
+// (L1), measured slower at 1024^2 x 256 (3.88 against 3.32 ms per launch, 292 bytes of
+// spills).  The input rows arrive one component at a time through two staging buffers,
+// loaded two components ahead with 16-byte cp.async; a row of a buffer is XG / 2 chunks of
+// 16 bytes (columns 2h, 2h + 1), chunk h stored at h ^ (row bits), which keeps the column
+// reads of a half warp to two rows per bank.  The output of each component goes through a
+// padded staging area (odd pitch: conflict-free column writes) and leaves as 16-byte
+// stores.
+template <int N, int XG_, int GR_ = 1>
 struct Col5 {
   static_assert(N == 1024, "warp-owned transforms of 1024 points");
-  static_assert(XG_ == 4 || XG_ == 8, "4 or 8 columns per block");
-  static constexpr int XG = XG_;                // columns per group = warps per block
-  static constexpr int BLOCK = 32 * XG;
+  static_assert((XG_ == 4 || XG_ == 8) && (GR_ == 1 || (GR_ == 2 && XG_ == 4)), "8 x 1 or 4 x 1 / 4 x 2 columns");
+  static constexpr int XG = XG_;                // columns per group = warps per group
+  static constexpr int GR = GR_;                // independent groups per block (own buffers, own barriers)
+  static constexpr int BLOCK = 32 * XG * GR;
   static constexpr int K = N / 3, P = 2 * K + 1;
   static constexpr int OP = XG + 1;             // output staging pitch (complex)
-  static constexpr bool STAB = XG == 8;         // tables in shared memory
-  static constexpr int MINB = 8 / XG;
-  static constexpr size_t smem = ((size_t)XG * kWBuf + 2 * (size_t)P * XG + (size_t)P * OP + (STAB ? N : 0)) *
-                                     sizeof(cx<float>) + (STAB ? (size_t)N * sizeof(float2) : 0);
+  static constexpr bool STAB = XG * GR == 8;    // tables in shared memory (one 8-warp block per SM)
+  static constexpr int MINB = 8 / (XG * GR);
+  // complex per group, rounded up to 16 bytes: every group's staging buffers start on the
+  // 16-byte boundary the cp.async copies into them need
+  static constexpr size_t group_smem = (2 * (size_t)P * XG + (size_t)P * OP + 1) & ~(size_t)1;
+  static_assert((XG * GR * kWBuf) % 2 == 0 && (2 * P * XG) % 2 == 0, "16-byte aligned staging buffers");
+  static constexpr size_t smem = ((size_t)XG * GR * kWBuf + GR * group_smem + (STAB ? N : 0)) * sizeof(cx<float>) +
+                                 (STAB ? (size_t)N * sizeof(float2) : 0);
   static_assert(MINB * (smem + 1024) <= 233472, "blocks fit the shared memory of an SM");
   // complex index of column xi of staged row iy in an input buffer
   __device__ __forceinline__ static int in_at(int iy, int xi) {
@@ -267,17 +274,29 @@ struct Col5 {
   }
 };
 
-template <int N, int XG>
-__global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_kernel(FineArgs a, int step, int stage) {
-  using G = Col5<N, XG>;
-  constexpr int K = G::K, P = G::P, OP = G::OP, GPF = N / XG, H = XG / 2;
+// The barrier of a group: the whole block when it is one group, else a named barrier of
+// the group's warps (ids 1 and 2), so that the groups run out of step with each other.
+template <int GR>
+__device__ __forceinline__ void group_bar(int grp, int threads) {
+  if constexpr (GR == 1)
+    __syncthreads();
+  else
+    named_bar(1 + grp, threads);
+}
+
+template <int N, int XG, int GR>
+__global__ void __launch_bounds__(Col5<N, XG, GR>::BLOCK, Col5<N, XG, GR>::MINB)
+    col5_kernel(FineArgs a, int step, int stage) {
+  using G = Col5<N, XG, GR>;
+  constexpr int K = G::K, P = G::P, OP = G::OP, GPF = N / XG, H = XG / 2, GT = 32 * XG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* Tb = (cx<float>*)smem_raw;             // [XG][kWBuf] transpose buffers
-  cx<float>* In = Tb + XG * kWBuf;                  // [2][P][XG] staged input rows (swizzled chunks)
-  cx<float>* Out = In + 2 * P * XG;                 // [P][OP] output staging
-  cx<float>* s_tw = Out + P * OP;                   // [32][32] twiddles (STAB)
-  float2* s_cs = (float2*)(s_tw + N);               // (cos, sin)(2 pi j / N) (STAB)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp / XG, wl = warp - grp * XG, gtid = threadIdx.x - grp * GT;
+  cx<float>* Tb = (cx<float>*)smem_raw;                        // [XG GR][kWBuf] transpose buffers
+  cx<float>* In = Tb + XG * GR * kWBuf + grp * G::group_smem;  // [2][P][XG] staged input rows (swizzled chunks)
+  cx<float>* Out = In + 2 * P * XG;                            // [P][OP] output staging
+  cx<float>* s_tw = Tb + XG * GR * kWBuf + GR * G::group_smem; // [32][32] twiddles (STAB)
+  float2* s_cs = (float2*)(s_tw + N);                          // (cos, sin)(2 pi j / N) (STAB)
   cx<float>* S = Tb + warp * kWBuf;
   const cx<float>* g_tw = (const cx<float>*)a.tw;
   const float* g_cos = (const float*)a.cosg;
@@ -286,6 +305,7 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
     wfft_table(s_tw, g_tw);
     for (int i = threadIdx.x; i < N; i += blockDim.x) s_cs[i] = make_float2(g_cos[i], g_sin[i]);
   }
+  if constexpr (GR > 1) __syncthreads();   // the tables, before the groups part ways
   auto twf = [&](int q) {
     if constexpr (G::STAB) {
       return s_tw[q * 32 + lane];
@@ -296,19 +316,20 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
   };
   auto csf = [&](int j) { return G::STAB ? s_cs[j] : make_float2(__ldg(&g_cos[j]), __ldg(&g_sin[j])); };
   const long groups = (long)a.batch * GPF;
-  const long mine = groups > (long)blockIdx.x ? (groups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long first = (long)blockIdx.x * GR + grp, stride = (long)gridDim.x * GR;
+  const long mine = groups > first ? (groups - 1 - first) / stride + 1 : 0;
   const cx<float>* M = (const cx<float>*)a.M;
   cx<float>* W = (cx<float>*)a.W;
-  // load k of this block: component k % 3 of its group k / 3 into buffer k % 2
+  // load k of this group: component k % 3 of its column group k / 3 into buffer k % 2
   auto load = [&](long k) {
     if (k < 3 * mine) {
-      const long g = blockIdx.x + (k / 3) * (long)gridDim.x;
+      const long g = first + (k / 3) * stride;
       const int c = (int)(k % 3);
       const long b = g / GPF;
       const int x0 = (int)(g - b * GPF) * XG;
       const cx<float>* src = M + ((b * 3 + c) * (long)P) * N + x0;
       cx<float>* dst = In + (k & 1) * P * XG;
-      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+      for (int i = gtid; i < P * H; i += GT) {
         const int h = i & (H - 1), iy = i / H;
         cp_async16(dst + G::in_at(iy, 2 * h), src + (long)iy * N + 2 * h, true);
       }
@@ -319,10 +340,10 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
   load(0);
   load(1);
   for (long j = 0; j < mine; ++j) {
-    const long g = blockIdx.x + j * (long)gridDim.x;
+    const long g = first + j * stride;
     const long b = g / GPF;
     const int x0 = (int)(g - b * GPF) * XG;
-    const int x = x0 + warp;
+    const int x = x0 + wl;
     const Phase<float> ph = load_phase<float>(a, b, step, stage);
     const float A = flow_amp<float>(a, b);
     cx<float> v0[32], v1[32], v2[32];
@@ -330,7 +351,7 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
     auto fetch = [&](cx<float>(&v)[32], int c) {
       const long k = 3 * j + c;
       cp_async_wait_group1();
-      __syncthreads();   // load k visible to the block (and, first time, the tables)
+      group_bar<GR>(grp, GT);   // load k visible to the group (and, first time, the tables)
       const cx<float>* buf = In + (k & 1) * P * XG;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
@@ -339,9 +360,9 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
         if (wfft_never_kept<N>(q))
           v[q] = mk(0.f, 0.f);
         else
-          v[q] = (ky >= -K && ky <= K) ? buf[G::in_at(ky + K, warp)] : mk(0.f, 0.f);
+          v[q] = (ky >= -K && ky <= K) ? buf[G::in_at(ky + K, wl)] : mk(0.f, 0.f);
       }
-      __syncthreads();   // the buffer is read: it takes load k + 2
+      group_bar<GR>(grp, GT);   // the buffer is read: it takes load k + 2
       load(k + 2);
       wfft1024<+1>(v, lane, S, twf);               // ky -> y: v[p] = b_c(x, y = lane + 32 p)
     };
@@ -367,17 +388,17 @@ __global__ void __launch_bounds__(Col5<N, XG>::BLOCK, Col5<N, XG>::MINB) col5_ke
     // component c: forward FFT in y -> kept ky rows -> staging -> W
     auto emit = [&](cx<float>(&v)[32], int c) {
       wfft1024<-1>(v, lane, S, twf);               // y -> ky: v[p] = w_c(x, yy = lane + 32 p)
-      __syncthreads();   // the staging area is free (previous component stored)
+      group_bar<GR>(grp, GT);   // the staging area is free (previous component stored)
 #pragma unroll
       for (int p = 0; p < 32; ++p) {
         if (wfft_never_kept<N>(p)) continue;
         const int yy = lane + 32 * p;
         const int ky = yy < N / 2 ? yy : yy - N;
-        if (ky >= -K && ky <= K) Out[(ky + K) * OP + warp] = v[p];
+        if (ky >= -K && ky <= K) Out[(ky + K) * OP + wl] = v[p];
       }
-      __syncthreads();
+      group_bar<GR>(grp, GT);
       cx<float>* dst = W + ((b * 3 + c) * (long)P) * N + x0;
-      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+      for (int i = gtid; i < P * H; i += GT) {
         const int h = i & (H - 1), row = i / H;
         const cx<float> e0 = Out[row * OP + 2 * h], e1 = Out[row * OP + 2 * h + 1];
         *(float4*)(dst + (long)row * N + 2 * h) = make_float4(e0.x, e0.y, e1.x, e1.y);

@@ -18,7 +18,8 @@
 //                     7, 8 = 8 values per thread, staged | registers (n = 512)
 //   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), one warp per component,
 //                     4 columns per block; 5 = warp-owned transforms, one warp per column,
-//                     8 columns per block
+//                     8 columns per block; 6 = the same with two independent groups of
+//                     4 columns per block
 //             row:    7 = warp-owned transforms, one row per block
 #pragma once
 #include "kd_fine2c.cuh"
@@ -251,16 +252,16 @@ struct Fine3Set {
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr bool W4 = WIDE && N == 1024;
-  static constexpr int kW4Col = 4, kW5Col = 5, kW4Row = kRow4Variant;
+  static constexpr int kW4Col = 4, kW5Col = 5, kW6Col = 6, kW4Row = kRow4Variant;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
-  static int ncol() { return WIDE ? (R8 ? 5 : (W4 ? 6 : 4)) : 1; }
+  static int ncol() { return WIDE ? (R8 ? 5 : (W4 ? 7 : 4)) : 1; }
   // plan of a context that is not autotuned: the warp-transform kernels where they exist
   static FinePlan default_plan() {
     FinePlan p;
     if (W4) {
-      p.col = kW5Col;
+      p.col = kW6Col;
       p.row = kW4Row;
     }
     return p;
@@ -272,8 +273,11 @@ struct Fine3Set {
       if ((e = cudaFuncSetAttribute(col4_kernel<N, kCol4Copy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Col4<N, kCol4Copy>::smem)) != cudaSuccess)
         return e;
-      if ((e = cudaFuncSetAttribute(col5_kernel<N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)Col5<N, 8>::smem)) != cudaSuccess)
+      if ((e = cudaFuncSetAttribute(col5_kernel<N, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col5<N, 8, 1>::smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(col5_kernel<N, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col5<N, 4, 2>::smem)) != cudaSuccess)
         return e;
       if ((e = prepare_row4<N, 0>()) != cudaSuccess) return e;
       if ((e = prepare_row4<N, 1>()) != cudaSuccess) return e;
@@ -318,9 +322,15 @@ struct Fine3Set {
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
     if constexpr (W4) {
       if (v == kW5Col) {
-        using C5 = Col5<N, 8>;
-        launch_k(col5_kernel<N, 8>, persistent_grid((long)a.batch * (N / C5::XG)), C5::BLOCK, C5::smem, st, pdl, a,
-                 s, j);
+        using C5 = Col5<N, 8, 1>;
+        launch_k(col5_kernel<N, 8, 1>, persistent_grid((long)a.batch * (N / C5::XG)), C5::BLOCK, C5::smem, st, pdl,
+                 a, s, j);
+        return;
+      }
+      if (v == kW6Col) {
+        using C6 = Col5<N, 4, 2>;
+        const long groups = (long)a.batch * (N / C6::XG);
+        launch_k(col5_kernel<N, 4, 2>, persistent_grid((groups + 1) / 2), C6::BLOCK, C6::smem, st, pdl, a, s, j);
         return;
       }
       if (v == kW4Col) {

@@ -120,7 +120,7 @@ def test_state_in_the_callers_layout_at_1024(kd, nsteps):
     t0 = [0.4, 77.0]
     ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64))
     try:
-        assert tuple(kd.kd_get_plan(ctx, kd.KD_GRID_FINE)) == (5, 7)
+        assert tuple(kd.kd_get_plan(ctx, kd.KD_GRID_FINE)) == (6, 7)
         x = torch.tensor(b, dtype=torch.complex64, device="cuda")
         y = torch.full_like(x, float("nan"))
         tt = torch.tensor(t0, dtype=torch.float64, device="cuda")
