@@ -115,6 +115,7 @@ static bool variants_T(int n, int* ncol, int* nrow) {
 
 FinePlan fine_default_plan(int n, int prec) {
   if (fine_fft_grid(n) == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
+  if (fine_fft_grid(n) == 512 && prec == 0) return fine3_default_plan<float, 512>();
   return FinePlan();
 }
 

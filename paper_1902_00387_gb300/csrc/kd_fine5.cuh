@@ -1,0 +1,343 @@
+// Fine-step kernels for n = 512 on a warp-owned 512-point FFT (512 = 32 x 16), complex64.
+//
+// A 512-point transform of one field component of one grid column (column kernel) or one
+// ky row (row kernel) belongs to one warp, 16 values a lane, in one of two layouts:
+//   layout A: lane a holds x[a + 32 k], k < 16 (the spectral side: ky or kx)
+//   layout B: lane l holds x[(l & 15) + 16 p + 256 (l >> 4)], p < 16 (the physical side)
+// w512_a_to_b (n = a + 32 k, m = m1 + 16 m2): a 16-point DFT over k inside the lane, the
+// twiddle w_512^(a m1), a transpose through a shared buffer private to the warp after which
+// lane l = m1 + 16 e holds the odd (e = 1) or even (e = 0) a of row m1, a 16-point DFT over
+// those, and the last radix-2 step of the 32-point DFT over a between lanes l and l ^ 16
+// (one shuffle a value).  w512_b_to_a is the same sequence backwards.  Both compute
+// X[m] = sum_n x[n] exp(DIR 2 pi i n m / 512) without normalisation.  The column pass
+// takes ky in layout A to y in layout B and back; the row pass x in layout B to kx in
+// layout A and back, so nothing is re-ordered between the transforms and the pointwise
+// steps.  The kernels follow the 1024-point ones (kd_fine4.cuh): a column kernel with one
+// warp per column and all three components in registers (u x b formed in registers), a
+// row kernel with one warp per component of a row (the curl exchanged in shared memory).
+#pragma once
+#include "kd_fine4.cuh"
+
+namespace kd {
+
+constexpr int kW5Pitch = 18;              // complex per row of a warp's transpose buffer
+constexpr int kW5Buf = 32 * kW5Pitch;     // 16-byte row starts; conflict-free 16-byte row
+                                          // stores and 8-byte column accesses of a half warp
+
+// Twiddle table of the 512-point warp transforms in shared memory:
+// s_tw[m1 * 32 + a] = w_512^(a m1) (m1 < 16), so that w_32^p = w_512^(16 p) = s_tw[p * 32 + 16].
+__device__ __forceinline__ void w512_table(cx<float>* s_tw, const cx<float>* tw) {
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) s_tw[i] = tw[((i & 31) * (i >> 5)) & 511];
+}
+
+template <int DIR>
+__device__ __forceinline__ cx<float> w512_apply(cx<float> v, cx<float> w) {
+  return cmul(v, DIR < 0 ? w : conjf2(w));
+}
+
+// layout A -> layout B; tw: s_tw of w512_table
+template <int DIR>
+__device__ __forceinline__ void w512_a_to_b(cx<float> (&v)[16], int lane, cx<float>* S, const cx<float>* tw) {
+  dft_dif<float, 16, DIR>(v);                      // Y[m1] at v[bitrev(m1)]
+#pragma unroll
+  for (int m1 = 0; m1 < 16; m1 += 2) {
+    cx<float> y0 = v[bitrev<16>(m1)], y1 = v[bitrev<16>(m1 + 1)];
+    if (m1 != 0) y0 = w512_apply<DIR>(y0, tw[m1 * 32 + lane]);
+    y1 = w512_apply<DIR>(y1, tw[(m1 + 1) * 32 + lane]);
+    *(float4*)&S[lane * kW5Pitch + m1] = make_float4(y0.x, y0.y, y1.x, y1.y);
+  }
+  __syncwarp();
+  const int m1 = lane & 15, e = lane >> 4;
+#pragma unroll
+  for (int ap = 0; ap < 16; ++ap) v[ap] = S[(2 * ap + e) * kW5Pitch + m1];
+  __syncwarp();
+  dft_dif<float, 16, DIR>(v);                      // E_e[p] at v[bitrev(p)]
+  cx<float> t[16];
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    // lane e = 1 sends w_32^p E_1[p], lane e = 0 sends E_0[p]
+    const cx<float> own = v[bitrev<16>(p)];
+    const cx<float> send = e ? w512_apply<DIR>(own, tw[p * 32 + 16]) : own;
+    const cx<float> recv = mk(__shfl_xor_sync(0xffffffffu, send.x, 16), __shfl_xor_sync(0xffffffffu, send.y, 16));
+    t[p] = e ? recv - send : send + recv;          // X[m1 + 16 p + 256 e]
+  }
+#pragma unroll
+  for (int p = 0; p < 16; ++p) v[p] = t[p];
+}
+
+// layout B -> layout A
+template <int DIR>
+__device__ __forceinline__ void w512_b_to_a(cx<float> (&v)[16], int lane, cx<float>* S, const cx<float>* tw) {
+  const int m1 = lane & 15, e = lane >> 4;
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    // e = 0: z0 + z1;  e = 1: (z0 - z1) w_32^p  (z_h the value of lane m1 + 16 h)
+    const cx<float> own = v[p];
+    const cx<float> par = mk(__shfl_xor_sync(0xffffffffu, own.x, 16), __shfl_xor_sync(0xffffffffu, own.y, 16));
+    v[p] = e ? w512_apply<DIR>(par - own, tw[p * 32 + 16]) : own + par;
+  }
+  dft_dif<float, 16, DIR>(v);                      // V[a'] at v[bitrev(a')], a = 2 a' + e
+#pragma unroll
+  for (int ap = 0; ap < 16; ++ap) S[(2 * ap + e) * kW5Pitch + m1] = v[bitrev<16>(ap)];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 16; q += 2) {
+    const float4 r = *(const float4*)&S[lane * kW5Pitch + q];
+    cx<float> y0 = mk(r.x, r.y), y1 = mk(r.z, r.w);
+    if (q != 0) y0 = w512_apply<DIR>(y0, tw[q * 32 + lane]);
+    y1 = w512_apply<DIR>(y1, tw[(q + 1) * 32 + lane]);
+    v[q] = y0;
+    v[q + 1] = y1;
+  }
+  __syncwarp();
+  dft_dif<float, 16, DIR>(v);                      // Z[a + 32 k] at v[bitrev(k)]
+  cx<float> t[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[k] = v[bitrev<16>(k)];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
+// physical index (y or x) of register p of `lane` in layout B
+__device__ __forceinline__ int w512_phys(int lane, int p) { return (lane & 15) + 16 * p + 256 * (lane >> 4); }
+
+// ------------------------------------------------------------------ column kernel
+// One warp per grid column with all three components; XG = 8 adjacent columns per block
+// (64-byte runs of a row), input rows staged two components ahead with 16-byte cp.async,
+// output through a padded staging area; two blocks per SM.
+template <int N>
+struct Col512 {
+  static_assert(N == 512, "warp-owned transforms of 512 points");
+  static constexpr int XG = 8, BLOCK = 32 * XG, MINB = 2;
+  static constexpr int K = N / 3, P = 2 * K + 1;
+  static constexpr int OP = XG + 1;
+  static constexpr size_t smem =
+      ((size_t)XG * kW5Buf + 2 * (size_t)P * XG + (((size_t)P * OP + 1) & ~(size_t)1) + N) * sizeof(cx<float>) +
+      (size_t)N * sizeof(float2);
+  static_assert(MINB * (smem + 1024) <= 233472, "blocks fit the shared memory of an SM");
+  __device__ __forceinline__ static int in_at(int iy, int xi) {
+    return iy * XG + ((((xi >> 1) ^ (iy >> 1)) & 3) << 1) + (xi & 1);
+  }
+};
+
+template <int N>
+__global__ void __launch_bounds__(Col512<N>::BLOCK, Col512<N>::MINB) col512_kernel(FineArgs a, int step, int stage) {
+  using G = Col512<N>;
+  constexpr int K = G::K, P = G::P, OP = G::OP, XG = G::XG, GPF = N / XG, H = XG / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* Tb = (cx<float>*)smem_raw;             // [XG][kW5Buf]
+  cx<float>* In = Tb + XG * kW5Buf;                 // [2][P][XG]
+  cx<float>* Out = In + 2 * P * XG;                 // [P][OP]
+  cx<float>* s_tw = Out + ((P * OP + 1) & ~1);      // [16][32]
+  float2* s_cs = (float2*)(s_tw + N);               // (cos, sin)(2 pi j / N)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cx<float>* S = Tb + warp * kW5Buf;
+  w512_table(s_tw, (const cx<float>*)a.tw);
+  {
+    const float* g_cos = (const float*)a.cosg;
+    const float* g_sin = (const float*)a.sing;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s_cs[i] = make_float2(g_cos[i], g_sin[i]);
+  }
+  const long groups = (long)a.batch * GPF;
+  const long mine = groups > (long)blockIdx.x ? (groups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const cx<float>* M = (const cx<float>*)a.M;
+  cx<float>* W = (cx<float>*)a.W;
+  auto load = [&](long k) {
+    if (k < 3 * mine) {
+      const long g = blockIdx.x + (k / 3) * (long)gridDim.x;
+      const int c = (int)(k % 3);
+      const long b = g / GPF;
+      const int x0 = (int)(g - b * GPF) * XG;
+      const cx<float>* src = M + ((b * 3 + c) * (long)P) * N + x0;
+      cx<float>* dst = In + (k & 1) * P * XG;
+      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+        const int h = i & (H - 1), iy = i / H;
+        cp_async16(dst + G::in_at(iy, 2 * h), src + (long)iy * N + 2 * h, true);
+      }
+    }
+    cp_async_commit();
+  };
+  griddep_wait();    // M is the predecessor's output
+  load(0);
+  load(1);
+  for (long j = 0; j < mine; ++j) {
+    const long g = blockIdx.x + j * (long)gridDim.x;
+    const long b = g / GPF;
+    const int x0 = (int)(g - b * GPF) * XG;
+    const int x = x0 + warp;
+    const Phase<float> ph = load_phase<float>(a, b, step, stage);
+    const float A = flow_amp<float>(a, b);
+    cx<float> v0[16], v1[16], v2[16];
+    auto fetch = [&](cx<float>(&v)[16], int c) {
+      const long k = 3 * j + c;
+      cp_async_wait_group1();
+      __syncthreads();   // load k visible to the block (and, first time, the tables)
+      const cx<float>* buf = In + (k & 1) * P * XG;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int yy = lane + 32 * q;
+        const int ky = yy < N / 2 ? yy : yy - N;
+        if (wfft_never_kept<N>(q))
+          v[q] = mk(0.f, 0.f);
+        else
+          v[q] = (ky >= -K && ky <= K) ? buf[G::in_at(ky + K, warp)] : mk(0.f, 0.f);
+      }
+      __syncthreads();   // the buffer is read: it takes load k + 2
+      load(k + 2);
+      w512_a_to_b<+1>(v, lane, S, s_tw);          // ky -> y (layout B)
+    };
+    fetch(v0, 0);
+    fetch(v1, 1);
+    fetch(v2, 2);
+    {
+      const float2 csx = s_cs[x];
+      const float uy = A * (csx.y * ph.cpx + csx.x * ph.spx);
+      const float uzx = csx.x * ph.cpx - csx.y * ph.spx;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const float2 csy = s_cs[w512_phys(lane, p)];
+        const float ux = A * (csy.x * ph.cpy - csy.y * ph.spy);
+        const float uz = A * (uzx + (csy.y * ph.cpy + csy.x * ph.spy));
+        const cx<float> bx = v0[p], by = v1[p], bz = v2[p];
+        v0[p] = bz * uy - by * uz;
+        v1[p] = bx * uz - bz * ux;
+        v2[p] = by * ux - bx * uy;
+      }
+    }
+    auto emit = [&](cx<float>(&v)[16], int c) {
+      w512_b_to_a<-1>(v, lane, S, s_tw);          // y -> ky (layout A)
+      __syncthreads();   // the staging area is free
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        if (wfft_never_kept<N>(p)) continue;
+        const int yy = lane + 32 * p;
+        const int ky = yy < N / 2 ? yy : yy - N;
+        if (ky >= -K && ky <= K) Out[(ky + K) * OP + warp] = v[p];
+      }
+      __syncthreads();
+      cx<float>* dst = W + ((b * 3 + c) * (long)P) * N + x0;
+      for (int i = threadIdx.x; i < P * H; i += G::BLOCK) {
+        const int h = i & (H - 1), row = i / H;
+        const cx<float> e0 = Out[row * OP + 2 * h], e1 = Out[row * OP + 2 * h + 1];
+        *(float4*)(dst + (long)row * N + 2 * h) = make_float4(e0.x, e0.y, e1.x, e1.y);
+      }
+    };
+    emit(v0, 0);
+    emit(v1, 1);
+    emit(v2, 2);
+  }
+  cp_async_wait_all();
+}
+
+// --------------------------------------------------------------------- row kernel
+// Slots of a lane's kept kx registers at n = 512: p <= 5 and p >= 10.
+constexpr int kRow512Slots = 12;
+__host__ __device__ constexpr int row512_slot(int p) { return p <= 5 ? p : p - 4; }
+
+template <int N, int MODE>
+struct Row512 {
+  static_assert(N == 512, "warp-owned transforms of 512 points");
+  static constexpr int WARPS = 3, BLOCK = 96;
+  static constexpr int K = N / 3, P = 2 * K + 1;
+  static constexpr int NPRE = row4_reads(MODE);
+  static constexpr int WSMEM = kW5Buf + NPRE * kRow512Slots * 32;
+  static constexpr size_t smem = ((size_t)WARPS * WSMEM + N) * sizeof(cx<float>);
+  static constexpr int MINB = (int)(233472 / (smem + 1024)) > 8 ? 8 : (int)(233472 / (smem + 1024));
+  static_assert(wfft_never_kept<N>(6) && wfft_never_kept<N>(9) && !wfft_never_kept<N>(5) && !wfft_never_kept<N>(10),
+                "kept registers are p <= 5 and p >= 10");
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Row512<N, MODE>::BLOCK, Row512<N, MODE>::MINB) row512_kernel(FineArgs a, int store_m) {
+  using G = Row512<N, MODE>;
+  constexpr int K = G::K, P = G::P, NPRE = G::NPRE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp, c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+  cx<float>* Tb = (cx<float>*)smem_raw;             // [3][WSMEM]
+  cx<float>* s_tw = Tb + G::WARPS * G::WSMEM;       // [16][32]
+  cx<float>* S = Tb + warp * G::WSMEM;
+  cx<float>* Q = S + kW5Buf;                        // [NPRE][slot][lane]
+  w512_table(s_tw, (const cx<float>*)a.tw);
+  __syncthreads();
+  const StageArrays<float> sa = stage_arrays<float>(a);
+  const cx<float>* src[3] = {MODE == 0 ? sa.X : (MODE == 1 ? sa.R2 : (MODE == 2 ? sa.R3 : sa.R4)),
+                             MODE == 1 ? sa.R3 : (MODE == 2 ? sa.R4 : sa.X), MODE == 1 ? sa.R4 : sa.Xlo};
+  const int npre = MODE == 3 && !sa.lo_valid ? 2 : NPRE;
+  const long rows = (long)a.batch * P;
+  griddep_wait();    // W (and the stage arrays) come from the predecessors
+  for (long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const long b = row / P;
+    const int iy = (int)(row - b * P);
+    const long sbase = ((b * 3 + c) * P + iy) * (long)P + K;   // compact index of kx = 0
+    cx<float> v[16];
+    if (MODE == 4) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int xx = lane + 32 * k;
+        const int kx = xx < N / 2 ? xx : xx - N;
+        v[k] = !wfft_never_kept<N>(k) && kx >= -K && kx <= K ? sa.X[sbase + kx] : mk(0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NPRE; ++j)
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          if (wfft_never_kept<N>(p) || j >= npre) continue;
+          const int xx = lane + 32 * p;
+          const int kx = xx < N / 2 ? xx : xx - N;
+          if (kx >= -K && kx <= K) cp_async8(Q + (j * kRow512Slots + row512_slot(p)) * 32 + lane, src[j] + sbase + kx);
+        }
+      cp_async_commit();
+      const cx<float>* Wr = (const cx<float>*)a.W + ((b * 3 + c) * P + iy) * (long)N;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) v[p] = Wr[w512_phys(lane, p)];
+      w512_b_to_a<-1>(v, lane, S, s_tw);          // x -> kx: v[k] = n^2 w_hat_c(kx index lane + 32 k)
+#pragma unroll
+      for (int p = 0; p < 16; p += 2)
+        *(float4*)&S[lane * kW5Pitch + p] = make_float4(v[p].x, v[p].y, v[p + 1].x, v[p + 1].y);
+      __syncthreads();                             // the row's three components are in place
+      cp_async_wait_all();
+      const StageCoef<float> sc = stage_coef<float>(a, b);
+      const float inv_n2 = 1.f / ((float)N * (float)N);
+      const float fky = (float)(iy - K);
+      const float lam_y = (fky * fky + sc.kz * sc.kz);
+      const cx<float>* S1 = Tb + c1 * G::WSMEM;
+      const cx<float>* S2 = Tb + c2 * G::WSMEM;
+#pragma unroll
+      for (int p = 0; p < 16; p += 2) {
+        const float4 e1 = *(const float4*)&S1[lane * kW5Pitch + p], e2 = *(const float4*)&S2[lane * kW5Pitch + p];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pp = p + h;
+          const int xx = lane + 32 * pp;
+          const int kx = xx < N / 2 ? xx : xx - N;
+          if (wfft_never_kept<N>(pp) || kx < -K || kx > K) {
+            v[pp] = mk(0.f, 0.f);
+          } else {
+            const float fkx = (float)kx;
+            const float k1 = (c == 0 ? fky : (c == 1 ? sc.kz : fkx)) * inv_n2;
+            const float k2 = (c == 0 ? sc.kz : (c == 1 ? fkx : fky)) * inv_n2;
+            const cx<float> w1 = h ? mk(e1.z, e1.w) : mk(e1.x, e1.y), w2 = h ? mk(e2.z, e2.w) : mk(e2.x, e2.y);
+            const cx<float> f = mul_i(w2 * k1 - w1 * k2);
+            const float lam = (fkx * fkx + lam_y) * sc.inv_rm;
+            const float g = implicit_gain(sc.dt * 0.5f * lam);
+            cx<float> r[3];
+#pragma unroll
+            for (int j = 0; j < NPRE; ++j)
+              r[j] = j < npre ? Q[(j * kRow512Slots + row512_slot(pp)) * 32 + lane] : mk(0.f, 0.f);
+            v[pp] = stage_update_1<MODE>(sc, sa, sbase + kx, g, sc.dt * lam, r, f, nullptr);
+          }
+        }
+      }
+      __syncthreads();                             // the exchange is read before S is rewritten
+      if (!store_m) continue;                      // uniform over the grid
+    }
+    w512_a_to_b<+1>(v, lane, S, s_tw);            // kx -> x (layout B)
+    cx<float>* Mr = (cx<float>*)a.M + ((b * 3 + c) * P + iy) * (long)N;
+#pragma unroll
+    for (int p = 0; p < 16; ++p) Mr[w512_phys(lane, p)] = v[p];
+  }
+}
+
+}  // namespace kd

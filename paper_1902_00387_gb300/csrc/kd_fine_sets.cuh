@@ -11,11 +11,14 @@
 //                     6, 7 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
 //   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
 //                     2 = persistent prefetching kernel; 3 = component-split kernel;
-//                     4 = 8 values per thread (n = 512)
+//                     4 = 8 values per thread (n = 512); 5 = 512-point warp transforms,
+//                     one warp per column (kd_fine5.cuh; n = 512)
 //             row:    0..3 = three-pass, 16 values, (RT0 | RT0/2) x (staged | registers);
 //                     4 = persistent prefetching kernel (in registers);
 //                     5, 6 = component-split kernels with RT0 | RT0/2 rows per block;
-//                     7, 8 = 8 values per thread, staged | registers (n = 512)
+//                     7, 8 = 8 values per thread, staged | registers (n = 512);
+//                     9 = 512-point warp transforms, one warp per component of a row
+//                     (kd_fine5.cuh; n = 512)
 //   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), one warp per component,
 //                     4 columns per block; 5 = warp-owned transforms, one warp per column,
 //                     8 columns per block; 6 = the same with two independent groups of
@@ -27,6 +30,7 @@
 #include "kd_fine3c.cuh"
 #include "kd_fine2f.cuh"
 #include "kd_fine4.cuh"
+#include "kd_fine5.cuh"
 
 namespace kd {
 
@@ -246,6 +250,29 @@ static cudaError_t prepare_row4() {
                               (int)G::smem);
 }
 
+// Warp-transform kernels of the n = 512 complex64 grid (kd_fine5.cuh).
+template <int N>
+static void launch_col512(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = Col512<N>;
+  const long groups = (long)a.batch * (N / C::XG);
+  const long cap = (long)persistent_grid(1L << 30) * C::MINB;
+  launch_k(col512_kernel<N>, (unsigned)(groups < cap ? groups : cap), C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <int N, int MODE>
+static void launch_row512(const FineArgs& a, int store, cudaStream_t st, bool pdl) {
+  using G = Row512<N, MODE>;
+  const long rows = (long)a.batch * a.P;
+  const long cap = (long)persistent_grid(1L << 30) * G::MINB;
+  launch_k(row512_kernel<N, MODE>, (unsigned)(rows < cap ? rows : cap), G::BLOCK, G::smem, st, pdl, a, store);
+}
+
+template <int N, int MODE>
+static cudaError_t prepare_row512() {
+  return cudaFuncSetAttribute(row512_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Row512<N, MODE>::smem);
+}
+
 template <typename T, int N>
 struct Fine3Set {
   using Sh = Shapes3<T, N>;
@@ -253,22 +280,37 @@ struct Fine3Set {
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr bool W4 = WIDE && N == 1024;
   static constexpr int kW4Col = 4, kW5Col = 5, kW6Col = 6, kW4Row = kRow4Variant;
+  // n = 512: column variant 5 and row variant 9 are the 512-point warp-transform kernels
+  static constexpr int kC512Col = 5, kC512Row = 9;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
-  static int ncol() { return WIDE ? (R8 ? 5 : (W4 ? 7 : 4)) : 1; }
+  static int ncol() { return WIDE ? (R8 ? 6 : (W4 ? 7 : 4)) : 1; }
   // plan of a context that is not autotuned: the warp-transform kernels where they exist
   static FinePlan default_plan() {
     FinePlan p;
     if (W4) {
       p.col = kW6Col;
       p.row = kW4Row;
+    } else if (R8) {
+      p.col = kC512Col;
+      p.row = kC512Row;
     }
     return p;
   }
-  static int nrow() { return WIDE ? (R8 ? 9 : (W4 ? 8 : 7)) : 1; }
+  static int nrow() { return WIDE ? (R8 ? 10 : (W4 ? 8 : 7)) : 1; }
   static cudaError_t prepare() {
     cudaError_t e;
+    if constexpr (R8) {
+      if ((e = cudaFuncSetAttribute(col512_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Col512<N>::smem)) != cudaSuccess)
+        return e;
+      if ((e = prepare_row512<N, 0>()) != cudaSuccess) return e;
+      if ((e = prepare_row512<N, 1>()) != cudaSuccess) return e;
+      if ((e = prepare_row512<N, 2>()) != cudaSuccess) return e;
+      if ((e = prepare_row512<N, 3>()) != cudaSuccess) return e;
+      if ((e = prepare_row512<N, 4>()) != cudaSuccess) return e;
+    }
     if constexpr (W4) {
       if ((e = cudaFuncSetAttribute(col4_kernel<N, kCol4Copy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Col4<N, kCol4Copy>::smem)) != cudaSuccess)
@@ -345,6 +387,7 @@ struct Fine3Set {
     }
     if constexpr (R8) {
       if (v == 4) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
+      if (v == kC512Col) return launch_col512<N>(a, s, j, st, pdl);
     }
     if (WIDE && v == 2) {
       using C = Col3P<T, N, Sh::XT0>;
@@ -378,6 +421,15 @@ struct Fine3Set {
     if constexpr (R8) {
       if (v == 7) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
       if (v == 8) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
+      if (v == kC512Row) {
+        switch (mode) {
+          case 0: return launch_row512<N, 0>(a, store, st, pdl);
+          case 1: return launch_row512<N, 1>(a, store, st, pdl);
+          case 2: return launch_row512<N, 2>(a, store, st, pdl);
+          case 3: return launch_row512<N, 3>(a, store, st, pdl);
+          default: return launch_row512<N, 4>(a, store, st, pdl);
+        }
+      }
     }
     if (v == 4 && mode == 4) v = 0;   // the prologue runs on the tiled kernel
     if (v == 4) {
