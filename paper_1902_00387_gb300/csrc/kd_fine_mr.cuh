@@ -1,6 +1,7 @@
-// Fine-step kernels for grid sides n = 32 R that are not powers of two (R = 3, 5, 6: n = 96,
-// 160, 192; Table 1's N_F = 160 and the refinement 96 / 128 / 160 of Sec. 5.2), on a
-// mixed-radix FFT owned by one warp.
+// Fine-step kernels for grid sides n = 32 R, on a mixed-radix FFT owned by one warp: the
+// only kernels of the sides that are not powers of two (R = 3, 5, 6: n = 96, 160, 192;
+// Table 1's N_F = 160 and the refinement 96 / 128 / 160 of Sec. 5.2), and a launch-plan
+// variant of the sides 32, 64, 128, 256 (R = 1, 2, 4, 8).
 //
 // Transform of N = 32 R points, R values a lane (Cooley-Tukey with factors R and 32):
 //   layout A: lane a holds x[a + 32 k], register k < R
@@ -17,6 +18,7 @@
 // or row live in one warp's registers (3 R complex values a lane), so u x b and the curl
 // need no exchange; a warp barrier is never needed (shuffles only).
 #pragma once
+#include "kd_fft2.cuh"
 #include "kd_fine.h"
 #include "kd_stage.cuh"
 
@@ -69,9 +71,21 @@ __device__ __forceinline__ double mr_sin<6>(int m) {
   }
 }
 
-// In-lane R-point DFT, X[k] = sum_j x[j] exp(DIR 2 pi i j k / R) (direct; R <= 6).
+// In-lane R-point DFT, X[k] = sum_j x[j] exp(DIR 2 pi i j k / R): radix 2 for R = 1, 2,
+// 4, 8 (the sides 32, 64, 128, 256), direct for R = 3, 5, 6.
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void mr_dft(cx<T> (&v)[R]) {
+  if constexpr (R == 1) {
+    return;
+  } else if constexpr ((R & (R - 1)) == 0) {
+    dft_dif<T, R, DIR>(v);                         // X[k] at v[bitrev(k)]
+    cx<T> t[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) t[k] = v[bitrev<R>(k)];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = t[k];
+    return;
+  }
   cx<T> out[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) {

@@ -2,13 +2,15 @@
 // step loop (kd_fine.h: fine_run).  Included by the instantiation units kd_fine2_*.cu
 // and kd_fine3_*.cu.
 //
-// complex64 variants (complex128 has variant 0 only):
+// complex64 variants (complex128 has variant 0, and the mixed-radix variant at n >= 32):
 //   n <= 256  column: 0, 1 = four-step kernels with XT0, XT0/2 columns per block;
 //                     2 = component-split four-step kernel (one component per thread);
 //                     3 = three-pass kernel with 8 values per thread (n = 128, 256)
 //             row:    0..3 = four-step kernels, (RT0 | RT0/2 rows) x (staged | registers);
 //                     4, 5 = component-split kernels with 8 | 4 rows per block;
 //                     6, 7 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
+//             both:   the last variant = the warp-owned mixed-radix kernels of kd_fine_mr.cuh
+//                     (one warp per column / row with its three components; n = 32 .. 256)
 //   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
 //                     2 = persistent prefetching kernel; 3 = component-split kernel;
 //                     4 = 8 values per thread (n = 512); 5 = 512-point warp transforms,
@@ -31,6 +33,7 @@
 #include "kd_fine2f.cuh"
 #include "kd_fine4.cuh"
 #include "kd_fine5.cuh"
+#include "kd_fine_mr.cuh"
 
 namespace kd {
 
@@ -51,6 +54,38 @@ static void launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t 
   cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, k, args...);
 }
+
+// The warp-owned mixed-radix kernels (kd_fine_mr.cuh) of the side 32 R as a launch plan
+// (no shared memory to set up).
+template <typename T, int R>
+struct FineMrSet {
+  static constexpr int N = 32 * R;
+  static constexpr bool FUSED = false;
+  static constexpr int kFusedCol = -1;
+  static constexpr unsigned BLOCK = 32 * kMrWarps;
+  static int ncol() { return 1; }
+  static int nrow() { return 1; }
+  static unsigned blocks(long warps) { return (unsigned)((warps + kMrWarps - 1) / kMrWarps); }
+  static void col(int, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    launch_k(colmr_kernel<T, R>, blocks((long)a.batch * N), BLOCK, 0, st, pdl, a, s, j);
+  }
+  template <int SCH, int MODE>
+  static void row_k(const FineArgs& a, int store, cudaStream_t st, bool pdl) {
+    launch_k(rowmr_kernel<T, R, SCH, MODE>, blocks((long)a.batch * a.P), BLOCK, 0, st, pdl, a, store);
+  }
+  static void row(int, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+    if (mode == 4) return row_k<SCHEME_RK443, 4>(a, store, st, pdl);   // prologue (scheme-free)
+    if (a.scheme == SCHEME_RK111) return row_k<SCHEME_RK111, 0>(a, store, st, pdl);
+    if (a.scheme == SCHEME_RK222)
+      return mode == 0 ? row_k<SCHEME_RK222, 0>(a, store, st, pdl) : row_k<SCHEME_RK222, 1>(a, store, st, pdl);
+    switch (mode) {
+      case 0: return row_k<SCHEME_RK443, 0>(a, store, st, pdl);
+      case 1: return row_k<SCHEME_RK443, 1>(a, store, st, pdl);
+      case 2: return row_k<SCHEME_RK443, 2>(a, store, st, pdl);
+      default: return row_k<SCHEME_RK443, 3>(a, store, st, pdl);
+    }
+  }
+};
 
 template <typename T, int N, int XT>
 static cudaError_t prepare_col2() {
@@ -142,8 +177,13 @@ struct Fine2Set {
   // variant does not apply)
   static constexpr bool FUSED = WIDE && N == 128;
   static constexpr int kFusedCol = 4;
-  static int ncol() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
-  static int nrow() { return WIDE ? (R8 ? 8 : 6) : 1; }
+  // the warp-owned mixed-radix kernels (FineMrSet) as the last column / row variant of the
+  // sides 32 R
+  static constexpr bool MR = N % 32 == 0;
+  static int ncol0() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
+  static int nrow0() { return WIDE ? (R8 ? 8 : 6) : 1; }
+  static int ncol() { return ncol0() + (MR ? 1 : 0); }
+  static int nrow() { return nrow0() + (MR ? 1 : 0); }
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
@@ -180,6 +220,9 @@ struct Fine2Set {
     return cudaSuccess;
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+    if constexpr (MR) {
+      if (v == ncol0()) return FineMrSet<T, N / 32>::col(0, a, s, j, st, pdl);
+    }
     if constexpr (WIDE) {
       if (v == 2) return launch_col2c<T, N, ShC::XT>(a, s, j, st, pdl);
     }
@@ -192,6 +235,9 @@ struct Fine2Set {
       launch_col2<T, N, Sh::xt(0)>(a, s, j, st, pdl);
   }
   static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+    if constexpr (MR) {
+      if (v == nrow0()) return FineMrSet<T, N / 32>::row(0, a, mode, store, st, pdl);   // every scheme
+    }
     if (!WIDE) v = 0;
     // the lower-order schemes run on the default row kernel (prologue included)
     if (a.scheme == SCHEME_RK222) return launch_row2<T, N, Sh::rt(0), true, SCHEME_RK222>(a, mode, store, st, pdl);

@@ -210,3 +210,32 @@ def test_table1_roberts_growth_rate_on_the_fft_path(kd):
     assert s == kd.KD_OK, (rate, its)
     assert abs(rate - gamma) < 1e-4, (rate, gamma)
     assert float("%.2g" % rate) == 0.11
+
+
+@pytest.mark.parametrize("n", [32, 64, 128, 256])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_mixed_radix_plan_on_power_of_two_sides(kd, n, prec):
+    """The warp-owned kernels as the last launch-plan variant of the sides 32 R (R = 1, 2,
+    4, 8: the in-lane transform is radix 2, the cross-lane one unchanged), against the
+    oracle, RK443 and RK222."""
+    import torch
+    P = kd.KD_C64 if prec == "c64" else kd.KD_C128
+    kz, Rm, dt = 0.57, 100.0, 5e-3
+    b = I.initial_batch(n, kz, [41, 42, 43])
+    t0 = [0.0, 0.7, 2.4]
+    for sch, tab in ((kd.KD_RK443, O.RK443), (kd.KD_RK222, O.RK222)):
+        ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, P, fine_scheme=sch))
+        try:
+            ncol, nrow = kd.kd_plan_variants(ctx, kd.KD_GRID_FINE)
+            kd.kd_set_plan(ctx, kd.KD_GRID_FINE, ncol - 1, nrow - 1)
+            dtype = torch.complex128 if P == kd.KD_C128 else torch.complex64
+            x = torch.tensor(b, dtype=dtype, device="cuda")
+            y = torch.empty_like(x)
+            kd.kd_fine_batched(ctx, x, y, torch.tensor(t0, dtype=torch.float64, device="cuda"), 3, 3, P)
+            torch.cuda.synchronize()
+            out = y.cpu().numpy().astype(np.complex128)
+        finally:
+            kd.kd_destroy(ctx)
+        p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+        for i in range(3):
+            assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 3, tab=tab)) < (TOL32 if P == kd.KD_C64 else TOL64), i
