@@ -24,8 +24,7 @@
 //   n = 1024  column: 4 = warp-owned transforms (kd_fine4.cuh), one warp per component,
 //                     4 columns per block; 5 = warp-owned transforms, one warp per column,
 //                     8 columns per block; 6 = the same with two independent groups of
-//                     4 columns per block; 7 = a pair of warps per column (kd_fine6.cuh),
-//                     8 columns per block
+//                     4 columns per block
 //             row:    7 = warp-owned transforms, one row per block
 #pragma once
 #include "kd_fine2c.cuh"
@@ -34,7 +33,6 @@
 #include "kd_fine2f.cuh"
 #include "kd_fine4.cuh"
 #include "kd_fine5.cuh"
-#include "kd_fine6.cuh"
 #include "kd_fine_mr.cuh"
 
 namespace kd {
@@ -327,13 +325,13 @@ struct Fine3Set {
   static constexpr bool WIDE = sizeof(T) == 4;
   static constexpr bool R8 = WIDE && N == 512;
   static constexpr bool W4 = WIDE && N == 1024;
-  static constexpr int kW4Col = 4, kW5Col = 5, kW6Col = 6, kW7Col = 7, kW4Row = kRow4Variant;
+  static constexpr int kW4Col = 4, kW5Col = 5, kW6Col = 6, kW4Row = kRow4Variant;
   // n = 512: column variant 5 and row variant 9 are the 512-point warp-transform kernels
   static constexpr int kC512Col = 5, kC512Row = 9;
   static constexpr int XTC = Sh::XT0, RTC0 = Sh::RT0, RTC1 = Sh::RT0 / 2;
   static constexpr bool FUSED = false;   // no persistent fused step at these sizes
   static constexpr int kFusedCol = -1;
-  static int ncol() { return WIDE ? (R8 ? 6 : (W4 ? 8 : 4)) : 1; }
+  static int ncol() { return WIDE ? (R8 ? 6 : (W4 ? 7 : 4)) : 1; }
   // plan of a context that is not autotuned: the warp-transform kernels where they exist
   static FinePlan default_plan() {
     FinePlan p;
@@ -368,9 +366,6 @@ struct Fine3Set {
         return e;
       if ((e = cudaFuncSetAttribute(col5_kernel<N, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Col5<N, 4, 2>::smem)) != cudaSuccess)
-        return e;
-      if ((e = cudaFuncSetAttribute(col7_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)Col7<N>::smem)) != cudaSuccess)
         return e;
       if ((e = prepare_row4<N, 0>()) != cudaSuccess) return e;
       if ((e = prepare_row4<N, 1>()) != cudaSuccess) return e;
@@ -418,12 +413,6 @@ struct Fine3Set {
         using C5 = Col5<N, 8, 1>;
         launch_k(col5_kernel<N, 8, 1>, persistent_grid((long)a.batch * (N / C5::XG)), C5::BLOCK, C5::smem, st, pdl,
                  a, s, j);
-        return;
-      }
-      if (v == kW7Col) {
-        using C7 = Col7<N>;
-        launch_k(col7_kernel<N>, persistent_grid((long)a.batch * (N / C7::XG)), C7::BLOCK, C7::smem, st, pdl, a, s,
-                 j);
         return;
       }
       if (v == kW6Col) {
