@@ -170,6 +170,35 @@ def test_host_buffer_call_equals_device_call(kd, n, chunk, pinned):
         kd.kd_destroy(ctx)
 
 
+def test_host_buffer_call_edge_cases(kd):
+    """No fields is a no-op; zero steps copies the masked input (entries outside the kept
+    square zeroed) through the host-buffer call as through the device call, at 1024^2
+    (the plan that keeps the state in the caller's layout when it steps)."""
+    import torch
+    n = 1024
+    b = I.initial_batch(n, 0.57, [3])
+    b[:, :, n // 2, n // 2] = 1.0                     # an entry outside the kept square
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, 0.57, 1e4, 1e-3, kd.KD_C64))
+    try:
+        x = torch.tensor(b, dtype=torch.complex64)
+        y = torch.full_like(x, float("nan"))
+        t0 = np.zeros(1)
+        kd.kd_fine_batched_host(ctx, x, y, t0, 3, 0)
+        assert torch.isnan(y).all()
+        kd.kd_fine_batched_host(ctx, x, y, t0, 0, 1)
+        xd, yd = x.cuda(), torch.full_like(x, float("nan")).cuda()
+        kd.kd_fine_batched(ctx, xd, yd, torch.zeros(1, dtype=torch.float64, device="cuda"), 0, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(y, yd.cpu())
+    finally:
+        kd.kd_destroy(ctx)
+    k = I.fft_wavenumbers(n)
+    kept = (np.abs(k)[None, :] <= n // 3) & (np.abs(k)[:, None] <= n // 3)
+    out = y.numpy()
+    assert np.all(out[:, :, ~kept] == 0)
+    assert np.array_equal(out[:, :, kept], b.astype(np.complex64)[:, :, kept])
+
+
 @pytest.mark.parametrize("n,nsteps", [(128, 20), (512, 6), (1024, 4)])
 def test_flat_spectrum_edge_ring(kd, n, nsteps):
     """A flat-spectrum solenoidal input puts as much energy on the edge ring of the kept
