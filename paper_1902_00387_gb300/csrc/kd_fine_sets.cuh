@@ -9,8 +9,10 @@
 //             row:    0..3 = four-step kernels, (RT0 | RT0/2 rows) x (staged | registers);
 //                     4, 5 = component-split kernels with 8 | 4 rows per block;
 //                     6, 7 = three-pass, 8 values per thread, staged | registers (n = 128, 256)
-//             both:   the last variant = the warp-owned mixed-radix kernels of kd_fine_mr.cuh
-//                     (one warp per column / row with its three components; n = 32 .. 256)
+//             both:   the next variant = the warp-owned mixed-radix kernels of kd_fine_mr.cuh
+//                     (one warp per column / row with its three components; n = 32 .. 256);
+//                     at n = 256 the last = the 256-point warp-transform kernels of
+//                     kd_fine5.cuh (the row kernel for RK443)
 //   n >= 512  column: 0, 1 = three-pass, 16 values per thread, XT0, XT0/2 columns;
 //                     2 = persistent prefetching kernel; 3 = component-split kernel;
 //                     4 = 8 values per thread (n = 512); 5 = 512-point warp transforms,
@@ -86,6 +88,55 @@ struct FineMrSet {
     }
   }
 };
+
+// Warp-transform kernels of the n = 512 and 256 complex64 grids (kd_fine5.cuh).
+template <int N>
+static void launch_colw(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
+  using C = ColW<N>;
+  const long groups = (long)a.batch * (N / C::XG);
+  const long cap = (long)persistent_grid(1L << 30) * C::MINB;
+  launch_k(colw_kernel<N>, (unsigned)(groups < cap ? groups : cap), C::BLOCK, C::smem, st, pdl, a, s, j);
+}
+
+template <int N, int MODE>
+static void launch_roww_mode(const FineArgs& a, int store, cudaStream_t st, bool pdl) {
+  using G = RowW<N, MODE>;
+  const long rows = (long)a.batch * a.P;
+  const long cap = (long)persistent_grid(1L << 30) * G::MINB;
+  launch_k(roww_kernel<N, MODE>, (unsigned)(rows < cap ? rows : cap), G::BLOCK, G::smem, st, pdl, a, store);
+}
+
+template <int N>
+static void launch_roww(const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
+  switch (mode) {
+    case 0: return launch_roww_mode<N, 0>(a, store, st, pdl);
+    case 1: return launch_roww_mode<N, 1>(a, store, st, pdl);
+    case 2: return launch_roww_mode<N, 2>(a, store, st, pdl);
+    case 3: return launch_roww_mode<N, 3>(a, store, st, pdl);
+    default: return launch_roww_mode<N, 4>(a, store, st, pdl);
+  }
+}
+
+template <int N>
+static cudaError_t prepare_w() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(colw_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ColW<N>::smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(roww_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RowW<N, 0>::smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(roww_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RowW<N, 1>::smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(roww_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RowW<N, 2>::smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(roww_kernel<N, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RowW<N, 3>::smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(roww_kernel<N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RowW<N, 4>::smem);
+}
 
 template <typename T, int N, int XT>
 static cudaError_t prepare_col2() {
@@ -180,10 +231,12 @@ struct Fine2Set {
   // the warp-owned mixed-radix kernels (FineMrSet) as the last column / row variant of the
   // sides 32 R
   static constexpr bool MR = N % 32 == 0;
+  // complex64 n = 256: the 256-point warp-transform kernels (kd_fine5.cuh) after that
+  static constexpr bool WT = WIDE && N == 256;
   static int ncol0() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
   static int nrow0() { return WIDE ? (R8 ? 8 : 6) : 1; }
-  static int ncol() { return ncol0() + (MR ? 1 : 0); }
-  static int nrow() { return nrow0() + (MR ? 1 : 0); }
+  static int ncol() { return ncol0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
+  static int nrow() { return nrow0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
@@ -217,11 +270,17 @@ struct Fine2Set {
       if ((e = prepare_row3<T, N, Shapes8<N>::RT, true, 8>()) != cudaSuccess) return e;
       if ((e = prepare_row3<T, N, Shapes8<N>::RT, false, 8>()) != cudaSuccess) return e;
     }
+    if constexpr (WT) {
+      if ((e = prepare_w<N>()) != cudaSuccess) return e;
+    }
     return cudaSuccess;
   }
   static void col(int v, const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
     if constexpr (MR) {
       if (v == ncol0()) return FineMrSet<T, N / 32>::col(0, a, s, j, st, pdl);
+    }
+    if constexpr (WT) {
+      if (v == ncol0() + 1) return launch_colw<N>(a, s, j, st, pdl);
     }
     if constexpr (WIDE) {
       if (v == 2) return launch_col2c<T, N, ShC::XT>(a, s, j, st, pdl);
@@ -237,6 +296,9 @@ struct Fine2Set {
   static void row(int v, const FineArgs& a, int mode, int store, cudaStream_t st, bool pdl) {
     if constexpr (MR) {
       if (v == nrow0()) return FineMrSet<T, N / 32>::row(0, a, mode, store, st, pdl);   // every scheme
+    }
+    if constexpr (WT) {   // RK443 only; the lower-order schemes take the default row kernel below
+      if (v == nrow0() + 1 && a.scheme == SCHEME_RK443) return launch_roww<N>(a, mode, store, st, pdl);
     }
     if (!WIDE) v = 0;
     // the lower-order schemes run on the default row kernel (prologue included)
@@ -296,29 +358,6 @@ static cudaError_t prepare_row4() {
                               (int)G::smem);
 }
 
-// Warp-transform kernels of the n = 512 complex64 grid (kd_fine5.cuh).
-template <int N>
-static void launch_col512(const FineArgs& a, int s, int j, cudaStream_t st, bool pdl) {
-  using C = Col512<N>;
-  const long groups = (long)a.batch * (N / C::XG);
-  const long cap = (long)persistent_grid(1L << 30) * C::MINB;
-  launch_k(col512_kernel<N>, (unsigned)(groups < cap ? groups : cap), C::BLOCK, C::smem, st, pdl, a, s, j);
-}
-
-template <int N, int MODE>
-static void launch_row512(const FineArgs& a, int store, cudaStream_t st, bool pdl) {
-  using G = Row512<N, MODE>;
-  const long rows = (long)a.batch * a.P;
-  const long cap = (long)persistent_grid(1L << 30) * G::MINB;
-  launch_k(row512_kernel<N, MODE>, (unsigned)(rows < cap ? rows : cap), G::BLOCK, G::smem, st, pdl, a, store);
-}
-
-template <int N, int MODE>
-static cudaError_t prepare_row512() {
-  return cudaFuncSetAttribute(row512_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Row512<N, MODE>::smem);
-}
-
 template <typename T, int N>
 struct Fine3Set {
   using Sh = Shapes3<T, N>;
@@ -348,14 +387,7 @@ struct Fine3Set {
   static cudaError_t prepare() {
     cudaError_t e;
     if constexpr (R8) {
-      if ((e = cudaFuncSetAttribute(col512_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)Col512<N>::smem)) != cudaSuccess)
-        return e;
-      if ((e = prepare_row512<N, 0>()) != cudaSuccess) return e;
-      if ((e = prepare_row512<N, 1>()) != cudaSuccess) return e;
-      if ((e = prepare_row512<N, 2>()) != cudaSuccess) return e;
-      if ((e = prepare_row512<N, 3>()) != cudaSuccess) return e;
-      if ((e = prepare_row512<N, 4>()) != cudaSuccess) return e;
+      if ((e = prepare_w<N>()) != cudaSuccess) return e;
     }
     if constexpr (W4) {
       if ((e = cudaFuncSetAttribute(col4_kernel<N, kCol4Copy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -433,7 +465,7 @@ struct Fine3Set {
     }
     if constexpr (R8) {
       if (v == 4) return launch_col3<T, N, Shapes8<N>::XT, 8>(a, s, j, st, pdl);
-      if (v == kC512Col) return launch_col512<N>(a, s, j, st, pdl);
+      if (v == kC512Col) return launch_colw<N>(a, s, j, st, pdl);
     }
     if (WIDE && v == 2) {
       using C = Col3P<T, N, Sh::XT0>;
@@ -467,15 +499,7 @@ struct Fine3Set {
     if constexpr (R8) {
       if (v == 7) return launch_row3<T, N, Shapes8<N>::RT, true, 8>(a, mode, store, st, pdl);
       if (v == 8) return launch_row3<T, N, Shapes8<N>::RT, false, 8>(a, mode, store, st, pdl);
-      if (v == kC512Row) {
-        switch (mode) {
-          case 0: return launch_row512<N, 0>(a, store, st, pdl);
-          case 1: return launch_row512<N, 1>(a, store, st, pdl);
-          case 2: return launch_row512<N, 2>(a, store, st, pdl);
-          case 3: return launch_row512<N, 3>(a, store, st, pdl);
-          default: return launch_row512<N, 4>(a, store, st, pdl);
-        }
-      }
+      if (v == kC512Row) return launch_roww<N>(a, mode, store, st, pdl);
     }
     if (v == 4 && mode == 4) v = 0;   // the prologue runs on the tiled kernel
     if (v == 4) {
