@@ -116,6 +116,7 @@ static bool variants_T(int n, int* ncol, int* nrow) {
 FinePlan fine_default_plan(int n, int prec) {
   if (fine_fft_grid(n) == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
   if (fine_fft_grid(n) == 512 && prec == 0) return fine3_default_plan<float, 512>();
+  if (fine_fft_grid(n) == 256 && prec == 0) return fine2_default_plan<float, 256>();
   return FinePlan();
 }
 

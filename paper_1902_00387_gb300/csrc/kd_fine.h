@@ -14,8 +14,8 @@ struct LaunchProbe {
 
 // Launch plan of the fine kernels: index of the column-kernel and row-kernel variant
 // (tile shape, stage-update style) among those instantiated for the grid and precision;
-// {0, 0} is the default ({6, 7} on the complex64 grid n = 1024 and {5, 9} at n = 512,
-// fine_default_plan).
+// {0, 0} is the default ({6, 7} on the complex64 grid n = 1024, {5, 9} at n = 512 and
+// {0, 9} at n = 256, fine_default_plan).
 // Chosen per (n, precision, batch) by the autotuner.
 struct FinePlan {
   int col = 0;
@@ -91,6 +91,8 @@ template <typename T, int N>
 cudaError_t fine2_prep();
 template <typename T, int N>
 void fine2_variants(int* ncol, int* nrow);
+template <typename T, int N>
+FinePlan fine2_default_plan();
 template <typename T, int N>
 int fine3_run(const FineArgs& a, const StepCfg& cfg);
 template <typename T, int N>

@@ -237,6 +237,13 @@ struct Fine2Set {
   static int nrow0() { return WIDE ? (R8 ? 8 : 6) : 1; }
   static int ncol() { return ncol0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
   static int nrow() { return nrow0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
+  // plan of a context that is not autotuned: at n = 256 the warp-transform row kernel with
+  // the four-step column kernel (measured fastest of the fixed plans)
+  static FinePlan default_plan() {
+    FinePlan p;
+    if (WT) p.row = nrow0() + 1;
+    return p;
+  }
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_col2<T, N, Sh::xt(0)>()) != cudaSuccess) return e;
@@ -585,6 +592,11 @@ void fine2_variants(int* ncol, int* nrow) {
 }
 
 template <typename T, int N>
+FinePlan fine2_default_plan() {
+  return Fine2Set<T, N>::default_plan();
+}
+
+template <typename T, int N>
 int fine3_run(const FineArgs& a, const StepCfg& cfg) {
   return run_steps<Fine3Set<T, N>>(a, cfg);
 }
@@ -611,7 +623,8 @@ FinePlan fine3_default_plan() {
 #define KD_FINE2_INSTANTIATE(T, N)                                        \
   template int kd::fine2_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
   template cudaError_t kd::fine2_prep<T, N>();                             \
-  template void kd::fine2_variants<T, N>(int*, int*);
+  template void kd::fine2_variants<T, N>(int*, int*);                       \
+  template kd::FinePlan kd::fine2_default_plan<T, N>();
 #define KD_FINE3_INSTANTIATE(T, N)                                        \
   template int kd::fine3_run<T, N>(const kd::FineArgs&, const kd::StepCfg&); \
   template cudaError_t kd::fine3_prep<T, N>();                             \
