@@ -2,7 +2,7 @@
 // step loop (kd_fine.h: fine_run).  Included by the instantiation units kd_fine2_*.cu
 // and kd_fine3_*.cu.
 //
-// complex64 variants (complex128 has variant 0, and the mixed-radix variant at n >= 32):
+// complex64 variants (complex128 has variant 0 only):
 //   n <= 256  column: 0, 1 = four-step kernels with XT0, XT0/2 columns per block;
 //                     2 = component-split four-step kernel (one component per thread);
 //                     3 = three-pass kernel with 8 values per thread (n = 128, 256)
@@ -228,9 +228,11 @@ struct Fine2Set {
   // variant does not apply)
   static constexpr bool FUSED = WIDE && N == 128;
   static constexpr int kFusedCol = 4;
-  // the warp-owned mixed-radix kernels (FineMrSet) as the last column / row variant of the
-  // sides 32 R
-  static constexpr bool MR = N % 32 == 0;
+  // the warp-owned mixed-radix kernels (FineMrSet) as a further column / row variant of
+  // the sides 32 R, complex64 (complex128 keeps one plan: the serial fine run, tuned for
+  // one field, and the batched sweeps then take the same kernels, so a Parareal run of N
+  // iterations reproduces the serial fine run bit for bit)
+  static constexpr bool MR = WIDE && N % 32 == 0;
   // complex64 n = 256: the 256-point warp-transform kernels (kd_fine5.cuh) after that
   static constexpr bool WT = WIDE && N == 256;
   static int ncol0() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
