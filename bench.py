@@ -1223,7 +1223,7 @@ def run_fine_step(args):
         kd.kd_fine_batched_host(ctx, x_host, y_host, t0_host, W["steps_per_call"], B, E2E_CHUNK)
 
     e2e_step()
-    ms_e2e, _, _ = env.timed(e2e_step, max(2, args.steps // 4))
+    ms_e2e, _, _ = env.timed(e2e_step, max(2, args.steps // 2))
     e2e_total = env.max_over_ranks(sum(ms_e2e))
     e2e_value = units * env.world * len(ms_e2e) / (e2e_total / 1e3) / 1e6
     nbytes = x_host.numel() * x_host.element_size()
