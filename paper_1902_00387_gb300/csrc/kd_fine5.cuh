@@ -1,5 +1,5 @@
-// Fine-step kernels for n = 512 and n = 256 on a warp-owned FFT of n = 32 R points
-// (R = 16, 8 values a lane), complex64.
+// Fine-step kernels for n = 512, 256 and 128 on a warp-owned FFT of n = 32 R points
+// (R = 16, 8, 4 values a lane), complex64.
 //
 // A transform of one field component of one grid column (column kernel) or one ky row
 // (row kernel) belongs to one warp, R values a lane, in one of two layouts:
@@ -10,7 +10,7 @@
 // twiddle w_n^(a m1), a transpose through a shared buffer private to the warp after
 // which lane m1 + R e holds a = G a' + e of row m1, an R-point DFT over a', the twiddle
 // w_32^(e p), and a G-point DFT over e between the lanes m1 + R e (decimation in frequency
-// by shuffles: one stage for n = 512, two for n = 256).  wr_b_to_a is the same sequence
+// by shuffles: one stage for n = 512, two for n = 256, three for n = 128).  wr_b_to_a is the same sequence
 // backwards.  Both compute X[m] = sum_n x[n] exp(DIR 2 pi i n m / n) without
 // normalisation.  The column pass takes ky in layout A to y in layout B and back; the row
 // pass x in layout B to kx in layout A and back, so nothing is re-ordered between the
@@ -25,13 +25,13 @@ namespace kd {
 
 template <int N>
 struct WR {
-  static_assert(N == 512 || N == 256, "warp transforms of 512 or 256 points");
+  static_assert(N == 512 || N == 256 || N == 128, "warp transforms of 512, 256 or 128 points");
   static constexpr int R = N / 32;                // values a lane
-  static constexpr int LR = R == 16 ? 4 : 3;      // log2 R
+  static constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : 2);   // log2 R
   static constexpr int G = 32 / R;                // lanes sharing a row of the second pass
-  // complex per row of a warp's transpose buffer: 16-byte row starts, conflict-free
-  // 16-byte row stores of a quarter warp, column reads of a half warp at most 2-way
-  static constexpr int PITCH = R == 16 ? 18 : 10;
+  // complex per row of a warp's transpose buffer: 16-byte row starts, quarter-warp row
+  // stores and half-warp column reads at most 2-way in conflict
+  static constexpr int PITCH = R == 16 ? 18 : (R == 8 ? 10 : 4);
   static constexpr int BUF = 32 * PITCH;
 };
 
@@ -57,7 +57,38 @@ __device__ __forceinline__ cx<float> wr_rot(cx<float> v, int b) {
   return b ? (DIR > 0 ? mk(-v.y, v.x) : mk(v.y, -v.x)) : v;
 }
 
-__host__ __device__ constexpr int wr_brev(int e, int G) { return G == 2 ? e : (((e & 1) << 1) | (e >> 1)); }
+// bit reversal of e < G (G = 2, 4, 8)
+__host__ __device__ constexpr int wr_brev(int e, int G) {
+  return G == 2 ? e : (G == 4 ? (((e & 1) << 1) | (e >> 1)) : (((e & 1) << 2) | (e & 2) | (e >> 2)));
+}
+
+// The cross-lane stage of half size s (s = G/2 .. 1, lanes l and l ^ s R) of the G-point
+// DFT over e, decimation in frequency: the upper lane takes (partner - own) w_2s^(e mod s).
+// w_8^t (s = 4) comes from the table: w_8^t = w_N^(N t / 8) = s_tw[t * 32 + 4 R] (t < 4).
+template <int N, int DIR, int S_>
+__device__ __forceinline__ cx<float> wr_dif_stage(cx<float> x, int e, const cx<float>* tw) {
+  constexpr int R = WR<N>::R;
+  const cx<float> q = wr_shfl(x, S_ * R);
+  if (!(e & S_)) return x + q;
+  const cx<float> d = q - x;
+  if constexpr (S_ == 1) return d;
+  else if constexpr (S_ == 2) return wr_rot<DIR>(d, e & 1);
+  else return (e & 3) ? wr_apply<DIR>(d, tw[(e & 3) * 32 + 4 * R]) : d;
+}
+
+// The same stage for decimation in time (input bit-reversed): the upper lane's value is
+// multiplied first, then (partner - own) / (own + partner).
+template <int N, int DIR, int S_>
+__device__ __forceinline__ cx<float> wr_dit_stage(cx<float> x, int e, const cx<float>* tw) {
+  constexpr int R = WR<N>::R;
+  cx<float> own = x;
+  if (e & S_) {
+    if constexpr (S_ == 2) own = wr_rot<DIR>(x, e & 1);
+    else if constexpr (S_ == 4) own = (e & 3) ? wr_apply<DIR>(x, tw[(e & 3) * 32 + 4 * R]) : x;
+  }
+  const cx<float> q = wr_shfl(own, S_ * R);
+  return (e & S_) ? q - own : own + q;
+}
 
 // layout A -> layout B; tw: s_tw of wr_table
 template <int N, int DIR>
@@ -83,18 +114,16 @@ __device__ __forceinline__ void wr_a_to_b(cx<float> (&v)[N / 32], int lane, cx<f
 #pragma unroll
   for (int p = 1; p < R; ++p)
     if (e != 0) v[bitrev<R>(p)] = wr_apply<DIR>(v[bitrev<R>(p)], tw[p * 32 + R * e]);
-  if constexpr (G == 4) {
+  if constexpr (G == 8) {
 #pragma unroll
-    for (int p = 0; p < R; ++p) {
-      const cx<float> x = v[bitrev<R>(p)], q = wr_shfl(x, 2 * R);
-      v[bitrev<R>(p)] = (e & 2) ? wr_rot<DIR>(q - x, e & 1) : x + q;
-    }
+    for (int p = 0; p < R; ++p) v[bitrev<R>(p)] = wr_dif_stage<N, DIR, 4>(v[bitrev<R>(p)], e, tw);
+  }
+  if constexpr (G >= 4) {
+#pragma unroll
+    for (int p = 0; p < R; ++p) v[bitrev<R>(p)] = wr_dif_stage<N, DIR, 2>(v[bitrev<R>(p)], e, tw);
   }
 #pragma unroll
-  for (int p = 0; p < R; ++p) {
-    const cx<float> x = v[bitrev<R>(p)], q = wr_shfl(x, R);
-    v[bitrev<R>(p)] = (e & 1) ? q - x : x + q;
-  }
+  for (int p = 0; p < R; ++p) v[bitrev<R>(p)] = wr_dif_stage<N, DIR, 1>(v[bitrev<R>(p)], e, tw);
   cx<float> t[R];                                  // X[m1 + R p + R^2 brev(e)] into v[p]
 #pragma unroll
   for (int p = 0; p < R; ++p) t[p] = v[bitrev<R>(p)];
@@ -110,17 +139,14 @@ __device__ __forceinline__ void wr_b_to_a(cx<float> (&v)[N / 32], int lane, cx<f
   const int m1 = lane & (R - 1), e = lane >> W::LR;
   // G-point DFT over the lanes' (bit-reversed) h, decimation in time
 #pragma unroll
-  for (int p = 0; p < R; ++p) {
-    const cx<float> q = wr_shfl(v[p], R);
-    v[p] = (e & 1) ? q - v[p] : v[p] + q;
-  }
-  if constexpr (G == 4) {
+  for (int p = 0; p < R; ++p) v[p] = wr_dit_stage<N, DIR, 1>(v[p], e, tw);
+  if constexpr (G >= 4) {
 #pragma unroll
-    for (int p = 0; p < R; ++p) {
-      const cx<float> own = (e & 2) ? wr_rot<DIR>(v[p], e & 1) : v[p];
-      const cx<float> q = wr_shfl(own, 2 * R);
-      v[p] = (e & 2) ? q - own : own + q;
-    }
+    for (int p = 0; p < R; ++p) v[p] = wr_dit_stage<N, DIR, 2>(v[p], e, tw);
+  }
+  if constexpr (G == 8) {
+#pragma unroll
+    for (int p = 0; p < R; ++p) v[p] = wr_dit_stage<N, DIR, 4>(v[p], e, tw);
   }
 #pragma unroll
   for (int p = 1; p < R; ++p)                      // T_e[p] w_32^(e p)
@@ -161,7 +187,7 @@ __device__ __forceinline__ int wr_phys(int lane, int p) {
 template <int N>
 struct ColW {
   using W = WR<N>;
-  static constexpr int XG = 8, BLOCK = 32 * XG, MINB = N == 512 ? 2 : 3;
+  static constexpr int XG = 8, BLOCK = 32 * XG, MINB = N == 512 ? 2 : (N == 256 ? 3 : 4);
   static constexpr int K = N / 3, P = 2 * K + 1;
   static constexpr int OP = XG + 1;
   static constexpr int OUTSZ = (P * OP + 1) & ~1;

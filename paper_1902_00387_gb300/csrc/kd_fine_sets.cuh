@@ -233,8 +233,8 @@ struct Fine2Set {
   // one field, and the batched sweeps then take the same kernels, so a Parareal run of N
   // iterations reproduces the serial fine run bit for bit)
   static constexpr bool MR = WIDE && N % 32 == 0;
-  // complex64 n = 256: the 256-point warp-transform kernels (kd_fine5.cuh) after that
-  static constexpr bool WT = WIDE && N == 256;
+  // complex64 n = 256 and 128: the warp-transform kernels (kd_fine5.cuh) after that
+  static constexpr bool WT = WIDE && (N == 256 || N == 128);
   static int ncol0() { return WIDE ? (R8 ? (FUSED ? 5 : 4) : 3) : 1; }
   static int nrow0() { return WIDE ? (R8 ? 8 : 6) : 1; }
   static int ncol() { return ncol0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
@@ -243,7 +243,7 @@ struct Fine2Set {
   // the four-step column kernel (measured fastest of the fixed plans)
   static FinePlan default_plan() {
     FinePlan p;
-    if (WT) p.row = nrow0() + 1;
+    if (WT && N == 256) p.row = nrow0() + 1;
     return p;
   }
   static cudaError_t prepare() {
