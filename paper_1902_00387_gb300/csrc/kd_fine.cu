@@ -117,6 +117,7 @@ FinePlan fine_default_plan(int n, int prec) {
   if (fine_fft_grid(n) == 1024 && prec == 0) return fine3_default_plan<float, 1024>();
   if (fine_fft_grid(n) == 512 && prec == 0) return fine3_default_plan<float, 512>();
   if (fine_fft_grid(n) == 256 && prec == 0) return fine2_default_plan<float, 256>();
+  if (fine_fft_grid(n) == 128 && prec == 0) return fine2_default_plan<float, 128>();
   return FinePlan();
 }
 

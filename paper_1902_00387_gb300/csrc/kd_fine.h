@@ -15,7 +15,7 @@ struct LaunchProbe {
 // Launch plan of the fine kernels: index of the column-kernel and row-kernel variant
 // (tile shape, stage-update style) among those instantiated for the grid and precision;
 // {0, 0} is the default ({6, 7} on the complex64 grid n = 1024, {5, 9} at n = 512 and
-// {0, 9} at n = 256, fine_default_plan).
+// {0, 9} at n = 256, {1, 9} at n = 128, fine_default_plan).
 // Chosen per (n, precision, batch) by the autotuner.
 struct FinePlan {
   int col = 0;

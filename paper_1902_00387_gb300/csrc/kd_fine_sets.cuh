@@ -239,11 +239,13 @@ struct Fine2Set {
   static int nrow0() { return WIDE ? (R8 ? 8 : 6) : 1; }
   static int ncol() { return ncol0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
   static int nrow() { return nrow0() + (MR ? 1 : 0) + (WT ? 1 : 0); }
-  // plan of a context that is not autotuned: at n = 256 the warp-transform row kernel with
-  // the four-step column kernel (measured fastest of the fixed plans)
+  // plan of a context that is not autotuned: the warp-transform row kernel with the
+  // four-step column kernel (n = 256) or its second tile shape (n = 128), measured fastest
+  // of the fixed plans
   static FinePlan default_plan() {
     FinePlan p;
-    if (WT && N == 256) p.row = nrow0() + 1;
+    if (WT) p.row = nrow0() + 1;
+    if (WT && N == 128) p.col = 1;
     return p;
   }
   static cudaError_t prepare() {
