@@ -129,9 +129,12 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
                           int nsteps, int batch);
 
 /* The fine propagator of kd_fine_batched on fields in HOST memory: the batch moves in
- * chunks of `chunk` fields (0: batch / 32 rounded up), the copy in of a chunk, its propagation and
- * the copy out of the previous chunk overlapping on three streams (two device slots per
- * direction, allocated on first use and kept).  Same values as kd_fine_batched, field by
+ * chunks, the copy in of a chunk, its propagation and the copy out of the previous chunk
+ * overlapping on three streams (two device slots per direction, allocated on first use
+ * and kept).  chunk > 0: chunks of that many fields (the last one ragged); chunk = 0: a
+ * graded plan, chunks doubling from ceil(batch / 32) fields up to batch / 4, then back
+ * down (a short pipeline fill and drain, large batches for the steps in between; 8, 16,
+ * 32, 48, 48, 48, 32, 16, 8 for 256 fields).  Same values as kd_fine_batched, field by
  * field.  No counterpart in the paper (host I/O of this library).
  *   h_in, h_out : host, [batch][3][n][n] complex in params.prec_fine (page-locked memory
  *                 lets the copies overlap; pageable memory works, slower); may alias.
@@ -139,6 +142,36 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
  * Synchronous: returns when h_out holds the result. */
 kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0,
                                int nsteps, int batch, int chunk);
+
+/* The kept-mode layout of a field: [3][P][P] complex in params.prec_fine, P = 2K + 1,
+ * K = floor(n / 3); entry [c][iy][ix] holds component c of the coefficient of
+ * (kx, ky) = (ix - K, iy - K).  These are the modes the 2/3 rule keeps (Sec. 3: the
+ * dealiased pseudo-spectral discretisation), the only coefficients a fine step reads or
+ * writes: a field in the [3][n][n] layout of kd_fine_batched is this array with zeros
+ * around it (wavenumber k < 0 at index k + n).
+ *
+ * kd_fine_batched_kept: kd_fine_batched on device fields in the kept-mode layout; the
+ * same values, field by field.  No counterpart in the paper (a storage layout of this
+ * library).  The steps run in place on c_out (c_in is first copied there unless the two
+ * are the same buffer; partly overlapping buffers are not allowed).
+ *   c_in, c_out : device, [batch][3][P][P] complex in params.prec_fine, aligned to the
+ *                 complex element (KD_EINVAL otherwise).
+ *   t0          : device double[batch], as in kd_fine_batched.
+ * Asynchronous on the context stream.  nsteps = 0 copies the input. */
+kd_status kd_fine_batched_kept(kd_ctx* ctx, const void* c_in, void* c_out, const double* t0,
+                               int nsteps, int batch);
+
+/* kd_fine_batched_host on fields in the kept-mode layout: the chunks (`chunk` as in
+ * kd_fine_batched_host) move through four device slots, each chunk stepped in place
+ * in its slot, its copy in, its steps and the copy out of earlier chunks overlapping on
+ * three streams.  3 P^2 instead of 3 n^2 complex per field cross the host link.  Same
+ * values as kd_fine_batched_kept.  No counterpart in the paper (host I/O of this library).
+ *   h_in, h_out : host, [batch][3][P][P] complex in params.prec_fine (page-locked memory
+ *                 lets the copies overlap); may alias.
+ *   t0          : host double[batch] start times.
+ * Synchronous: returns when h_out holds the result. */
+kd_status kd_fine_batched_host_kept(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0,
+                                    int nsteps, int batch, int chunk);
 
 /* Classical coarse propagator G (Sec. 3.2, Sec. 5.2): restrict each field to the
  * N_C grid (Fourier truncation), take `nsteps` RK443 steps of params.dt_coarse in

@@ -12,6 +12,7 @@
 // skipped (after k iterations U_0..U_k equal the serial fine solution and their
 // coarse terms cancel exactly); this changes no value.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -875,17 +876,76 @@ kd_status kd_fine_batched(kd_ctx* ctx, const void* b_in, void* b_out, const doub
   return KD_OK;
 }
 
+kd_status kd_fine_batched_kept(kd_ctx* ctx, const void* c_in, void* c_out, const double* t0, int nsteps,
+                               int batch) {
+  if (!ctx) return KD_EINVAL;
+  if (!c_in || !c_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_kept: NULL buffer");
+  if (batch < 0 || nsteps < 0) return fail(ctx, KD_EINVAL, "kd_fine_batched_kept: negative batch or nsteps");
+  const int n = ctx->p.n, pf = ctx->p.prec_fine;
+  const size_t es = csize(pf);
+  if ((uintptr_t)c_in % es || (uintptr_t)c_out % es)
+    return fail(ctx, KD_EINVAL, "kd_fine_batched_kept: buffers not aligned to the complex element");
+  if (batch == 0) return KD_OK;
+  const size_t bytes = (size_t)batch * compact_len(n) * es;
+  kd_status s = ensure_ws(ctx, ctx->ws_f, n, pf, batch);
+  if (s != KD_OK) return s;
+  if (conv_op(ctx)) {
+    if ((s = ensure_conv_tmp(ctx, (size_t)batch * compact_len(n) * 16)) != KD_OK) return s;
+    double* tmp = (double*)ctx->conv_tmp;
+    KD_LAUNCH(compact_resample(pf, c_in, n, KD_C128, tmp, n, batch, ctx->st), "widen");
+    if (nsteps > 0 && (s = conv_fine(ctx, tmp, tmp, batch, nsteps, ctx->p.dt_fine, t0)) != KD_OK) return s;
+    KD_LAUNCH(compact_resample(KD_C128, tmp, n, pf, c_out, n, batch, ctx->st), "narrow");
+    return KD_OK;
+  }
+  // the kept-mode layout is the step's own state array: the steps run in place on c_out
+  if (c_in != c_out) KD_CUDA(cudaMemcpyAsync(c_out, c_in, bytes, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+  if (nsteps == 0) return KD_OK;
+  FineArgs a = fine_args(ctx, ctx->ws_f, ctx->tab_f, n, batch, ctx->p.dt_fine, t0);
+  a.X = c_out;
+  if ((s = with_phases(ctx, ctx->ws_f, a, nsteps)) != KD_OK) return s;
+  LaunchProbe pr = probe_of(ctx);
+  KD_LAUNCH(run_fine(ctx, 0, pf, a, nsteps, true, false, ctx->prof ? &pr : nullptr), "fine steps");
+  return KD_OK;
+}
+
+// Chunk sizes of a host-buffer call.  chunk > 0: equal chunks (the last one ragged).
+// chunk = 0: sizes that double from base = ceil(batch / 32) up to below cap = batch / 4,
+// then equal chunks of at most cap, then the same ramp down: the first copy in and the
+// last copy out (the pipeline's fill and drain) move base fields, while the steps in
+// between run on batches large enough to fill the GPU; every chunk's copies fit under
+// its neighbour's steps.
+static std::vector<int> chunk_plan(int batch, int chunk) {
+  std::vector<int> out;
+  if (chunk > 0) {
+    for (int f = 0; f < batch; f += chunk) out.push_back(batch - f < chunk ? batch - f : chunk);
+    return out;
+  }
+  const int base = (batch + 31) / 32, cap = batch / 4 > base ? batch / 4 : base;
+  std::vector<int> up;
+  int ramp = 0;
+  for (int c = base; c < cap; c *= 2) {
+    up.push_back(c);
+    ramp += c;
+  }
+  if (2 * ramp >= batch) return chunk_plan(batch, base);
+  const int middle = batch - 2 * ramp, m = (middle + cap - 1) / cap;
+  out = up;
+  for (int i = 0; i < m; ++i) out.push_back(middle / m + (i < middle % m ? 1 : 0));
+  out.insert(out.end(), up.rbegin(), up.rend());
+  return out;
+}
+
 // The chunk pipeline of kd_fine_batched_host (slots and streams set up by the caller);
 // enqueues everything and returns without waiting.
 static kd_status host_chunks(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
-                             int chunk, size_t fb) {
+                             const std::vector<int>& plan, size_t fb) {
   kd_status s;
   // events per slot q: hev[q] input copied in, hev[2 + q] computed, hev[4 + q] output copied out
   KD_CUDA(cudaMemcpyAsync(ctx->hio_t0, t0, (size_t)batch * 8, cudaMemcpyHostToDevice, ctx->st), "times");
   for (int q = 2; q < 6; ++q) KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st), "event");
-  const int nchunks = (batch + chunk - 1) / chunk;
-  for (int c = 0; c < nchunks; ++c) {
-    const int q = c & 1, f0 = c * chunk, nb = batch - f0 < chunk ? batch - f0 : chunk;
+  int f0 = 0;
+  for (int c = 0; c < (int)plan.size(); f0 += plan[c], ++c) {
+    const int q = c & 1, nb = plan[c];
     void *din = ctx->hio[q], *dout = ctx->hio[2 + q];
     // input slot q is free once chunk c - 2 has been computed
     KD_CUDA(cudaStreamWaitEvent(ctx->st_h2d, ctx->hev[2 + q], 0), "wait");
@@ -903,17 +963,38 @@ static kd_status host_chunks(kd_ctx* ctx, const void* h_in, void* h_out, const d
   return KD_OK;
 }
 
-kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
-                               int chunk) {
-  if (!ctx) return KD_EINVAL;
-  if (!h_in || !h_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: NULL buffer");
-  if (batch < 0 || nsteps < 0 || chunk < 0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: negative argument");
-  if (batch == 0) return KD_OK;
-  if (chunk == 0) chunk = (batch + 31) / 32;   // ~32 chunks: short pipeline fill and drain
-  if (chunk > batch) chunk = batch;
-  const int n = ctx->p.n;
-  const size_t fb = 3 * (size_t)n * n * csize(ctx->p.prec_fine);   // bytes of one field
-  const size_t slot = fb * chunk;
+// The chunk pipeline of kd_fine_batched_host_kept: chunk c stays in device slot c mod 4
+// from its copy in to its copy out and is stepped in place there.
+static kd_status host_chunks_kept(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps,
+                                  int batch, const std::vector<int>& plan, size_t fb) {
+  kd_status s;
+  // events per slot q: hev[q] copied in, hev[4 + q] computed, hev[8 + q] copied out
+  KD_CUDA(cudaMemcpyAsync(ctx->hio_t0, t0, (size_t)batch * 8, cudaMemcpyHostToDevice, ctx->st), "times");
+  for (int q = 0; q < 4; ++q) KD_CUDA(cudaEventRecord(ctx->hev[8 + q], ctx->st), "event");
+  int f0 = 0;
+  for (int c = 0; c < (int)plan.size(); f0 += plan[c], ++c) {
+    const int q = c & 3, nb = plan[c];
+    void* slot = ctx->hio[q];
+    // slot q is free once chunk c - 4 has been copied out
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_h2d, ctx->hev[8 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync(slot, (const char*)h_in + f0 * fb, nb * fb, cudaMemcpyHostToDevice, ctx->st_h2d), "copy in");
+    KD_CUDA(cudaEventRecord(ctx->hev[q], ctx->st_h2d), "event");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st, ctx->hev[q], 0), "wait");
+    if ((s = kd_fine_batched_kept(ctx, slot, slot, ctx->hio_t0 + f0, nsteps, nb)) != KD_OK) return s;
+    KD_CUDA(cudaEventRecord(ctx->hev[4 + q], ctx->st), "event");
+    KD_CUDA(cudaStreamWaitEvent(ctx->st_d2h, ctx->hev[4 + q], 0), "wait");
+    KD_CUDA(cudaMemcpyAsync((char*)h_out + f0 * fb, slot, nb * fb, cudaMemcpyDeviceToHost, ctx->st_d2h), "copy out");
+    KD_CUDA(cudaEventRecord(ctx->hev[8 + q], ctx->st_d2h), "event");
+  }
+  return KD_OK;
+}
+
+// Set-up shared by the host-buffer calls: the four device slots for the largest chunk of
+// `plan` at `slot_field` bytes a field, the start-time array and the copy streams.
+static kd_status host_setup(kd_ctx* ctx, int batch, const std::vector<int>& plan, size_t slot_field) {
+  int most = 0;
+  for (int c : plan) most = c > most ? c : most;
+  const size_t slot = slot_field * most;
   kd_status s;
   if (ctx->hio_bytes < slot) {
     for (void*& q : ctx->hio) {
@@ -937,14 +1018,47 @@ kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const
     KD_CUDA(cudaStreamCreateWithFlags(&ctx->st_d2h, cudaStreamNonBlocking), "copy stream");
     for (cudaEvent_t& e : ctx->hev) KD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
   }
-  s = host_chunks(ctx, h_in, h_out, t0, nsteps, batch, chunk, fb);
-  // whatever happened, no copy of the caller's memory is left in flight on return
+  return KD_OK;
+}
+
+// Waits for the three streams of a host-buffer call: whatever happened, no copy of the
+// caller's memory is left in flight on return.
+static kd_status host_finish(kd_ctx* ctx, kd_status s, const char* what) {
   const cudaError_t e1 = cudaStreamSynchronize(ctx->st_h2d), e2 = cudaStreamSynchronize(ctx->st_d2h);
   const cudaError_t e3 = cudaStreamSynchronize(ctx->st);
   if (s != KD_OK) return s;
   for (cudaError_t e : {e1, e2, e3})
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "kd_fine_batched_host");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
   return KD_OK;
+}
+
+kd_status kd_fine_batched_host(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps, int batch,
+                               int chunk) {
+  if (!ctx) return KD_EINVAL;
+  if (!h_in || !h_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: NULL buffer");
+  if (batch < 0 || nsteps < 0 || chunk < 0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host: negative argument");
+  if (batch == 0) return KD_OK;
+  const int n = ctx->p.n;
+  const size_t fb = 3 * (size_t)n * n * csize(ctx->p.prec_fine);   // bytes of one field
+  const std::vector<int> plan = chunk_plan(batch, chunk);
+  kd_status s = host_setup(ctx, batch, plan, fb);
+  if (s != KD_OK) return s;
+  return host_finish(ctx, host_chunks(ctx, h_in, h_out, t0, nsteps, batch, plan, fb), "kd_fine_batched_host");
+}
+
+kd_status kd_fine_batched_host_kept(kd_ctx* ctx, const void* h_in, void* h_out, const double* t0, int nsteps,
+                                    int batch, int chunk) {
+  if (!ctx) return KD_EINVAL;
+  if (!h_in || !h_out || !t0) return fail(ctx, KD_EINVAL, "kd_fine_batched_host_kept: NULL buffer");
+  if (batch < 0 || nsteps < 0 || chunk < 0)
+    return fail(ctx, KD_EINVAL, "kd_fine_batched_host_kept: negative argument");
+  if (batch == 0) return KD_OK;
+  const size_t fb = compact_len(ctx->p.n) * csize(ctx->p.prec_fine);   // bytes of one field
+  const std::vector<int> plan = chunk_plan(batch, chunk);
+  kd_status s = host_setup(ctx, batch, plan, fb);
+  if (s != KD_OK) return s;
+  return host_finish(ctx, host_chunks_kept(ctx, h_in, h_out, t0, nsteps, batch, plan, fb),
+                     "kd_fine_batched_host_kept");
 }
 
 kd_status kd_coarse(kd_ctx* ctx, const double* b_in, double* b_out, const double* t0, int nsteps, int batch) {

@@ -77,7 +77,7 @@ struct kd_ctx {
   double* hio_t0 = nullptr;
   int hio_t0_cap = 0;
   cudaStream_t st_h2d = nullptr, st_d2h = nullptr;
-  cudaEvent_t hev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t hev[12] = {};   // host-buffer calls: per device slot copied in / computed / copied out
   cudaStream_t st = nullptr;
   int device = 0;
   kdi::Tables tab_f, tab_c;

@@ -75,7 +75,8 @@ class kd_sweep_stats(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_fine_batched_host", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
+EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_fine_batched_host", "kd_fine_batched_kept",
+           "kd_fine_batched_host_kept", "kd_coarse", "kd_parareal_run", "kd_fine_serial",
            "kd_energy", "kd_growth_rate", "kd_launch_count", "kd_profile", "kd_profile_read", "kd_last_error",
            "kd_version", "kd_fine_batched_static", "kd_learned_init", "kd_learned_pairs", "kd_learned_train",
            "kd_learned_eval", "kd_learned_loss_grad", "kd_learned_apply", "kd_plan_variants", "kd_set_plan",
@@ -102,6 +103,8 @@ def load():
         "kd_destroy": (I, [P]),
         "kd_fine_batched": (I, [P, P, P, P, I, I]),
         "kd_fine_batched_host": (I, [P, P, P, P, I, I, I]),
+        "kd_fine_batched_kept": (I, [P, P, P, P, I, I]),
+        "kd_fine_batched_host_kept": (I, [P, P, P, P, I, I, I]),
         "kd_coarse": (I, [P, P, P, P, I, I]),
         "kd_parareal_run": (I, [P, P, D, I, I, D, P, ctypes.POINTER(kd_parareal_stats)]),
         "kd_fine_serial": (I, [P, P, D, I, P]),
@@ -296,14 +299,55 @@ def _host_ptr(x, dtype):
 
 def kd_fine_batched_host(ctx, h_in, h_out, t0, nsteps, batch, chunk=0, prec=KD_C64):
     """F on fields in host memory (numpy arrays or CPU tensors, page-locked for overlap):
-    the batch streams through the GPU in chunks of `chunk` fields (0: batch / 32); t0 is a
-    host float64 array.  Returns when h_out holds the result."""
+    the batch streams through the GPU in chunks of `chunk` fields (0: a graded plan from
+    batch / 32 up to batch / 4 and back); t0 is a host float64 array.  Returns when h_out
+    holds the result."""
     dt = _cdt(prec)
     _need(ctx, h_in, batch, "h_in")
     _need(ctx, h_out, batch, "h_out")
     _need_count(t0, batch, "t0")
     return _check(ctx, load().kd_fine_batched_host(ctx, _host_ptr(h_in, dt), _host_ptr(h_out, dt),
                                                    _host_ptr(t0, "float64"), int(nsteps), int(batch), int(chunk)))
+
+
+def kept_side(n):
+    """P = 2 floor(n / 3) + 1: the side of a field's kept-mode square (|kx|, |ky| <= n / 3)."""
+    return 2 * (int(n) // 3) + 1
+
+
+def _need_kept(ctx, x, fields, what):
+    """Raise ValueError unless buffer x holds `fields` kept-mode fields [3][P][P]."""
+    n = _CTX_N.get(_addr(ctx))
+    if n is None:
+        return
+    P = kept_side(n)
+    want = int(fields) * 3 * P * P
+    if _numel(x) < want:
+        raise ValueError("%s holds %d elements; %d kept-mode fields of 3 x %d x %d need %d" % (
+            what, _numel(x), fields, P, P, want))
+
+
+def kd_fine_batched_kept(ctx, c_in, c_out, t0, nsteps, batch, prec=KD_C64):
+    """F on device fields in the kept-mode layout [batch][3][P][P] (P = kept_side(n); entry
+    [c][iy][ix] is the coefficient of kx = ix - n // 3, ky = iy - n // 3); steps in place on
+    c_out."""
+    dt = _cdt(prec)
+    _need_kept(ctx, c_in, batch, "c_in")
+    _need_kept(ctx, c_out, batch, "c_out")
+    _need_count(t0, batch, "t0")
+    return _check(ctx, load().kd_fine_batched_kept(ctx, _ptr(c_in, dt), _ptr(c_out, dt), _ptr(t0, "float64"),
+                                                   int(nsteps), int(batch)))
+
+
+def kd_fine_batched_host_kept(ctx, h_in, h_out, t0, nsteps, batch, chunk=0, prec=KD_C64):
+    """kd_fine_batched_host on host fields in the kept-mode layout [batch][3][P][P]."""
+    dt = _cdt(prec)
+    _need_kept(ctx, h_in, batch, "h_in")
+    _need_kept(ctx, h_out, batch, "h_out")
+    _need_count(t0, batch, "t0")
+    return _check(ctx, load().kd_fine_batched_host_kept(ctx, _host_ptr(h_in, dt), _host_ptr(h_out, dt),
+                                                        _host_ptr(t0, "float64"), int(nsteps), int(batch),
+                                                        int(chunk)))
 
 
 def kd_fine_batched_static(params, b_in, b_out, t0, nsteps, batch, stream=None):
