@@ -57,6 +57,26 @@ __device__ __forceinline__ cx<T> mul_w32(cx<T> a, int e) {
   return mk(a.x * c - a.y * s, a.x * s + a.y * c);
 }
 
+// cos(e pi / 16) for any integer e (folded into the range of cpi16)
+__device__ __forceinline__ double c16(int e) {
+  e &= 31;
+  if (e > 16) e = 32 - e;
+  return e <= 8 ? cpi16(e) : -cpi16(16 - e);
+}
+
+// a * w_32^e for any integer e (compile-time after unrolling): multiples of 8 are the
+// quarter turns (no multiply), the rest one complex product with constant factors.
+template <typename T, int DIR>
+__device__ __forceinline__ cx<T> mul_w32_any(cx<T> a, int e) {
+  e &= 31;
+  if (e == 0) return a;
+  if (e == 8) return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);     // times DIR i
+  if (e == 16) return mk(-a.x, -a.y);
+  if (e == 24) return DIR < 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);    // times -DIR i
+  const T c = (T)c16(e), s = (T)(DIR * c16(8 - e));
+  return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
 template <int R>
 __host__ __device__ constexpr int bitrev(int q) {
   int r = 0;
@@ -85,11 +105,51 @@ __device__ __forceinline__ void bfly<float>(cx<float>& a, cx<float>& b) {
   b = mk(d.x, d.y);
 }
 
-// In-register R-point DFT (R = 2, 4, 8, 16), radix-2 decimation in frequency.
+// Radix-2^2 decimation in frequency on the block v[O .. O + L) (L a power of two <= 32):
+// the data flow and output order of radix-2, with the non-trivial twiddles of two
+// stages applied once after the second.  With d = the block's upper-half differences,
+// the second stage's lower half combines d[i] and d[i + L/4] times w_4 (a quarter turn),
+// and the four quarter blocks then carry the twiddles w_L^(r' i), r' = 0, 2, 1, 3 (the
+// output residue mod 4 that each quarter block computes, in bit-reversed order).  32
+// points: 28 twiddle products instead of radix-2's 34; 16 points: 8 instead of 10.
+template <typename T, int DIR, int L, int O>
+__device__ __forceinline__ void dft_r22(cx<T>* v) {
+  if constexpr (L == 2) {
+    bfly(v[O], v[O + 1]);
+  } else if constexpr (L >= 4) {
+    constexpr int H = L / 2, Q = L / 4, U = 32 / L;   // w_L = w_32^U
+#pragma unroll
+    for (int i = 0; i < H; ++i) bfly(v[O + i], v[O + i + H]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[O + H + Q + i] = mul_w32_any<T, DIR>(v[O + H + Q + i], 8);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bfly(v[O + i], v[O + i + Q]);
+      bfly(v[O + H + i], v[O + H + i + Q]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      v[O + Q + i] = mul_w32_any<T, DIR>(v[O + Q + i], 2 * i * U);
+      v[O + H + i] = mul_w32_any<T, DIR>(v[O + H + i], i * U);
+      v[O + H + Q + i] = mul_w32_any<T, DIR>(v[O + H + Q + i], 3 * i * U);
+    }
+    dft_r22<T, DIR, Q, O>(v);
+    dft_r22<T, DIR, Q, O + Q>(v);
+    dft_r22<T, DIR, Q, O + H>(v);
+    dft_r22<T, DIR, Q, O + H + Q>(v);
+  }
+}
+
+// In-register R-point DFT (R = 2, 4, 8, 16, 32), decimation in frequency: radix-2 up to 8
+// points, radix-2^2 (dft_r22, same output order) at 16 and 32.
 // In: v[n] natural order.  Out: X[q] at v[bitrev<R>(q)].  PACKED selects the packed
-// butterflies of bfly (same results; faster in the n <= 256 kernels, slower at 1024).
+// butterflies of bfly in the radix-2 loop (same results).
 template <typename T, int R, int DIR, bool PACKED = true>
 __device__ __forceinline__ void dft_dif(cx<T>* v) {
+  if constexpr (R >= 16) {
+    dft_r22<T, DIR, R, 0>(v);
+    return;
+  }
 #pragma unroll
   for (int span = R / 2; span >= 1; span >>= 1) {
 #pragma unroll

@@ -108,6 +108,35 @@ def test_large_workload_late_slices_match_oracle(kd):
         assert rel(out[i], O.propagate(b[i], p, t0[i], dt, 20)) < TOL32, i
 
 
+def test_full_launch_configuration_1024_256_slices_sampled(kd):
+    """The fine step as the bench line times it: all 256 slices of the GP 1024^2 workload
+    in one call on the default plan (8 seeded fields tiled over the slices, slice i
+    starting at i T / 256), one step; the oracle steps three sampled slices one by one
+    (first, middle, last: different fields, start times and grid-stride positions)."""
+    import torch
+    n, kz, Rm, B = 1024, 0.57, 1e4, 256
+    T = 2 * math.pi * 32
+    dt = T / B / 786
+    base = I.initial_batch(n, kz, range(1000, 1008))
+    t0 = np.arange(B, dtype=np.float64) * (T / B)
+    picks = (0, 131, 255)
+    ctx = kd.kd_create(kd.make_params(O.GALLOWAY_PROCTOR, n, kz, Rm, dt, kd.KD_C64))
+    try:
+        assert tuple(kd.kd_get_plan(ctx, kd.KD_GRID_FINE)) == (6, 7)
+        x = torch.tensor(base, dtype=torch.complex64, device="cuda").repeat(B // 8, 1, 1, 1)
+        y = torch.empty_like(x)
+        kd.kd_fine_batched(ctx, x, y, torch.tensor(t0, device="cuda"), 1, B)
+        torch.cuda.synchronize()
+        outs = [y[i].cpu().numpy().astype(np.complex128) for i in picks]
+        del x, y
+    finally:
+        kd.kd_destroy(ctx)
+    torch.cuda.empty_cache()
+    p = O.Problem(O.GALLOWAY_PROCTOR, n, kz, Rm)
+    for i, out in zip(picks, outs):
+        assert rel(out, O.propagate(base[i % 8], p, t0[i], dt, 1)) < TOL32, i
+
+
 @pytest.mark.parametrize("nsteps", [1, 3])
 def test_state_in_the_callers_layout_at_1024(kd, nsteps):
     """The default 1024^2 complex64 plan reads the first step's state from the input and
