@@ -1142,15 +1142,15 @@ def run_parareal(args):
 
 # ------------------------------------------------- the default line: the fine step, c5
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the fine
-# kernels, from one ncu capture of the warp-transform plan (5, 7) at 1024^2 x 16 slices
+# kernels, from one ncu capture of the warp-transform plan (6, 7) at 1024^2 x 16 slices
 # (one fine step: the 4 stage launches of each kernel), averaged over the stages and
 # scaled by 16 to a 256-slice launch (the traffic grows with the slices); keyed by the
 # kernel's name as the bench reports it and its variant (column variant for the column
 # kernel, row variant for the row kernel).  A variant without a capture of its current
 # code reports null.
 FINE_TRAFFIC = {
-    ("fine row kernel", 7): 16 * (1196.98 + 1375.10 + 1022.11 + 785.55) / 4 * 1e6,
-    ("fine column kernel", 5): 16 * (484.47 + 484.48 + 484.51 + 484.42) / 4 * 1e6,
+    ("fine row kernel", 7): 16 * (1196.97 + 1374.91 + 1021.99 + 785.88) / 4 * 1e6,
+    ("fine column kernel", 6): 16 * (484.81 + 484.54 + 484.87 + 484.66) / 4 * 1e6,
 }
 
 
