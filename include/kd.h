@@ -467,6 +467,21 @@ kd_status kd_set_learned_gemm(kd_ctx* ctx, int engine);
  * usable.  Synchronous on cuda_stream. */
 kd_status kd_selftest_wait(int arrive, double max_ms, void* cuda_stream);
 
+/* Allocation limit of a context (failure injection of device out-of-memory without
+ * exhausting the GPU, and a memory budget for callers that share it).  No counterpart in
+ * the paper.  The limit caps the device bytes the context holds in its own buffers (grid
+ * tables, fine and coarse workspaces, Parareal arrays, staging; not CUDA's own objects
+ * such as streams, events and graph executables, nor the static array of
+ * kd_fine_batched_static).  max_bytes = 0 removes it (the default); a limit below what the
+ * context already holds keeps those buffers and refuses new ones.  A call that needs a
+ * buffer beyond the limit returns KD_ENOMEM, as a failed cudaMalloc does, with
+ * kd_last_error naming the buffer, its size, the bytes held and the limit; the context
+ * stays usable, and the same call succeeds once the limit allows it.  Contexts that
+ * kd_sweep_create makes for itself are not affected.  kd_get_alloc_bytes returns the bytes
+ * held and the limit (either pointer may be NULL).  Both are host-only: no CUDA call. */
+kd_status kd_set_alloc_limit(kd_ctx* ctx, size_t max_bytes);
+kd_status kd_get_alloc_bytes(kd_ctx* ctx, size_t* held, size_t* limit);
+
 /* The host routine that kd_growth_arnoldi uses for its small dense eigenproblem, exposed
  * for checking: eigenvalues of an m x m complex upper Hessenberg matrix h (row-major,
  * interleaved re / im; entries below the subdiagonal must be zero) by the shifted QR

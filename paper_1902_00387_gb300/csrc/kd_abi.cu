@@ -48,22 +48,42 @@ bool valid_n(int n) {
 kd_status dalloc(kd_ctx* ctx, void** p, size_t bytes, const char* what) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  // the context's allocation limit refuses the buffer as a failed cudaMalloc would
+  if (ctx->alloc_limit && (bytes > ctx->alloc_limit || ctx->alloc_held > ctx->alloc_limit - bytes))
+    return fail(ctx, KD_ENOMEM, std::string("allocation limit: ") + what + " (" + std::to_string(bytes) +
+                                    " B) with " + std::to_string(ctx->alloc_held) + " B held exceeds the limit of " +
+                                    std::to_string(ctx->alloc_limit) + " B");
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, KD_ENOMEM, std::string("cudaMalloc ") + what + " (" + std::to_string(bytes) + " B): " +
                                     cudaGetErrorString(e));
   }
-  ctx->allocs.push_back(*p);
+  size_t i = 0;
+  while (i < ctx->allocs.size() && ctx->allocs[i]) ++i;   // reuse a freed entry
+  if (i == ctx->allocs.size()) {
+    ctx->allocs.push_back(nullptr);
+    ctx->alloc_sizes.push_back(0);
+  }
+  ctx->allocs[i] = *p;
+  ctx->alloc_sizes[i] = bytes;
+  ctx->alloc_held += bytes;
   ++ctx->alloc_gen;
   return KD_OK;
 }
 
+// Release a live buffer of this context; any other pointer (NULL, one already released)
+// is left alone.
 void dfree(kd_ctx* ctx, void* p) {
   if (!p) return;
-  cudaFree(p);
-  for (auto& a : ctx->allocs)
-    if (a == p) a = nullptr;
+  for (size_t i = 0; i < ctx->allocs.size(); ++i)
+    if (ctx->allocs[i] == p) {
+      cudaFree(p);
+      ctx->allocs[i] = nullptr;
+      ctx->alloc_held -= ctx->alloc_sizes[i];
+      ctx->alloc_sizes[i] = 0;
+      return;
+    }
 }
 
 kd_status make_tables(kd_ctx* ctx, Tables& t, int n, int prec) {
@@ -265,6 +285,8 @@ kd_status ensure_slices(kd_ctx* ctx, long N) {
   dfree(ctx, ctx->t0f);
   dfree(ctx, ctx->t0c);
   dfree(ctx, ctx->Uprev);
+  // no stale pointer survives a failed allocation below
+  ctx->U = ctx->Fv = ctx->Gv = ctx->t0f = ctx->t0c = ctx->Uprev = nullptr;
   ctx->cap_slices = 0;
   const int n = ctx->p.n;
   kd_status s;
@@ -1902,6 +1924,19 @@ kd_status kd_learned_eval(kd_ctx* ctx, const float* x, const float* y, const int
 }
 
 long long kd_launch_count(kd_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+kd_status kd_set_alloc_limit(kd_ctx* ctx, size_t max_bytes) {
+  if (!ctx) return KD_EINVAL;
+  ctx->alloc_limit = max_bytes;
+  return KD_OK;
+}
+
+kd_status kd_get_alloc_bytes(kd_ctx* ctx, size_t* held, size_t* limit) {
+  if (!ctx) return KD_EINVAL;
+  if (held) *held = ctx->alloc_held;
+  if (limit) *limit = ctx->alloc_limit;
+  return KD_OK;
+}
 
 kd_status kd_profile(kd_ctx* ctx, int enable) {
   if (!ctx) return KD_EINVAL;

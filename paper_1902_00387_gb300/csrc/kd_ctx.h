@@ -99,7 +99,13 @@ struct kd_ctx {
   size_t full_tmp_bytes = 0;
   double* host_scal = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // the context's device buffers (dalloc / dfree): allocs[i] of alloc_sizes[i] bytes, a
+  // null entry once freed; alloc_held is their sum and alloc_limit its cap (0: none,
+  // kd_set_alloc_limit)
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;
+  size_t alloc_held = 0;
+  size_t alloc_limit = 0;
   std::string err;
   long long launches = 0;     // kernels launched by this context
   int cK = 0, cP = 0;         // coarse mode set k in [-cK, cP - cK)^2

@@ -85,7 +85,8 @@ EXPORTS = ["kd_create", "kd_destroy", "kd_fine_batched", "kd_fine_batched_host",
            "kd_block_fine", "kd_block_sweep", "kd_block_get_state", "kd_growth_power", "kd_growth_arnoldi", "kd_hessenberg_eig", "kd_gemm_bf16_tn",
            "kd_set_learned_gemm", "kd_learned_get", "kd_learned_set", "kd_selftest_wait", "kd_parareal_resume", "kd_set_graphs",
            "kd_set_reference", "kd_set_overlap", "kd_set_coarse_cluster",
-           "kd_set_coarse_sync", "kd_sweep_create", "kd_sweep_exec", "kd_sweep_set_graphs", "kd_sweep_destroy"]
+           "kd_set_coarse_sync", "kd_sweep_create", "kd_sweep_exec", "kd_sweep_set_graphs", "kd_sweep_destroy",
+           "kd_set_alloc_limit", "kd_get_alloc_bytes"]
 KD_STATIC_SCRATCH_BYTES = 33554432
 
 
@@ -153,6 +154,8 @@ def load():
         "kd_block_sweep": (I, [P, I, ctypes.POINTER(D)]),
         "kd_block_get_state": (I, [P, I, P]),
         "kd_launch_count": (ctypes.c_longlong, [P]),
+        "kd_set_alloc_limit": (I, [P, ctypes.c_size_t]),
+        "kd_get_alloc_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
         "kd_profile": (I, [P, I]),
         "kd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
         "kd_last_error": (ctypes.c_char_p, [P]),
@@ -759,6 +762,21 @@ def kd_block_get_state(ctx, i, u):
 
 def kd_launch_count(ctx):
     return int(load().kd_launch_count(ctx))
+
+
+def kd_set_alloc_limit(ctx, max_bytes):
+    """Cap the device bytes the context may hold in its own buffers (0: no cap); a call
+    that needs more raises KdError with status KD_ENOMEM."""
+    if int(max_bytes) < 0:
+        raise ValueError("max_bytes must be >= 0")
+    return _check(ctx, load().kd_set_alloc_limit(ctx, int(max_bytes)))
+
+
+def kd_get_alloc_bytes(ctx):
+    """(bytes held, limit) of the context's own device buffers (limit 0: none)."""
+    held, limit = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(ctx, load().kd_get_alloc_bytes(ctx, ctypes.byref(held), ctypes.byref(limit)))
+    return int(held.value), int(limit.value)
 
 
 def kd_profile(ctx, enable):

@@ -64,6 +64,19 @@ def test_null_arguments(kd):
     assert kd.kd_version().startswith("kd ")
 
 
+def test_allocation_limit_calls_need_a_context(kd):
+    """kd_set_alloc_limit / kd_get_alloc_bytes are host-only; without a context they
+    return KD_EINVAL, and the binding refuses a negative limit before the library."""
+    import ctypes
+    lib = kd.load()
+    held = ctypes.c_size_t(7)
+    assert lib.kd_set_alloc_limit(None, 1 << 20) == kd.KD_EINVAL
+    assert lib.kd_get_alloc_bytes(None, ctypes.byref(held), None) == kd.KD_EINVAL
+    assert held.value == 7
+    with pytest.raises(ValueError):
+        kd.kd_set_alloc_limit(ctypes.c_void_p(16), -1)
+
+
 def test_binding_rejects_short_buffers_before_the_library(kd, monkeypatch):
     """The binding knows each context's grid side and refuses buffers smaller than the
     fields the call will touch (the library takes plain pointers); nothing reaches the
