@@ -70,10 +70,22 @@ extern "C" kd_status kd_fine_batched_static(const kd_params* p, const void* b_in
   const size_t rs = prec == KD_C64 ? 4 : 8, cs = 2 * rs;
   const int K = n / 3, P = 2 * K + 1;
   const int m = fine_fft_grid(n);   // the transforms' side (n itself for the FFT sides)
+  // the per-field terms are bounded one by one first, so that their sum below cannot wrap
+  // around for any int batch and nsteps
+  const size_t lim = (size_t)KD_STATIC_SCRATCH_BYTES;
+  const bool gp = p->flow == KD_FLOW_GALLOWAY_PROCTOR;
+  if ((size_t)batch > lim / (3 * (size_t)P * P * cs) ||
+      (gp && nsteps > 0 && (size_t)batch > lim / ((size_t)nsteps * 16 * rs))) {
+    fprintf(stderr,
+            "kd_fine_batched_static: %d fields of %d steps need more than the %d bytes of the static scratch; "
+            "use a smaller batch or nsteps, or kd_fine_batched\n",
+            batch, nsteps, KD_STATIC_SCRATCH_BYTES);
+    return KD_EINVAL;
+  }
   const size_t tab = align256(m * cs) + 2 * align256(m * rs);
   const size_t spec = align256((size_t)batch * 3 * P * P * cs);
   const size_t mixed = align256((size_t)batch * 3 * P * m * cs);
-  const size_t phase = p->flow == KD_FLOW_GALLOWAY_PROCTOR ? align256(phase_table_bytes(prec, batch, nsteps)) : 0;
+  const size_t phase = gp ? align256(phase_table_bytes(prec, batch, nsteps)) : 0;
   const int nspec = prec == KD_C64 ? 5 : 4;   // X, R2, R3, R4 (+ the state's low part, complex64)
   const size_t need = tab + nspec * spec + 2 * mixed + phase;
   if (need > (size_t)KD_STATIC_SCRATCH_BYTES) {

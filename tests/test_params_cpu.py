@@ -64,6 +64,22 @@ def test_null_arguments(kd):
     assert kd.kd_version().startswith("kd ")
 
 
+def test_static_entry_refuses_oversized_requests_on_the_host(kd):
+    """kd_fine_batched_static bounds every workspace term before summing them, so sizes
+    whose byte counts would wrap a 64-bit sum are refused with KD_EINVAL before any CUDA
+    call (the pointers here are never dereferenced)."""
+    import ctypes
+    lib = kd.load()
+    fake = ctypes.c_void_p(256)
+    gp = params(kd)
+    gp.n = 16
+    # 2^30 fields x 2^30 steps: the phase table alone is 2^66 bytes (0 modulo 2^64);
+    # 2^31 - 1 fields x 1879047834 steps at n = 16: the six terms sum to 1536 modulo 2^64
+    for batch, nsteps in [(1 << 30, 1 << 30), (2**31 - 1, 1879047834), (2**31 - 1, 2**31 - 1), (1, 2**31 - 1),
+                          (11556, 1)]:
+        assert lib.kd_fine_batched_static(ctypes.byref(gp), fake, fake, fake, nsteps, batch, None) == kd.KD_EINVAL
+
+
 def test_allocation_limit_calls_need_a_context(kd):
     """kd_set_alloc_limit / kd_get_alloc_bytes are host-only; without a context they
     return KD_EINVAL, and the binding refuses a negative limit before the library."""
