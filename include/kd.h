@@ -441,7 +441,8 @@ kd_status kd_growth_arnoldi(kd_ctx* ctx, const double* b0, double t0, double tau
  * A and Bt row-major BF16 (K innermost, K a multiple of 8, base addresses 16-byte
  * aligned), C row-major FP32 with row
  * stride ldc >= N; all device pointers.  KD_GEMM_TCGEN05 (default for training): 5th-
- * generation tensor cores, tcgen05.mma into a tensor-memory accumulator, 128 x 128 tiles;
+ * generation tensor cores, tcgen05.mma into a tensor-memory accumulator, 128 x 256 tiles
+ * (128 x 128 where the wide tiles would be fewer than two per SM);
  * KD_GEMM_MMA_SYNC: the warp-level mma.sync kernel.  Synchronous on cuda_stream (NULL =
  * legacy default stream).  KD_EINVAL for bad arguments, KD_ECUDA on a launch failure or a
  * bounded wait inside the kernel that ran out. */

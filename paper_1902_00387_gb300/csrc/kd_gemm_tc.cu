@@ -349,7 +349,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-bool g_tma_ready[2] = {false, false};
 
 // 2-D tensor map of a row-major BF16 matrix [rows][K]: boxes of box_rows rows x 64 K, 128-byte swizzle
 bool make_map(CUtensorMap* map, const void* base, int rows, int K, int box_rows) {
@@ -372,8 +371,6 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int box_rows)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool g_tc_ready = false;
-
 }  // namespace
 
 int gemm_bf16_tn_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int M, int N, int K, int ldc,
@@ -384,23 +381,20 @@ int gemm_bf16_tn_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, i
   // per SM; fewer, larger tiles leave SMs idle, and there the 128-row tiles (and their
   // deeper 6-stage ring) win: measured 567 vs 302 TFLOP/s at 14406 x 512 x 7208, while
   // 256-row tiles win at 4096^3 (875 vs 636) and 8192^3
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-  }
+  // the current device's SM count and shared-memory opt-in, set on every call (host-side
+  // attribute calls): nothing cached outlives a device switch or a cudaDeviceReset
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    return -1;
   const long tiles256 = (long)((M + kBM - 1) / kBM) * ((N + 255) / 256);
   const bool wide = N > 128 && tiles256 >= 2L * sms;
   CUtensorMap ta, tb;
   if (make_map(&ta, A, M, K, kBM) && make_map(&tb, Bt, N, K, wide ? 256 : 128)) {
     const int smem = wide ? TmaCfg<256>::kSmem : TmaCfg<128>::kSmem;
-    if (!g_tma_ready[wide]) {
-      if (cudaFuncSetAttribute(wide ? k_gemm_tn_tma<256> : k_gemm_tn_tma<128>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -1;
-      g_tma_ready[wide] = true;
-    }
+    if (cudaFuncSetAttribute(wide ? k_gemm_tn_tma<256> : k_gemm_tn_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+      return -1;
     dim3 g2((unsigned)((N + (wide ? 255 : 127)) / (wide ? 256 : 128)), grid.y);
     if (wide)
       k_gemm_tn_tma<256><<<g2, kThreads, smem, st>>>(ta, tb, C, M, N, K, ldc, err);
@@ -408,11 +402,8 @@ int gemm_bf16_tn_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, i
       k_gemm_tn_tma<128><<<g2, kThreads, smem, st>>>(ta, tb, C, M, N, K, ldc, err);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
   }
-  if (!g_tc_ready) {
-    if (cudaFuncSetAttribute(k_gemm_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
-      return -1;
-    g_tc_ready = true;
-  }
+  if (cudaFuncSetAttribute(k_gemm_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    return -1;
   k_gemm_tn_tc<<<grid, kThreads, kSmemBytes, st>>>(A, Bt, C, M, N, K, ldc, err);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
