@@ -33,6 +33,11 @@ int main(void) {
   if (!((fabs(eig[0] - 2.0) < 1e-14 && fabs(eig[2] - 3.0) < 1e-14) ||
         (fabs(eig[0] - 3.0) < 1e-14 && fabs(eig[2] - 2.0) < 1e-14))) return 5;
   if (kd_hessenberg_eig(0, h, eig, NULL) != KD_EINVAL) return 6;
+  {
+    size_t held = 7, limit = 7;
+    if (kd_set_alloc_limit(NULL, 1u << 20) != KD_EINVAL) return 7;
+    if (kd_get_alloc_bytes(NULL, &held, &limit) != KD_EINVAL || held != 7 || limit != 7) return 8;
+  }
   printf("%s\n", kd_version());
   return 0;
 }
@@ -98,3 +103,17 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(name, "sizeof")] == K.ctypes.sizeof(st), name
         for f in st._fields_:
             assert got[(name, f[0])] == getattr(st, f[0]).offset, (name, f[0])
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_readme_c_example_compiles(tmp_path):
+    """The C calling sequence shown in README.md compiles as C99 against include/kd.h."""
+    import re
+    text = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
+    assert blocks, "README.md has no C example"
+    src = tmp_path / "readme.c"
+    src.write_text(blocks[0])
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                        "-o", str(tmp_path / "readme.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
